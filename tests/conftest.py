@@ -1,0 +1,20 @@
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a GB300 and the built CUDA library")
+    config.addinivalue_line("markers", "slow: long-running (still bounded) test")
+
+
+@pytest.fixture(scope="session")
+def lib():
+    """The CUDA library through its C-ABI binding (GPU tests only)."""
+    from paper_2509_16793_gb300 import gempic
+    return gempic.load()

@@ -1,0 +1,192 @@
+/*
+ * gempic.h -- C-ABI of the GB300 GEM-PIC hot path (Galilean electromagnetic particle-in-cell,
+ * Pukhov, Elkina, Wilson, arXiv 2509.16793).
+ *
+ * One simulation = one persistent spectral field state on the device plus its particle
+ * stores.  Each s-step (slow coordinate, step Delta) marches the zeta-slices from the front
+ * of the window to the back (Sec. 4.1): fresh plasma is injected at the front (Sec. 4.1,
+ * "Current Deposition", Q_f = q n h_x h_y Delta), particles are gathered, pushed along zeta
+ * with the GT2 characteristics (Sec. 4, Eqs. after Vlasov2, trap2) and deposited, and the
+ * universal reduced Maxwell system (Eqs. RxGu..EzGu) is advanced slice by slice with the
+ * semi-implicit scheme of Sec. 4.1 (Eqs. RxN..eqall, closed form of App. B).  Particles that
+ * pass the back boundary are removed; particles whose slow-coordinate budget is used up stay
+ * in the box as stored (trapped) particles and are pushed along s.
+ *
+ * Conventions
+ *   - Units: the paper's normalisation (Sec. 3): c = 1, lengths in c/omega_0, time in
+ *     1/omega_0, fields in m c omega_0/e, densities in n_cr.
+ *   - Grid: nx x ny transverse nodes x_i = i hx, y_j = j hy (periodic), nzeta slices
+ *     zeta_n = n h, n = 0..nzeta-1, plus a field-free ghost slice zeta_nzeta at the front.
+ *     ny == 1 selects the 2-D (x, zeta) slab.  nx, ny powers of two (ny may be 1),
+ *     nx in [8, 1024], ny <= 1024.
+ *   - Ownership: every device buffer belongs to the library.  Pointers passed in are
+ *     borrowed for the duration of the call only.  No call keeps a caller pointer.
+ *   - Errors: every call returns a gempic_status; no C++ exception crosses this boundary.
+ *     After a CUDA or device-side error the simulation is sticky-failed: later calls return
+ *     GEMPIC_ESTATE until gempic_destroy.
+ *   - Threading: one simulation per host thread at a time.  Calls on one simulation are
+ *     issued on its CUDA stream (gempic_config.cuda_stream, NULL = legacy default stream).
+ */
+#ifndef GEMPIC_H
+#define GEMPIC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  GEMPIC_OK = 0,
+  GEMPIC_EINVAL = -1,     /* bad argument or unsupported size                              */
+  GEMPIC_ENOMEM = -2,     /* device or host allocation failed                               */
+  GEMPIC_ECUDA = -3,      /* a CUDA runtime call failed                                     */
+  GEMPIC_EUNSTABLE = -4,  /* Delta h omega_p^2 > 4, outside the stability bound (Sec. 4.2)   */
+  GEMPIC_ETIMEOUT = -5,   /* a bounded device-side wait gave up                             */
+  GEMPIC_ESTATE = -6,     /* simulation failed earlier, or call not valid in this state     */
+  GEMPIC_EOVERFLOW = -7   /* a fixed-capacity particle store overflowed (particles dropped) */
+} gempic_status;
+
+/* Transverse grid and slices (Sec. 4.1: large step Delta in s, fine step h in zeta). */
+typedef struct {
+  int32_t nx, ny, nzeta;
+  double hx, hy, h;       /* 2-D: hy is the per-unit-length depth, normally 1 */
+} gempic_grid;
+
+/* A background species swept by the window and injected fresh at the front each s-step
+ * (Sec. 4.1, Q_f = q n h_x h_y Delta, split over ppc macroparticles per transverse cell,
+ * cold, at uniform random in-cell offsets drawn from a counter-based SplitMix64 stream keyed
+ * by (seed, s-step, particle)). */
+typedef struct {
+  double charge, mass;    /* in e and m_e */
+  double density;         /* in n_cr */
+  int32_t ppc;
+  int32_t reserved;
+} gempic_species;
+
+/* Laser driver at s = 0: E = e_pol a0 cos(phi) exp(-phi^2/T^2) exp(-r^2/R^2),
+ * phi = zeta - zeta_center (Eq. E_laser), laid as a forward wave R = 2E, L = 0 (Eqs. Rx, Ry),
+ * centred on the middle transverse node. */
+typedef struct {
+  double a0, waist, duration, zeta_center;
+  int32_t pol;            /* 0 = x, 1 = y */
+  int32_t reserved;
+} gempic_laser;
+
+/* Flags */
+#define GEMPIC_FLAG_DIAG      1u  /* FP64 diagnostics every s-step (default on)           */
+#define GEMPIC_FLAG_SNAPSHOT  2u  /* keep real-space E, B, j of the last s-step of a call */
+
+typedef struct {
+  gempic_grid grid;
+  double delta;                  /* s-step Delta (Sec. 4.1) */
+  int32_t precision;             /* 32 or 64: arithmetic of push, deposit and field update */
+  uint32_t flags;
+  uint64_t seed;
+  int32_t nspecies;              /* 1..4 */
+  int32_t cluster_ctas;          /* CTAs per slice march (thread-block cluster); 0 = auto */
+  const gempic_species* species; /* nspecies entries, copied at create */
+  const gempic_laser* laser;     /* NULL: no driver */
+  int32_t stored_bucket_capacity;/* stored particles per zeta-cell and s-level; 0 = auto */
+  int32_t particle_headroom;     /* extra streaming slots per CTA for rejoining particles; 0 = auto */
+  int32_t pipeline_depth;        /* s-steps marched concurrently (wavefront); 0 = auto, 1 = none */
+  int32_t reserved;
+  void* cuda_stream;             /* cudaStream_t; NULL = legacy default stream */
+} gempic_config;
+
+/* Per-s-step diagnostics, accumulated on the device in FP64. */
+typedef struct {
+  int64_t step;                 /* s-steps completed */
+  double field_energy;          /* 1/2 sum (E^2 + B^2) hx hy h over the box at the new level */
+  double kinetic_energy;        /* streaming: sum N m (gamma-1) dt/Delta per crossing;
+                                   stored: sum N m (gamma-1); N = Q/q physical particles     */
+  double charge_flux;           /* sum over slice planes of (rho - j_z) hx hy h              */
+  int64_t n_trapped;            /* streaming particles whose s-budget ran out this step     */
+  int64_t n_stored;             /* stored particles at the new level                         */
+  int64_t n_rejoined;           /* stored particles that rejoined the zeta march this step   */
+  int64_t pushes;               /* streaming crossings performed this step                   */
+} gempic_diag;
+
+/* Create a simulation: validates the config (GEMPIC_EUNSTABLE if Delta h omega_p^2 > 4),
+ * allocates the device state, lays the laser into the spectral state, and runs the Delta = 0
+ * consistency march that fills E_z, B_z and L from R at s = 0.  *out receives the handle. */
+gempic_status gempic_create(const gempic_config* cfg, struct gempic_sim** out);
+
+/* Place macroparticles inside the box at the current level (beam / driver particles,
+ * Sec. 4.1 Q_b): absolute positions, momenta u = p/(m c) and charge Q (host FP64 arrays of
+ * length n, species[i] < nspecies).  Valid only before the first gempic_step. */
+gempic_status gempic_add_particles(struct gempic_sim* sim, int64_t n, const double* x,
+                                   const double* y, const double* zeta, const double* ux,
+                                   const double* uy, const double* uz, const double* weight,
+                                   const int32_t* species);
+
+/* Advance n s-steps (one persistent device launch), then wait and check the device status. */
+gempic_status gempic_step(struct gempic_sim* sim, int32_t n);
+
+/* Same, without waiting: launches on the simulation's stream and returns. */
+gempic_status gempic_step_async(struct gempic_sim* sim, int32_t n);
+
+/* Wait for the stream and check the device status word of the simulation. */
+gempic_status gempic_sync(struct gempic_sim* sim);
+
+/* End-to-end step through host buffers: copy the spectral state in from host memory, advance
+ * n s-steps, copy the state back out and return the diagnostics of the last step.  state_in
+ * may be NULL (keep the device state); state_out may be NULL.  Both use the layout of
+ * gempic_get_state; pinned host memory gives the fastest copies. */
+gempic_status gempic_step_host(struct gempic_sim* sim, int32_t n, const void* state_in,
+                               void* state_out, size_t state_bytes, gempic_diag* diag_out);
+
+/* Size in bytes of the spectral state of gempic_get_state. */
+size_t gempic_state_bytes(const struct gempic_sim* sim);
+
+/* Copy the spectral field state (Sec. 4.1: what the scheme needs at s^0): complex values in
+ * the simulation's precision, layout [6][nzeta][ny][nx/2] for R_x, R_y, E_z, B_z on the
+ * slices and j_x, j_y on the half-slices (index n <-> zeta_{n+1/2}); kx = 2 pi m/(nx hx),
+ * m = 0..nx/2-1; ky in FFT order.  dst_is_device selects a device or host destination. */
+gempic_status gempic_get_state(struct gempic_sim* sim, void* dst, size_t bytes,
+                               int32_t dst_is_device);
+
+/* Replace the spectral state (same layout as gempic_get_state). */
+gempic_status gempic_set_state(struct gempic_sim* sim, const void* src, size_t bytes,
+                               int32_t src_is_device);
+
+/* Real-space fields of the last s-step of the last call (needs GEMPIC_FLAG_SNAPSHOT):
+ * comp 0..5 = E_x, E_y, E_z, B_x, B_y, B_z on the slices, 6..8 = j_x, j_y, j_z on the
+ * half-slices (j_x at x + hx/2; in 3-D j_y at y + hy/2); layout [nzeta][ny][nx] in the
+ * simulation's precision. */
+gempic_status gempic_get_fields(struct gempic_sim* sim, int32_t comp, void* dst, size_t bytes,
+                                int32_t dst_is_device);
+
+/* Stored (trapped / beam) particles.  kind 0: particles at the next level, already pushed
+ * along s with the fields of the current level; kind 1: particles queued to rejoin the next
+ * zeta march.  On entry *n_inout is the capacity of the host FP64 arrays; on return the
+ * number of particles (if larger than the capacity nothing is copied and GEMPIC_EINVAL is
+ * returned).  Any array pointer may be NULL. */
+gempic_status gempic_get_particles(struct gempic_sim* sim, int32_t kind, int64_t* n_inout,
+                                   double* x, double* y, double* zeta, double* ux, double* uy,
+                                   double* uz, double* weight, int32_t* species);
+
+/* Diagnostics of the last completed s-step. */
+gempic_status gempic_get_diagnostics(struct gempic_sim* sim, gempic_diag* out);
+
+/* On-axis E_z(zeta_n), n = 0..nzeta-1, of the last completed s-step (FP64 host array). */
+gempic_status gempic_get_onaxis_ez(struct gempic_sim* sim, double* dst, int32_t n);
+
+/* Device kernels this library launched since create (for launch accounting). */
+int64_t gempic_launch_count(const struct gempic_sim* sim);
+
+/* Launch shape chosen at create: CTAs per cluster, threads per CTA, dynamic shared bytes,
+ * s-steps marched concurrently. */
+gempic_status gempic_launch_shape(const struct gempic_sim* sim, int32_t* cluster_ctas,
+                                  int32_t* threads, int32_t* smem_bytes, int32_t* pipeline);
+
+const char* gempic_strerror(gempic_status s);
+
+void gempic_destroy(struct gempic_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GEMPIC_H */

@@ -1,0 +1,622 @@
+// Host side of the GEM-PIC C-ABI (include/gempic.h): validation, launch shape, device
+// allocations, initial condition, stepping and copies.  All compute runs in the kernels of
+// gempic_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/gempic.h"
+#include "gempic_internal.h"
+
+using gempic::Params;
+
+struct gempic_sim {
+  gempic_config cfg;
+  gempic_species species[gempic::kMaxSpecies];
+  gempic_laser laser;
+  bool has_laser = false;
+  Params p{};                      // launch template
+  int eb = 8;                      // bytes per real
+  int pmax = 1;                    // concurrent marches
+  cudaStream_t stream = nullptr;
+  long long k = 0;                 // s-steps completed
+  bool initialized = false;
+  gempic_status failed = GEMPIC_OK;
+  long long launches = 0;
+  int diag_cap = 0;
+  long long last_launch_k0 = 0;
+  int last_launch_n = 0;
+  std::vector<void*> allocs;
+  // particles placed before the first step: absolute positions
+  std::vector<double> px, py, pz, pux, puy, puz, pq;
+  std::vector<int> psp;
+};
+
+namespace {
+
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+gempic_status cuda_fail(gempic_sim* s, cudaError_t e) {
+  if (e == cudaSuccess) return GEMPIC_OK;
+  if (s) s->failed = GEMPIC_ECUDA;
+  return GEMPIC_ECUDA;
+}
+
+template <typename Tp>
+cudaError_t dalloc(gempic_sim* s, Tp** ptr, size_t bytes) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, bytes > 0 ? bytes : 16);
+  if (e != cudaSuccess) return e;
+  s->allocs.push_back(v);
+  e = cudaMemsetAsync(v, 0, bytes > 0 ? bytes : 16, s->stream);
+  *ptr = (Tp*)v;
+  return e;
+}
+
+gempic_status check_device_error(gempic_sim* s) {
+  int err = 0;
+  cudaError_t e = cudaMemcpyAsync(&err, s->p.err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  if (err == 0) return GEMPIC_OK;
+  gempic_status st = (err & gempic::ERR_TIMEOUT) ? GEMPIC_ETIMEOUT
+                     : (err & (gempic::ERR_PCAP | gempic::ERR_BCAP | gempic::ERR_QCAP))
+                         ? GEMPIC_EOVERFLOW
+                         : GEMPIC_ESTATE;
+  s->failed = st;
+  return st;
+}
+
+cudaError_t ensure_diag_cap(gempic_sim* s, int n) {
+  if (n <= s->diag_cap) return cudaSuccess;
+  double *d = nullptr, *o = nullptr;
+  cudaError_t e = dalloc(s, &d, (size_t)n * gempic::kNDiag * s->p.C * sizeof(double));
+  if (e != cudaSuccess) return e;
+  e = dalloc(s, &o, (size_t)n * s->p.nz * sizeof(double));
+  if (e != cudaSuccess) return e;
+  s->p.diag_out = d;
+  s->p.onaxis = o;
+  s->diag_cap = n;
+  return cudaSuccess;
+}
+
+// stored particles given in absolute coordinates -> level-0 buckets (ring slot 0)
+gempic_status upload_particles(gempic_sim* s) {
+  const size_t n = s->px.size();
+  if (n == 0) return GEMPIC_OK;
+  const Params& p = s->p;
+  const size_t cap = (size_t)p.nz * p.bcap;
+  std::vector<int> cnt(p.nz, 0), cell(cap, 0);
+  std::vector<double> f[7];
+  for (auto& v : f) v.assign(cap, 0.0);
+  for (size_t i = 0; i < n; ++i) {
+    const double X = s->px[i] / p.hx, Y = p.ny > 1 ? s->py[i] / p.hy : 0.0;
+    const double Z = s->pz[i] / p.h;
+    const double fX = std::floor(X), fY = std::floor(Y);
+    const int m = (int)std::ceil(Z) - 1;
+    if (m < 0 || m >= p.nz) continue;
+    const int ix = ((int)fX % p.nx + p.nx) % p.nx, iy = ((int)fY % p.ny + p.ny) % p.ny;
+    if (cnt[m] >= p.bcap) return GEMPIC_EOVERFLOW;
+    const size_t e = (size_t)m * p.bcap + cnt[m]++;
+    cell[e] = ix | (iy << 10) | (s->psp[i] << 20);
+    f[0][e] = X - fX;
+    f[1][e] = Y - fY;
+    f[2][e] = Z - m;
+    f[3][e] = s->pux[i];
+    f[4][e] = s->puy[i];
+    f[5][e] = s->puz[i];
+    f[6][e] = s->pq[i];
+  }
+  cudaError_t e = cudaMemcpyAsync(p.st.cnt, cnt.data(), p.nz * sizeof(int), cudaMemcpyHostToDevice, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(p.st.cell, cell.data(), cap * sizeof(int), cudaMemcpyHostToDevice, s->stream);
+  void* dst[7] = {p.st.fx, p.st.fy, p.st.fz, p.st.ux, p.st.uy, p.st.uz, p.st.q};
+  std::vector<float> ff(cap);
+  for (int j = 0; j < 7 && e == cudaSuccess; ++j) {
+    if (s->eb == 8) {
+      e = cudaMemcpyAsync(dst[j], f[j].data(), cap * 8, cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    } else {
+      for (size_t i = 0; i < cap; ++i) ff[i] = (float)f[j][i];
+      e = cudaMemcpyAsync(dst[j], ff.data(), cap * 4, cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_fail(s, e);
+}
+
+gempic_status ensure_initialized(gempic_sim* s) {
+  if (s->failed != GEMPIC_OK) return GEMPIC_ESTATE;
+  if (s->initialized) return GEMPIC_OK;
+  const int prec = s->cfg.precision;
+  cudaError_t e = cudaSuccess;
+  if (s->has_laser) {
+    e = gempic::launch_laser_init(prec, s->p, s->laser.a0, s->laser.waist, s->laser.duration,
+                                  s->laser.zeta_center, s->laser.pol, s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return cuda_fail(s, e);
+  }
+  gempic_status st = upload_particles(s);
+  if (st != GEMPIC_OK) return st;
+  // Delta = 0 consistency march: R^1 = R^0, fills E_z, B_z, L of the initial laser and
+  // pushes the particles placed at level 0 to level 1.
+  e = ensure_diag_cap(s, 1);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  Params q = s->p;
+  q.k0 = -1;
+  q.nsteps = 1;
+  q.P = 1;
+  q.inject = 0;
+  q.delta_field = 0.0;
+  q.diag = 1;
+  q.snapshot = 0;
+  e = gempic::launch_march(prec, q, s->stream);
+  s->launches++;
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  st = check_device_error(s);
+  if (st != GEMPIC_OK) return st;
+  s->initialized = true;
+  s->last_launch_k0 = -1;
+  s->last_launch_n = 1;
+  return GEMPIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* gempic_strerror(gempic_status s) {
+  switch (s) {
+    case GEMPIC_OK: return "ok";
+    case GEMPIC_EINVAL: return "invalid argument or unsupported size";
+    case GEMPIC_ENOMEM: return "out of memory";
+    case GEMPIC_ECUDA: return "CUDA runtime error";
+    case GEMPIC_EUNSTABLE: return "Delta h omega_p^2 > 4: outside the stability bound";
+    case GEMPIC_ETIMEOUT: return "a bounded device wait gave up";
+    case GEMPIC_ESTATE: return "simulation failed earlier or call not valid in this state";
+    case GEMPIC_EOVERFLOW: return "a fixed-capacity particle store overflowed";
+  }
+  return "unknown status";
+}
+
+gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
+  if (!cfg || !out) return GEMPIC_EINVAL;
+  *out = nullptr;
+  const gempic_grid& g = cfg->grid;
+  if (!pow2(g.nx) || g.nx < 8 || g.nx > 1024) return GEMPIC_EINVAL;
+  if (!pow2(g.ny) || g.ny > 1024) return GEMPIC_EINVAL;
+  if (g.nzeta < 2 || !(g.hx > 0) || !(g.hy > 0) || !(g.h > 0) || !(cfg->delta >= 0))
+    return GEMPIC_EINVAL;
+  if (cfg->precision != 32 && cfg->precision != 64) return GEMPIC_EINVAL;
+  if (cfg->nspecies < 0 || cfg->nspecies > gempic::kMaxSpecies) return GEMPIC_EINVAL;
+  if (cfg->nspecies > 0 && !cfg->species) return GEMPIC_EINVAL;
+  double wp2 = 0.0;
+  int ppc_sum = 0;
+  for (int i = 0; i < cfg->nspecies; ++i) {
+    const gempic_species& sp = cfg->species[i];
+    if (sp.ppc < 1 || !(sp.mass > 0) || !(sp.density >= 0)) return GEMPIC_EINVAL;
+    if (sp.density > 0 && sp.charge == 0) return GEMPIC_EINVAL;
+    wp2 += sp.charge * sp.charge * sp.density / sp.mass;
+    ppc_sum += sp.ppc;
+  }
+  if (cfg->delta * g.h * wp2 > 4.0 * (1.0 + 1e-12)) return GEMPIC_EUNSTABLE;
+
+  gempic_sim* s = new (std::nothrow) gempic_sim();
+  if (!s) return GEMPIC_ENOMEM;
+  s->cfg = *cfg;
+  for (int i = 0; i < cfg->nspecies; ++i) s->species[i] = cfg->species[i];
+  s->cfg.species = nullptr;
+  if (cfg->laser) {
+    s->laser = *cfg->laser;
+    s->has_laser = true;
+  }
+  s->cfg.laser = nullptr;
+  s->stream = (cudaStream_t)cfg->cuda_stream;
+  s->eb = cfg->precision == 64 ? 8 : 4;
+
+  Params& p = s->p;
+  p.nx = g.nx;
+  p.ny = g.ny;
+  p.nz = g.nzeta;
+  p.lognx = ilog2(g.nx);
+  p.logny = ilog2(g.ny);
+  p.hx = g.hx;
+  p.hy = g.hy;
+  p.h = g.h;
+  p.delta = cfg->delta;
+  p.delta_field = cfg->delta;
+  p.nspecies = cfg->nspecies;
+  p.seed = cfg->seed;
+  int off = 0;
+  for (int i = 0; i < cfg->nspecies; ++i) {
+    const gempic_species& sp = s->species[i];
+    p.qm[i] = sp.charge / sp.mass;
+    p.Qf[i] = sp.charge * sp.density * g.hx * g.hy * cfg->delta / sp.ppc;
+    p.wd[i] = p.Qf[i] / (g.hx * g.hy * cfg->delta);
+    p.m_over_q[i] = sp.charge != 0 ? sp.mass / sp.charge : 0.0;
+    p.ppc[i] = sp.ppc;
+    p.poff[i] = off;
+    off += g.nx * g.ny * sp.ppc;
+  }
+  p.nlayer = off;
+
+  // launch shape: C CTAs per cluster own ny/C rows and (nx/2)/C kx columns; one spectral
+  // mode per thread (M <= 512).
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  int smem_optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) {
+    delete s;
+    return GEMPIC_ECUDA;
+  }
+  const int nxh = g.nx / 2;
+  int C = cfg->cluster_ctas;
+  bool chosen = false;
+  for (int cand = (C > 0 ? C : 1); cand <= (C > 0 ? C : 16); cand *= 2) {
+    if (g.ny % cand || nxh % cand) continue;
+    if (g.ny == 1 && cand != 1) continue;
+    const int RB = g.ny / cand, KB = nxh / cand, M = KB * g.ny;
+    if (M > 512) continue;
+    const int fresh = RB * g.nx * ppc_sum;
+    int NT = std::max(M, fresh / 4);
+    NT = std::min(512, std::max(128, (NT + 31) / 32 * 32));
+    const int head = cfg->particle_headroom > 0 ? cfg->particle_headroom : std::max(32, fresh / 4);
+    p.C = cand;
+    p.RB = RB;
+    p.KB = KB;
+    p.M = M;
+    p.nthreads = NT;
+    p.pcap = fresh + head;
+    p.nwork = std::min(NT / 32, 3 * RB);
+    if (gempic::smem_layout(p, s->eb) <= smem_optin) {
+      chosen = true;
+      break;
+    }
+  }
+  if (!chosen) {
+    delete s;
+    return GEMPIC_EINVAL;
+  }
+  p.bcap = cfg->stored_bucket_capacity > 0 ? cfg->stored_bucket_capacity
+                                           : std::max(256, g.nx * g.ny * std::max(ppc_sum, 1) / 4);
+  p.wait_spin_limit = 20000000;
+  p.diag = (cfg->flags & GEMPIC_FLAG_DIAG) ? 1 : 0;
+  p.snapshot = (cfg->flags & GEMPIC_FLAG_SNAPSHOT) ? 1 : 0;
+
+  e = gempic::configure_kernels(cfg->precision, p.smem_bytes, p.C);
+  int maxcl = 1;
+  if (e == cudaSuccess) e = gempic::max_active_clusters(cfg->precision, p, &maxcl);
+  if (e != cudaSuccess) {
+    delete s;
+    return GEMPIC_ECUDA;
+  }
+  s->pmax = cfg->pipeline_depth > 0 ? cfg->pipeline_depth : std::max(1, std::min(maxcl, 16));
+  if (s->pmax > std::max(1, maxcl)) s->pmax = std::max(1, maxcl);
+  p.ring = s->pmax + 2;
+
+  // device memory
+  const size_t eb = s->eb;
+  const size_t nperp = (size_t)g.nx * g.ny;
+  const size_t ring = p.ring;
+  const size_t bslots = ring * g.nzeta * (size_t)p.bcap;
+#define ALLOC(ptr, bytes)                  \
+  do {                                     \
+    e = dalloc(s, &(ptr), (bytes));        \
+    if (e != cudaSuccess) goto fail;       \
+  } while (0)
+  {
+    ALLOC(p.state, (size_t)(g.nzeta + 1) * 6 * nxh * g.ny * 2 * eb);
+    ALLOC(p.progress, (size_t)std::max(s->pmax, 1) * sizeof(unsigned long long));
+    ALLOC(p.err, sizeof(int));
+    void* tab = nullptr;
+    const int nyh = g.ny > 1 ? g.ny / 2 : 1;
+    const size_t ncx = nxh + nyh + nxh + g.ny, nr = nxh + g.ny;
+    ALLOC(tab, (ncx * 2 + nr) * eb);
+    p.tables = tab;
+    // twiddles and shifts in FP64 on the host
+    std::vector<double> t(ncx * 2 + nr);
+    size_t o = 0;
+    const double pi = 3.14159265358979323846;
+    for (int k = 0; k < nxh; ++k, o += 2) { t[o] = std::cos(-2 * pi * k / g.nx); t[o + 1] = std::sin(-2 * pi * k / g.nx); }
+    for (int k = 0; k < nyh; ++k, o += 2) {
+      const double a = g.ny > 1 ? -2 * pi * k / g.ny : 0.0;
+      t[o] = std::cos(a); t[o + 1] = std::sin(a);
+    }
+    std::vector<double> kx(nxh), ky(g.ny);
+    for (int k = 0; k < nxh; ++k) kx[k] = 2 * pi * k / (g.nx * g.hx);
+    for (int j = 0; j < g.ny; ++j) {
+      // FFT order: j < ny/2 -> j, else j - ny (fftfreq)
+      const int f = (g.ny == 1) ? 0 : (j < (g.ny + 1) / 2 ? j : j - g.ny);
+      ky[j] = 2 * pi * (double)f / ((double)g.ny * g.hy);
+    }
+    for (int k = 0; k < nxh; ++k, o += 2) { t[o] = std::cos(-0.5 * kx[k] * g.hx); t[o + 1] = std::sin(-0.5 * kx[k] * g.hx); }
+    for (int j = 0; j < g.ny; ++j, o += 2) { t[o] = std::cos(-0.5 * ky[j] * g.hy); t[o + 1] = std::sin(-0.5 * ky[j] * g.hy); }
+    for (int k = 0; k < nxh; ++k) t[o++] = kx[k];
+    for (int j = 0; j < g.ny; ++j) t[o++] = ky[j];
+    if (eb == 8) {
+      e = cudaMemcpyAsync(tab, t.data(), t.size() * 8, cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    } else {
+      std::vector<float> tf(t.begin(), t.end());
+      e = cudaMemcpyAsync(tab, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    }
+    if (e != cudaSuccess) goto fail;
+    gempic::PartStore* stores[2] = {&p.st, &p.rq};
+    for (gempic::PartStore* S : stores) {
+      ALLOC(S->cnt, ring * g.nzeta * sizeof(int));
+      ALLOC(S->cell, bslots * sizeof(int));
+      ALLOC(S->fx, bslots * eb);
+      ALLOC(S->fy, bslots * eb);
+      ALLOC(S->fz, bslots * eb);
+      ALLOC(S->ux, bslots * eb);
+      ALLOC(S->uy, bslots * eb);
+      ALLOC(S->uz, bslots * eb);
+      ALLOC(S->q, bslots * eb);
+    }
+    ALLOC(p.jbeam, ring * g.nzeta * 3 * nperp * eb);
+    ALLOC(p.jflag, ring * g.nzeta * sizeof(int));
+    if (p.snapshot) ALLOC(p.snap, (size_t)9 * g.nzeta * nperp * eb);
+  }
+#undef ALLOC
+  e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) goto fail;
+  *out = s;
+  return GEMPIC_OK;
+fail:
+  for (void* v : s->allocs) cudaFree(v);
+  delete s;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? GEMPIC_ENOMEM : GEMPIC_ECUDA;
+}
+
+gempic_status gempic_add_particles(gempic_sim* s, int64_t n, const double* x, const double* y,
+                                   const double* zeta, const double* ux, const double* uy,
+                                   const double* uz, const double* weight, const int32_t* species) {
+  if (!s) return GEMPIC_EINVAL;
+  if (s->failed != GEMPIC_OK || s->initialized) return GEMPIC_ESTATE;
+  if (n < 0 || (n > 0 && (!x || !zeta || !ux || !uy || !uz || !weight || !species)))
+    return GEMPIC_EINVAL;
+  if (s->p.ny > 1 && n > 0 && !y) return GEMPIC_EINVAL;
+  for (int64_t i = 0; i < n; ++i) {
+    if (species[i] < 0 || species[i] >= std::max(1, s->p.nspecies)) return GEMPIC_EINVAL;
+    if (!(zeta[i] > 0) || !(zeta[i] <= s->p.nz * s->p.h)) return GEMPIC_EINVAL;
+  }
+  for (int64_t i = 0; i < n; ++i) {
+    s->px.push_back(x[i]);
+    s->py.push_back(y ? y[i] : 0.0);
+    s->pz.push_back(zeta[i]);
+    s->pux.push_back(ux[i]);
+    s->puy.push_back(uy[i]);
+    s->puz.push_back(uz[i]);
+    s->pq.push_back(weight[i]);
+    s->psp.push_back(species[i]);
+  }
+  return GEMPIC_OK;
+}
+
+gempic_status gempic_step_async(gempic_sim* s, int32_t n) {
+  if (!s || n < 0) return GEMPIC_EINVAL;
+  gempic_status st = ensure_initialized(s);
+  if (st != GEMPIC_OK) return st;
+  if (n == 0) return GEMPIC_OK;
+  cudaError_t e = ensure_diag_cap(s, n);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  Params q = s->p;
+  q.k0 = s->k;
+  q.nsteps = n;
+  q.P = std::min(s->pmax, n);
+  q.inject = q.nspecies > 0 ? 1 : 0;
+  q.delta_field = s->p.delta;
+  e = gempic::launch_march(s->cfg.precision, q, s->stream);
+  s->launches++;
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  s->last_launch_k0 = s->k;
+  s->last_launch_n = n;
+  s->k += n;
+  return GEMPIC_OK;
+}
+
+gempic_status gempic_sync(gempic_sim* s) {
+  if (!s) return GEMPIC_EINVAL;
+  if (s->failed != GEMPIC_OK) return GEMPIC_ESTATE;
+  return check_device_error(s);
+}
+
+gempic_status gempic_step(gempic_sim* s, int32_t n) {
+  gempic_status st = gempic_step_async(s, n);
+  if (st != GEMPIC_OK) return st;
+  return gempic_sync(s);
+}
+
+size_t gempic_state_bytes(const gempic_sim* s) {
+  if (!s) return 0;
+  return (size_t)6 * s->p.nz * s->p.ny * (s->p.nx / 2) * 2 * s->eb;
+}
+
+static gempic_status copy_state(gempic_sim* s, void* ptr, size_t bytes, int is_device, bool out) {
+  if (!s || !ptr) return GEMPIC_EINVAL;
+  if (bytes < gempic_state_bytes(s)) return GEMPIC_EINVAL;
+  gempic_status st = ensure_initialized(s);
+  if (st != GEMPIC_OK) return st;
+  const size_t nb = gempic_state_bytes(s);
+  void* dev = ptr;
+  void* tmp = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (!is_device) {
+    e = cudaMallocAsync(&tmp, nb, s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+    dev = tmp;
+    if (!out) e = cudaMemcpyAsync(tmp, ptr, nb, cudaMemcpyHostToDevice, s->stream);
+  }
+  if (e == cudaSuccess)
+    e = out ? gempic::launch_export_state(s->cfg.precision, s->p, dev, s->stream)
+            : gempic::launch_import_state(s->cfg.precision, s->p, dev, s->stream);
+  s->launches++;
+  if (e == cudaSuccess && !is_device && out)
+    e = cudaMemcpyAsync(ptr, tmp, nb, cudaMemcpyDeviceToHost, s->stream);
+  if (tmp) cudaFreeAsync(tmp, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_fail(s, e);
+}
+
+gempic_status gempic_get_state(gempic_sim* s, void* dst, size_t bytes, int32_t dst_is_device) {
+  return copy_state(s, dst, bytes, dst_is_device, true);
+}
+
+gempic_status gempic_set_state(gempic_sim* s, const void* src, size_t bytes, int32_t src_is_device) {
+  return copy_state(s, const_cast<void*>(src), bytes, src_is_device, false);
+}
+
+gempic_status gempic_step_host(gempic_sim* s, int32_t n, const void* state_in, void* state_out,
+                               size_t state_bytes, gempic_diag* diag_out) {
+  if (!s) return GEMPIC_EINVAL;
+  gempic_status st = GEMPIC_OK;
+  if (state_in) st = gempic_set_state(s, state_in, state_bytes, 0);
+  if (st == GEMPIC_OK) st = gempic_step(s, n);
+  if (st == GEMPIC_OK && state_out) st = gempic_get_state(s, state_out, state_bytes, 0);
+  if (st == GEMPIC_OK && diag_out) st = gempic_get_diagnostics(s, diag_out);
+  return st;
+}
+
+gempic_status gempic_get_fields(gempic_sim* s, int32_t comp, void* dst, size_t bytes,
+                                int32_t dst_is_device) {
+  if (!s || !dst || comp < 0 || comp > 8) return GEMPIC_EINVAL;
+  if (!s->p.snapshot || s->k == 0) return GEMPIC_ESTATE;
+  const size_t nb = (size_t)s->p.nz * s->p.ny * s->p.nx * s->eb;
+  if (bytes < nb) return GEMPIC_EINVAL;
+  if (s->failed != GEMPIC_OK) return GEMPIC_ESTATE;
+  cudaError_t e = cudaMemcpyAsync(dst, (const char*)s->p.snap + (size_t)comp * nb, nb,
+                                  dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_fail(s, e);
+}
+
+gempic_status gempic_get_particles(gempic_sim* s, int32_t kind, int64_t* n_inout, double* x,
+                                   double* y, double* zeta, double* ux, double* uy, double* uz,
+                                   double* weight, int32_t* species) {
+  if (!s || !n_inout || (kind != 0 && kind != 1)) return GEMPIC_EINVAL;
+  gempic_status st = ensure_initialized(s);
+  if (st != GEMPIC_OK) return st;
+  const Params& p = s->p;
+  const gempic::PartStore& S = kind == 0 ? p.st : p.rq;
+  const int slot = (int)((s->k + 1) % p.ring);
+  const size_t cap = (size_t)p.nz * p.bcap;
+  const size_t base = (size_t)slot * cap;
+  std::vector<int> cnt(p.nz), cell(cap);
+  std::vector<char> raw[7];
+  void* src[7] = {S.fx, S.fy, S.fz, S.ux, S.uy, S.uz, S.q};
+  cudaError_t e = cudaMemcpyAsync(cnt.data(), S.cnt + (size_t)slot * p.nz, p.nz * sizeof(int),
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(cell.data(), S.cell + base, cap * sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  for (int j = 0; j < 7 && e == cudaSuccess; ++j) {
+    raw[j].resize(cap * s->eb);
+    e = cudaMemcpyAsync(raw[j].data(), (const char*)src[j] + base * s->eb, cap * s->eb,
+                        cudaMemcpyDeviceToHost, s->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  int64_t total = 0;
+  for (int b = 0; b < p.nz; ++b) total += std::min(cnt[b], p.bcap);
+  if (total > *n_inout) {
+    *n_inout = total;
+    return GEMPIC_EINVAL;
+  }
+  auto val = [&](int j, size_t i) -> double {
+    return s->eb == 8 ? ((const double*)raw[j].data())[i] : (double)((const float*)raw[j].data())[i];
+  };
+  int64_t o = 0;
+  for (int b = 0; b < p.nz; ++b) {
+    for (int i = 0; i < std::min(cnt[b], p.bcap); ++i, ++o) {
+      const size_t e2 = (size_t)b * p.bcap + i;
+      const int c = cell[e2];
+      const int ix = c & 1023, iy = (c >> 10) & 1023, sp = (c >> 20) & 3;
+      if (x) x[o] = (ix + val(0, e2)) * p.hx;
+      if (y) y[o] = p.ny > 1 ? (iy + val(1, e2)) * p.hy : 0.0;
+      if (zeta) zeta[o] = (b + val(2, e2)) * p.h;
+      if (ux) ux[o] = val(3, e2);
+      if (uy) uy[o] = val(4, e2);
+      if (uz) uz[o] = val(5, e2);
+      if (weight) weight[o] = val(6, e2);
+      if (species) species[o] = sp;
+    }
+  }
+  *n_inout = total;
+  return GEMPIC_OK;
+}
+
+gempic_status gempic_get_diagnostics(gempic_sim* s, gempic_diag* out) {
+  if (!s || !out) return GEMPIC_EINVAL;
+  gempic_status st = ensure_initialized(s);
+  if (st != GEMPIC_OK) return st;
+  st = check_device_error(s);
+  if (st != GEMPIC_OK) return st;
+  const Params& p = s->p;
+  const int sl = s->last_launch_n - 1;
+  std::vector<double> d((size_t)gempic::kNDiag * p.C);
+  cudaError_t e = cudaMemcpyAsync(d.data(), p.diag_out + (size_t)sl * gempic::kNDiag * p.C,
+                                  d.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  double v[gempic::kNDiag];
+  for (int i = 0; i < gempic::kNDiag; ++i) {
+    v[i] = 0.0;
+    for (int r = 0; r < p.C; ++r) v[i] += d[(size_t)i * p.C + r];
+  }
+  out->step = s->k;
+  out->field_energy = v[gempic::DG_FIELD];
+  out->kinetic_energy = v[gempic::DG_KIN];
+  out->charge_flux = v[gempic::DG_FLUX];
+  out->n_trapped = (int64_t)std::llround(v[gempic::DG_TRAP]);
+  out->n_stored = (int64_t)std::llround(v[gempic::DG_STORED]);
+  out->n_rejoined = (int64_t)std::llround(v[gempic::DG_REJOIN]);
+  out->pushes = (int64_t)std::llround(v[gempic::DG_PUSH]);
+  return GEMPIC_OK;
+}
+
+gempic_status gempic_get_onaxis_ez(gempic_sim* s, double* dst, int32_t n) {
+  if (!s || !dst || n < s->p.nz) return GEMPIC_EINVAL;
+  gempic_status st = ensure_initialized(s);
+  if (st != GEMPIC_OK) return st;
+  const int sl = s->last_launch_n - 1;
+  cudaError_t e = cudaMemcpyAsync(dst, s->p.onaxis + (size_t)sl * s->p.nz, s->p.nz * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_fail(s, e);
+}
+
+int64_t gempic_launch_count(const gempic_sim* s) { return s ? s->launches : 0; }
+
+gempic_status gempic_launch_shape(const gempic_sim* s, int32_t* cluster_ctas, int32_t* threads,
+                                  int32_t* smem_bytes, int32_t* pipeline) {
+  if (!s) return GEMPIC_EINVAL;
+  if (cluster_ctas) *cluster_ctas = s->p.C;
+  if (threads) *threads = s->p.nthreads;
+  if (smem_bytes) *smem_bytes = s->p.smem_bytes;
+  if (pipeline) *pipeline = s->pmax;
+  return GEMPIC_OK;
+}
+
+void gempic_destroy(gempic_sim* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  for (void* v : s->allocs) cudaFree(v);
+  cudaGetLastError();
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Internal interface between the host API (gempic_api.cu) and the device kernels
+// (gempic_kernels.cu).  Not part of the public C-ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gempic {
+
+constexpr int kMaxSpecies = 4;
+constexpr int kNDiag = 8;        // per-CTA FP64 diagnostic partials per s-step
+enum DiagSlot { DG_FIELD = 0, DG_KIN, DG_FLUX, DG_TRAP, DG_STORED, DG_REJOIN, DG_PUSH, DG_LOST };
+
+// Device error word bits.
+enum ErrBits : int {
+  ERR_TIMEOUT = 1,       // a bounded wait on another march gave up
+  ERR_PCAP = 2,          // streaming particle capacity of a CTA exceeded
+  ERR_BCAP = 4,          // stored bucket capacity exceeded
+  ERR_QCAP = 8,          // rejoin queue capacity exceeded
+  ERR_NONFINITE = 16     // non-finite particle momentum met
+};
+
+// Stored-particle store: ring of s-levels x nzeta buckets x capacity, structure of arrays.
+// The cell word packs ix | iy << 10 | species << 20; fx, fy in [0,1) are transverse in-cell
+// offsets and fz in (0,1] the in-cell zeta offset: zeta = (bucket + fz) h.
+struct PartStore {
+  int* cnt;          // [ring][nzeta]
+  int* cell;         // [ring][nzeta][cap]
+  void* fx; void* fy; void* fz;
+  void* ux; void* uy; void* uz; void* q;
+};
+
+struct Params {
+  // grid and decomposition
+  int nx, ny, nz;                 // transverse nodes, slices
+  int C, RB, KB, M;               // CTAs per cluster, rows per CTA, kx per CTA, modes per CTA
+  int lognx, logny;
+  int nthreads;
+  // physics
+  double hx, hy, h, delta, delta_field;
+  int nspecies, nlayer;
+  double qm[kMaxSpecies];         // q/m
+  double wd[kMaxSpecies];         // (rho - j_z) weight Q_f/(hx hy Delta) of a fresh particle
+  double Qf[kMaxSpecies];         // fresh macroparticle charge q n hx hy Delta/ppc
+  double m_over_q[kMaxSpecies];   // m/q: kinetic energy of N = Q/q particles is Q (m/q)(gamma-1)
+  int ppc[kMaxSpecies], poff[kMaxSpecies];
+  unsigned long long seed;
+  // launch
+  long long k0;                   // s-step index of the first march of this launch (-1: init)
+  int nsteps;                     // marches in this launch
+  int P;                          // concurrent marches (clusters)
+  int inject, diag, snapshot;
+  int pcap;                       // streaming particle slots per CTA
+  int bcap, ring;                 // stored bucket capacity, ring of s-levels
+  int wait_spin_limit;            // bounded wait: polls before giving up
+  int nwork;                      // FFT work rows per CTA
+  // shared-memory layout (byte offsets)
+  int o_f0, o_f1, o_j, o_sr, o_sc, o_work, o_tw, o_part, o_misc, smem_bytes;
+  // device memory
+  void* state;                    // blocks [nz+1][C][6][M] complex
+  unsigned long long* progress;   // [P] completed-iteration counters
+  int* err;
+  const void* tables;             // twx[nx/2], twy[ny/2], shx[nx/2], shy[ny], kx[nx/2], ky[ny]
+  PartStore st;                   // stored particles (trapped / beam)
+  PartStore rq;                   // rejoin queues
+  void* jbeam;                    // [ring][nz][3][ny][nx]
+  int* jflag;                     // [ring][nz]
+  double* diag_out;               // [nsteps][kNDiag][C]
+  double* onaxis;                 // [nsteps][nz]
+  void* snap;                     // [9][nz][ny][nx]
+};
+
+// Host-side helpers implemented in gempic_kernels.cu
+int smem_layout(Params& p, int elem_bytes);           // fills offsets, returns total bytes
+cudaError_t configure_kernels(int precision, int smem_bytes, int cluster);
+cudaError_t launch_march(int precision, const Params& p, cudaStream_t s);
+cudaError_t launch_laser_init(int precision, const Params& p, double a0, double waist,
+                              double duration, double zeta_c, int pol, cudaStream_t s);
+cudaError_t launch_export_state(int precision, const Params& p, void* dst, cudaStream_t s);
+cudaError_t launch_import_state(int precision, const Params& p, const void* src, cudaStream_t s);
+cudaError_t max_active_clusters(int precision, const Params& p, int* n);
+
+}  // namespace gempic

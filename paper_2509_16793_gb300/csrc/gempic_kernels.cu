@@ -1,0 +1,1234 @@
+// GEM-PIC hot path on sm_103a: the zeta march of one s-step as a persistent kernel run by a
+// thread-block cluster, and (optionally) several s-steps in flight as a wavefront.
+//
+// One cluster of C CTAs marches one s-step (Sec. 4.1: "we start marching along zeta from the
+// right boundary").  CTA r owns
+//   * real-space rows y in [r RB, (r+1) RB) of every slice plane (fields for the gather,
+//     current accumulators for the deposit), and the fresh particles injected into them;
+//   * spectral columns kx in [r KB, (r+1) KB) for all ky (per-mode slice solve, App. B),
+//     with one mode per thread whose carried state lives in registers.
+// Per slice n = nz-1 .. 0 (zeta_n = n h):
+//   A  gather E,B of slice n+1 at every streaming particle, push it to plane n along the GT2
+//      characteristics (two-pass Boris, budget rule of Eq. trap2), deposit the transverse
+//      current by the 2-D Esirkepov decomposition and j_z by CIC into shared memory
+//      (distributed shared memory atomics for rows of another CTA); trapped particles go to
+//      the stored set; rejoining stored particles join here; the beam current is added.
+//   B  row FFTs of the currents, transposed into the kx-owner CTAs (DSMEM stores).
+//   C  column FFTs; per mode: corrector of R at slice n+1, write of the new level at slice
+//      n+1 to HBM, App. B solve at slice n, fields E,B; inverse column FFTs, transposed back.
+//   D  inverse row FFTs: real-space E,B of slice n into shared memory (next gather).
+//   E  stored particles in cell (zeta_n, zeta_{n+1}] are pushed along s with the fields of
+//      slices n and n+1 (Sec. 4.1, last paragraph), depositing the next level's beam current.
+//
+// Wavefront: the march of s-step k+1 on another cluster needs, at slice n, only what the march
+// of step k produced at slices >= n-1.  Marches publish per-slice progress in global memory
+// and wait on their predecessor with bounded spins; every device wait has a limit and sets an
+// error bit instead of hanging.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "gempic_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace gempic {
+
+// ------------------------------------------------------------------------------------------
+// small complex / vector helpers
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct alignas(2 * sizeof(T)) Cx {
+  T re, im;
+};
+template <typename T>
+__device__ __forceinline__ Cx<T> cx(T a, T b) { return Cx<T>{a, b}; }
+template <typename T>
+__device__ __forceinline__ Cx<T> operator+(Cx<T> a, Cx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+__device__ __forceinline__ Cx<T> operator-(Cx<T> a, Cx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T>
+__device__ __forceinline__ Cx<T> operator*(Cx<T> a, Cx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__device__ __forceinline__ Cx<T> operator*(T s, Cx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T>
+__device__ __forceinline__ Cx<T> conjg(Cx<T> a) { return {a.re, -a.im}; }
+template <typename T>
+__device__ __forceinline__ Cx<T> mul_i(Cx<T> a) { return {-a.im, a.re}; }   // i a
+
+template <typename T>
+struct V3 {
+  T x, y, z;
+};
+
+template <typename T>
+__device__ __forceinline__ T gamma_of(V3<T> u) {   // sqrt(1 + ux^2 + uy^2 + uz^2)
+  return sqrt(((T(1) + u.x * u.x) + u.y * u.y) + u.z * u.z);
+}
+// gamma - u_z, as (1 + u_perp^2)/(gamma + u_z) where u_z > 0 (no cancellation).
+template <typename T>
+__device__ __forceinline__ T gamma_minus_uz(V3<T> u, T g) {
+  return u.z > T(0) ? ((T(1) + u.x * u.x) + u.y * u.y) / (g + u.z) : g - u.z;
+}
+
+// Relativistic Boris rotation over lab time dt: du/dt = (q/m)(E + u x B / gamma).
+template <typename T>
+__device__ __forceinline__ V3<T> boris(V3<T> u, const T* E, const T* B, T qm, T dt) {
+  const T a = T(0.5) * qm * dt;
+  V3<T> um{u.x + a * E[0], u.y + a * E[1], u.z + a * E[2]};
+  const T gm = sqrt(T(1) + ((um.x * um.x + um.y * um.y) + um.z * um.z));
+  const T tx = a * B[0] / gm, ty = a * B[1] / gm, tz = a * B[2] / gm;
+  V3<T> up{um.x + (um.y * tz - um.z * ty), um.y + (um.z * tx - um.x * tz),
+           um.z + (um.x * ty - um.y * tx)};
+  const T den = T(1) + ((tx * tx + ty * ty) + tz * tz);
+  const T sx = T(2) * tx / den, sy = T(2) * ty / den, sz = T(2) * tz / den;
+  V3<T> upl{um.x + (up.y * sz - up.z * sy), um.y + (up.z * sx - up.x * sz),
+            um.z + (up.x * sy - up.y * sx)};
+  return V3<T>{upl.x + a * E[0], upl.y + a * E[1], upl.z + a * E[2]};
+}
+
+// ------------------------------------------------------------------------------------------
+// memory-model helpers: data exchanged between clusters is read at L2 (ld.global.cg) and the
+// progress word is published / observed with release / acquire at GPU scope.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) { return __ldcg(p); }
+template <>
+__device__ __forceinline__ Cx<float> ldcg(const Cx<float>* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return Cx<float>{v.x, v.y};
+}
+template <>
+__device__ __forceinline__ Cx<double> ldcg(const Cx<double>* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return Cx<double>{v.x, v.y};
+}
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ int imod(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+// Counter-based SplitMix64 (Steele, Lea, Flood 2014): output c of the stream seeded with s.
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long s,
+                                                         unsigned long long c) {
+  unsigned long long z = s + (c + 1ull) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+// 24 random bits as a uniform in [0,1), exact in float and double.
+__device__ __forceinline__ double uniform24(unsigned long long s, unsigned long long c) {
+  return (double)(splitmix64(s, c) >> 40) * (1.0 / 16777216.0);
+}
+
+// ------------------------------------------------------------------------------------------
+// warp-level radix-2 FFT on shared memory (length N = 2^logN, unnormalised).
+// tw[k] = exp(-2 pi i k / N), k < N/2.  inverse: conjugate twiddles.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ void warp_fft(Cx<T>* d, int logN, const Cx<T>* tw, bool inverse) {
+  const int N = 1 << logN;
+  const int lane = threadIdx.x & 31;
+  if (N == 1) return;
+  for (int i = lane; i < N; i += 32) {
+    const int r = (int)(__brev((unsigned)i) >> (32 - logN));
+    if (i < r) {
+      Cx<T> t = d[i];
+      d[i] = d[r];
+      d[r] = t;
+    }
+  }
+  __syncwarp();
+  for (int s = 1; s <= logN; ++s) {
+    const int half = 1 << (s - 1);
+    const int tstride = N >> s;
+    for (int b = lane; b < N / 2; b += 32) {
+      const int grp = b >> (s - 1);
+      const int j = b & (half - 1);
+      const int i0 = grp * (half << 1) + j;
+      const int i1 = i0 + half;
+      Cx<T> w = tw[j * tstride];
+      if (inverse) w.im = -w.im;
+      const Cx<T> t = w * d[i1];
+      const Cx<T> u = d[i0];
+      d[i0] = u + t;
+      d[i1] = u - t;
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// per-kernel shared-memory views
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct Sm {
+  T* F[2];          // [6][RB][nx] real-space fields (Ex,Ey,Ez,Bx,By,Bz)
+  T* J;             // [3][RB][nx] current accumulators (jx on x-edges, jy (3-D: y-edges), jz)
+  Cx<T>* SR;        // [6][RB][nx/2] row spectra received for the inverse transform
+  Cx<T>* SC;        // [6][KB][ny] column spectra (forward: 3 currents; inverse: 6 fields)
+  Cx<T>* work;      // [nwork][nx]
+  Cx<T>* twx;       // [nx/2]
+  Cx<T>* twy;       // [max(ny/2,1)]
+  Cx<T>* shx;       // [nx/2]  exp(-i kx hx/2)
+  Cx<T>* shy;       // [ny]    exp(-i ky hy/2)
+  T* kx;            // [nx/2]
+  T* ky;            // [ny]
+  int* pcell;       // [pcap] ix | iy << 10 | sp << 20, -1 = empty
+  T *pfx, *pfy, *pux, *puy, *puz, *psig, *pq;
+  int* misc;        // [0] particle count
+  double* dacc;     // [kNDiag]
+};
+
+template <typename T>
+__device__ Sm<T> carve(const Params& p, unsigned char* base) {
+  Sm<T> s;
+  s.F[0] = (T*)(base + p.o_f0);
+  s.F[1] = (T*)(base + p.o_f1);
+  s.J = (T*)(base + p.o_j);
+  s.SR = (Cx<T>*)(base + p.o_sr);
+  s.SC = (Cx<T>*)(base + p.o_sc);
+  s.work = (Cx<T>*)(base + p.o_work);
+  Cx<T>* tw = (Cx<T>*)(base + p.o_tw);
+  const int nyh = p.ny > 1 ? p.ny / 2 : 1;
+  s.twx = tw;
+  s.twy = s.twx + p.nx / 2;
+  s.shx = s.twy + nyh;
+  s.shy = s.shx + p.nx / 2;
+  s.kx = (T*)(s.shy + p.ny);
+  s.ky = s.kx + p.nx / 2;
+  unsigned char* pp = base + p.o_part;
+  s.pcell = (int*)pp;
+  T* pt = (T*)(pp + ((p.pcap * 4 + 15) / 16) * 16);
+  s.pfx = pt;
+  s.pfy = pt + p.pcap;
+  s.pux = pt + 2 * p.pcap;
+  s.puy = pt + 3 * p.pcap;
+  s.puz = pt + 4 * p.pcap;
+  s.psig = pt + 5 * p.pcap;
+  s.pq = pt + 6 * p.pcap;
+  s.misc = (int*)(base + p.o_misc);
+  s.dacc = (double*)(base + p.o_misc + 16);
+  return s;
+}
+
+// copy the FP64-built tables (already converted to T on the host) into shared memory
+template <typename T>
+__device__ void load_tables(const Params& p, const Sm<T>& s) {
+  const int nyh = p.ny > 1 ? p.ny / 2 : 1;
+  const int ncx = p.nx / 2 + nyh + p.nx / 2 + p.ny;
+  const int nr = p.nx / 2 + p.ny;
+  const Cx<T>* src = (const Cx<T>*)p.tables;
+  for (int i = threadIdx.x; i < ncx; i += blockDim.x) s.twx[i] = src[i];
+  const T* srcr = (const T*)(src + ncx);
+  for (int i = threadIdx.x; i < nr; i += blockDim.x) s.kx[i] = srcr[i];
+}
+
+// ------------------------------------------------------------------------------------------
+// cluster helpers
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T* at_rank(const cg::cluster_group& cl, T* local, int r, int me) {
+  return r == me ? local : cl.map_shared_rank(local, r);
+}
+
+// pointer to element (comp, global row y, column x) of a [comp][RB][nx] plane set
+template <typename T>
+__device__ __forceinline__ T* plane_ptr(const cg::cluster_group& cl, T* base, const Params& p,
+                                        int comp, int y, int x, int me) {
+  const int r = y / p.RB;
+  const int yl = y - r * p.RB;
+  return at_rank(cl, base + ((size_t)comp * p.RB + yl) * p.nx + x, r, me);
+}
+
+// ------------------------------------------------------------------------------------------
+// Forward transverse transform of the three current planes J (own rows) into the kx-owner
+// CTAs' SC[0..2] (DSMEM).  stagger: apply exp(-i kx hx/2) to j_x (x-edge values).
+// `snapcomp` >= 0 also writes the real-space rows to the snapshot.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ void forward_rows(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
+                             int me, bool stagger) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int nxh = p.nx / 2;
+  const int ntask = 2 * p.RB;                 // (row, pair): pair 0 = jx + i jy, 1 = jz
+  if (warp >= p.nwork) return;
+  (void)nwarps;
+  for (int task = warp; task < ntask; task += p.nwork) {
+    Cx<T>* w = s.work + (size_t)warp * p.nx;
+    const int yl = task >> 1, pr = task & 1;
+    const T* a = s.J + ((size_t)(pr == 0 ? 0 : 2) * p.RB + yl) * p.nx;
+    const T* b = s.J + ((size_t)1 * p.RB + yl) * p.nx;
+    for (int x = lane; x < p.nx; x += 32) w[x] = cx<T>(a[x], pr == 0 ? b[x] : T(0));
+    __syncwarp();
+    warp_fft(w, p.lognx, s.twx, false);
+    const int y = me * p.RB + yl;
+    for (int k = lane; k < nxh; k += 32) {
+      const Cx<T> zk = w[k];
+      const Cx<T> zm = conjg(w[(p.nx - k) & (p.nx - 1)]);
+      Cx<T> X = T(0.5) * (zk + zm);                     // spectrum of the real part
+      const Cx<T> Y = T(0.5) * mul_i(zm - zk);          // spectrum of the imaginary part
+      const int rd = k / p.KB, kxl = k - rd * p.KB;
+      if (pr == 0) {
+        if (stagger) X = X * s.shx[k];
+        *at_rank(cl, s.SC + ((size_t)0 * p.KB + kxl) * p.ny + y, rd, me) = X;
+        *at_rank(cl, s.SC + ((size_t)1 * p.KB + kxl) * p.ny + y, rd, me) = Y;
+      } else {
+        *at_rank(cl, s.SC + ((size_t)2 * p.KB + kxl) * p.ny + y, rd, me) = X;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// column FFTs of SC[c0..c1) (in place), forward or inverse
+template <typename T>
+__device__ void column_ffts(const Params& p, const Sm<T>& s, int c0, int c1, bool inverse) {
+  if (p.ny == 1) return;
+  const int warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int ntask = (c1 - c0) * p.KB;
+  for (int task = warp; task < ntask; task += nwarps) {
+    const int c = c0 + task / p.KB, kxl = task % p.KB;
+    warp_fft(s.SC + ((size_t)c * p.KB + kxl) * p.ny, p.logny, s.twy, inverse);
+  }
+}
+
+// scatter the 6 inverse-column-transformed field spectra to the row owners' SR
+template <typename T>
+__device__ void scatter_to_rows(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
+                                int me) {
+  const int n = 6 * p.KB * p.ny;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const int c = i / (p.KB * p.ny);
+    const int rem = i - c * p.KB * p.ny;
+    const int kxl = rem / p.ny, y = rem - kxl * p.ny;
+    const int ro = y / p.RB, yl = y - ro * p.RB;
+    *at_rank(cl, s.SR + ((size_t)c * p.RB + yl) * (p.nx / 2) + me * p.KB + kxl, ro, me) =
+        s.SC[i];
+  }
+}
+
+// inverse row transforms: SR pairs (Ex,Ey), (Ez,Bx), (By,Bz) -> real rows of Fdst
+template <typename T>
+__device__ void inverse_rows(const Params& p, const Sm<T>& s, T* Fdst, double& fe) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int nxh = p.nx / 2;
+  const T scale = T(1.0 / ((double)p.nx * (double)p.ny));
+  const int ntask = 3 * p.RB;
+  T acc = T(0);
+  (void)nwarps;
+  for (int task = (warp < p.nwork ? warp : ntask); task < ntask; task += p.nwork) {
+    Cx<T>* w = s.work + (size_t)warp * p.nx;
+    const int yl = task / 3, pr = task % 3;
+    const Cx<T>* X = s.SR + ((size_t)(2 * pr) * p.RB + yl) * nxh;
+    const Cx<T>* Y = s.SR + ((size_t)(2 * pr + 1) * p.RB + yl) * nxh;
+    for (int k = lane; k < nxh; k += 32) {
+      Cx<T> x = X[k], y = Y[k];
+      if (k == 0) {
+        w[0] = cx<T>(x.re, y.re);                         // real DC of each field
+      } else {
+        w[k] = cx<T>(x.re - y.im, x.im + y.re);           // X + i Y
+        w[p.nx - k] = cx<T>(x.re + y.im, y.re - x.im);    // conj(X) + i conj(Y)
+      }
+    }
+    if (lane == 0) w[nxh] = cx<T>(T(0), T(0));            // Nyquist projected out
+    __syncwarp();
+    warp_fft(w, p.lognx, s.twx, true);
+    T* a = Fdst + ((size_t)(2 * pr) * p.RB + yl) * p.nx;
+    T* b = Fdst + ((size_t)(2 * pr + 1) * p.RB + yl) * p.nx;
+    for (int x = lane; x < p.nx; x += 32) {
+      const T va = w[x].re * scale, vb = w[x].im * scale;
+      a[x] = va;
+      b[x] = vb;
+      acc += va * va + vb * vb;
+    }
+    __syncwarp();
+  }
+  fe += (double)acc;
+}
+
+// ------------------------------------------------------------------------------------------
+// particle gather (CIC on the transverse nodes) of the 6 fields of a plane set
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void gather6(const cg::cluster_group& cl, const Params& p, T* Fb,
+                                        int ix, T fx, int iy, T fy, int me, T* out) {
+  const int ix1 = ix + 1 == p.nx ? 0 : ix + 1;
+  if (p.ny == 1) {
+    for (int c = 0; c < 6; ++c) {
+      const T* r = Fb + (size_t)c * p.nx;
+      out[c] = (T(1) - fx) * r[ix] + fx * r[ix1];
+    }
+    return;
+  }
+  const int iy1 = iy + 1 == p.ny ? 0 : iy + 1;
+  const T w00 = (T(1) - fx) * (T(1) - fy), w10 = fx * (T(1) - fy);
+  const T w01 = (T(1) - fx) * fy, w11 = fx * fy;
+  for (int c = 0; c < 6; ++c) {
+    const T* r0 = plane_ptr(cl, Fb, p, c, iy, 0, me);
+    const T* r1 = plane_ptr(cl, Fb, p, c, iy1, 0, me);
+    out[c] = ((w00 * r0[ix] + w10 * r0[ix1]) + w01 * r1[ix]) + w11 * r1[ix1];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void jadd(const cg::cluster_group& cl, const Params& p, T* J, int comp,
+                                     int y, int x, T v, int me) {
+  if (v != T(0)) atomicAdd(plane_ptr(cl, J, p, comp, imod(y, p.ny), imod(x, p.nx), me), v);
+}
+
+// Esirkepov (Comput. Phys. Commun. 135, 2001) transverse current of a move (X0,Y0)->(X1,Y1)
+// in cell units relative to node (ix, iy); w is the (rho - j_z) weight.  With D = w S the
+// deposit satisfies (D_new - D_old) + h div J = 0 on every node.
+template <typename T>
+__device__ void esirkepov(const cg::cluster_group& cl, const Params& p, T* J, int ix, int iy,
+                          T X0, T Y0, T X1, T Y1, T w, T dyo, int me) {
+  const T h = T(p.h);
+  const T dX = X1 - X0;
+  const T dY = Y1 - Y0;
+  const T m = fmax(fabs(dX), fabs(dY));
+  const int nsub = m > T(1) ? (int)ceil(m) : 1;
+  const T cx_ = -(w * T(p.hx) / h);
+  const T cy_ = -(w * T(p.hy) / h);
+  for (int s = 0; s < nsub; ++s) {
+    const T xa = X0 + dX * (T(s) / T(nsub));
+    const T xb = X0 + dX * (T(s + 1) / T(nsub));
+    const T bx = floor(fmin(xa, xb));
+    T S0x[3], S1x[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      S0x[a] = fmax(T(0), T(1) - fabs(xa - (bx + T(a))));
+      S1x[a] = fmax(T(0), T(1) - fabs(xb - (bx + T(a))));
+    }
+    const int gx = ix + (int)bx;
+    if (p.ny == 1) {
+      T cum = T(0);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        cum = cum + (S1x[a] - S0x[a]);
+        jadd(cl, p, J, 0, 0, gx + a, cx_ * cum, me);
+      }
+      const T dyv = dyo / T(nsub);
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        jadd(cl, p, J, 1, 0, gx + a, w * (dyv / h) * T(0.5) * (S0x[a] + S1x[a]), me);
+      continue;
+    }
+    const T ya = Y0 + dY * (T(s) / T(nsub));
+    const T yb = Y0 + dY * (T(s + 1) / T(nsub));
+    const T by = floor(fmin(ya, yb));
+    T S0y[3], S1y[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      S0y[b] = fmax(T(0), T(1) - fabs(ya - (by + T(b))));
+      S1y[b] = fmax(T(0), T(1) - fabs(yb - (by + T(b))));
+    }
+    const int gy = iy + (int)by;
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      T cum = T(0);
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        cum = cum + (S1x[a] - S0x[a]) * T(0.5) * (S0y[b] + S1y[b]);
+        jadd(cl, p, J, 0, gy + b, gx + a, cx_ * cum, me);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      T cum = T(0);
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        cum = cum + (S1y[b] - S0y[b]) * T(0.5) * (S0x[a] + S1x[a]);
+        jadd(cl, p, J, 1, gy + b, gx + a, cy_ * cum, me);
+      }
+    }
+  }
+}
+
+// CIC deposit of value v at (X, Y) relative to node (ix, iy)
+template <typename T>
+__device__ __forceinline__ void cic_add(const cg::cluster_group& cl, const Params& p, T* J,
+                                        int comp, int ix, int iy, T X, T Y, T v, int me) {
+  const T i0 = floor(X);
+  const T fx = X - i0;
+  const int gx = ix + (int)i0;
+  if (p.ny == 1) {
+    jadd(cl, p, J, comp, 0, gx, (T(1) - fx) * v, me);
+    jadd(cl, p, J, comp, 0, gx + 1, fx * v, me);
+    return;
+  }
+  const T j0 = floor(Y);
+  const T fy = Y - j0;
+  const int gy = iy + (int)j0;
+  jadd(cl, p, J, comp, gy, gx, ((T(1) - fx) * (T(1) - fy)) * v, me);
+  jadd(cl, p, J, comp, gy, gx + 1, (fx * (T(1) - fy)) * v, me);
+  jadd(cl, p, J, comp, gy + 1, gx, ((T(1) - fx) * fy) * v, me);
+  jadd(cl, p, J, comp, gy + 1, gx + 1, (fx * fy) * v, me);
+}
+
+// ------------------------------------------------------------------------------------------
+// One streaming push from the plane above to plane n (zeta distance d): gather at the
+// particle, budget rule (Eq. trap2), two-pass Boris, deposit.  Returns true if trapped; on
+// return the particle state holds the new values (cell-relative position at plane n, or at
+// zeta_n + (d - hc) when trapped, reported through fz_trap).
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct PState {
+  int ix, iy, sp;
+  T fx, fy;
+  V3<T> u;
+  T sig, q;
+};
+
+template <typename T>
+__device__ bool stream_push(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
+                            T* Fcur, PState<T>& P, T d, int me, T& fz_trap, double* acc) {
+  T E[6];
+  gather6(cl, p, Fcur, P.ix, P.fx, P.iy, P.fy, me, E);
+  const T D = T(p.delta);
+  const T h = T(p.h);
+  const T qm = T(p.qm[P.sp]);
+  V3<T> u = P.u;
+  const T g0 = gamma_of(u);
+  const T gmu0 = gamma_minus_uz(u, g0);
+  T hlim = u.z > T(0) ? (D - P.sig) * gmu0 / u.z : T(INFINITY);
+  hlim = fmax(hlim, T(0));
+  const bool trap = hlim < d;
+  const T hc = trap ? hlim : d;
+  // two passes: the lab time of the step is evaluated at the step's mean momentum
+  const T dt1 = hc * g0 / gmu0;
+  const V3<T> us = boris(u, E, E + 3, qm, dt1);
+  const V3<T> ub{T(0.5) * (u.x + us.x), T(0.5) * (u.y + us.y), T(0.5) * (u.z + us.z)};
+  const T gb = gamma_of(ub);
+  const T dt2 = hc * gb / gamma_minus_uz(ub, gb);
+  const V3<T> un = boris(u, E, E + 3, qm, dt2);
+  const T gn = gamma_of(un);
+  const T den = gamma_minus_uz(un, gn);
+  const T dx = hc * un.x / den, dy = hc * un.y / den, ds = hc * un.z / den;
+  // deposit: w = Q/(hx hy Delta) is the particle's (rho - j_z) density weight (Sec. 4.1)
+  const T w = P.q / (T(p.hx) * T(p.hy) * D);
+  const T X1 = P.fx + dx / T(p.hx);
+  const T Y1 = p.ny > 1 ? P.fy + dy / T(p.hy) : P.fy;
+  esirkepov(cl, p, s.J, P.ix, P.iy, P.fx, P.fy, X1, Y1, w, dy, me);
+  cic_add(cl, p, s.J, 2, P.ix, P.iy, X1, Y1, w * ds / h, me);
+  // diagnostics: kinetic energy N m (gamma-1) dt/Delta, (rho - j_z) flux through plane n
+  const T dtl = hc * gn / den;
+  acc[DG_KIN] += (double)(P.q * T(p.m_over_q[P.sp]) * (gn - T(1)) * dtl / D);
+  if (!trap) acc[DG_FLUX] += (double)(w * T(p.hx) * T(p.hy) * h);
+  acc[DG_PUSH] += 1.0;
+  // new cell-relative position
+  const T fX = floor(X1);
+  P.ix = imod(P.ix + (int)fX, p.nx);
+  P.fx = X1 - fX;
+  if (p.ny > 1) {
+    const T fY = floor(Y1);
+    P.iy = imod(P.iy + (int)fY, p.ny);
+    P.fy = Y1 - fY;
+  }
+  P.u = un;
+  P.sig = P.sig + ds;
+  fz_trap = (d - hc) / h;
+  return trap;
+}
+
+// write a particle into a stored store (ring slot, bucket); false on overflow
+template <typename T>
+__device__ bool store_append(const PartStore& S, const Params& p, int slot, int bucket,
+                             const PState<T>& P, T fz) {
+  int* cnt = S.cnt + (size_t)slot * p.nz + bucket;
+  const int i = atomicAdd(cnt, 1);
+  if (i >= p.bcap) return false;
+  const size_t e = ((size_t)slot * p.nz + bucket) * p.bcap + i;
+  S.cell[e] = P.ix | (P.iy << 10) | (P.sp << 20);
+  ((T*)S.fx)[e] = P.fx;
+  ((T*)S.fy)[e] = P.fy;
+  ((T*)S.fz)[e] = fz;
+  ((T*)S.ux)[e] = P.u.x;
+  ((T*)S.uy)[e] = P.u.y;
+  ((T*)S.uz)[e] = P.u.z;
+  ((T*)S.q)[e] = P.q;
+  return true;
+}
+
+template <typename T>
+__device__ PState<T> store_read(const PartStore& S, const Params& p, size_t e, T& fz) {
+  PState<T> P;
+  const int c = ldcg(S.cell + e);
+  P.ix = c & 1023;
+  P.iy = (c >> 10) & 1023;
+  P.sp = (c >> 20) & 3;
+  P.fx = ldcg((const T*)S.fx + e);
+  P.fy = ldcg((const T*)S.fy + e);
+  fz = ldcg((const T*)S.fz + e);
+  P.u = V3<T>{ldcg((const T*)S.ux + e), ldcg((const T*)S.uy + e), ldcg((const T*)S.uz + e)};
+  P.q = ldcg((const T*)S.q + e);
+  P.sig = T(0);
+  return P;
+}
+
+// ------------------------------------------------------------------------------------------
+// Stored particle along s (Sec. 4.1: trapped / beam particles are integrated along s):
+// bucket n of level k+1, fields of slices n (Fn) and n+1 (Fn1) of that level.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ void stored_phase(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
+                             T* Fn, T* Fn1, long long k, int n, int me, double* acc) {
+  const int s1 = (int)(((k + 1) % p.ring + p.ring) % p.ring);
+  const int s2 = (int)(((k + 2) % p.ring + p.ring) % p.ring);
+  const int cnt = min(ldcg(p.st.cnt + (size_t)s1 * p.nz + n), p.bcap);
+  const T D = T(p.delta), h = T(p.h);
+  for (int e0 = me * blockDim.x + threadIdx.x; e0 < cnt; e0 += p.C * blockDim.x) {
+    T fz;
+    PState<T> P = store_read<T>(p.st, p, ((size_t)s1 * p.nz + n) * p.bcap + e0, fz);
+    const T g = gamma_of(P.u);
+    acc[DG_KIN] += (double)(P.q * T(p.m_over_q[P.sp]) * (g - T(1)));
+    acc[DG_STORED] += 1.0;
+    const T gmu = gamma_minus_uz(P.u, g);
+    const bool spush = (P.u.z > T(0)) && (D * gmu < h * fmax(P.u.z, T(0)));
+    if (!spush) {
+      // moves more than one cell per s-step: rejoins the next zeta march at this slice
+      if (!store_append(p.rq, p, s2, n, P, fz)) atomicOr(p.err, ERR_QCAP);
+      continue;
+    }
+    T lo[6], hi[6], E[6];
+    gather6(cl, p, Fn, P.ix, P.fx, P.iy, P.fy, me, lo);
+    gather6(cl, p, Fn1, P.ix, P.fx, P.iy, P.fy, me, hi);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) E[c] = (T(1) - fz) * lo[c] + fz * hi[c];
+    const T dt = D * g / P.u.z;
+    const V3<T> un = boris(P.u, E, E + 3, T(p.qm[P.sp]), dt);
+    const T gn = gamma_of(un);
+    P.u = un;
+    int m = n;
+    if (un.z > T(0)) {
+      const T X = P.fx + D * un.x / un.z / T(p.hx);
+      const T fX = floor(X);
+      P.ix = imod(P.ix + (int)fX, p.nx);
+      P.fx = X - fX;
+      if (p.ny > 1) {
+        const T Y = P.fy + D * un.y / un.z / T(p.hy);
+        const T fY = floor(Y);
+        P.iy = imod(P.iy + (int)fY, p.ny);
+        P.fy = Y - fY;
+      }
+      const T Z = fz - D * gamma_minus_uz(un, gn) / un.z / h;
+      const T cZ = ceil(Z) - T(1);
+      m = n + (int)cZ;
+      fz = Z - cZ;
+      if (m < 0) {                              // left the box at the back
+        acc[DG_LOST] += 1.0;
+        continue;
+      }
+      // beam current of the next level j = Q u/(gamma hx hy h), CIC across, linear in zeta
+      const T amp = P.q / (T(p.hx) * T(p.hy) * h * gn);
+      const T tz = fz - T(0.5);
+      const T ftz = floor(tz);
+      const int i0 = m + (int)ftz;
+      const T f = tz - ftz;
+      T* jb = (T*)p.jbeam;
+      for (int t = 0; t < 2; ++t) {
+        const int iz = i0 + t;
+        if (iz < 0 || iz >= p.nz) continue;
+        const T a = amp * (t == 0 ? T(1) - f : f);
+        T* base = jb + (((size_t)s2 * p.nz + iz) * 3) * (size_t)p.nx * p.ny;
+        const T vals[3] = {a * un.x, a * un.y, a * un.z};
+        for (int c = 0; c < 3; ++c) {
+          const T sx = (c == 0) ? T(-0.5) : T(0);
+          const T sy = (c == 1 && p.ny > 1) ? T(-0.5) : T(0);
+          const T X = P.fx + sx, Y = P.fy + sy;
+          const T i0f = floor(X), fx = X - i0f;
+          const int gx = P.ix + (int)i0f;
+          T* pl = base + (size_t)c * p.nx * p.ny;
+          if (p.ny == 1) {
+            atomicAdd(pl + imod(gx, p.nx), (T(1) - fx) * vals[c]);
+            atomicAdd(pl + imod(gx + 1, p.nx), fx * vals[c]);
+          } else {
+            const T j0f = floor(Y), fy = Y - j0f;
+            const int gy = P.iy + (int)j0f;
+            atomicAdd(pl + (size_t)imod(gy, p.ny) * p.nx + imod(gx, p.nx),
+                      ((T(1) - fx) * (T(1) - fy)) * vals[c]);
+            atomicAdd(pl + (size_t)imod(gy, p.ny) * p.nx + imod(gx + 1, p.nx),
+                      (fx * (T(1) - fy)) * vals[c]);
+            atomicAdd(pl + (size_t)imod(gy + 1, p.ny) * p.nx + imod(gx, p.nx),
+                      ((T(1) - fx) * fy) * vals[c]);
+            atomicAdd(pl + (size_t)imod(gy + 1, p.ny) * p.nx + imod(gx + 1, p.nx),
+                      (fx * fy) * vals[c]);
+          }
+        }
+        atomicExch(p.jflag + (size_t)s2 * p.nz + iz, 1);
+      }
+    }
+    if (!store_append(p.st, p, s2, m, P, fz)) atomicOr(p.err, ERR_BCAP);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// App. B closed form of the slice system (Eqs. RxN..eqall, LyN read with B_z0^1 + B_z1^1,
+// eqall with +i k_y, T4 = -2 h Delta E_z0^0 K^2) for one mode.
+// ------------------------------------------------------------------------------------------
+template <typename T>
+struct Mode6 {
+  Cx<T> Rx, Ry, Lx, Ly, Ez, Bz;
+};
+
+template <typename T>
+__device__ __forceinline__ Mode6<T> slice_solve(T kx, T ky, T h, T Dl, const Mode6<T>& n1,
+                                                Cx<T> Rxo, Cx<T> Ryo, Cx<T> Ezo, Cx<T> Bzo,
+                                                Cx<T> jx0m, Cx<T> jy0m, Cx<T> jx0p, Cx<T> jy0p,
+                                                Cx<T> jx1p, Cx<T> jy1p, Cx<T> jz1p) {
+  const T K2 = kx * kx + ky * ky;
+  const T Dd = T(16) + h * (T(2) * Dl + h) * K2;
+  // predictor j^1_{-1/2} := j^1_{+1/2}
+  const Cx<T> Jx = (jx0m + jx0p) + T(2) * jx1p;
+  const Cx<T> Jy = (jy0m + jy0p) + T(2) * jy1p;
+  const Cx<T> Wx = (n1.Rx + Rxo) - T(2) * n1.Lx;
+  const Cx<T> Wy = (n1.Ry + Ryo) - T(2) * n1.Ly;
+  const Cx<T> Ux = (n1.Rx + Rxo) + T(2) * n1.Lx;
+  const Cx<T> Uy = (n1.Ry + Ryo) + T(2) * n1.Ly;
+  const T c16 = T(16) - h * h * K2;
+  const T hD = h * Dl;
+  Cx<T> numE = c16 * n1.Ez - (T(16) * h) * jz1p;
+  numE = numE - mul_i(hD * (kx * Jx + ky * Jy));
+  numE = numE - (T(2) * hD * K2) * Ezo;
+  numE = numE + mul_i((T(2) * h * h) * (kx * jx1p + ky * jy1p));
+  numE = numE + mul_i((T(4) * h) * (kx * Wx + ky * Wy));
+  Cx<T> numB = c16 * n1.Bz + mul_i((T(2) * h * h) * (kx * jy1p - ky * jx1p));
+  numB = numB + mul_i(hD * (kx * Jy - ky * Jx));
+  numB = numB - (T(2) * hD * K2) * Bzo;
+  numB = numB + mul_i((T(4) * h) * (ky * Ux - kx * Uy));
+  const T invD = T(1) / Dd;
+  Mode6<T> o;
+  o.Ez = invD * numE;
+  o.Bz = invD * numB;
+  // RxN, RyN (trapezoid in s)
+  const Cx<T> sEz = o.Ez + Ezo, sBz = o.Bz + Bzo;
+  o.Rx = Rxo + Dl * (mul_i(T(0.5) * (kx * sEz + ky * sBz)) - T(0.25) * Jx);
+  o.Ry = Ryo + Dl * (mul_i(T(0.5) * (ky * sEz - kx * sBz)) - T(0.25) * Jy);
+  // LxN, LyN (box scheme in zeta)
+  const Cx<T> tEz = n1.Ez + o.Ez, tBz = o.Bz + n1.Bz;
+  o.Lx = n1.Lx - (T(0.5) * h) * (mul_i(T(0.5) * (kx * tEz - ky * tBz)) + jx1p);
+  o.Ly = n1.Ly - (T(0.5) * h) * (mul_i(T(0.5) * (ky * tEz + kx * tBz)) + jy1p);
+  return o;
+}
+
+// ------------------------------------------------------------------------------------------
+// progress / waits between concurrently marching clusters
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long prog_value(long long k, int nz, int completed) {
+  return (unsigned long long)(k + 2) * (unsigned long long)(nz + 1) + (unsigned long long)completed;
+}
+
+__device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
+  int spins = 0;
+  while (ld_acquire_u64(p.progress + pcid) < target) {
+    if (atomicAdd(p.err, 0) & ERR_TIMEOUT) return;
+    __nanosleep(200);
+    if (++spins > p.wait_spin_limit) {
+      atomicOr(p.err, ERR_TIMEOUT);
+      return;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// the march of one s-step k (computes level k+1)
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& cl, long long k,
+                      int cid) {
+  const int me = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  const int NT = blockDim.x;
+  const bool waits = p.P > 1 && k > p.k0;
+  const int pcid = (cid + p.P - 1) % p.P;
+  const int nz = p.nz;
+  const int nxh = p.nx / 2;
+  const int s1 = (int)(((k + 1) % p.ring + p.ring) % p.ring);
+  const int s2 = (int)(((k + 2) % p.ring + p.ring) % p.ring);
+  const T h = T(p.h), Dl = T(p.delta_field);
+  const long long sl = k - p.k0;                    // step index within this launch
+
+  double acc[kNDiag];
+#pragma unroll
+  for (int i = 0; i < kNDiag; ++i) acc[i] = 0.0;
+  double fe = 0.0;
+
+  // reset the next level's stored buckets and rejoin queues (free: their last reader, the
+  // march of step k+1-ring, has completed)
+  for (int b = me * NT + tid; b < nz; b += p.C * NT) {
+    p.st.cnt[(size_t)s2 * nz + b] = 0;
+    p.rq.cnt[(size_t)s2 * nz + b] = 0;
+  }
+  // fresh particles at the front ghost plane (Sec. 4.1: Q_f = q n hx hy Delta / ppc)
+  if (tid == 0) s.misc[0] = 0;
+  __syncthreads();
+  if (p.inject) {
+    const int per_row = p.nlayer / p.ny;          // particles per transverse row
+    const int nmine = per_row * p.RB;
+    for (int i = tid; i < nmine; i += NT) {
+      // particle order within a row: species-major, then cell, then k (matches the layer index)
+      const int yl = i / per_row;
+      int r = i - yl * per_row;
+      int sp = 0;
+      while (sp + 1 < p.nspecies && r >= p.ppc[sp] * p.nx) {
+        r -= p.ppc[sp] * p.nx;
+        ++sp;
+      }
+      const int ix = r / p.ppc[sp], kk = r - ix * p.ppc[sp];
+      const int iy = me * p.RB + yl;
+      const int cell = iy * p.nx + ix;
+      const unsigned long long g =
+          (unsigned long long)(p.poff[sp] + cell * p.ppc[sp] + kk);
+      const unsigned long long c =
+          ((unsigned long long)k * (unsigned long long)p.nlayer + g) * 2ull;
+      s.pcell[i] = ix | (iy << 10) | (sp << 20);
+      s.pfx[i] = T(uniform24(p.seed, c));
+      s.pfy[i] = p.ny > 1 ? T(uniform24(p.seed, c + 1)) : T(0);
+      s.pux[i] = T(0);
+      s.puy[i] = T(0);
+      s.puz[i] = T(0);
+      s.psig[i] = T(0);
+      s.pq[i] = T(p.Qf[sp]);
+    }
+    if (tid == 0) s.misc[0] = nmine;
+  }
+  // ghost slice: field-free
+  T* Fcur = s.F[0];
+  T* Fnew = s.F[1];
+  for (int i = tid; i < 6 * p.RB * p.nx; i += NT) Fcur[i] = T(0);
+  for (int i = tid; i < 3 * p.RB * p.nx; i += NT) s.J[i] = T(0);
+
+  // per-mode carried state (one mode per thread)
+  const int m = tid;
+  const bool has_mode = m < p.M;
+  const int kxl = has_mode ? m / p.ny : 0, kyi = has_mode ? m % p.ny : 0;
+  const T kx = has_mode ? s.kx[me * p.KB + kxl] : T(0);
+  const T ky = has_mode ? s.ky[kyi] : T(0);
+  const bool masked = p.ny > 1 && kyi == p.ny / 2;
+  Mode6<T> S1;
+  S1.Rx = S1.Ry = S1.Lx = S1.Ly = S1.Ez = S1.Bz = cx<T>(T(0), T(0));
+  Cx<T> jpx = cx<T>(T(0), T(0)), jpy = jpx;       // j^1 at n + 3/2 (predictor of the last solve)
+  Cx<T> o[6];                                     // old level, block n
+  Cx<T> j0px, j0py;                               // old level j at n + 1/2
+  const Cx<T>* st = (const Cx<T>*)p.state;
+  Cx<T>* stw = (Cx<T>*)p.state;
+  auto blk = [&](int b, int c) -> size_t {
+    return (((size_t)b * p.C + me) * 6 + c) * (size_t)p.M + m;
+  };
+
+  if (waits && tid == 0 && me == 0)
+    wait_for(p, pcid, prog_value(k - 1, nz, min(nz, 3)));   // predecessor done down to nz-3
+  cl.sync();
+  if (has_mode) {
+    j0px = ldcg(st + blk(nz, 4));
+    j0py = ldcg(st + blk(nz, 5));
+#pragma unroll
+    for (int c = 0; c < 6; ++c) o[c] = ldcg(st + blk(nz - 1, c));
+  }
+
+  for (int n = nz - 1; n >= 0; --n) {
+    // ---------------- A: streaming push from plane n+1 to plane n -----------------------
+    {
+      const int cnt0 = s.misc[0];
+      for (int i = tid; i < cnt0; i += NT) {
+        const int cw = s.pcell[i];
+        if (cw < 0) continue;
+        PState<T> P;
+        P.ix = cw & 1023;
+        P.iy = (cw >> 10) & 1023;
+        P.sp = (cw >> 20) & 3;
+        P.fx = s.pfx[i];
+        P.fy = s.pfy[i];
+        P.u = V3<T>{s.pux[i], s.puy[i], s.puz[i]};
+        P.sig = s.psig[i];
+        P.q = s.pq[i];
+        T fzt;
+        const bool trap = stream_push(cl, p, s, Fcur, P, h, me, fzt, acc);
+        if (trap) {
+          s.pcell[i] = -1;
+          acc[DG_TRAP] += 1.0;
+          if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
+        } else {
+          s.pcell[i] = P.ix | (P.iy << 10) | (P.sp << 20);
+          s.pfx[i] = P.fx;
+          s.pfy[i] = P.fy;
+          s.pux[i] = P.u.x;
+          s.puy[i] = P.u.y;
+          s.puz[i] = P.u.z;
+          s.psig[i] = P.sig;
+        }
+      }
+      // stored particles that rejoin the march at this slice: partial first step
+      const int nq = min(ldcg(p.rq.cnt + (size_t)s1 * nz + n), p.bcap);
+      for (int e = me + p.C * tid; e < nq; e += p.C * NT) {
+        T fz;
+        PState<T> P = store_read<T>(p.rq, p, ((size_t)s1 * nz + n) * p.bcap + e, fz);
+        acc[DG_REJOIN] += 1.0;
+        T fzt;
+        const bool trap = stream_push(cl, p, s, Fcur, P, fz * h, me, fzt, acc);
+        if (trap) {
+          acc[DG_TRAP] += 1.0;
+          if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
+        } else {
+          const int slot = atomicAdd(s.misc, 1);
+          if (slot < p.pcap) {
+            s.pcell[slot] = P.ix | (P.iy << 10) | (P.sp << 20);
+            s.pfx[slot] = P.fx;
+            s.pfy[slot] = P.fy;
+            s.pux[slot] = P.u.x;
+            s.puy[slot] = P.u.y;
+            s.puz[slot] = P.u.z;
+            s.psig[slot] = P.sig;
+            s.pq[slot] = P.q;
+          } else {
+            atomicOr(p.err, ERR_PCAP);
+          }
+        }
+      }
+    }
+    // publish: iteration n+1 complete (its stored phase and this push have been issued)
+    __syncthreads();
+    if (tid == 0) {
+      if (s.misc[0] > p.pcap) s.misc[0] = p.pcap;
+      __threadfence();
+    }
+    cl.sync();                                                      // B1: deposits done
+    if (p.P > 1 && me == 0 && tid == 0 && n + 1 <= nz - 1)
+      st_release_u64(p.progress + cid, prog_value(k, nz, nz - (n + 1)));
+    // beam current of this level at the half-slice n + 1/2 (own rows)
+    {
+      const int* fl = p.jflag + (size_t)s1 * nz + n;
+      if (ldcg(fl)) {
+        T* jb = (T*)p.jbeam + (((size_t)s1 * nz + n) * 3) * (size_t)p.nx * p.ny;
+        for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
+          const int c = i / (p.RB * p.nx);
+          const int rem = i - c * p.RB * p.nx;
+          const size_t g = (size_t)c * p.nx * p.ny + (size_t)me * p.RB * p.nx + rem;
+          s.J[i] += ldcg(jb + g);
+          jb[g] = T(0);
+        }
+      }
+    }
+    // (the flag is cleared by CTA 0 after B2, once every CTA has read it)
+    if (p.snapshot && k == p.k0 + p.nsteps - 1) {
+      T* sn = (T*)p.snap;
+      for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
+        const int c = i / (p.RB * p.nx);
+        const int rem = i - c * p.RB * p.nx;
+        sn[(((size_t)(6 + c) * nz + n) * p.ny + me * p.RB) * p.nx + rem] = s.J[i];
+      }
+    }
+    __syncthreads();
+    // ---------------- B: row FFTs of the currents, transposed to the kx owners ------------
+    forward_rows(cl, p, s, me, true);
+    cl.sync();                                                      // B2
+    if (tid == 0 && me == 0) p.jflag[(size_t)s1 * nz + n] = 0;
+    // ---------------- C: column FFTs, per-mode solve, inverse column FFTs ------------------
+    for (int i = tid; i < 3 * p.RB * p.nx; i += NT) s.J[i] = T(0);
+    column_ffts(p, s, 0, 3, false);
+    __syncthreads();
+    if (has_mode) {
+      Cx<T> Jx = s.SC[((size_t)0 * p.KB + kxl) * p.ny + kyi];
+      Cx<T> Jy = s.SC[((size_t)1 * p.KB + kxl) * p.ny + kyi];
+      Cx<T> Jz = s.SC[((size_t)2 * p.KB + kxl) * p.ny + kyi];
+      if (p.ny > 1) Jy = Jy * s.shy[kyi];
+      if (masked) Jx = Jy = Jz = cx<T>(T(0), T(0));
+      // corrector: R at slice n+1 was built with j_{n+1/2} := j_{n+3/2}
+      if (n + 1 < nz) {
+        S1.Rx = S1.Rx - (T(0.25) * Dl) * (Jx - jpx);
+        S1.Ry = S1.Ry - (T(0.25) * Dl) * (Jy - jpy);
+      }
+      // new level, block n+1 = {R, E_z, B_z at slice n+1; j at n+1/2}
+      stw[blk(n + 1, 0)] = S1.Rx;
+      stw[blk(n + 1, 1)] = S1.Ry;
+      stw[blk(n + 1, 2)] = S1.Ez;
+      stw[blk(n + 1, 3)] = S1.Bz;
+      stw[blk(n + 1, 4)] = Jx;
+      stw[blk(n + 1, 5)] = Jy;
+      // old level at slice n; j^0 at n -/+ 1/2
+      const Cx<T> j0mx = n > 0 ? o[4] : j0px;
+      const Cx<T> j0my = n > 0 ? o[5] : j0py;
+      Mode6<T> S0;
+      if (masked) {
+        S0.Rx = S0.Ry = S0.Lx = S0.Ly = S0.Ez = S0.Bz = cx<T>(T(0), T(0));
+      } else {
+        S0 = slice_solve(kx, ky, h, Dl, S1, o[0], o[1], o[2], o[3], j0mx, j0my, j0px, j0py, Jx,
+                         Jy, Jz);
+      }
+      // fields E, B (Eqs. Rx..Ly) for the inverse transform
+      Cx<T>* sc = s.SC + (size_t)kxl * p.ny + kyi;
+      const size_t cs = (size_t)p.KB * p.ny;
+      sc[0 * cs] = T(0.5) * (S0.Rx + S0.Lx);
+      sc[1 * cs] = T(0.5) * (S0.Ry + S0.Ly);
+      sc[2 * cs] = S0.Ez;
+      sc[3 * cs] = T(0.5) * (S0.Ly - S0.Ry);
+      sc[4 * cs] = T(0.5) * (S0.Rx - S0.Lx);
+      sc[5 * cs] = S0.Bz;
+      S1 = S0;
+      jpx = Jx;
+      jpy = Jy;
+      j0px = j0mx;
+      j0py = j0my;
+      if (n == 0) {
+        stw[blk(0, 0)] = S0.Rx;
+        stw[blk(0, 1)] = S0.Ry;
+        stw[blk(0, 2)] = S0.Ez;
+        stw[blk(0, 3)] = S0.Bz;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 6; ++c) o[c] = ldcg(st + blk(n - 1, c));
+      }
+    }
+    __syncthreads();
+    column_ffts(p, s, 0, 6, true);
+    __syncthreads();
+    scatter_to_rows(cl, p, s, me);
+    if (waits && tid == 0 && me == 0)
+      wait_for(p, pcid, prog_value(k - 1, nz, min(nz, nz - n + 3)));   // down to n-3
+    cl.sync();                                                      // B3
+    // ---------------- D: inverse rows -> real-space fields of slice n ----------------------
+    inverse_rows(p, s, Fnew, fe);
+    cl.sync();                                                      // B4: fields of slice n
+    if (p.diag) {
+      const int yc = p.ny / 2;
+      if (tid == 0 && yc / p.RB == me)
+        p.onaxis[sl * nz + n] = (double)Fnew[((size_t)2 * p.RB + (yc - me * p.RB)) * p.nx + nxh];
+    }
+    if (p.snapshot && k == p.k0 + p.nsteps - 1) {
+      T* sn = (T*)p.snap;
+      for (int i = tid; i < 6 * p.RB * p.nx; i += NT) {
+        const int c = i / (p.RB * p.nx);
+        const int rem = i - c * p.RB * p.nx;
+        sn[(((size_t)c * nz + n) * p.ny + me * p.RB) * p.nx + rem] = Fnew[i];
+      }
+    }
+    // ---------------- E: stored particles of cell (zeta_n, zeta_{n+1}] along s -------------
+    stored_phase(cl, p, s, Fnew, Fcur, k, n, me, acc);
+    T* t = Fcur;
+    Fcur = Fnew;
+    Fnew = t;
+  }
+  // publish completion of the march
+  __syncthreads();
+  if (tid == 0) __threadfence();
+  cl.sync();
+  if (p.P > 1 && me == 0 && tid == 0) st_release_u64(p.progress + cid, prog_value(k, nz, nz));
+
+  // diagnostics: per-CTA FP64 partials
+  if (p.diag) {
+    acc[DG_FIELD] = fe;
+    for (int i = 0; i < kNDiag; ++i) {
+      double v = acc[i];
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if ((tid & 31) == 0) atomicAdd(s.dacc + i, v);
+    }
+    __syncthreads();
+    if (tid < kNDiag) {
+      const double hv = tid == DG_FIELD ? 0.5 * p.hx * p.hy * p.h : 1.0;
+      p.diag_out[((size_t)sl * kNDiag + tid) * p.C + me] = s.dacc[tid] * hv;
+      s.dacc[tid] = 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512, 1) march_kernel(const Params p) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const Sm<T> s = carve<T>(p, smem);
+  load_tables(p, s);
+  if (threadIdx.x < kNDiag) s.dacc[threadIdx.x] = 0.0;
+  __syncthreads();
+  const int cid = (int)(blockIdx.x / p.C);
+  for (long long k = p.k0 + cid; k < p.k0 + p.nsteps; k += p.P) march<T>(p, s, cl, k, cid);
+}
+
+// ------------------------------------------------------------------------------------------
+// laser initial condition (Eq. E_laser): R = 2E (forward wave) on every slice, spectral
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(512, 1)
+    laser_kernel(const Params p, double a0, double waist, double dur, double zc, int pol) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cg::cluster_group cl = cg::this_cluster();
+  const Sm<T> s = carve<T>(p, smem);
+  load_tables(p, s);
+  __syncthreads();
+  const int me = (int)cl.block_rank();
+  const int cid = (int)(blockIdx.x / p.C);
+  const int ncl = (int)(gridDim.x / p.C);
+  Cx<T>* stw = (Cx<T>*)p.state;
+  const double xc = 0.5 * p.nx * p.hx, yc = 0.5 * p.ny * p.hy;
+  for (int n = cid; n < p.nz; n += ncl) {
+    const double phi = n * p.h - zc;
+    const double env = a0 * cos(phi) * exp(-phi * phi / (dur * dur));
+    for (int i = threadIdx.x; i < 3 * p.RB * p.nx; i += blockDim.x) {
+      const int c = i / (p.RB * p.nx);
+      const int rem = i - c * p.RB * p.nx;
+      const int yl = rem / p.nx, x = rem - yl * p.nx;
+      const double dx = x * p.hx - xc;
+      const double dy = p.ny > 1 ? (me * p.RB + yl) * p.hy - yc : 0.0;
+      const double E = env * exp(-(dy * dy + dx * dx) / (waist * waist));
+      s.J[i] = (c == 2) ? T(2.0 * E) : T(0);
+    }
+    __syncthreads();
+    forward_rows(cl, p, s, me, false);
+    cl.sync();
+    column_ffts(p, s, 2, 3, false);
+    __syncthreads();
+    for (int m = threadIdx.x; m < p.M; m += blockDim.x) {
+      const int kxl = m / p.ny, kyi = m % p.ny;
+      Cx<T> v = s.SC[((size_t)2 * p.KB + kxl) * p.ny + kyi];
+      if (p.ny > 1 && kyi == p.ny / 2) v = cx<T>(T(0), T(0));
+      const Cx<T> z = cx<T>(T(0), T(0));
+      for (int c = 0; c < 6; ++c)
+        stw[(((size_t)n * p.C + me) * 6 + c) * p.M + m] = (c == pol) ? v : z;
+    }
+    cl.sync();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// layout conversion of the spectral state: blocks [nz+1][C][6][M] <-> [6][nz][ny][nx/2]
+// ------------------------------------------------------------------------------------------
+template <typename T>
+__global__ void export_kernel(const Params p, Cx<T>* dst, const Cx<T>* src, int dir) {
+  const size_t nxh = p.nx / 2;
+  const size_t total = (size_t)6 * p.nz * p.ny * nxh;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int kx = (int)(i % nxh);
+    const int ky = (int)((i / nxh) % p.ny);
+    const int n = (int)((i / (nxh * p.ny)) % p.nz);
+    const int c = (int)(i / (nxh * p.ny * p.nz));
+    const int b = c >= 4 ? n + 1 : n;
+    const int r = kx / p.KB, kxl = kx % p.KB;
+    const size_t e = (((size_t)b * p.C + r) * 6 + c) * p.M + (size_t)kxl * p.ny + ky;
+    if (dir == 0)
+      dst[i] = src[e];
+    else
+      dst[e] = src[i];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host-side launchers
+// ------------------------------------------------------------------------------------------
+static int align16(int v) { return (v + 15) / 16 * 16; }
+
+int smem_layout(Params& p, int eb) {
+  const int nxh = p.nx / 2;
+  const int nyh = p.ny > 1 ? p.ny / 2 : 1;
+  int o = 0;
+  p.o_f0 = o;
+  o += align16(6 * p.RB * p.nx * eb);
+  p.o_f1 = o;
+  o += align16(6 * p.RB * p.nx * eb);
+  p.o_j = o;
+  o += align16(3 * p.RB * p.nx * eb);
+  p.o_sr = o;
+  o += align16(6 * p.RB * nxh * 2 * eb);
+  p.o_sc = o;
+  o += align16(6 * p.KB * p.ny * 2 * eb);
+  p.o_work = o;
+  o += align16(p.nwork * p.nx * 2 * eb);
+  p.o_tw = o;
+  o += align16((nxh + nyh + nxh + p.ny) * 2 * eb + (nxh + p.ny) * eb);
+  p.o_part = o;
+  o += align16(p.pcap * 4) + 7 * align16(p.pcap * eb) + 16 * 7;
+  p.o_misc = o;
+  o += 16 + kNDiag * 8;
+  p.smem_bytes = align16(o);
+  return p.smem_bytes;
+}
+
+template <typename T>
+static cudaError_t cfg_one(int smem) {
+  cudaError_t e = cudaFuncSetAttribute(march_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(march_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(laser_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(laser_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+cudaError_t configure_kernels(int precision, int smem, int) {
+  return precision == 64 ? cfg_one<double>(smem) : cfg_one<float>(smem);
+}
+
+static cudaLaunchConfig_t make_cfg(const Params& p, int nclusters, cudaStream_t s,
+                                   cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t c = {};
+  c.gridDim = dim3((unsigned)(nclusters * p.C), 1, 1);
+  c.blockDim = dim3((unsigned)p.nthreads, 1, 1);
+  c.dynamicSmemBytes = (size_t)p.smem_bytes;
+  c.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)p.C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  c.attrs = attr;
+  c.numAttrs = 1;
+  return c;
+}
+
+cudaError_t launch_march(int precision, const Params& p, cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t c = make_cfg(p, p.P, s, attr);
+  if (precision == 64) return cudaLaunchKernelEx(&c, march_kernel<double>, p);
+  return cudaLaunchKernelEx(&c, march_kernel<float>, p);
+}
+
+cudaError_t launch_laser_init(int precision, const Params& p, double a0, double waist, double dur,
+                              double zc, int pol, cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  int ncl = 1;
+  max_active_clusters(precision, p, &ncl);
+  if (ncl < 1) ncl = 1;
+  if (ncl > p.nz) ncl = p.nz;
+  cudaLaunchConfig_t c = make_cfg(p, ncl, s, attr);
+  if (precision == 64) return cudaLaunchKernelEx(&c, laser_kernel<double>, p, a0, waist, dur, zc, pol);
+  return cudaLaunchKernelEx(&c, laser_kernel<float>, p, a0, waist, dur, zc, pol);
+}
+
+cudaError_t launch_export_state(int precision, const Params& p, void* dst, cudaStream_t s) {
+  if (precision == 64)
+    export_kernel<double><<<264, 256, 0, s>>>(p, (Cx<double>*)dst, (const Cx<double>*)p.state, 0);
+  else
+    export_kernel<float><<<264, 256, 0, s>>>(p, (Cx<float>*)dst, (const Cx<float>*)p.state, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_import_state(int precision, const Params& p, const void* src, cudaStream_t s) {
+  if (precision == 64)
+    export_kernel<double><<<264, 256, 0, s>>>(p, (Cx<double>*)p.state, (const Cx<double>*)src, 1);
+  else
+    export_kernel<float><<<264, 256, 0, s>>>(p, (Cx<float>*)p.state, (const Cx<float>*)src, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t max_active_clusters(int precision, const Params& p, int* n) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t c = make_cfg(p, 1, 0, attr);
+  if (precision == 64) return cudaOccupancyMaxActiveClusters(n, march_kernel<double>, &c);
+  return cudaOccupancyMaxActiveClusters(n, march_kernel<float>, &c);
+}
+
+}  // namespace gempic

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of libgempic.so (include/gempic.h).
+
+Argument marshalling only: every step of the GEM-PIC path runs in the library's CUDA
+kernels.  The functions keep the C names (gempic_create, gempic_step, ...); `Sim` wraps one
+simulation handle.  There is no fallback: if libgempic.so is missing or no GPU is present,
+`load()` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (POINTER, Structure, c_char_p, c_double, c_int32, c_int64, c_size_t,
+                    c_uint32, c_uint64, c_void_p, byref)
+from typing import Optional
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libgempic.so")
+
+GEMPIC_FLAG_DIAG = 1
+GEMPIC_FLAG_SNAPSHOT = 2
+STATUS = {0: "GEMPIC_OK", -1: "GEMPIC_EINVAL", -2: "GEMPIC_ENOMEM", -3: "GEMPIC_ECUDA",
+          -4: "GEMPIC_EUNSTABLE", -5: "GEMPIC_ETIMEOUT", -6: "GEMPIC_ESTATE",
+          -7: "GEMPIC_EOVERFLOW"}
+FIELDS = {"Ex": 0, "Ey": 1, "Ez": 2, "Bx": 3, "By": 4, "Bz": 5, "jx": 6, "jy": 7, "jz": 8}
+
+
+class GempicError(RuntimeError):
+    def __init__(self, status: int, what: str, msg: str = ""):
+        super().__init__(f"{what}: {STATUS.get(status, status)} ({msg})")
+        self.status = status
+
+
+class gempic_grid(Structure):
+    _fields_ = [("nx", c_int32), ("ny", c_int32), ("nzeta", c_int32),
+                ("hx", c_double), ("hy", c_double), ("h", c_double)]
+
+
+class gempic_species(Structure):
+    _fields_ = [("charge", c_double), ("mass", c_double), ("density", c_double),
+                ("ppc", c_int32), ("reserved", c_int32)]
+
+
+class gempic_laser(Structure):
+    _fields_ = [("a0", c_double), ("waist", c_double), ("duration", c_double),
+                ("zeta_center", c_double), ("pol", c_int32), ("reserved", c_int32)]
+
+
+class gempic_config(Structure):
+    _fields_ = [("grid", gempic_grid), ("delta", c_double), ("precision", c_int32),
+                ("flags", c_uint32), ("seed", c_uint64), ("nspecies", c_int32),
+                ("cluster_ctas", c_int32), ("species", POINTER(gempic_species)),
+                ("laser", POINTER(gempic_laser)), ("stored_bucket_capacity", c_int32),
+                ("particle_headroom", c_int32), ("pipeline_depth", c_int32),
+                ("reserved", c_int32), ("cuda_stream", c_void_p)]
+
+
+class gempic_diag(Structure):
+    _fields_ = [("step", c_int64), ("field_energy", c_double), ("kinetic_energy", c_double),
+                ("charge_flux", c_double), ("n_trapped", c_int64), ("n_stored", c_int64),
+                ("n_rejoined", c_int64), ("pushes", c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+# exported symbols and their signatures (include/gempic.h)
+SIGNATURES = {
+    "gempic_create": (c_int32, [POINTER(gempic_config), POINTER(c_void_p)]),
+    "gempic_add_particles": (c_int32, [c_void_p, c_int64] + [c_void_p] * 8),
+    "gempic_step": (c_int32, [c_void_p, c_int32]),
+    "gempic_step_async": (c_int32, [c_void_p, c_int32]),
+    "gempic_sync": (c_int32, [c_void_p]),
+    "gempic_step_host": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_size_t, POINTER(gempic_diag)]),
+    "gempic_state_bytes": (c_size_t, [c_void_p]),
+    "gempic_get_state": (c_int32, [c_void_p, c_void_p, c_size_t, c_int32]),
+    "gempic_set_state": (c_int32, [c_void_p, c_void_p, c_size_t, c_int32]),
+    "gempic_get_fields": (c_int32, [c_void_p, c_int32, c_void_p, c_size_t, c_int32]),
+    "gempic_get_particles": (c_int32, [c_void_p, c_int32, POINTER(c_int64)] + [c_void_p] * 8),
+    "gempic_get_diagnostics": (c_int32, [c_void_p, POINTER(gempic_diag)]),
+    "gempic_get_onaxis_ez": (c_int32, [c_void_p, c_void_p, c_int32]),
+    "gempic_launch_count": (c_int64, [c_void_p]),
+    "gempic_launch_shape": (c_int32, [c_void_p] + [POINTER(c_int32)] * 4),
+    "gempic_strerror": (c_char_p, [c_int32]),
+    "gempic_destroy": (None, [c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libgempic.so and declare its signatures (raises if it is missing)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int, what: str):
+    if st != 0:
+        raise GempicError(st, what, load().gempic_strerror(st).decode())
+
+
+def _ptr(a) -> int:
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int = 0,
+                         pipeline_depth: int = 0, bucket_capacity: int = 0,
+                         headroom: int = 0, stream: Optional[int] = None):
+    """gempic_config for a paper_2509_16793_gb300.workloads.Workload (plus the arrays it
+    points to, returned so that they outlive the create call)."""
+    n = len(w.species)
+    sp = (gempic_species * max(n, 1))()
+    for i, s in enumerate(w.species):
+        sp[i] = gempic_species(s.charge, s.mass, s.density, s.ppc, 0)
+    las = None
+    if w.laser is not None:
+        L = w.laser
+        las = gempic_laser(L.a0, L.waist, L.duration, L.zeta_center, L.pol, 0)
+    if w.snapshot:
+        flags |= GEMPIC_FLAG_SNAPSHOT
+    cfg = gempic_config(
+        grid=gempic_grid(w.nx, w.ny, w.nzeta, w.hx, w.hy, w.h), delta=w.delta,
+        precision=w.precision, flags=flags, seed=w.seed, nspecies=n, cluster_ctas=cluster_ctas,
+        species=ctypes.cast(sp, POINTER(gempic_species)),
+        laser=ctypes.pointer(las) if las is not None else None,
+        stored_bucket_capacity=bucket_capacity, particle_headroom=headroom,
+        pipeline_depth=pipeline_depth, reserved=0, cuda_stream=stream)
+    return cfg, (sp, las)
+
+
+class Sim:
+    """One GEM-PIC simulation on the GPU (gempic_create ... gempic_destroy)."""
+
+    def __init__(self, w, **kw):
+        lib = load()
+        self.w = w
+        self.lib = lib
+        cfg, self._keep = config_from_workload(w, **kw)
+        h = c_void_p()
+        _check(lib.gempic_create(byref(cfg), byref(h)), "gempic_create")
+        self.h = h
+        self.dtype = np.complex128 if w.precision == 64 else np.complex64
+        self.rdtype = np.float64 if w.precision == 64 else np.float32
+        if w.stored is not None and w.stored.n > 0:
+            st = w.stored
+            arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in
+                    (st.x, st.y, st.zeta, st.ux, st.uy, st.uz, st.weight)]
+            spc = np.ascontiguousarray(st.species, dtype=np.int32)
+            _check(lib.gempic_add_particles(self.h, st.n, *[a.ctypes.data for a in arrs],
+                                            spc.ctypes.data), "gempic_add_particles")
+
+    def gempic_step(self, n: int = 1):
+        _check(self.lib.gempic_step(self.h, n), "gempic_step")
+
+    step = gempic_step
+
+    def gempic_step_async(self, n: int = 1):
+        _check(self.lib.gempic_step_async(self.h, n), "gempic_step_async")
+
+    step_async = gempic_step_async
+
+    def gempic_sync(self):
+        _check(self.lib.gempic_sync(self.h), "gempic_sync")
+
+    sync = gempic_sync
+
+    def state_bytes(self) -> int:
+        return int(self.lib.gempic_state_bytes(self.h))
+
+    def state_shape(self):
+        w = self.w
+        return (6, w.nzeta, w.ny, w.nx // 2)
+
+    def gempic_get_state(self, out=None) -> np.ndarray:
+        """Spectral state [6, nzeta, ny, nx/2] (Rx, Ry, Ez, Bz, jx, jy) on the host, or into
+        a device tensor `out`."""
+        if out is not None and hasattr(out, "data_ptr") and out.is_cuda:
+            _check(self.lib.gempic_get_state(self.h, out.data_ptr(), self.state_bytes(), 1), "gempic_get_state")
+            return out
+        a = np.empty(self.state_shape(), self.dtype)
+        _check(self.lib.gempic_get_state(self.h, a.ctypes.data, a.nbytes, 0), "gempic_get_state")
+        return a
+
+    state = gempic_get_state
+
+    def gempic_set_state(self, a):
+        if hasattr(a, "data_ptr") and a.is_cuda:
+            _check(self.lib.gempic_set_state(self.h, a.data_ptr(), self.state_bytes(), 1), "gempic_set_state")
+            return
+        a = np.ascontiguousarray(a, self.dtype)
+        _check(self.lib.gempic_set_state(self.h, a.ctypes.data, a.nbytes, 0), "gempic_set_state")
+
+    def gempic_step_host(self, n: int, state_in: Optional[np.ndarray], state_out: Optional[np.ndarray]):
+        d = gempic_diag()
+        nb = self.state_bytes()
+        _check(self.lib.gempic_step_host(self.h, n, _ptr(state_in), _ptr(state_out), nb, byref(d)),
+               "gempic_step_host")
+        return d.as_dict()
+
+    def gempic_get_fields(self, comp) -> np.ndarray:
+        c = FIELDS[comp] if isinstance(comp, str) else int(comp)
+        w = self.w
+        a = np.empty((w.nzeta, w.ny, w.nx), self.rdtype)
+        _check(self.lib.gempic_get_fields(self.h, c, a.ctypes.data, a.nbytes, 0), "gempic_get_fields")
+        return a
+
+    fields = gempic_get_fields
+
+    def gempic_get_particles(self, kind: int = 0) -> dict:
+        n = c_int64(0)
+        st = self.lib.gempic_get_particles(self.h, kind, byref(n), *([None] * 8))
+        if st not in (0, -1):
+            _check(st, "gempic_get_particles")
+        cnt = n.value
+        out = {k: np.empty(cnt) for k in ("x", "y", "zeta", "ux", "uy", "uz", "weight")}
+        out["species"] = np.empty(cnt, np.int32)
+        n = c_int64(cnt)
+        _check(self.lib.gempic_get_particles(
+            self.h, kind, byref(n), *[out[k].ctypes.data for k in
+                                      ("x", "y", "zeta", "ux", "uy", "uz", "weight", "species")]),
+            "gempic_get_particles")
+        return out
+
+    particles = gempic_get_particles
+
+    def gempic_get_diagnostics(self) -> dict:
+        d = gempic_diag()
+        _check(self.lib.gempic_get_diagnostics(self.h, byref(d)), "gempic_get_diagnostics")
+        return d.as_dict()
+
+    diagnostics = gempic_get_diagnostics
+
+    def gempic_get_onaxis_ez(self) -> np.ndarray:
+        a = np.empty(self.w.nzeta)
+        _check(self.lib.gempic_get_onaxis_ez(self.h, a.ctypes.data, a.size), "gempic_get_onaxis_ez")
+        return a
+
+    onaxis_ez = gempic_get_onaxis_ez
+
+    def launch_count(self) -> int:
+        return int(self.lib.gempic_launch_count(self.h))
+
+    def launch_shape(self) -> dict:
+        v = [c_int32() for _ in range(4)]
+        _check(self.lib.gempic_launch_shape(self.h, *[byref(x) for x in v]), "gempic_launch_shape")
+        return dict(cluster_ctas=v[0].value, threads=v[1].value, smem_bytes=v[2].value,
+                    pipeline=v[3].value)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.gempic_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

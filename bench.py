@@ -1,0 +1,335 @@
+"""Benchmark of the GEM-PIC hot path on GB300 (one JSON line on stdout).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Workload: 3-D LWFA 128 x 128 x 1024, 2 ppc, FP32 push/deposit on cell-relative positions,
+a0 = 2.5 (the configuration the particle-pushes/s metric is quoted on).  A step is one
+s-step of the whole hot path: front injection, gather + push + deposit of every streaming
+particle across every slice, the per-slice transverse FFTs and slice solve, the stored
+(trapped) particle s-push, back removal and the FP64 diagnostics.  Multi-GPU runs are
+independent replicas (the method does not shard without a per-slice exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic work per unit (counted from the kernels):
+FLOP_PER_PUSH = 330.0            # gather 52 + two-pass Boris 156 + advance 22 + Esirkepov/CIC 100
+FLOP_PER_MODE = 150.0            # corrector + App. B closed form + fields, complex arithmetic
+BYTES_PER_CELL = {32: 48.0, 64: 96.0}   # spectral state read + written once per s-step
+
+
+def fft_flops(n: int) -> float:
+    return 5.0 * n * math.log2(n) if n > 1 else 0.0
+
+
+def algorithmic_flops(w) -> float:
+    """FLOP per s-step: pushes, transverse FFTs (3 forward + 6 inverse real 2-D transforms,
+    done as paired complex row transforms and complex column transforms) and the solve."""
+    nxh = w.nx // 2
+    per_slice_fft = (2 * w.ny + 3 * w.ny) * fft_flops(w.nx) + (3 + 6) * nxh * fft_flops(w.ny)
+    return (w.pushes_per_step * FLOP_PER_PUSH
+            + w.nzeta * (per_slice_fft + nxh * w.ny * FLOP_PER_MODE))
+
+
+def algorithmic_bytes(w) -> float:
+    return w.nx * w.ny * w.nzeta * BYTES_PER_CELL[w.precision]
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """Plain FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 FLOP (FMA) x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = max(mx, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(w, seconds: float, max_steps: int):
+    """Time the FP64 oracle on a bounded sample of the workload: the same transverse grid and
+    particles per cell over a 64-slice window; pushes/s extrapolate per slice."""
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import RefSim
+    sample = w.with_(nzeta=64, precision=64,
+                     laser=w.laser.__class__(**{**w.laser.__dict__, "zeta_center": 32 * w.h}))
+    sim = RefSim(sample)
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        sim.step()
+        steps += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    pushes = sample.pushes_per_step * steps
+    return {"value": pushes / dt, "unit": "pushes/s", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} s-step(s) of a {sample.nx}x{sample.ny}x{sample.nzeta} window "
+                      f"of the workload ({sample.pushes_per_step} pushes/step), FP64 numpy, "
+                      f"single thread, {dt:.1f} s",
+            "ms_per_step": dt / steps * 1e3}
+
+
+def run_reference(args, w):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import RefSim  # noqa: F401
+    # warm-up steps and timed steps on the bounded sample
+    base = oracle_sample(w, seconds=1e9, max_steps=max(1, args.warmup))
+    cb = oracle_sample(w, seconds=1e9, max_steps=max(1, args.steps))
+    line = {"impl": "reference", "metric": "particle-pushes/s", "value": cb["value"],
+            "unit": "pushes/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": cb["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(w),
+            "cpu_baseline": {"value": cb["value"], "unit": "pushes/s", "cores": 1,
+                             "kind": "oracle", "sample": cb["sample"]},
+            "e2e": {"value": cb["value"], "unit": "pushes/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    del base
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_dict(w, shape=None):
+    d = {"workload": w.name, "grid": [w.nx, w.ny, w.nzeta], "h": w.h, "hx": w.hx,
+         "delta": w.delta, "ppc": sum(s.ppc for s in w.species), "precision": w.precision,
+         "laser_a0": w.laser.a0 if w.laser else None,
+         "pushes_per_step": w.pushes_per_step,
+         "l2": "spectral state (24 B/cell, 403 MB) read and rewritten every s-step: inputs larger than L2"}
+    if shape:
+        d["launch"] = shape
+    return d
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=48)
+    ap.add_argument("--warmup", type=int, default=8)
+    ap.add_argument("--impl", default="gempic", choices=["gempic", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the end-to-end leg")
+    ap.add_argument("--nzeta", type=int, default=0,
+                    help="profiling only: shorter window of the same workload")
+    ap.add_argument("--pipeline", type=int, default=0, help="s-steps marched concurrently (0 = auto)")
+    ap.add_argument("--bucket-capacity", type=int, default=0)
+    args = ap.parse_args()
+
+    from paper_2509_16793_gb300 import workloads as W
+    w = W.lwfa_3d_128x128x1024()
+    if args.nzeta:
+        w = w.with_(nzeta=args.nzeta, name=f"{w.name}_nzeta{args.nzeta}",
+                    laser=W.Laser(**{**w.laser.__dict__,
+                                     "zeta_center": args.nzeta * w.h - 2.0 * w.laser.duration}))
+    if args.impl == "reference":
+        return run_reference(args, w)
+
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2509_16793_gb300 import build, gempic
+    if rank == 0 or world == 1:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    stream = torch.cuda.current_stream()
+    # replicas: each rank simulates its own plasma (seed offset), no data-path collective
+    wr = w.with_(seed=w.seed + rank)
+    sim = gempic.Sim(wr, stream=stream.cuda_stream, pipeline_depth=args.pipeline,
+                     bucket_capacity=args.bucket_capacity)
+    shape = sim.launch_shape()
+    sim.step(args.warmup)
+    launches0 = sim.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step_async(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+    sim.sync()
+    launches = sim.launch_count() - launches0
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = world * w.pushes_per_step * args.steps / (ms / 1e3)
+    diag = sim.diagnostics()
+
+    # end to end through the C-ABI with host buffers: the spectral state comes in from pinned
+    # host memory, one s-step runs, the state and the diagnostics go back, every step
+    nb = sim.state_bytes()
+    e2e_s = float("nan")
+    if args.e2e_steps > 0:
+        hin = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        hout = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
+        sim.gempic_step_host(0, None, hout.numpy())
+        hin.copy_(hout)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            sim.gempic_step_host(1, hin.numpy(), hout.numpy())
+            hin, hout = hout, hin
+        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * w.pushes_per_step / e2e_s
+
+    if rank != 0:
+        sim.close()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return 0
+
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    peak_alu = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    flops = algorithmic_flops(w) * args.steps
+    achieved = flops / (ms / 1e3) / 1e12
+    hbm = algorithmic_bytes(w) * args.steps / (ms / 1e3) / 1e9
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "march_traffic.json")
+    if os.path.exists(tf):
+        try:
+            tj = json.load(open(tf))
+            if tj.get("kernel_hash") == kernel_hash():
+                traffic = tj["bytes_per_step"] * args.steps
+        except Exception:
+            traffic = None
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
+            "frac": achieved / peak_alu, "traffic": traffic,
+            "peak_source": "152 SM x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)",
+            "kernel": "march_kernel<float>",
+            "hbm": {"achieved": hbm, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                    "frac": hbm / peaks.get("hbm_gbs", 6800.0), "of": "measured"}}
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            cpu = oracle_sample(w, seconds=15.0, max_steps=20)
+            cpu.pop("ms_per_step", None)
+        except Exception as ex:  # the baseline is reported, never the target
+            cpu = {"error": str(ex)}
+    line = {"metric": "particle-pushes/s", "value": value, "unit": "pushes/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": config_dict(w, shape), "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "pushes/s", "h2d_bytes_per_step": nb,
+                    "d2h_bytes_per_step": nb + 64},
+            "gpu_launches": launches, "clocks": clocks,
+            "diag": {k: diag[k] for k in ("field_energy", "kinetic_energy", "n_stored", "pushes")}}
+    print(json.dumps(line), flush=True)
+    sim.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("gempic_kernels.cu", "gempic_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2509_16793_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -272,18 +272,27 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     const int fresh = RB * g.nx * ppc_sum;
     int NT = std::max(M, fresh / 4);
     NT = std::min(512, std::max(128, (NT + 31) / 32 * 32));
-    const int head = cfg->particle_headroom > 0 ? cfg->particle_headroom : std::max(32, fresh / 4);
+    // streaming slots beyond the fresh layer hold stored particles that rejoin the march;
+    // by default as many as the shared-memory budget allows, up to max(256, fresh)
+    int head = cfg->particle_headroom > 0 ? cfg->particle_headroom : std::max(256, fresh);
     p.C = cand;
     p.RB = RB;
     p.KB = KB;
+    p.logRB = ilog2(RB);
+    p.logKB = ilog2(KB);
     p.M = M;
     p.nthreads = NT;
-    p.pcap = fresh + head;
     p.nwork = std::min(NT / 32, 3 * RB);
-    if (gempic::smem_layout(p, s->eb) <= smem_optin) {
-      chosen = true;
-      break;
+    for (;;) {
+      p.pcap = fresh + head;
+      if (gempic::smem_layout(p, s->eb) <= smem_optin) {
+        chosen = true;
+        break;
+      }
+      if (cfg->particle_headroom > 0 || head <= 32) break;
+      head = head * 3 / 4;
     }
+    if (chosen) break;
   }
   if (!chosen) {
     delete s;
@@ -369,6 +378,9 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     ALLOC(p.jbeam, ring * g.nzeta * 3 * nperp * eb);
     ALLOC(p.jflag, ring * g.nzeta * sizeof(int));
     if (p.snapshot) ALLOC(p.snap, (size_t)9 * g.nzeta * nperp * eb);
+#ifdef GEMPIC_PHASE_TIMERS
+    ALLOC(p.timers, 64 * sizeof(unsigned long long));
+#endif
   }
 #undef ALLOC
   e = cudaStreamSynchronize(s->stream);
@@ -600,6 +612,18 @@ gempic_status gempic_get_onaxis_ez(gempic_sim* s, double* dst, int32_t n) {
 }
 
 int64_t gempic_launch_count(const gempic_sim* s) { return s ? s->launches : 0; }
+
+#ifdef GEMPIC_PHASE_TIMERS
+// profiling builds only: accumulated clock64 cycles per march phase (thread 0 of each CTA)
+gempic_status gempic_phase_timers(gempic_sim* s, unsigned long long* out, int32_t n) {
+  if (!s || !out || n < 1) return GEMPIC_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(out, s->p.timers, std::min(n, 64) * sizeof(unsigned long long),
+                                  cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->p.timers, 0, 64 * sizeof(unsigned long long), s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_fail(s, e);
+}
+#endif
 
 gempic_status gempic_launch_shape(const gempic_sim* s, int32_t* cluster_ctas, int32_t* threads,
                                   int32_t* smem_bytes, int32_t* pipeline) {

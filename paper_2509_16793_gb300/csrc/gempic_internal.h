@@ -33,7 +33,7 @@ struct Params {
   // grid and decomposition
   int nx, ny, nz;                 // transverse nodes, slices
   int C, RB, KB, M;               // CTAs per cluster, rows per CTA, kx per CTA, modes per CTA
-  int lognx, logny;
+  int lognx, logny, logRB, logKB;
   int nthreads;
   // physics
   double hx, hy, h, delta, delta_field;
@@ -67,6 +67,7 @@ struct Params {
   double* diag_out;               // [nsteps][kNDiag][C]
   double* onaxis;                 // [nsteps][nz]
   void* snap;                     // [9][nz][ny][nx]
+  unsigned long long* timers;     // phase timers (builds with GEMPIC_PHASE_TIMERS only)
 };
 
 // Host-side helpers implemented in gempic_kernels.cu

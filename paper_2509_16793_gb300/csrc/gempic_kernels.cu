@@ -115,9 +115,46 @@ __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned l
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__device__ __forceinline__ int imod(int a, int n) {
-  int r = a % n;
-  return r < 0 ? r + n : r;
+// shared memory of this CTA and of other CTAs of the cluster, addressed explicitly
+__device__ __forceinline__ uint32_t sh_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t cluster_addr(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float lds(uint32_t a, float) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ double lds(uint32_t a, double) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ float ldc(uint32_t a, float) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ double ldc(uint32_t a, double) {
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ void red_local(uint32_t a, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_local(uint32_t a, double v) {
+  asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+}
+__device__ __forceinline__ void red_cluster(uint32_t a, float v) {
+  asm volatile("red.shared::cluster.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_cluster(uint32_t a, double v) {
+  asm volatile("red.shared::cluster.add.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
 }
 
 // Counter-based SplitMix64 (Steele, Lea, Flood 2014): output c of the stream seeded with s.
@@ -173,6 +210,11 @@ __device__ void warp_fft(Cx<T>* d, int logN, const Cx<T>* tw, bool inverse) {
 // ------------------------------------------------------------------------------------------
 // per-kernel shared-memory views
 // ------------------------------------------------------------------------------------------
+enum CstSlot {
+  K_H = 0, K_INVH, K_HX, K_HY, K_D, K_DF, K_WSCALE, K_CX, K_CY, K_INVHX, K_INVHY, K_FLUX,
+  K_BEAM, K_QM = 16, K_MOQ = 20, K_QF = 24, K_N = 28
+};
+
 template <typename T>
 struct Sm {
   T* F[2];          // [6][RB][nx] real-space fields (Ex,Ey,Ez,Bx,By,Bz)
@@ -190,6 +232,7 @@ struct Sm {
   T *pfx, *pfy, *pux, *puy, *puz, *psig, *pq;
   int* misc;        // [0] particle count
   double* dacc;     // [kNDiag]
+  T* cst;           // [K_N] constants in the working precision
 };
 
 template <typename T>
@@ -209,6 +252,7 @@ __device__ Sm<T> carve(const Params& p, unsigned char* base) {
   s.shy = s.shx + p.nx / 2;
   s.kx = (T*)(s.shy + p.ny);
   s.ky = s.kx + p.nx / 2;
+  s.cst = s.ky + p.ny;
   unsigned char* pp = base + p.o_part;
   s.pcell = (int*)pp;
   T* pt = (T*)(pp + ((p.pcap * 4 + 15) / 16) * 16);
@@ -224,7 +268,7 @@ __device__ Sm<T> carve(const Params& p, unsigned char* base) {
   return s;
 }
 
-// copy the FP64-built tables (already converted to T on the host) into shared memory
+// tables built in FP64 on the host (already in the working precision) and the constants
 template <typename T>
 __device__ void load_tables(const Params& p, const Sm<T>& s) {
   const int nyh = p.ny > 1 ? p.ny / 2 : 1;
@@ -234,39 +278,76 @@ __device__ void load_tables(const Params& p, const Sm<T>& s) {
   for (int i = threadIdx.x; i < ncx; i += blockDim.x) s.twx[i] = src[i];
   const T* srcr = (const T*)(src + ncx);
   for (int i = threadIdx.x; i < nr; i += blockDim.x) s.kx[i] = srcr[i];
+  if (threadIdx.x == 0) {
+    T* c = s.cst;
+    c[K_H] = T(p.h);
+    c[K_INVH] = T(1.0 / p.h);
+    c[K_HX] = T(p.hx);
+    c[K_HY] = T(p.hy);
+    c[K_D] = T(p.delta);
+    c[K_DF] = T(p.delta_field);
+    c[K_WSCALE] = T(1.0 / (p.hx * p.hy * p.delta));
+    c[K_CX] = T(p.hx / p.h);
+    c[K_CY] = T(p.hy / p.h);
+    c[K_INVHX] = T(1.0 / p.hx);
+    c[K_INVHY] = T(1.0 / p.hy);
+    c[K_FLUX] = T(p.hx * p.hy * p.h);
+    c[K_BEAM] = T(1.0 / (p.hx * p.hy * p.h));
+    for (int i = 0; i < kMaxSpecies; ++i) {
+      c[K_QM + i] = T(p.qm[i]);
+      c[K_MOQ + i] = T(p.m_over_q[i]);
+      c[K_QF + i] = T(p.Qf[i]);
+    }
+  }
 }
 
 // ------------------------------------------------------------------------------------------
-// cluster helpers
+// phase timers (profiling builds only)
 // ------------------------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ T* at_rank(const cg::cluster_group& cl, T* local, int r, int me) {
-  return r == me ? local : cl.map_shared_rank(local, r);
-}
-
-// pointer to element (comp, global row y, column x) of a [comp][RB][nx] plane set
-template <typename T>
-__device__ __forceinline__ T* plane_ptr(const cg::cluster_group& cl, T* base, const Params& p,
-                                        int comp, int y, int x, int me) {
-  const int r = y / p.RB;
-  const int yl = y - r * p.RB;
-  return at_rank(cl, base + ((size_t)comp * p.RB + yl) * p.nx + x, r, me);
-}
+enum Phase { PH_A = 0, PH_B1, PH_BEAM, PH_FWD, PH_B2, PH_COLF, PH_SOLVE, PH_COLI, PH_SCAT, PH_B3,
+             PH_INV, PH_B4, PH_E, PH_N };
+#ifdef GEMPIC_PHASE_TIMERS
+#define TIMER_DECL long long t_last = clock64(); long long t_acc[PH_N] = {0};
+#define TIMER_MARK(ph)                      \
+  do {                                      \
+    const long long t_now = clock64();      \
+    t_acc[ph] += t_now - t_last;            \
+    t_last = t_now;                         \
+  } while (0)
+#define TIMER_FLUSH                                                                      \
+  do {                                                                                   \
+    if (threadIdx.x == 0 && p.timers)                                                    \
+      for (int i_ = 0; i_ < PH_N; ++i_)                                                  \
+        atomicAdd(p.timers + i_, (unsigned long long)t_acc[i_]);                         \
+  } while (0)
+#else
+#define TIMER_DECL
+#define TIMER_MARK(ph) \
+  do {                 \
+  } while (0)
+#define TIMER_FLUSH \
+  do {              \
+  } while (0)
+#endif
 
 // ------------------------------------------------------------------------------------------
 // Forward transverse transform of the three current planes J (own rows) into the kx-owner
 // CTAs' SC[0..2] (DSMEM).  stagger: apply exp(-i kx hx/2) to j_x (x-edge values).
-// `snapcomp` >= 0 also writes the real-space rows to the snapshot.
 // ------------------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void st_cx(const cg::cluster_group& cl, Cx<T>* local, int r, int me,
+                                      Cx<T> v) {
+  Cx<T>* q = r == me ? local : cl.map_shared_rank(local, r);
+  *q = v;
+}
+
 template <typename T>
 __device__ void forward_rows(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
                              int me, bool stagger) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
   const int nxh = p.nx / 2;
   const int ntask = 2 * p.RB;                 // (row, pair): pair 0 = jx + i jy, 1 = jz
   if (warp >= p.nwork) return;
-  (void)nwarps;
   for (int task = warp; task < ntask; task += p.nwork) {
     Cx<T>* w = s.work + (size_t)warp * p.nx;
     const int yl = task >> 1, pr = task & 1;
@@ -275,19 +356,19 @@ __device__ void forward_rows(const cg::cluster_group& cl, const Params& p, const
     for (int x = lane; x < p.nx; x += 32) w[x] = cx<T>(a[x], pr == 0 ? b[x] : T(0));
     __syncwarp();
     warp_fft(w, p.lognx, s.twx, false);
-    const int y = me * p.RB + yl;
+    const int y = (me << p.logRB) + yl;
     for (int k = lane; k < nxh; k += 32) {
       const Cx<T> zk = w[k];
       const Cx<T> zm = conjg(w[(p.nx - k) & (p.nx - 1)]);
       Cx<T> X = T(0.5) * (zk + zm);                     // spectrum of the real part
       const Cx<T> Y = T(0.5) * mul_i(zm - zk);          // spectrum of the imaginary part
-      const int rd = k / p.KB, kxl = k - rd * p.KB;
+      const int rd = k >> p.logKB, kxl = k & (p.KB - 1);
       if (pr == 0) {
         if (stagger) X = X * s.shx[k];
-        *at_rank(cl, s.SC + ((size_t)0 * p.KB + kxl) * p.ny + y, rd, me) = X;
-        *at_rank(cl, s.SC + ((size_t)1 * p.KB + kxl) * p.ny + y, rd, me) = Y;
+        st_cx(cl, s.SC + ((size_t)0 * p.KB + kxl) * p.ny + y, rd, me, X);
+        st_cx(cl, s.SC + ((size_t)1 * p.KB + kxl) * p.ny + y, rd, me, Y);
       } else {
-        *at_rank(cl, s.SC + ((size_t)2 * p.KB + kxl) * p.ny + y, rd, me) = X;
+        st_cx(cl, s.SC + ((size_t)2 * p.KB + kxl) * p.ny + y, rd, me, X);
       }
     }
     __syncwarp();
@@ -300,9 +381,9 @@ __device__ void column_ffts(const Params& p, const Sm<T>& s, int c0, int c1, boo
   if (p.ny == 1) return;
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
-  const int ntask = (c1 - c0) * p.KB;
+  const int ntask = (c1 - c0) << p.logKB;
   for (int task = warp; task < ntask; task += nwarps) {
-    const int c = c0 + task / p.KB, kxl = task % p.KB;
+    const int c = c0 + (task >> p.logKB), kxl = task & (p.KB - 1);
     warp_fft(s.SC + ((size_t)c * p.KB + kxl) * p.ny, p.logny, s.twy, inverse);
   }
 }
@@ -311,30 +392,27 @@ __device__ void column_ffts(const Params& p, const Sm<T>& s, int c0, int c1, boo
 template <typename T>
 __device__ void scatter_to_rows(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
                                 int me) {
-  const int n = 6 * p.KB * p.ny;
+  const int lc = p.logKB + p.logny;
+  const int n = 6 << lc;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int c = i / (p.KB * p.ny);
-    const int rem = i - c * p.KB * p.ny;
-    const int kxl = rem / p.ny, y = rem - kxl * p.ny;
-    const int ro = y / p.RB, yl = y - ro * p.RB;
-    *at_rank(cl, s.SR + ((size_t)c * p.RB + yl) * (p.nx / 2) + me * p.KB + kxl, ro, me) =
-        s.SC[i];
+    const int c = i >> lc;
+    const int rem = i & ((1 << lc) - 1);
+    const int kxl = rem >> p.logny, y = rem & (p.ny - 1);
+    const int ro = y >> p.logRB, yl = y & (p.RB - 1);
+    st_cx(cl, s.SR + ((size_t)c * p.RB + yl) * (p.nx / 2) + (me << p.logKB) + kxl, ro, me, s.SC[i]);
   }
 }
 
 // inverse row transforms: SR pairs (Ex,Ey), (Ez,Bx), (By,Bz) -> real rows of Fdst
 template <typename T>
-__device__ void inverse_rows(const Params& p, const Sm<T>& s, T* Fdst, double& fe) {
+__device__ void inverse_rows(const Params& p, const Sm<T>& s, T* Fdst, T& fe) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
   const int nxh = p.nx / 2;
   const T scale = T(1.0 / ((double)p.nx * (double)p.ny));
   const int ntask = 3 * p.RB;
-  T acc = T(0);
-  (void)nwarps;
   for (int task = (warp < p.nwork ? warp : ntask); task < ntask; task += p.nwork) {
     Cx<T>* w = s.work + (size_t)warp * p.nx;
-    const int yl = task / 3, pr = task % 3;
+    const int yl = task / 3, pr = task - 3 * yl;
     const Cx<T>* X = s.SR + ((size_t)(2 * pr) * p.RB + yl) * nxh;
     const Cx<T>* Y = s.SR + ((size_t)(2 * pr + 1) * p.RB + yl) * nxh;
     for (int k = lane; k < nxh; k += 32) {
@@ -355,59 +433,103 @@ __device__ void inverse_rows(const Params& p, const Sm<T>& s, T* Fdst, double& f
       const T va = w[x].re * scale, vb = w[x].im * scale;
       a[x] = va;
       b[x] = vb;
-      acc += va * va + vb * vb;
+      fe += va * va + vb * vb;
     }
     __syncwarp();
   }
-  fe += (double)acc;
 }
 
 // ------------------------------------------------------------------------------------------
-// particle gather (CIC on the transverse nodes) of the 6 fields of a plane set
+// addressing of a [comp][RB][nx] plane set of the cluster: shared-memory address of
+// (comp 0, global row y, column 0) and the owning CTA
 // ------------------------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void gather6(const cg::cluster_group& cl, const Params& p, T* Fb,
-                                        int ix, T fx, int iy, T fy, int me, T* out) {
-  const int ix1 = ix + 1 == p.nx ? 0 : ix + 1;
+struct RowRef {
+  uint32_t a;        // address of (comp 0, row, col 0) in the owner's window (or local)
+  bool remote;
+};
+
+template <typename T>
+__device__ __forceinline__ RowRef<T> row_ref(const Params& p, const T* base, int y, int me) {
+  const int r = y >> p.logRB;
+  const int yl = y & (p.RB - 1);
+  uint32_t a = sh_addr(base + (size_t)yl * p.nx);
+  RowRef<T> rr;
+  rr.remote = r != me;
+  rr.a = rr.remote ? cluster_addr(a, r) : a;
+  return rr;
+}
+
+template <typename T>
+__device__ __forceinline__ T row_ld(const RowRef<T>& rr, uint32_t off_elems) {
+  const uint32_t a = rr.a + off_elems * (uint32_t)sizeof(T);
+  return rr.remote ? ldc(a, T(0)) : lds(a, T(0));
+}
+
+template <typename T>
+__device__ __forceinline__ void row_red(const RowRef<T>& rr, uint32_t off_elems, T v) {
+  const uint32_t a = rr.a + off_elems * (uint32_t)sizeof(T);
+  if (rr.remote)
+    red_cluster(a, v);
+  else
+    red_local(a, v);
+}
+
+// CIC gather of the 6 fields of a plane set at (ix + fx, iy + fy)
+template <typename T>
+__device__ __forceinline__ void gather6(const Params& p, const T* Fb, int ix, T fx, int iy, T fy,
+                                        int me, T* out) {
+  const int ix1 = (ix + 1) & (p.nx - 1);
+  const uint32_t cs = (uint32_t)(p.RB * p.nx);     // component stride
   if (p.ny == 1) {
+    const uint32_t a = sh_addr(Fb);
+#pragma unroll
     for (int c = 0; c < 6; ++c) {
-      const T* r = Fb + (size_t)c * p.nx;
-      out[c] = (T(1) - fx) * r[ix] + fx * r[ix1];
+      const uint32_t b = a + (c * cs) * (uint32_t)sizeof(T);
+      out[c] = (T(1) - fx) * lds(b + ix * (uint32_t)sizeof(T), T(0)) +
+               fx * lds(b + ix1 * (uint32_t)sizeof(T), T(0));
     }
     return;
   }
-  const int iy1 = iy + 1 == p.ny ? 0 : iy + 1;
+  const int iy1 = (iy + 1) & (p.ny - 1);
+  const RowRef<T> r0 = row_ref(p, Fb, iy, me);
+  const RowRef<T> r1 = row_ref(p, Fb, iy1, me);
   const T w00 = (T(1) - fx) * (T(1) - fy), w10 = fx * (T(1) - fy);
   const T w01 = (T(1) - fx) * fy, w11 = fx * fy;
+#pragma unroll
   for (int c = 0; c < 6; ++c) {
-    const T* r0 = plane_ptr(cl, Fb, p, c, iy, 0, me);
-    const T* r1 = plane_ptr(cl, Fb, p, c, iy1, 0, me);
-    out[c] = ((w00 * r0[ix] + w10 * r0[ix1]) + w01 * r1[ix]) + w11 * r1[ix1];
+    const uint32_t o = c * cs;
+    out[c] = ((w00 * row_ld(r0, o + ix) + w10 * row_ld(r0, o + ix1)) + w01 * row_ld(r1, o + ix)) +
+             w11 * row_ld(r1, o + ix1);
   }
 }
 
+// add v to current plane `comp` at (global row y, column x), both already wrapped
 template <typename T>
-__device__ __forceinline__ void jadd(const cg::cluster_group& cl, const Params& p, T* J, int comp,
-                                     int y, int x, T v, int me) {
-  if (v != T(0)) atomicAdd(plane_ptr(cl, J, p, comp, imod(y, p.ny), imod(x, p.nx), me), v);
+__device__ __forceinline__ void jadd(const Params& p, const T* J, int comp, int y, int x, T v,
+                                     int me) {
+  if (v == T(0)) return;
+  const RowRef<T> rr = row_ref(p, J, y, me);
+  row_red(rr, (uint32_t)(comp * p.RB * p.nx + x), v);
 }
 
 // Esirkepov (Comput. Phys. Commun. 135, 2001) transverse current of a move (X0,Y0)->(X1,Y1)
 // in cell units relative to node (ix, iy); w is the (rho - j_z) weight.  With D = w S the
 // deposit satisfies (D_new - D_old) + h div J = 0 on every node.
 template <typename T>
-__device__ void esirkepov(const cg::cluster_group& cl, const Params& p, T* J, int ix, int iy,
-                          T X0, T Y0, T X1, T Y1, T w, T dyo, int me) {
-  const T h = T(p.h);
+__device__ void esirkepov(const Params& p, const Sm<T>& s, int ix, int iy, T X0, T Y0, T X1,
+                          T Y1, T w, T dyo, int me) {
+  const T invh = s.cst[K_INVH];
   const T dX = X1 - X0;
   const T dY = Y1 - Y0;
   const T m = fmax(fabs(dX), fabs(dY));
   const int nsub = m > T(1) ? (int)ceil(m) : 1;
-  const T cx_ = -(w * T(p.hx) / h);
-  const T cy_ = -(w * T(p.hy) / h);
-  for (int s = 0; s < nsub; ++s) {
-    const T xa = X0 + dX * (T(s) / T(nsub));
-    const T xb = X0 + dX * (T(s + 1) / T(nsub));
+  const T cx_ = -(w * s.cst[K_CX]);
+  const T cy_ = -(w * s.cst[K_CY]);
+  const int mx = p.nx - 1, my = p.ny - 1;
+  for (int sb = 0; sb < nsub; ++sb) {
+    const T xa = X0 + dX * (T(sb) / T(nsub));
+    const T xb = X0 + dX * (T(sb + 1) / T(nsub));
     const T bx = floor(fmin(xa, xb));
     T S0x[3], S1x[3];
 #pragma unroll
@@ -421,16 +543,16 @@ __device__ void esirkepov(const cg::cluster_group& cl, const Params& p, T* J, in
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         cum = cum + (S1x[a] - S0x[a]);
-        jadd(cl, p, J, 0, 0, gx + a, cx_ * cum, me);
+        jadd(p, s.J, 0, 0, (gx + a) & mx, cx_ * cum, me);
       }
       const T dyv = dyo / T(nsub);
 #pragma unroll
       for (int a = 0; a < 3; ++a)
-        jadd(cl, p, J, 1, 0, gx + a, w * (dyv / h) * T(0.5) * (S0x[a] + S1x[a]), me);
+        jadd(p, s.J, 1, 0, (gx + a) & mx, w * (dyv * invh) * T(0.5) * (S0x[a] + S1x[a]), me);
       continue;
     }
-    const T ya = Y0 + dY * (T(s) / T(nsub));
-    const T yb = Y0 + dY * (T(s + 1) / T(nsub));
+    const T ya = Y0 + dY * (T(sb) / T(nsub));
+    const T yb = Y0 + dY * (T(sb + 1) / T(nsub));
     const T by = floor(fmin(ya, yb));
     T S0y[3], S1y[3];
 #pragma unroll
@@ -441,44 +563,60 @@ __device__ void esirkepov(const cg::cluster_group& cl, const Params& p, T* J, in
     const int gy = iy + (int)by;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
+      const int yy = (gy + b) & my;
+      const T hy2 = T(0.5) * (S0y[b] + S1y[b]);
+      if (hy2 == T(0)) continue;
+      const RowRef<T> rr = row_ref(p, s.J, yy, me);
       T cum = T(0);
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
-        cum = cum + (S1x[a] - S0x[a]) * T(0.5) * (S0y[b] + S1y[b]);
-        jadd(cl, p, J, 0, gy + b, gx + a, cx_ * cum, me);
+        cum = cum + (S1x[a] - S0x[a]) * hy2;
+        const T v = cx_ * cum;
+        if (v != T(0)) row_red(rr, (uint32_t)((gx + a) & mx), v);
       }
     }
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      T cum = T(0);
+    for (int b = 0; b < 2; ++b) {
+      const int yy = (gy + b) & my;
+      const RowRef<T> rr = row_ref(p, s.J, yy, me);
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        cum = cum + (S1y[b] - S0y[b]) * T(0.5) * (S0x[a] + S1x[a]);
-        jadd(cl, p, J, 1, gy + b, gx + a, cy_ * cum, me);
+      for (int a = 0; a < 3; ++a) {
+        // cumulative sum over b of (S1y - S0y)(S0x + S1x)/2 at column a
+        T cum = (S1y[0] - S0y[0]) * T(0.5) * (S0x[a] + S1x[a]);
+        if (b == 1) cum = cum + (S1y[1] - S0y[1]) * T(0.5) * (S0x[a] + S1x[a]);
+        const T v = cy_ * cum;
+        if (v != T(0)) row_red(rr, (uint32_t)(p.RB * p.nx + ((gx + a) & mx)), v);
       }
     }
   }
 }
 
-// CIC deposit of value v at (X, Y) relative to node (ix, iy)
+// CIC deposit of value v at (X, Y) relative to node (ix, iy) into current plane comp
 template <typename T>
-__device__ __forceinline__ void cic_add(const cg::cluster_group& cl, const Params& p, T* J,
-                                        int comp, int ix, int iy, T X, T Y, T v, int me) {
+__device__ __forceinline__ void cic_add(const Params& p, const Sm<T>& s, int comp, int ix,
+                                        int iy, T X, T Y, T v, int me) {
   const T i0 = floor(X);
   const T fx = X - i0;
-  const int gx = ix + (int)i0;
+  const int gx = (ix + (int)i0) & (p.nx - 1);
+  const int gx1 = (gx + 1) & (p.nx - 1);
   if (p.ny == 1) {
-    jadd(cl, p, J, comp, 0, gx, (T(1) - fx) * v, me);
-    jadd(cl, p, J, comp, 0, gx + 1, fx * v, me);
+    jadd(p, s.J, comp, 0, gx, (T(1) - fx) * v, me);
+    jadd(p, s.J, comp, 0, gx1, fx * v, me);
     return;
   }
   const T j0 = floor(Y);
   const T fy = Y - j0;
-  const int gy = iy + (int)j0;
-  jadd(cl, p, J, comp, gy, gx, ((T(1) - fx) * (T(1) - fy)) * v, me);
-  jadd(cl, p, J, comp, gy, gx + 1, (fx * (T(1) - fy)) * v, me);
-  jadd(cl, p, J, comp, gy + 1, gx, ((T(1) - fx) * fy) * v, me);
-  jadd(cl, p, J, comp, gy + 1, gx + 1, (fx * fy) * v, me);
+  const int gy = (iy + (int)j0) & (p.ny - 1);
+  const int gy1 = (gy + 1) & (p.ny - 1);
+  const uint32_t o = (uint32_t)(comp * p.RB * p.nx);
+  const RowRef<T> r0 = row_ref(p, s.J, gy, me);
+  const RowRef<T> r1 = row_ref(p, s.J, gy1, me);
+  T v00 = ((T(1) - fx) * (T(1) - fy)) * v, v10 = (fx * (T(1) - fy)) * v;
+  T v01 = ((T(1) - fx) * fy) * v, v11 = (fx * fy) * v;
+  if (v00 != T(0)) row_red(r0, o + gx, v00);
+  if (v10 != T(0)) row_red(r0, o + gx1, v10);
+  if (v01 != T(0)) row_red(r1, o + gx, v01);
+  if (v11 != T(0)) row_red(r1, o + gx1, v11);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -496,13 +634,19 @@ struct PState {
 };
 
 template <typename T>
-__device__ bool stream_push(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
-                            T* Fcur, PState<T>& P, T d, int me, T& fz_trap, double* acc) {
+struct SliceAcc {     // per-thread, per-slice diagnostics in the working precision
+  T kin, flux;
+  int push;
+};
+
+template <typename T>
+__device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PState<T>& P, T d,
+                            int me, T& fz_trap, SliceAcc<T>& acc) {
   T E[6];
-  gather6(cl, p, Fcur, P.ix, P.fx, P.iy, P.fy, me, E);
-  const T D = T(p.delta);
-  const T h = T(p.h);
-  const T qm = T(p.qm[P.sp]);
+  gather6(p, Fcur, P.ix, P.fx, P.iy, P.fy, me, E);
+  const T D = s.cst[K_D];
+  const T invh = s.cst[K_INVH];
+  const T qm = s.cst[K_QM + P.sp];
   V3<T> u = P.u;
   const T g0 = gamma_of(u);
   const T gmu0 = gamma_minus_uz(u, g0);
@@ -521,28 +665,28 @@ __device__ bool stream_push(const cg::cluster_group& cl, const Params& p, const 
   const T den = gamma_minus_uz(un, gn);
   const T dx = hc * un.x / den, dy = hc * un.y / den, ds = hc * un.z / den;
   // deposit: w = Q/(hx hy Delta) is the particle's (rho - j_z) density weight (Sec. 4.1)
-  const T w = P.q / (T(p.hx) * T(p.hy) * D);
-  const T X1 = P.fx + dx / T(p.hx);
-  const T Y1 = p.ny > 1 ? P.fy + dy / T(p.hy) : P.fy;
-  esirkepov(cl, p, s.J, P.ix, P.iy, P.fx, P.fy, X1, Y1, w, dy, me);
-  cic_add(cl, p, s.J, 2, P.ix, P.iy, X1, Y1, w * ds / h, me);
+  const T w = P.q * s.cst[K_WSCALE];
+  const T X1 = P.fx + dx * s.cst[K_INVHX];
+  const T Y1 = p.ny > 1 ? P.fy + dy * s.cst[K_INVHY] : P.fy;
+  esirkepov(p, s, P.ix, P.iy, P.fx, P.fy, X1, Y1, w, dy, me);
+  cic_add(p, s, 2, P.ix, P.iy, X1, Y1, w * ds * invh, me);
   // diagnostics: kinetic energy N m (gamma-1) dt/Delta, (rho - j_z) flux through plane n
   const T dtl = hc * gn / den;
-  acc[DG_KIN] += (double)(P.q * T(p.m_over_q[P.sp]) * (gn - T(1)) * dtl / D);
-  if (!trap) acc[DG_FLUX] += (double)(w * T(p.hx) * T(p.hy) * h);
-  acc[DG_PUSH] += 1.0;
+  acc.kin += P.q * s.cst[K_MOQ + P.sp] * (gn - T(1)) * dtl / D;
+  if (!trap) acc.flux += w;
+  acc.push += 1;
   // new cell-relative position
   const T fX = floor(X1);
-  P.ix = imod(P.ix + (int)fX, p.nx);
+  P.ix = (P.ix + (int)fX) & (p.nx - 1);
   P.fx = X1 - fX;
   if (p.ny > 1) {
     const T fY = floor(Y1);
-    P.iy = imod(P.iy + (int)fY, p.ny);
+    P.iy = (P.iy + (int)fY) & (p.ny - 1);
     P.fy = Y1 - fY;
   }
   P.u = un;
   P.sig = P.sig + ds;
-  fz_trap = (d - hc) / h;
+  fz_trap = (d - hc) * invh;
   return trap;
 }
 
@@ -586,17 +730,18 @@ __device__ PState<T> store_read(const PartStore& S, const Params& p, size_t e, T
 // bucket n of level k+1, fields of slices n (Fn) and n+1 (Fn1) of that level.
 // ------------------------------------------------------------------------------------------
 template <typename T>
-__device__ void stored_phase(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
-                             T* Fn, T* Fn1, long long k, int n, int me, double* acc) {
+__device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const T* Fn1,
+                             long long k, int n, int me, double* acc) {
   const int s1 = (int)(((k + 1) % p.ring + p.ring) % p.ring);
   const int s2 = (int)(((k + 2) % p.ring + p.ring) % p.ring);
   const int cnt = min(ldcg(p.st.cnt + (size_t)s1 * p.nz + n), p.bcap);
-  const T D = T(p.delta), h = T(p.h);
+  const T D = s.cst[K_D], h = s.cst[K_H], invh = s.cst[K_INVH];
+  const int mx = p.nx - 1, my = p.ny - 1;
   for (int e0 = me * blockDim.x + threadIdx.x; e0 < cnt; e0 += p.C * blockDim.x) {
     T fz;
     PState<T> P = store_read<T>(p.st, p, ((size_t)s1 * p.nz + n) * p.bcap + e0, fz);
     const T g = gamma_of(P.u);
-    acc[DG_KIN] += (double)(P.q * T(p.m_over_q[P.sp]) * (g - T(1)));
+    acc[DG_KIN] += (double)(P.q * s.cst[K_MOQ + P.sp] * (g - T(1)));
     acc[DG_STORED] += 1.0;
     const T gmu = gamma_minus_uz(P.u, g);
     const bool spush = (P.u.z > T(0)) && (D * gmu < h * fmax(P.u.z, T(0)));
@@ -606,27 +751,27 @@ __device__ void stored_phase(const cg::cluster_group& cl, const Params& p, const
       continue;
     }
     T lo[6], hi[6], E[6];
-    gather6(cl, p, Fn, P.ix, P.fx, P.iy, P.fy, me, lo);
-    gather6(cl, p, Fn1, P.ix, P.fx, P.iy, P.fy, me, hi);
+    gather6(p, Fn, P.ix, P.fx, P.iy, P.fy, me, lo);
+    gather6(p, Fn1, P.ix, P.fx, P.iy, P.fy, me, hi);
 #pragma unroll
     for (int c = 0; c < 6; ++c) E[c] = (T(1) - fz) * lo[c] + fz * hi[c];
     const T dt = D * g / P.u.z;
-    const V3<T> un = boris(P.u, E, E + 3, T(p.qm[P.sp]), dt);
+    const V3<T> un = boris(P.u, E, E + 3, s.cst[K_QM + P.sp], dt);
     const T gn = gamma_of(un);
     P.u = un;
     int m = n;
     if (un.z > T(0)) {
-      const T X = P.fx + D * un.x / un.z / T(p.hx);
+      const T X = P.fx + D * un.x / un.z * s.cst[K_INVHX];
       const T fX = floor(X);
-      P.ix = imod(P.ix + (int)fX, p.nx);
+      P.ix = (P.ix + (int)fX) & mx;
       P.fx = X - fX;
       if (p.ny > 1) {
-        const T Y = P.fy + D * un.y / un.z / T(p.hy);
+        const T Y = P.fy + D * un.y / un.z * s.cst[K_INVHY];
         const T fY = floor(Y);
-        P.iy = imod(P.iy + (int)fY, p.ny);
+        P.iy = (P.iy + (int)fY) & my;
         P.fy = Y - fY;
       }
-      const T Z = fz - D * gamma_minus_uz(un, gn) / un.z / h;
+      const T Z = fz - D * gamma_minus_uz(un, gn) / un.z * invh;
       const T cZ = ceil(Z) - T(1);
       m = n + (int)cZ;
       fz = Z - cZ;
@@ -635,7 +780,7 @@ __device__ void stored_phase(const cg::cluster_group& cl, const Params& p, const
         continue;
       }
       // beam current of the next level j = Q u/(gamma hx hy h), CIC across, linear in zeta
-      const T amp = P.q / (T(p.hx) * T(p.hy) * h * gn);
+      const T amp = P.q * s.cst[K_BEAM] / gn;
       const T tz = fz - T(0.5);
       const T ftz = floor(tz);
       const int i0 = m + (int)ftz;
@@ -652,22 +797,18 @@ __device__ void stored_phase(const cg::cluster_group& cl, const Params& p, const
           const T sy = (c == 1 && p.ny > 1) ? T(-0.5) : T(0);
           const T X = P.fx + sx, Y = P.fy + sy;
           const T i0f = floor(X), fx = X - i0f;
-          const int gx = P.ix + (int)i0f;
+          const int gx = (P.ix + (int)i0f) & mx, gx1 = (gx + 1) & mx;
           T* pl = base + (size_t)c * p.nx * p.ny;
           if (p.ny == 1) {
-            atomicAdd(pl + imod(gx, p.nx), (T(1) - fx) * vals[c]);
-            atomicAdd(pl + imod(gx + 1, p.nx), fx * vals[c]);
+            atomicAdd(pl + gx, (T(1) - fx) * vals[c]);
+            atomicAdd(pl + gx1, fx * vals[c]);
           } else {
             const T j0f = floor(Y), fy = Y - j0f;
-            const int gy = P.iy + (int)j0f;
-            atomicAdd(pl + (size_t)imod(gy, p.ny) * p.nx + imod(gx, p.nx),
-                      ((T(1) - fx) * (T(1) - fy)) * vals[c]);
-            atomicAdd(pl + (size_t)imod(gy, p.ny) * p.nx + imod(gx + 1, p.nx),
-                      (fx * (T(1) - fy)) * vals[c]);
-            atomicAdd(pl + (size_t)imod(gy + 1, p.ny) * p.nx + imod(gx, p.nx),
-                      ((T(1) - fx) * fy) * vals[c]);
-            atomicAdd(pl + (size_t)imod(gy + 1, p.ny) * p.nx + imod(gx + 1, p.nx),
-                      (fx * fy) * vals[c]);
+            const int gy = (P.iy + (int)j0f) & my, gy1 = (gy + 1) & my;
+            atomicAdd(pl + (size_t)gy * p.nx + gx, ((T(1) - fx) * (T(1) - fy)) * vals[c]);
+            atomicAdd(pl + (size_t)gy * p.nx + gx1, (fx * (T(1) - fy)) * vals[c]);
+            atomicAdd(pl + (size_t)gy1 * p.nx + gx, ((T(1) - fx) * fy) * vals[c]);
+            atomicAdd(pl + (size_t)gy1 * p.nx + gx1, (fx * fy) * vals[c]);
           }
         }
         atomicExch(p.jflag + (size_t)s2 * p.nz + iz, 1);
@@ -760,13 +901,15 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   const int nxh = p.nx / 2;
   const int s1 = (int)(((k + 1) % p.ring + p.ring) % p.ring);
   const int s2 = (int)(((k + 2) % p.ring + p.ring) % p.ring);
-  const T h = T(p.h), Dl = T(p.delta_field);
+  const T h = s.cst[K_H], Dl = s.cst[K_DF];
   const long long sl = k - p.k0;                    // step index within this launch
+  const int plane = p.RB * p.nx;                    // elements of one component's rows
+  TIMER_DECL
 
   double acc[kNDiag];
 #pragma unroll
   for (int i = 0; i < kNDiag; ++i) acc[i] = 0.0;
-  double fe = 0.0;
+  T fe = T(0);
 
   // reset the next level's stored buckets and rejoin queues (free: their last reader, the
   // march of step k+1-ring, has completed)
@@ -778,10 +921,10 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   if (tid == 0) s.misc[0] = 0;
   __syncthreads();
   if (p.inject) {
-    const int per_row = p.nlayer / p.ny;          // particles per transverse row
+    const int per_row = p.nlayer >> p.logny;        // particles per transverse row
     const int nmine = per_row * p.RB;
     for (int i = tid; i < nmine; i += NT) {
-      // particle order within a row: species-major, then cell, then k (matches the layer index)
+      // particle order within a row: species-major, then cell, then k (the layer index)
       const int yl = i / per_row;
       int r = i - yl * per_row;
       int sp = 0;
@@ -790,7 +933,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         ++sp;
       }
       const int ix = r / p.ppc[sp], kk = r - ix * p.ppc[sp];
-      const int iy = me * p.RB + yl;
+      const int iy = (me << p.logRB) + yl;
       const int cell = iy * p.nx + ix;
       const unsigned long long g =
           (unsigned long long)(p.poff[sp] + cell * p.ppc[sp] + kk);
@@ -803,28 +946,28 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       s.puy[i] = T(0);
       s.puz[i] = T(0);
       s.psig[i] = T(0);
-      s.pq[i] = T(p.Qf[sp]);
+      s.pq[i] = s.cst[K_QF + sp];
     }
     if (tid == 0) s.misc[0] = nmine;
   }
   // ghost slice: field-free
   T* Fcur = s.F[0];
   T* Fnew = s.F[1];
-  for (int i = tid; i < 6 * p.RB * p.nx; i += NT) Fcur[i] = T(0);
-  for (int i = tid; i < 3 * p.RB * p.nx; i += NT) s.J[i] = T(0);
+  for (int i = tid; i < 6 * plane; i += NT) Fcur[i] = T(0);
+  for (int i = tid; i < 3 * plane; i += NT) s.J[i] = T(0);
 
   // per-mode carried state (one mode per thread)
   const int m = tid;
   const bool has_mode = m < p.M;
-  const int kxl = has_mode ? m / p.ny : 0, kyi = has_mode ? m % p.ny : 0;
-  const T kx = has_mode ? s.kx[me * p.KB + kxl] : T(0);
+  const int kxl = has_mode ? m >> p.logny : 0, kyi = has_mode ? m & (p.ny - 1) : 0;
+  const T kx = has_mode ? s.kx[(me << p.logKB) + kxl] : T(0);
   const T ky = has_mode ? s.ky[kyi] : T(0);
   const bool masked = p.ny > 1 && kyi == p.ny / 2;
   Mode6<T> S1;
   S1.Rx = S1.Ry = S1.Lx = S1.Ly = S1.Ez = S1.Bz = cx<T>(T(0), T(0));
   Cx<T> jpx = cx<T>(T(0), T(0)), jpy = jpx;       // j^1 at n + 3/2 (predictor of the last solve)
   Cx<T> o[6];                                     // old level, block n
-  Cx<T> j0px, j0py;                               // old level j at n + 1/2
+  Cx<T> j0px = jpx, j0py = jpx;                   // old level j at n + 1/2
   const Cx<T>* st = (const Cx<T>*)p.state;
   Cx<T>* stw = (Cx<T>*)p.state;
   auto blk = [&](int b, int c) -> size_t {
@@ -840,9 +983,11 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
 #pragma unroll
     for (int c = 0; c < 6; ++c) o[c] = ldcg(st + blk(nz - 1, c));
   }
+  const bool snap_step = p.snapshot && k == p.k0 + p.nsteps - 1;
 
   for (int n = nz - 1; n >= 0; --n) {
     // ---------------- A: streaming push from plane n+1 to plane n -----------------------
+    SliceAcc<T> sa{T(0), T(0), 0};
     {
       const int cnt0 = s.misc[0];
       for (int i = tid; i < cnt0; i += NT) {
@@ -858,7 +1003,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         P.sig = s.psig[i];
         P.q = s.pq[i];
         T fzt;
-        const bool trap = stream_push(cl, p, s, Fcur, P, h, me, fzt, acc);
+        const bool trap = stream_push(p, s, Fcur, P, h, me, fzt, sa);
         if (trap) {
           s.pcell[i] = -1;
           acc[DG_TRAP] += 1.0;
@@ -880,7 +1025,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         PState<T> P = store_read<T>(p.rq, p, ((size_t)s1 * nz + n) * p.bcap + e, fz);
         acc[DG_REJOIN] += 1.0;
         T fzt;
-        const bool trap = stream_push(cl, p, s, Fcur, P, fz * h, me, fzt, acc);
+        const bool trap = stream_push(p, s, Fcur, P, fz * h, me, fzt, sa);
         if (trap) {
           acc[DG_TRAP] += 1.0;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
@@ -901,6 +1046,10 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         }
       }
     }
+    acc[DG_KIN] += (double)sa.kin;
+    acc[DG_FLUX] += (double)sa.flux;
+    acc[DG_PUSH] += (double)sa.push;
+    TIMER_MARK(PH_A);
     // publish: iteration n+1 complete (its stored phase and this push have been issued)
     __syncthreads();
     if (tid == 0) {
@@ -910,38 +1059,40 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     cl.sync();                                                      // B1: deposits done
     if (p.P > 1 && me == 0 && tid == 0 && n + 1 <= nz - 1)
       st_release_u64(p.progress + cid, prog_value(k, nz, nz - (n + 1)));
-    // beam current of this level at the half-slice n + 1/2 (own rows)
-    {
-      const int* fl = p.jflag + (size_t)s1 * nz + n;
-      if (ldcg(fl)) {
-        T* jb = (T*)p.jbeam + (((size_t)s1 * nz + n) * 3) * (size_t)p.nx * p.ny;
-        for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
-          const int c = i / (p.RB * p.nx);
-          const int rem = i - c * p.RB * p.nx;
-          const size_t g = (size_t)c * p.nx * p.ny + (size_t)me * p.RB * p.nx + rem;
-          s.J[i] += ldcg(jb + g);
-          jb[g] = T(0);
-        }
+    TIMER_MARK(PH_B1);
+    // beam current of this level at the half-slice n + 1/2 (own rows); the flag is cleared
+    // by CTA 0 after B2, once every CTA has read it
+    if (ldcg(p.jflag + (size_t)s1 * nz + n)) {
+      T* jb = (T*)p.jbeam + (((size_t)s1 * nz + n) * 3) * (size_t)p.nx * p.ny;
+      for (int i = tid; i < 3 * plane; i += NT) {
+        const int c = i / plane;
+        const int rem = i - c * plane;
+        const size_t g = (size_t)c * p.nx * p.ny + ((size_t)me << p.logRB) * p.nx + rem;
+        s.J[i] += ldcg(jb + g);
+        jb[g] = T(0);
       }
     }
-    // (the flag is cleared by CTA 0 after B2, once every CTA has read it)
-    if (p.snapshot && k == p.k0 + p.nsteps - 1) {
+    if (snap_step) {
       T* sn = (T*)p.snap;
-      for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
-        const int c = i / (p.RB * p.nx);
-        const int rem = i - c * p.RB * p.nx;
-        sn[(((size_t)(6 + c) * nz + n) * p.ny + me * p.RB) * p.nx + rem] = s.J[i];
+      for (int i = tid; i < 3 * plane; i += NT) {
+        const int c = i / plane;
+        const int rem = i - c * plane;
+        sn[(((size_t)(6 + c) * nz + n) * p.ny + (me << p.logRB)) * p.nx + rem] = s.J[i];
       }
     }
     __syncthreads();
+    TIMER_MARK(PH_BEAM);
     // ---------------- B: row FFTs of the currents, transposed to the kx owners ------------
     forward_rows(cl, p, s, me, true);
+    TIMER_MARK(PH_FWD);
     cl.sync();                                                      // B2
     if (tid == 0 && me == 0) p.jflag[(size_t)s1 * nz + n] = 0;
+    TIMER_MARK(PH_B2);
     // ---------------- C: column FFTs, per-mode solve, inverse column FFTs ------------------
-    for (int i = tid; i < 3 * p.RB * p.nx; i += NT) s.J[i] = T(0);
+    for (int i = tid; i < 3 * plane; i += NT) s.J[i] = T(0);
     column_ffts(p, s, 0, 3, false);
     __syncthreads();
+    TIMER_MARK(PH_COLF);
     if (has_mode) {
       Cx<T> Jx = s.SC[((size_t)0 * p.KB + kxl) * p.ny + kyi];
       Cx<T> Jy = s.SC[((size_t)1 * p.KB + kxl) * p.ny + kyi];
@@ -995,30 +1146,37 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       }
     }
     __syncthreads();
+    TIMER_MARK(PH_SOLVE);
     column_ffts(p, s, 0, 6, true);
     __syncthreads();
+    TIMER_MARK(PH_COLI);
     scatter_to_rows(cl, p, s, me);
+    TIMER_MARK(PH_SCAT);
     if (waits && tid == 0 && me == 0)
       wait_for(p, pcid, prog_value(k - 1, nz, min(nz, nz - n + 3)));   // down to n-3
     cl.sync();                                                      // B3
+    TIMER_MARK(PH_B3);
     // ---------------- D: inverse rows -> real-space fields of slice n ----------------------
     inverse_rows(p, s, Fnew, fe);
+    TIMER_MARK(PH_INV);
     cl.sync();                                                      // B4: fields of slice n
+    TIMER_MARK(PH_B4);
     if (p.diag) {
       const int yc = p.ny / 2;
-      if (tid == 0 && yc / p.RB == me)
-        p.onaxis[sl * nz + n] = (double)Fnew[((size_t)2 * p.RB + (yc - me * p.RB)) * p.nx + nxh];
+      if (tid == 0 && (yc >> p.logRB) == me)
+        p.onaxis[sl * nz + n] = (double)Fnew[((size_t)2 * p.RB + (yc & (p.RB - 1))) * p.nx + nxh];
     }
-    if (p.snapshot && k == p.k0 + p.nsteps - 1) {
+    if (snap_step) {
       T* sn = (T*)p.snap;
-      for (int i = tid; i < 6 * p.RB * p.nx; i += NT) {
-        const int c = i / (p.RB * p.nx);
-        const int rem = i - c * p.RB * p.nx;
-        sn[(((size_t)c * nz + n) * p.ny + me * p.RB) * p.nx + rem] = Fnew[i];
+      for (int i = tid; i < 6 * plane; i += NT) {
+        const int c = i / plane;
+        const int rem = i - c * plane;
+        sn[(((size_t)c * nz + n) * p.ny + (me << p.logRB)) * p.nx + rem] = Fnew[i];
       }
     }
     // ---------------- E: stored particles of cell (zeta_n, zeta_{n+1}] along s -------------
-    stored_phase(cl, p, s, Fnew, Fcur, k, n, me, acc);
+    stored_phase(p, s, Fnew, Fcur, k, n, me, acc);
+    TIMER_MARK(PH_E);
     T* t = Fcur;
     Fcur = Fnew;
     Fnew = t;
@@ -1028,10 +1186,11 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   if (tid == 0) __threadfence();
   cl.sync();
   if (p.P > 1 && me == 0 && tid == 0) st_release_u64(p.progress + cid, prog_value(k, nz, nz));
+  TIMER_FLUSH;
 
   // diagnostics: per-CTA FP64 partials
   if (p.diag) {
-    acc[DG_FIELD] = fe;
+    acc[DG_FIELD] = (double)fe;
     for (int i = 0; i < kNDiag; ++i) {
       double v = acc[i];
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -1039,7 +1198,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     }
     __syncthreads();
     if (tid < kNDiag) {
-      const double hv = tid == DG_FIELD ? 0.5 * p.hx * p.hy * p.h : 1.0;
+      const double hv = tid == DG_FIELD ? 0.5 * p.hx * p.hy * p.h
+                        : tid == DG_FLUX ? p.hx * p.hy * p.h
+                                         : 1.0;
       p.diag_out[((size_t)sl * kNDiag + tid) * p.C + me] = s.dacc[tid] * hv;
       s.dacc[tid] = 0.0;
     }
@@ -1075,15 +1236,16 @@ __global__ void __launch_bounds__(512, 1)
   const int ncl = (int)(gridDim.x / p.C);
   Cx<T>* stw = (Cx<T>*)p.state;
   const double xc = 0.5 * p.nx * p.hx, yc = 0.5 * p.ny * p.hy;
+  const int plane = p.RB * p.nx;
   for (int n = cid; n < p.nz; n += ncl) {
     const double phi = n * p.h - zc;
     const double env = a0 * cos(phi) * exp(-phi * phi / (dur * dur));
-    for (int i = threadIdx.x; i < 3 * p.RB * p.nx; i += blockDim.x) {
-      const int c = i / (p.RB * p.nx);
-      const int rem = i - c * p.RB * p.nx;
+    for (int i = threadIdx.x; i < 3 * plane; i += blockDim.x) {
+      const int c = i / plane;
+      const int rem = i - c * plane;
       const int yl = rem / p.nx, x = rem - yl * p.nx;
       const double dx = x * p.hx - xc;
-      const double dy = p.ny > 1 ? (me * p.RB + yl) * p.hy - yc : 0.0;
+      const double dy = p.ny > 1 ? ((me << p.logRB) + yl) * p.hy - yc : 0.0;
       const double E = env * exp(-(dy * dy + dx * dx) / (waist * waist));
       s.J[i] = (c == 2) ? T(2.0 * E) : T(0);
     }
@@ -1093,7 +1255,7 @@ __global__ void __launch_bounds__(512, 1)
     column_ffts(p, s, 2, 3, false);
     __syncthreads();
     for (int m = threadIdx.x; m < p.M; m += blockDim.x) {
-      const int kxl = m / p.ny, kyi = m % p.ny;
+      const int kxl = m >> p.logny, kyi = m & (p.ny - 1);
       Cx<T> v = s.SC[((size_t)2 * p.KB + kxl) * p.ny + kyi];
       if (p.ny > 1 && kyi == p.ny / 2) v = cx<T>(T(0), T(0));
       const Cx<T> z = cx<T>(T(0), T(0));
@@ -1149,7 +1311,7 @@ int smem_layout(Params& p, int eb) {
   p.o_work = o;
   o += align16(p.nwork * p.nx * 2 * eb);
   p.o_tw = o;
-  o += align16((nxh + nyh + nxh + p.ny) * 2 * eb + (nxh + p.ny) * eb);
+  o += align16((nxh + nyh + nxh + p.ny) * 2 * eb + (nxh + p.ny + 32) * eb);
   p.o_part = o;
   o += align16(p.pcap * 4) + 7 * align16(p.pcap * eb) + 16 * 7;
   p.o_misc = o;

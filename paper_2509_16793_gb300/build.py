@@ -19,6 +19,9 @@ LIB = os.path.join(PKG, "libgempic.so")
 SOURCES = ["gempic_kernels.cu", "gempic_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         # FP32 only: flush denormals, approximate division and square root (<= 2 ulp);
+         # FP64 arithmetic is unaffected
+         "-ftz=true", "-prec-div=false", "-prec-sqrt=false",
          "--expt-relaxed-constexpr", "-I", os.path.join(ROOT, "include")]
 
 

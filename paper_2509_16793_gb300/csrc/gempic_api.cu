@@ -250,6 +250,7 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     off += g.nx * g.ny * sp.ppc;
   }
   p.nlayer = off;
+  p.ppc_sum = ppc_sum;
 
   // launch shape: C CTAs per cluster own ny/C rows and (nx/2)/C kx columns; one spectral
   // mode per thread (M <= 512).

@@ -37,7 +37,7 @@ struct Params {
   int nthreads;
   // physics
   double hx, hy, h, delta, delta_field;
-  int nspecies, nlayer;
+  int nspecies, nlayer, ppc_sum;
   double qm[kMaxSpecies];         // q/m
   double wd[kMaxSpecies];         // (rho - j_z) weight Q_f/(hx hy Delta) of a fresh particle
   double Qf[kMaxSpecies];         // fresh macroparticle charge q n hx hy Delta/ppc

@@ -171,14 +171,22 @@ __device__ __forceinline__ double uniform24(unsigned long long s, unsigned long 
 }
 
 // ------------------------------------------------------------------------------------------
-// warp-level radix-2 FFT on shared memory (length N = 2^logN, unnormalised).
-// tw[k] = exp(-2 pi i k / N), k < N/2.  inverse: conjugate twiddles.
+// warp-level FFTs on shared memory (length N = 2^logN, unnormalised, in place).
+// tw[k] = exp(-2 pi i k / N), k < N/2; inverse: conjugate twiddles.
 // ------------------------------------------------------------------------------------------
 template <typename T>
-__device__ void warp_fft(Cx<T>* d, int logN, const Cx<T>* tw, bool inverse) {
+__device__ __forceinline__ Cx<T> twiddle(const Cx<T>* tw, int N, int m, bool inverse) {
+  m &= N - 1;
+  Cx<T> w = m < (N >> 1) ? tw[m] : cx<T>(-tw[m - (N >> 1)].re, -tw[m - (N >> 1)].im);
+  if (inverse) w.im = -w.im;
+  return w;
+}
+
+// radix-2, any N = 2^logN (used for N < 32 and N > 256)
+template <typename T>
+__device__ void warp_fft_r2(Cx<T>* d, int logN, const Cx<T>* tw, bool inverse) {
   const int N = 1 << logN;
   const int lane = threadIdx.x & 31;
-  if (N == 1) return;
   for (int i = lane; i < N; i += 32) {
     const int r = (int)(__brev((unsigned)i) >> (32 - logN));
     if (i < r) {
@@ -204,6 +212,80 @@ __device__ void warp_fft(Cx<T>* d, int logN, const Cx<T>* tw, bool inverse) {
       d[i1] = u - t;
     }
     __syncwarp();
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ Cx<T> shfl_xor_cx(Cx<T> v, int m) {
+  return cx<T>(__shfl_xor_sync(0xffffffffu, v.re, m), __shfl_xor_sync(0xffffffffu, v.im, m));
+}
+
+// N = 32 R: lane l holds x[l + 32 r]; R-point DFT in registers, twiddle W_N^{l k2}, then a
+// 32-point decimation-in-frequency DFT across the lanes (shuffles); X[k2 + R k1] ends in
+// lane bitrev5(k1).
+template <typename T, int R>
+__device__ void warp_fft_reg(Cx<T>* d, const Cx<T>* tw, bool inverse) {
+  constexpr int N = 32 * R;
+  const int l = threadIdx.x & 31;
+  Cx<T> a[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) a[r] = d[l + 32 * r];
+  // R-point DFT over r (radix-2, decimation in time on bit-reversed inputs)
+  if (R > 1) {
+    constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : 3;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int rr = (int)(__brev((unsigned)r) >> (32 - LR));
+      if (r < rr) {
+        Cx<T> t = a[r];
+        a[r] = a[rr];
+        a[rr] = t;
+      }
+    }
+#pragma unroll
+    for (int s = 1; s <= LR; ++s) {
+      const int half = 1 << (s - 1);
+#pragma unroll
+      for (int b = 0; b < R / 2; ++b) {
+        const int grp = b >> (s - 1), j = b & (half - 1);
+        const int i0 = grp * (half << 1) + j, i1 = i0 + half;
+        const Cx<T> w = twiddle(tw, N, j * (N / (half << 1)), inverse);
+        const Cx<T> t = w * a[i1];
+        const Cx<T> u = a[i0];
+        a[i0] = u + t;
+        a[i1] = u - t;
+      }
+    }
+#pragma unroll
+    for (int k2 = 1; k2 < R; ++k2) a[k2] = twiddle(tw, N, l * k2, inverse) * a[k2];
+  }
+  // 32-point DFT across lanes
+#pragma unroll
+  for (int half = 16; half >= 1; half >>= 1) {
+    const bool bottom = (l & half) != 0;
+    const Cx<T> w = twiddle(tw, N, (l & (half - 1)) * (16 / half) * R, inverse);
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) {
+      const Cx<T> o = shfl_xor_cx(a[k2], half);
+      a[k2] = bottom ? w * (o - a[k2]) : a[k2] + o;
+    }
+  }
+  __syncwarp();
+  const int k1 = (int)(__brev((unsigned)l) >> 27);
+#pragma unroll
+  for (int k2 = 0; k2 < R; ++k2) d[k2 + R * k1] = a[k2];
+  __syncwarp();
+}
+
+template <typename T>
+__device__ void warp_fft(Cx<T>* d, int logN, const Cx<T>* tw, bool inverse) {
+  switch (logN) {
+    case 0: return;
+    case 5: warp_fft_reg<T, 1>(d, tw, inverse); return;
+    case 6: warp_fft_reg<T, 2>(d, tw, inverse); return;
+    case 7: warp_fft_reg<T, 4>(d, tw, inverse); return;
+    case 8: warp_fft_reg<T, 8>(d, tw, inverse); return;
+    default: warp_fft_r2(d, logN, tw, inverse); return;
   }
 }
 
@@ -924,15 +1006,18 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     const int per_row = p.nlayer >> p.logny;        // particles per transverse row
     const int nmine = per_row * p.RB;
     for (int i = tid; i < nmine; i += NT) {
-      // particle order within a row: species-major, then cell, then k (the layer index)
-      const int yl = i / per_row;
-      int r = i - yl * per_row;
+      // storage order: segments of nx particles with fixed (row, species, k); inside a segment
+      // position j holds cell ix = 5 j mod nx, so the 32 lanes of a warp deposit into cells 5
+      // apart (disjoint stencils, distinct shared-memory banks)
+      const int seg = i >> p.lognx, j = i & (p.nx - 1);
+      const int yl = seg / p.ppc_sum;
+      int kk = seg - yl * p.ppc_sum;
       int sp = 0;
-      while (sp + 1 < p.nspecies && r >= p.ppc[sp] * p.nx) {
-        r -= p.ppc[sp] * p.nx;
+      while (sp + 1 < p.nspecies && kk >= p.ppc[sp]) {
+        kk -= p.ppc[sp];
         ++sp;
       }
-      const int ix = r / p.ppc[sp], kk = r - ix * p.ppc[sp];
+      const int ix = (5 * j) & (p.nx - 1);
       const int iy = (me << p.logRB) + yl;
       const int cell = iy * p.nx + ix;
       const unsigned long long g =

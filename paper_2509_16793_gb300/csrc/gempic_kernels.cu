@@ -387,7 +387,7 @@ __device__ void load_tables(const Params& p, const Sm<T>& s) {
 // phase timers (profiling builds only)
 // ------------------------------------------------------------------------------------------
 enum Phase { PH_A = 0, PH_B1, PH_BEAM, PH_FWD, PH_B2, PH_COLF, PH_SOLVE, PH_COLI, PH_SCAT, PH_B3,
-             PH_INV, PH_B4, PH_E, PH_N };
+             PH_INV, PH_B4, PH_E, PH_AG, PH_AM, PH_AD, PH_N };
 #ifdef GEMPIC_PHASE_TIMERS
 #define TIMER_DECL long long t_last = clock64(); long long t_acc[PH_N] = {0};
 #define TIMER_MARK(ph)                      \
@@ -398,9 +398,20 @@ enum Phase { PH_A = 0, PH_B1, PH_BEAM, PH_FWD, PH_B2, PH_COLF, PH_SOLVE, PH_COLI
   } while (0)
 #define TIMER_FLUSH                                                                      \
   do {                                                                                   \
-    if (threadIdx.x == 0 && p.timers)                                                    \
-      for (int i_ = 0; i_ < PH_N; ++i_)                                                  \
+    if (threadIdx.x == 0 && p.timers) {                                                  \
+      for (int i_ = 0; i_ < PH_AG; ++i_)                                                 \
         atomicAdd(p.timers + i_, (unsigned long long)t_acc[i_]);                         \
+      for (int i_ = PH_AG; i_ < PH_N; ++i_)                                              \
+        atomicAdd(p.timers + i_, (unsigned long long)g_sub[i_ - PH_AG]);                 \
+    }                                                                                    \
+  } while (0)
+// sub-phases of the push (gather / push arithmetic / deposit), thread 0 only
+#define SUB_DECL long long s_t0 = clock64();
+#define SUB_MARK(i)                                   \
+  do {                                                \
+    const long long s_t1 = clock64();                 \
+    if (threadIdx.x == 0) sub[i] += s_t1 - s_t0;      \
+    s_t0 = s_t1;                                      \
   } while (0)
 #else
 #define TIMER_DECL
@@ -408,6 +419,10 @@ enum Phase { PH_A = 0, PH_B1, PH_BEAM, PH_FWD, PH_B2, PH_COLF, PH_SOLVE, PH_COLI
   do {                 \
   } while (0)
 #define TIMER_FLUSH \
+  do {              \
+  } while (0)
+#define SUB_DECL
+#define SUB_MARK(i) \
   do {              \
   } while (0)
 #endif
@@ -723,9 +738,11 @@ struct SliceAcc {     // per-thread, per-slice diagnostics in the working precis
 
 template <typename T>
 __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PState<T>& P, T d,
-                            int me, T& fz_trap, SliceAcc<T>& acc) {
+                            int me, T& fz_trap, SliceAcc<T>& acc, long long* sub) {
+  SUB_DECL
   T E[6];
   gather6(p, Fcur, P.ix, P.fx, P.iy, P.fy, me, E);
+  SUB_MARK(0);
   const T D = s.cst[K_D];
   const T invh = s.cst[K_INVH];
   const T qm = s.cst[K_QM + P.sp];
@@ -750,8 +767,10 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   const T w = P.q * s.cst[K_WSCALE];
   const T X1 = P.fx + dx * s.cst[K_INVHX];
   const T Y1 = p.ny > 1 ? P.fy + dy * s.cst[K_INVHY] : P.fy;
+  SUB_MARK(1);
   esirkepov(p, s, P.ix, P.iy, P.fx, P.fy, X1, Y1, w, dy, me);
   cic_add(p, s, 2, P.ix, P.iy, X1, Y1, w * ds * invh, me);
+  SUB_MARK(2);
   // diagnostics: kinetic energy N m (gamma-1) dt/Delta, (rho - j_z) flux through plane n
   const T dtl = hc * gn / den;
   acc.kin += P.q * s.cst[K_MOQ + P.sp] * (gn - T(1)) * dtl / D;
@@ -986,6 +1005,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   const T h = s.cst[K_H], Dl = s.cst[K_DF];
   const long long sl = k - p.k0;                    // step index within this launch
   const int plane = p.RB * p.nx;                    // elements of one component's rows
+  long long g_sub[3] = {0, 0, 0};
   TIMER_DECL
 
   double acc[kNDiag];
@@ -1088,7 +1108,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         P.sig = s.psig[i];
         P.q = s.pq[i];
         T fzt;
-        const bool trap = stream_push(p, s, Fcur, P, h, me, fzt, sa);
+        const bool trap = stream_push(p, s, Fcur, P, h, me, fzt, sa, g_sub);
         if (trap) {
           s.pcell[i] = -1;
           acc[DG_TRAP] += 1.0;
@@ -1110,7 +1130,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         PState<T> P = store_read<T>(p.rq, p, ((size_t)s1 * nz + n) * p.bcap + e, fz);
         acc[DG_REJOIN] += 1.0;
         T fzt;
-        const bool trap = stream_push(p, s, Fcur, P, fz * h, me, fzt, sa);
+        const bool trap = stream_push(p, s, Fcur, P, fz * h, me, fzt, sa, g_sub);
         if (trap) {
           acc[DG_TRAP] += 1.0;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);

@@ -181,6 +181,31 @@ int64_t gempic_launch_count(const struct gempic_sim* sim);
 gempic_status gempic_launch_shape(const struct gempic_sim* sim, int32_t* cluster_ctas,
                                   int32_t* threads, int32_t* smem_bytes, int32_t* pipeline);
 
+/* Allocation-free s-step.  The paper has no counterpart: this entry point is for callers that
+ * cannot allocate device memory -- for example code whose host application owns every device
+ * allocation under a fixed budget, or a plug-in that is not allowed to call cudaMalloc.
+ * It advances the caller's spectral state by the s-step numbered `step` (0 for the first
+ * s-step; it selects the fresh-particle offsets) and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   state        device memory owned by the caller, layout of gempic_get_state, updated in
+ *                place; state_bytes must cover it.  There is no laser set-up here: pass a
+ *                state prepared elsewhere (e.g. copied out with gempic_get_state).
+ *   cfg          grid, delta, precision, seed, species, cluster_ctas and cuda_stream are
+ *                used; laser, flags, capacities and pipeline_depth are ignored.
+ *   diag_out     host, may be NULL: diagnostics of the step.
+ *   onaxis_out   host, may be NULL: nzeta doubles of on-axis E_z.
+ * Working memory: one 256 KiB array in device memory, declared at file scope in the library;
+ * every GPU that loads the library holds it until the process exits.  Limits: nx, ny <= 1024,
+ * nzeta <= 4096, at most 16 CTAs per cluster; larger sizes return GEMPIC_EINVAL before any
+ * work.  The first call on a device looks up the array's device address (set-up); make that
+ * first call before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (each call clears what must start at zero): calls that overlap on the GPU,
+ * from several streams or threads, race -- serialise them.  There is no stored-particle
+ * store: if a particle is trapped during the step the state is still advanced, the trapped
+ * particle is dropped, and GEMPIC_EOVERFLOW is returned.  The call waits for its stream. */
+gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t step, void* state,
+                                  size_t state_bytes, gempic_diag* diag_out, double* onaxis_out);
+
 const char* gempic_strerror(gempic_status s);
 
 void gempic_destroy(struct gempic_sim* sim);

@@ -79,5 +79,9 @@ cudaError_t launch_laser_init(int precision, const Params& p, double a0, double 
 cudaError_t launch_export_state(int precision, const Params& p, void* dst, cudaStream_t s);
 cudaError_t launch_import_state(int precision, const Params& p, const void* src, cudaStream_t s);
 cudaError_t max_active_clusters(int precision, const Params& p, int* n);
+// allocation-free entry point: march on a caller's state in the public layout
+cudaError_t configure_march_canon(int precision, int smem_bytes);
+cudaError_t launch_march_canon(int precision, const Params& p, cudaStream_t s);
+cudaError_t launch_tables(int precision, const Params& p, void* dst, cudaStream_t s);
 
 }  // namespace gempic

@@ -990,7 +990,10 @@ __device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
 // ------------------------------------------------------------------------------------------
 // the march of one s-step k (computes level k+1)
 // ------------------------------------------------------------------------------------------
-template <typename T>
+// CANON = false: the library's block layout [nz+1][C][6][M].  CANON = true: the public layout
+// of gempic_get_state ([6][nz][ny][nx/2]; j at half-slice index n <-> block n+1), used by the
+// allocation-free entry point on a caller's buffer.
+template <typename T, bool CANON = false>
 __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& cl, long long k,
                       int cid) {
   const int me = (int)cl.block_rank();
@@ -1076,7 +1079,21 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   const Cx<T>* st = (const Cx<T>*)p.state;
   Cx<T>* stw = (Cx<T>*)p.state;
   auto blk = [&](int b, int c) -> size_t {
-    return (((size_t)b * p.C + me) * 6 + c) * (size_t)p.M + m;
+    if constexpr (CANON) {
+      const int kxg = (me << p.logKB) + kxl;
+      const int sl_ = c < 4 ? b : b - 1;
+      return (((size_t)c * p.nz + sl_) * p.ny + kyi) * (size_t)nxh + kxg;
+    } else {
+      return (((size_t)b * p.C + me) * 6 + c) * (size_t)p.M + m;
+    }
+  };
+  // the public layout has no ghost slice and no j at half-slice -1
+  auto blk_ok = [&](int b, int c) -> bool {
+    if constexpr (CANON) {
+      return c < 4 ? b < p.nz : b >= 1;
+    } else {
+      return true;
+    }
   };
 
   if (waits && tid == 0 && me == 0)
@@ -1210,10 +1227,12 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         S1.Ry = S1.Ry - (T(0.25) * Dl) * (Jy - jpy);
       }
       // new level, block n+1 = {R, E_z, B_z at slice n+1; j at n+1/2}
-      stw[blk(n + 1, 0)] = S1.Rx;
-      stw[blk(n + 1, 1)] = S1.Ry;
-      stw[blk(n + 1, 2)] = S1.Ez;
-      stw[blk(n + 1, 3)] = S1.Bz;
+      if (blk_ok(n + 1, 0)) {
+        stw[blk(n + 1, 0)] = S1.Rx;
+        stw[blk(n + 1, 1)] = S1.Ry;
+        stw[blk(n + 1, 2)] = S1.Ez;
+        stw[blk(n + 1, 3)] = S1.Bz;
+      }
       stw[blk(n + 1, 4)] = Jx;
       stw[blk(n + 1, 5)] = Jy;
       // old level at slice n; j^0 at n -/+ 1/2
@@ -1247,7 +1266,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         stw[blk(0, 3)] = S0.Bz;
       } else {
 #pragma unroll
-        for (int c = 0; c < 6; ++c) o[c] = ldcg(st + blk(n - 1, c));
+        for (int c = 0; c < 6; ++c)
+          o[c] = blk_ok(n - 1, c) ? ldcg(st + blk(n - 1, c)) : cx<T>(T(0), T(0));
       }
     }
     __syncthreads();
@@ -1313,7 +1333,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   }
 }
 
-template <typename T>
+template <typename T, bool CANON = false>
 __global__ void __launch_bounds__(512, 1) march_kernel(const Params p) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -1322,7 +1342,34 @@ __global__ void __launch_bounds__(512, 1) march_kernel(const Params p) {
   if (threadIdx.x < kNDiag) s.dacc[threadIdx.x] = 0.0;
   __syncthreads();
   const int cid = (int)(blockIdx.x / p.C);
-  for (long long k = p.k0 + cid; k < p.k0 + p.nsteps; k += p.P) march<T>(p, s, cl, k, cid);
+  for (long long k = p.k0 + cid; k < p.k0 + p.nsteps; k += p.P) march<T, CANON>(p, s, cl, k, cid);
+}
+
+// tables of the allocation-free entry point, built on the device (same formulas as the host
+// tables of gempic_create): twx, twy, shx, shy (complex), kx, ky (real)
+template <typename T>
+__global__ void tables_kernel(const Params p, void* dst) {
+  const double pi = 3.14159265358979323846;
+  const int nxh = p.nx / 2, nyh = p.ny > 1 ? p.ny / 2 : 1;
+  Cx<T>* c = (Cx<T>*)dst;
+  T* r = (T*)(c + nxh + nyh + nxh + p.ny);
+  for (int i = threadIdx.x; i < nxh; i += blockDim.x) {
+    const double a = -2 * pi * i / p.nx;
+    c[i] = cx<T>(T(cos(a)), T(sin(a)));
+    const double kx = 2 * pi * i / (p.nx * p.hx);
+    c[nxh + nyh + i] = cx<T>(T(cos(-0.5 * kx * p.hx)), T(sin(-0.5 * kx * p.hx)));
+    r[i] = T(kx);
+  }
+  for (int j = threadIdx.x; j < nyh; j += blockDim.x) {
+    const double a = p.ny > 1 ? -2 * pi * j / p.ny : 0.0;
+    c[nxh + j] = cx<T>(T(cos(a)), T(sin(a)));
+  }
+  for (int j = threadIdx.x; j < p.ny; j += blockDim.x) {
+    const int f = (p.ny == 1) ? 0 : (j < (p.ny + 1) / 2 ? j : j - p.ny);
+    const double ky = 2 * pi * (double)f / ((double)p.ny * p.hy);
+    c[nxh + nyh + nxh + j] = cx<T>(T(cos(-0.5 * ky * p.hy)), T(sin(-0.5 * ky * p.hy)));
+    r[nxh + j] = T(ky);
+  }
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1488,6 +1535,36 @@ cudaError_t launch_import_state(int precision, const Params& p, const void* src,
     export_kernel<double><<<264, 256, 0, s>>>(p, (Cx<double>*)p.state, (const Cx<double>*)src, 1);
   else
     export_kernel<float><<<264, 256, 0, s>>>(p, (Cx<float>*)p.state, (const Cx<float>*)src, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t configure_march_canon(int precision, int smem) {
+  if (precision == 64) {
+    cudaError_t e = cudaFuncSetAttribute(march_kernel<double, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(march_kernel<double, true>,
+                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  }
+  cudaError_t e = cudaFuncSetAttribute(march_kernel<float, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(march_kernel<float, true>,
+                              cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+}
+
+cudaError_t launch_march_canon(int precision, const Params& p, cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t c = make_cfg(p, 1, s, attr);
+  if (precision == 64) return cudaLaunchKernelEx(&c, march_kernel<double, true>, p);
+  return cudaLaunchKernelEx(&c, march_kernel<float, true>, p);
+}
+
+cudaError_t launch_tables(int precision, const Params& p, void* dst, cudaStream_t s) {
+  if (precision == 64)
+    tables_kernel<double><<<1, 256, 0, s>>>(p, dst);
+  else
+    tables_kernel<float><<<1, 256, 0, s>>>(p, dst);
   return cudaGetLastError();
 }
 

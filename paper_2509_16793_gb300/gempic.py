@@ -82,6 +82,8 @@ SIGNATURES = {
     "gempic_get_onaxis_ez": (c_int32, [c_void_p, c_void_p, c_int32]),
     "gempic_launch_count": (c_int64, [c_void_p]),
     "gempic_launch_shape": (c_int32, [c_void_p] + [POINTER(c_int32)] * 4),
+    "gempic_step_noalloc": (c_int32, [POINTER(gempic_config), c_int64, c_void_p, c_size_t,
+                                       POINTER(gempic_diag), c_void_p]),
     "gempic_strerror": (c_char_p, [c_int32]),
     "gempic_destroy": (None, [c_void_p]),
 }
@@ -143,6 +145,21 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
         stored_bucket_capacity=bucket_capacity, particle_headroom=headroom,
         pipeline_depth=pipeline_depth, reserved=0, cuda_stream=stream)
     return cfg, (sp, las)
+
+
+def gempic_step_noalloc(w, step: int, state, onaxis: bool = False, stream: Optional[int] = None,
+                        cluster_ctas: int = 0):
+    """One allocation-free s-step on a caller-owned device state (torch tensor in the layout of
+    gempic_get_state).  Returns (status, diagnostics dict, on-axis E_z or None)."""
+    lib = load()
+    cfg, keep = config_from_workload(w, cluster_ctas=cluster_ctas, stream=stream)
+    d = gempic_diag()
+    ez = np.empty(w.nzeta) if onaxis else None
+    st = lib.gempic_step_noalloc(byref(cfg), step, state.data_ptr(),
+                                 state.numel() * state.element_size(), byref(d),
+                                 ez.ctypes.data if ez is not None else None)
+    del keep
+    return st, d.as_dict(), ez
 
 
 class Sim:

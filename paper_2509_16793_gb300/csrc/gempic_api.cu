@@ -250,6 +250,16 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     off += g.nx * g.ny * sp.ppc;
   }
   p.nlayer = off;
+  {
+    // fixed-point range of the FP32 deposit: 4 x the largest (rho - j_z) weight times the
+    // largest transverse cell-to-slice ratio; a larger contribution takes the float path
+    double wmax = 0.0;
+    for (int i = 0; i < cfg->nspecies; ++i)
+      wmax = std::max(wmax, std::fabs(cfg->species[i].charge * cfg->species[i].density /
+                                      cfg->species[i].ppc));
+    const double ratio = std::max(1.0, std::max(g.hx, g.hy) / g.h);
+    p.jref = wmax > 0 ? 4.0 * wmax * ratio : 1.0;
+  }
   p.ppc_sum = ppc_sum;
 
   // launch shape: C CTAs per cluster own ny/C rows and (nx/2)/C kx columns; one spectral
@@ -268,6 +278,8 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
   for (int cand = (C > 0 ? C : 1); cand <= (C > 0 ? C : 16); cand *= 2) {
     if (g.ny % cand || nxh % cand) continue;
     if (g.ny == 1 && cand != 1) continue;
+    // 3-D bands need two rows or more (the current halo reaches two rows above the band)
+    if (g.ny > 1 && g.ny / cand < 2) continue;
     const int RB = g.ny / cand, KB = nxh / cand, M = KB * g.ny;
     if (M > 512) continue;
     const int fresh = RB * g.nx * ppc_sum;
@@ -283,7 +295,6 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     p.logKB = ilog2(KB);
     p.M = M;
     p.nthreads = NT;
-    p.nwork = std::min(NT / 32, 3 * RB);
     for (;;) {
       p.pcap = fresh + head;
       if (gempic::smem_layout(p, s->eb) <= smem_optin) {
@@ -378,6 +389,10 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     }
     ALLOC(p.jbeam, ring * g.nzeta * 3 * nperp * eb);
     ALLOC(p.jflag, ring * g.nzeta * sizeof(int));
+    // overflow particle slots: bands that gain particles (radial expulsion, rejoining stored
+    // particles) spill beyond their shared-memory capacity into these
+    p.gcap = std::max(1024, g.nx * (g.ny / p.C) * std::max(ppc_sum, 1) * 2);
+    ALLOC(p.pover, (size_t)std::max(s->pmax, 1) * p.C * p.gcap * (4 + 7 * eb));
     if (p.snapshot) ALLOC(p.snap, (size_t)9 * g.nzeta * nperp * eb);
 #ifdef GEMPIC_PHASE_TIMERS
     ALLOC(p.timers, 64 * sizeof(unsigned long long));
@@ -615,6 +630,12 @@ gempic_status gempic_get_onaxis_ez(gempic_sim* s, double* dst, int32_t n) {
 int64_t gempic_launch_count(const gempic_sim* s) { return s ? s->launches : 0; }
 
 #ifdef GEMPIC_PHASE_TIMERS
+// profiling builds only: the raw device error word
+int gempic_debug_error_word(gempic_sim* s) {
+  int err = -1;
+  if (cudaMemcpy(&err, s->p.err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return -2;
+  return err;
+}
 // profiling builds only: accumulated clock64 cycles per march phase (thread 0 of each CTA)
 gempic_status gempic_phase_timers(gempic_sim* s, unsigned long long* out, int32_t n) {
   if (!s || !out || n < 1) return GEMPIC_EINVAL;

@@ -33,10 +33,14 @@ struct Params {
   // grid and decomposition
   int nx, ny, nz;                 // transverse nodes, slices
   int C, RB, KB, M;               // CTAs per cluster, rows per CTA, kx per CTA, modes per CTA
+  int FR, JR, JOFF;               // field rows per CTA (own + halo above), current rows (own +
+                                  // halo below/above), row offset of own row 0 in the currents
   int lognx, logny, logRB, logKB;
   int nthreads;
   // physics
   double hx, hy, h, delta, delta_field;
+  double jref;                    // FP32 deposit: contributions below jref add in 32-bit fixed
+                                  // point with resolution jref / 2^22 (exact integer sums)
   int nspecies, nlayer, ppc_sum;
   double qm[kMaxSpecies];         // q/m
   double wd[kMaxSpecies];         // (rho - j_z) weight Q_f/(hx hy Delta) of a fresh particle
@@ -49,12 +53,15 @@ struct Params {
   int nsteps;                     // marches in this launch
   int P;                          // concurrent marches (clusters)
   int inject, diag, snapshot;
-  int pcap;                       // streaming particle slots per CTA
+  int pcap;                       // streaming particle slots per CTA in shared memory
+  int gcap;                       // further slots per CTA in global memory (overflow)
   int bcap, ring;                 // stored bucket capacity, ring of s-levels
   int wait_spin_limit;            // bounded wait: polls before giving up
   int nwork;                      // FFT work rows per CTA
+  int mig_cap;                    // migrating particles a CTA can receive per slice
   // shared-memory layout (byte offsets)
-  int o_f0, o_f1, o_j, o_sr, o_sc, o_work, o_tw, o_part, o_misc, smem_bytes;
+  int o_f0, o_f1, o_j, o_recv, o_sr, o_sc, o_workB, o_workD, o_tw, o_inbox, o_part, o_misc,
+      smem_bytes;
   // device memory
   void* state;                    // blocks [nz+1][C][6][M] complex
   unsigned long long* progress;   // [P] completed-iteration counters
@@ -67,6 +74,7 @@ struct Params {
   double* diag_out;               // [nsteps][kNDiag][C]
   double* onaxis;                 // [nsteps][nz]
   void* snap;                     // [9][nz][ny][nx]
+  void* pover;                    // overflow particle slots [P*C][int cell; 7 reals][gcap]
   unsigned long long* timers;     // phase timers (builds with GEMPIC_PHASE_TIMERS only)
 };
 

@@ -27,6 +27,7 @@
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "gempic_internal.h"
@@ -145,16 +146,19 @@ __device__ __forceinline__ double ldc(uint32_t a, double) {
   return v;
 }
 __device__ __forceinline__ void red_local(uint32_t a, float v) {
-  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(a), "f"(v));
 }
 __device__ __forceinline__ void red_local(uint32_t a, double v) {
-  asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+  asm volatile("red.shared.add.f64 [%0], %1;" ::"r"(a), "d"(v));
+}
+__device__ __forceinline__ void red_local_u32(uint32_t a, int v) {
+  asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
 }
 __device__ __forceinline__ void red_cluster(uint32_t a, float v) {
-  asm volatile("red.shared::cluster.add.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+  asm volatile("red.shared::cluster.add.f32 [%0], %1;" ::"r"(a), "f"(v));
 }
 __device__ __forceinline__ void red_cluster(uint32_t a, double v) {
-  asm volatile("red.shared::cluster.add.f64 [%0], %1;" ::"r"(a), "d"(v) : "memory");
+  asm volatile("red.shared::cluster.add.f64 [%0], %1;" ::"r"(a), "d"(v));
 }
 
 // Counter-based SplitMix64 (Steele, Lea, Flood 2014): output c of the stream seeded with s.
@@ -277,6 +281,96 @@ __device__ void warp_fft_reg(Cx<T>* d, const Cx<T>* tw, bool inverse) {
   __syncwarp();
 }
 
+// One or two transforms per warp with the layout of warp_fft_reg, reading element j of
+// transform t through ld(t, j) and writing element k through st(t, k, value); the second
+// transform (t1 >= 0) runs interleaved with the first for instruction-level parallelism.
+template <typename T, int R, bool PAIR, typename LD, typename ST>
+__device__ __forceinline__ void wfft2(const LD& ld, const ST& st, int t0, int t1,
+                                      const Cx<T>* tw, bool inverse) {
+  constexpr int N = 32 * R;
+  const int l = threadIdx.x & 31;
+  const bool two = PAIR && t1 >= 0;
+  Cx<T> a[R], b[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    a[r] = ld(t0, l + 32 * r);
+    b[r] = two ? ld(t1, l + 32 * r) : a[r];
+  }
+  if (R > 1) {
+    constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : 3;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int rr = (int)(__brev((unsigned)r) >> (32 - LR));
+      if (r < rr) {
+        Cx<T> t = a[r];
+        a[r] = a[rr];
+        a[rr] = t;
+        t = b[r];
+        b[r] = b[rr];
+        b[rr] = t;
+      }
+    }
+#pragma unroll
+    for (int s = 1; s <= LR; ++s) {
+      const int half = 1 << (s - 1);
+#pragma unroll
+      for (int q = 0; q < R / 2; ++q) {
+        const int grp = q >> (s - 1), j = q & (half - 1);
+        const int i0 = grp * (half << 1) + j, i1 = i0 + half;
+        const Cx<T> w = twiddle(tw, N, j * (N / (half << 1)), inverse);
+        const Cx<T> ta = w * a[i1], tb = w * b[i1];
+        const Cx<T> ua = a[i0], ub = b[i0];
+        a[i0] = ua + ta;
+        a[i1] = ua - ta;
+        b[i0] = ub + tb;
+        b[i1] = ub - tb;
+      }
+    }
+#pragma unroll
+    for (int k2 = 1; k2 < R; ++k2) {
+      const Cx<T> w = twiddle(tw, N, l * k2, inverse);
+      a[k2] = w * a[k2];
+      b[k2] = w * b[k2];
+    }
+  }
+#pragma unroll
+  for (int half = 16; half >= 1; half >>= 1) {
+    const bool bottom = (l & half) != 0;
+    const Cx<T> w = twiddle(tw, N, (l & (half - 1)) * (16 / half) * R, inverse);
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) {
+      const Cx<T> oa = shfl_xor_cx(a[k2], half);
+      const Cx<T> ob = shfl_xor_cx(b[k2], half);
+      a[k2] = bottom ? w * (oa - a[k2]) : a[k2] + oa;
+      b[k2] = bottom ? w * (ob - b[k2]) : b[k2] + ob;
+    }
+  }
+  __syncwarp();
+  const int k1 = (int)(__brev((unsigned)l) >> 27);
+#pragma unroll
+  for (int k2 = 0; k2 < R; ++k2) {
+    st(t0, k2 + R * k1, a[k2]);
+    if (two) st(t1, k2 + R * k1, b[k2]);
+  }
+  __syncwarp();
+}
+
+// dispatch on the transform length; false if it has no register version (caller falls back)
+template <typename T, typename LD, typename ST>
+__device__ __forceinline__ bool wfft2_dispatch(int logN, const LD& ld, const ST& st, int t0, int t1,
+                                               const Cx<T>* tw, bool inverse) {
+  // two transforms per warp up to length 128; longer ones run one at a time (registers)
+  switch (logN) {
+    case 5: wfft2<T, 1, false>(ld, st, t0, -1, tw, inverse); break;
+    case 6: wfft2<T, 2, false>(ld, st, t0, -1, tw, inverse); break;
+    case 7: wfft2<T, 4, false>(ld, st, t0, -1, tw, inverse); break;
+    case 8: wfft2<T, 8, false>(ld, st, t0, -1, tw, inverse); break;
+    default: return false;
+  }
+  if (t1 >= 0) wfft2_dispatch<T>(logN, ld, st, t1, -1, tw, inverse);
+  return true;
+}
+
 template <typename T>
 __device__ void warp_fft(Cx<T>* d, int logN, const Cx<T>* tw, bool inverse) {
   switch (logN) {
@@ -294,27 +388,37 @@ __device__ void warp_fft(Cx<T>* d, int logN, const Cx<T>* tw, bool inverse) {
 // ------------------------------------------------------------------------------------------
 enum CstSlot {
   K_H = 0, K_INVH, K_HX, K_HY, K_D, K_DF, K_WSCALE, K_CX, K_CY, K_INVHX, K_INVHY, K_FLUX,
-  K_BEAM, K_QM = 16, K_MOQ = 20, K_QF = 24, K_N = 28
+  K_BEAM, K_JREF, K_JSCALE, K_JINV, K_QM = 16, K_MOQ = 20, K_QF = 24, K_N = 28
 };
+enum MiscSlot { M_PCOUNT = 0, M_FTOP, M_INBOX, M_RQN, M_JFLAG, M_STN, M_PAD0, M_PAD1 };
 
+// Shared memory of one CTA.  Plane sets are [comp][rows][nx]: the fields F keep the CTA's RB
+// rows plus one halo row above (FR = RB + 1); the currents J keep rows -1 .. RB + 1 of the
+// band (JR = RB + 3, own row 0 at index JOFF = 1).  In 2-D FR = JR = 1, JOFF = 0.
 template <typename T>
 struct Sm {
-  T* F[2];          // [6][RB][nx] real-space fields (Ex,Ey,Ez,Bx,By,Bz)
-  T* J;             // [3][RB][nx] current accumulators (jx on x-edges, jy (3-D: y-edges), jz)
-  Cx<T>* SR;        // [6][RB][nx/2] row spectra received for the inverse transform
+  T* F[2];          // [6][FR][nx] real-space fields (Ex,Ey,Ez,Bx,By,Bz)
+  T* J;             // [3][JR][nx] current accumulators (jx on x-edges, jy (3-D: y-edges), jz)
+  int* Jint;        // [3][JR][nx] fixed-point accumulators of the push phase (FP32; aliases SR)
+  T* recv;          // [3][3][nx] halo currents received: rows 0, 1 (from below), RB-1 (above)
+  Cx<T>* SR;        // [6][FR][nx/2] row spectra received for the inverse transform
   Cx<T>* SC;        // [6][KB][ny] column spectra (forward: 3 currents; inverse: 6 fields)
-  Cx<T>* work;      // [nwork][nx]
+  Cx<T>* workB;     // [nwork][nx] row FFT work of the forward transform (aliases SR)
+  Cx<T>* workD;     // [nwork][nx] row FFT work of the inverse transform (aliases SC)
   Cx<T>* twx;       // [nx/2]
   Cx<T>* twy;       // [max(ny/2,1)]
   Cx<T>* shx;       // [nx/2]  exp(-i kx hx/2)
   Cx<T>* shy;       // [ny]    exp(-i ky hy/2)
   T* kx;            // [nx/2]
   T* ky;            // [ny]
+  T* cst;           // [K_N] constants in the working precision
+  int* icell;       // [mig_cap] inbox of particles migrating in
+  T *ifx, *ify, *iux, *iuy, *iuz, *isig, *iq;
   int* pcell;       // [pcap] ix | iy << 10 | sp << 20, -1 = empty
   T *pfx, *pfy, *pux, *puy, *puz, *psig, *pq;
-  int* misc;        // [0] particle count
+  int* fstack;      // [pcap] free particle slots
+  int* misc;        // MiscSlot
   double* dacc;     // [kNDiag]
-  T* cst;           // [K_N] constants in the working precision
 };
 
 template <typename T>
@@ -323,9 +427,12 @@ __device__ Sm<T> carve(const Params& p, unsigned char* base) {
   s.F[0] = (T*)(base + p.o_f0);
   s.F[1] = (T*)(base + p.o_f1);
   s.J = (T*)(base + p.o_j);
+  s.recv = (T*)(base + p.o_recv);
   s.SR = (Cx<T>*)(base + p.o_sr);
+  s.Jint = (int*)(base + p.o_sr);
   s.SC = (Cx<T>*)(base + p.o_sc);
-  s.work = (Cx<T>*)(base + p.o_work);
+  s.workB = (Cx<T>*)(base + p.o_workB);
+  s.workD = (Cx<T>*)(base + p.o_workD);
   Cx<T>* tw = (Cx<T>*)(base + p.o_tw);
   const int nyh = p.ny > 1 ? p.ny / 2 : 1;
   s.twx = tw;
@@ -335,6 +442,17 @@ __device__ Sm<T> carve(const Params& p, unsigned char* base) {
   s.kx = (T*)(s.shy + p.ny);
   s.ky = s.kx + p.nx / 2;
   s.cst = s.ky + p.ny;
+  unsigned char* ib = base + p.o_inbox;
+  const int mcap = p.mig_cap;
+  s.icell = (int*)ib;
+  T* it = (T*)(ib + ((mcap * 4 + 15) / 16) * 16);
+  s.ifx = it;
+  s.ify = it + mcap;
+  s.iux = it + 2 * mcap;
+  s.iuy = it + 3 * mcap;
+  s.iuz = it + 4 * mcap;
+  s.isig = it + 5 * mcap;
+  s.iq = it + 6 * mcap;
   unsigned char* pp = base + p.o_part;
   s.pcell = (int*)pp;
   T* pt = (T*)(pp + ((p.pcap * 4 + 15) / 16) * 16);
@@ -345,8 +463,9 @@ __device__ Sm<T> carve(const Params& p, unsigned char* base) {
   s.puz = pt + 4 * p.pcap;
   s.psig = pt + 5 * p.pcap;
   s.pq = pt + 6 * p.pcap;
+  s.fstack = (int*)(pt + 7 * p.pcap);
   s.misc = (int*)(base + p.o_misc);
-  s.dacc = (double*)(base + p.o_misc + 16);
+  s.dacc = (double*)(base + p.o_misc + 32);
   return s;
 }
 
@@ -375,6 +494,9 @@ __device__ void load_tables(const Params& p, const Sm<T>& s) {
     c[K_INVHY] = T(1.0 / p.hy);
     c[K_FLUX] = T(p.hx * p.hy * p.h);
     c[K_BEAM] = T(1.0 / (p.hx * p.hy * p.h));
+    c[K_JREF] = T(p.jref);
+    c[K_JSCALE] = T(4194304.0 / p.jref);   // 2^22 / jref
+    c[K_JINV] = T(p.jref / 4194304.0);
     for (int i = 0; i < kMaxSpecies; ++i) {
       c[K_QM + i] = T(p.qm[i]);
       c[K_MOQ + i] = T(p.m_over_q[i]);
@@ -405,7 +527,6 @@ enum Phase { PH_A = 0, PH_B1, PH_BEAM, PH_FWD, PH_B2, PH_COLF, PH_SOLVE, PH_COLI
         atomicAdd(p.timers + i_, (unsigned long long)g_sub[i_ - PH_AG]);                 \
     }                                                                                    \
   } while (0)
-// sub-phases of the push (gather / push arithmetic / deposit), thread 0 only
 #define SUB_DECL long long s_t0 = clock64();
 #define SUB_MARK(i)                                   \
   do {                                                \
@@ -446,10 +567,10 @@ __device__ void forward_rows(const cg::cluster_group& cl, const Params& p, const
   const int ntask = 2 * p.RB;                 // (row, pair): pair 0 = jx + i jy, 1 = jz
   if (warp >= p.nwork) return;
   for (int task = warp; task < ntask; task += p.nwork) {
-    Cx<T>* w = s.work + (size_t)warp * p.nx;
+    Cx<T>* w = s.workB + (size_t)warp * p.nx;
     const int yl = task >> 1, pr = task & 1;
-    const T* a = s.J + ((size_t)(pr == 0 ? 0 : 2) * p.RB + yl) * p.nx;
-    const T* b = s.J + ((size_t)1 * p.RB + yl) * p.nx;
+    const T* a = s.J + ((size_t)(pr == 0 ? 0 : 2) * p.JR + yl + p.JOFF) * p.nx;
+    const T* b = s.J + ((size_t)1 * p.JR + yl + p.JOFF) * p.nx;
     for (int x = lane; x < p.nx; x += 32) w[x] = cx<T>(a[x], pr == 0 ? b[x] : T(0));
     __syncwarp();
     warp_fft(w, p.lognx, s.twx, false);
@@ -485,33 +606,86 @@ __device__ void column_ffts(const Params& p, const Sm<T>& s, int c0, int c1, boo
   }
 }
 
-// scatter the 6 inverse-column-transformed field spectra to the row owners' SR
+// scatter the 6 inverse-column-transformed field spectra to the row owners' SR; the first row
+// of each band also goes to the band below as its halo row FR - 1 = RB.  One thread per
+// (component, row) moves the CTA's KB consecutive kx values, 16 bytes per store.
 template <typename T>
 __device__ void scatter_to_rows(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
                                 int me) {
-  const int lc = p.logKB + p.logny;
-  const int n = 6 << lc;
+  const int nxh = p.nx / 2;
+  const int n = 6 * p.ny;
+  const size_t cs = (size_t)p.KB * p.ny;
+  const int kx0 = me << p.logKB;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int c = i >> lc;
-    const int rem = i & ((1 << lc) - 1);
-    const int kxl = rem >> p.logny, y = rem & (p.ny - 1);
+    const int c = i >> p.logny, y = i & (p.ny - 1);
     const int ro = y >> p.logRB, yl = y & (p.RB - 1);
-    st_cx(cl, s.SR + ((size_t)c * p.RB + yl) * (p.nx / 2) + (me << p.logKB) + kxl, ro, me, s.SC[i]);
+    const bool halo = p.ny > 1 && yl == 0;
+    const int rb = (ro + p.C - 1) & (p.C - 1);
+    Cx<T>* d0 = s.SR + ((size_t)c * p.FR + yl) * nxh + kx0;
+    Cx<T>* d1 = s.SR + ((size_t)c * p.FR + p.RB) * nxh + kx0;
+    Cx<T>* q0 = ro == me ? d0 : cl.map_shared_rank(d0, ro);
+    Cx<T>* q1 = rb == me ? d1 : cl.map_shared_rank(d1, rb);
+    const Cx<T>* src = s.SC + c * cs + y;
+    if (sizeof(Cx<T>) == 8 && (p.KB & 1) == 0) {
+      for (int kxl = 0; kxl < p.KB; kxl += 2) {
+        const Cx<T> a = src[(size_t)kxl * p.ny], b = src[(size_t)(kxl + 1) * p.ny];
+        const float4 v = make_float4((float)a.re, (float)a.im, (float)b.re, (float)b.im);
+        *reinterpret_cast<float4*>(q0 + kxl) = v;
+        if (halo) *reinterpret_cast<float4*>(q1 + kxl) = v;
+      }
+    } else {
+      for (int kxl = 0; kxl < p.KB; ++kxl) {
+        const Cx<T> a = src[(size_t)kxl * p.ny];
+        q0[kxl] = a;
+        if (halo) q1[kxl] = a;
+      }
+    }
   }
 }
 
-// inverse row transforms: SR pairs (Ex,Ey), (Ez,Bx), (By,Bz) -> real rows of Fdst
+// inverse row transforms: SR pairs (Ex,Ey), (Ez,Bx), (By,Bz) -> real rows of Fdst (own rows
+// and the halo row); the field energy counts own rows only.  For lengths with a register FFT
+// the spectrum X + iY (with X(-k) = conj X(k)) is formed while loading and the real and
+// imaginary parts are written straight to the two field rows, two transforms per warp.
 template <typename T>
 __device__ void inverse_rows(const Params& p, const Sm<T>& s, T* Fdst, T& fe) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
   const int nxh = p.nx / 2;
   const T scale = T(1.0 / ((double)p.nx * (double)p.ny));
-  const int ntask = 3 * p.RB;
+  const int ntask = 3 * p.FR;
+  if (p.lognx >= 5 && p.lognx <= 8) {
+    // task t: row yl = t / 3, pair pr = t % 3
+    const auto ld = [&](int t, int j) -> Cx<T> {
+      const int yl = t / 3, pr = t - 3 * (t / 3);
+      const Cx<T>* X = s.SR + ((size_t)(2 * pr) * p.FR + yl) * nxh;
+      const Cx<T>* Y = s.SR + ((size_t)(2 * pr + 1) * p.FR + yl) * nxh;
+      if (j == 0) return cx<T>(X[0].re, Y[0].re);             // real DC of each field
+      if (j == nxh) return cx<T>(T(0), T(0));                 // Nyquist projected out
+      if (j < nxh) {
+        const Cx<T> x = X[j], y = Y[j];
+        return cx<T>(x.re - y.im, x.im + y.re);               // X + i Y
+      }
+      const Cx<T> x = X[p.nx - j], y = Y[p.nx - j];
+      return cx<T>(x.re + y.im, y.re - x.im);                 // conj(X) + i conj(Y)
+    };
+    T acc = T(0);
+    const auto st = [&](int t, int k, Cx<T> v) {
+      const int yl = t / 3, pr = t - 3 * (t / 3);
+      const T va = v.re * scale, vb = v.im * scale;
+      Fdst[((size_t)(2 * pr) * p.FR + yl) * p.nx + k] = va;
+      Fdst[((size_t)(2 * pr + 1) * p.FR + yl) * p.nx + k] = vb;
+      if (yl < p.RB) acc += va * va + vb * vb;
+    };
+    for (int t = warp; t < ntask; t += nwarps) wfft2_dispatch<T>(p.lognx, ld, st, t, -1, s.twx, true);
+    fe += acc;
+    return;
+  }
   for (int task = (warp < p.nwork ? warp : ntask); task < ntask; task += p.nwork) {
-    Cx<T>* w = s.work + (size_t)warp * p.nx;
+    Cx<T>* w = s.workD + (size_t)warp * p.nx;
     const int yl = task / 3, pr = task - 3 * yl;
-    const Cx<T>* X = s.SR + ((size_t)(2 * pr) * p.RB + yl) * nxh;
-    const Cx<T>* Y = s.SR + ((size_t)(2 * pr + 1) * p.RB + yl) * nxh;
+    const Cx<T>* X = s.SR + ((size_t)(2 * pr) * p.FR + yl) * nxh;
+    const Cx<T>* Y = s.SR + ((size_t)(2 * pr + 1) * p.FR + yl) * nxh;
     for (int k = lane; k < nxh; k += 32) {
       Cx<T> x = X[k], y = Y[k];
       if (k == 0) {
@@ -523,22 +697,25 @@ __device__ void inverse_rows(const Params& p, const Sm<T>& s, T* Fdst, T& fe) {
     }
     if (lane == 0) w[nxh] = cx<T>(T(0), T(0));            // Nyquist projected out
     __syncwarp();
-    warp_fft(w, p.lognx, s.twx, true);
-    T* a = Fdst + ((size_t)(2 * pr) * p.RB + yl) * p.nx;
-    T* b = Fdst + ((size_t)(2 * pr + 1) * p.RB + yl) * p.nx;
+    warp_fft_r2(w, p.lognx, s.twx, true);
+    T* a = Fdst + ((size_t)(2 * pr) * p.FR + yl) * p.nx;
+    T* b = Fdst + ((size_t)(2 * pr + 1) * p.FR + yl) * p.nx;
+    const bool own = yl < p.RB;
     for (int x = lane; x < p.nx; x += 32) {
       const T va = w[x].re * scale, vb = w[x].im * scale;
       a[x] = va;
       b[x] = vb;
-      fe += va * va + vb * vb;
+      if (own) fe += va * va + vb * vb;
     }
     __syncwarp();
   }
 }
 
 // ------------------------------------------------------------------------------------------
-// addressing of a [comp][RB][nx] plane set of the cluster: shared-memory address of
-// (comp 0, global row y, column 0) and the owning CTA
+// Gather and deposit.  Fast path: a particle in the CTA's own rows reads fields of rows
+// yl, yl + 1 (halo) and deposits into current rows yl - 1 .. yl + 2, all in its own shared
+// memory.  Generic path (stored particles, particles outside the band, moves reaching past the
+// halo): any row of the cluster through distributed shared memory.
 // ------------------------------------------------------------------------------------------
 template <typename T>
 struct RowRef {
@@ -546,10 +723,13 @@ struct RowRef {
   bool remote;
 };
 
+// row y (global) of a plane set whose own row 0 sits at index `off` of `rows` rows per comp
 template <typename T>
-__device__ __forceinline__ RowRef<T> row_ref(const Params& p, const T* base, int y, int me) {
+__device__ __forceinline__ RowRef<T> row_ref(const Params& p, const T* base, int rows, int off,
+                                             int y, int me) {
   const int r = y >> p.logRB;
-  const int yl = y & (p.RB - 1);
+  const int yl = (y & (p.RB - 1)) + off;
+  (void)rows;
   uint32_t a = sh_addr(base + (size_t)yl * p.nx);
   RowRef<T> rr;
   rr.remote = r != me;
@@ -572,12 +752,12 @@ __device__ __forceinline__ void row_red(const RowRef<T>& rr, uint32_t off_elems,
     red_local(a, v);
 }
 
-// CIC gather of the 6 fields of a plane set at (ix + fx, iy + fy)
+// CIC gather of the 6 fields at (ix + fx, iy + fy), any row of the cluster
 template <typename T>
-__device__ __forceinline__ void gather6(const Params& p, const T* Fb, int ix, T fx, int iy, T fy,
-                                        int me, T* out) {
+__device__ __forceinline__ void gather6_g(const Params& p, const T* Fb, int ix, T fx, int iy, T fy,
+                                          int me, T* out) {
   const int ix1 = (ix + 1) & (p.nx - 1);
-  const uint32_t cs = (uint32_t)(p.RB * p.nx);     // component stride
+  const uint32_t cs = (uint32_t)(p.FR * p.nx);     // component stride
   if (p.ny == 1) {
     const uint32_t a = sh_addr(Fb);
 #pragma unroll
@@ -589,8 +769,8 @@ __device__ __forceinline__ void gather6(const Params& p, const T* Fb, int ix, T 
     return;
   }
   const int iy1 = (iy + 1) & (p.ny - 1);
-  const RowRef<T> r0 = row_ref(p, Fb, iy, me);
-  const RowRef<T> r1 = row_ref(p, Fb, iy1, me);
+  const RowRef<T> r0 = row_ref(p, Fb, p.FR, 0, iy, me);
+  const RowRef<T> r1 = row_ref(p, Fb, p.FR, 0, iy1, me);
   const T w00 = (T(1) - fx) * (T(1) - fy), w10 = fx * (T(1) - fy);
   const T w01 = (T(1) - fx) * fy, w11 = fx * fy;
 #pragma unroll
@@ -601,21 +781,88 @@ __device__ __forceinline__ void gather6(const Params& p, const T* Fb, int ix, T 
   }
 }
 
-// add v to current plane `comp` at (global row y, column x), both already wrapped
+// the same for a particle in own row yl (rows yl and yl + 1 <= RB are local)
 template <typename T>
-__device__ __forceinline__ void jadd(const Params& p, const T* J, int comp, int y, int x, T v,
-                                     int me) {
-  if (v == T(0)) return;
-  const RowRef<T> rr = row_ref(p, J, y, me);
-  row_red(rr, (uint32_t)(comp * p.RB * p.nx + x), v);
+__device__ __forceinline__ void gather6_l(const Params& p, const T* Fb, int ix, T fx, int yl, T fy,
+                                          T* out) {
+  const int ix1 = (ix + 1) & (p.nx - 1);
+  const uint32_t cs = (uint32_t)(p.FR * p.nx) * (uint32_t)sizeof(T);
+  const uint32_t a0 = sh_addr(Fb + (size_t)yl * p.nx);
+  const uint32_t i0 = ix * (uint32_t)sizeof(T), i1 = ix1 * (uint32_t)sizeof(T);
+  if (p.ny == 1) {
+#pragma unroll
+    for (int c = 0; c < 6; ++c) {
+      const uint32_t b = a0 + c * cs;
+      out[c] = (T(1) - fx) * lds(b + i0, T(0)) + fx * lds(b + i1, T(0));
+    }
+    return;
+  }
+  const uint32_t a1 = a0 + (uint32_t)p.nx * (uint32_t)sizeof(T);
+  const T w00 = (T(1) - fx) * (T(1) - fy), w10 = fx * (T(1) - fy);
+  const T w01 = (T(1) - fx) * fy, w11 = fx * fy;
+#pragma unroll
+  for (int c = 0; c < 6; ++c) {
+    const uint32_t b0 = a0 + c * cs, b1 = a1 + c * cs;
+    out[c] = ((w00 * lds(b0 + i0, T(0)) + w10 * lds(b0 + i1, T(0))) + w01 * lds(b1 + i0, T(0))) +
+             w11 * lds(b1 + i1, T(0));
+  }
 }
 
-// Esirkepov (Comput. Phys. Commun. 135, 2001) transverse current of a move (X0,Y0)->(X1,Y1)
-// in cell units relative to node (ix, iy); w is the (rho - j_z) weight.  With D = w S the
-// deposit satisfies (D_new - D_old) + h div J = 0 on every node.
+// Deposit targets.  Sink<T, true>: own current rows (row index relative to the particle's
+// row, band rows -1 .. RB + 1), local shared reductions with precomputed addresses; in FP32
+// a contribution below jref goes to the 32-bit fixed-point accumulators (native integer
+// reductions, exact sums, at most 2^9 such contributions per node), a larger one to the float
+// accumulators.  Sink<T, false>: any global row, through the CTA that owns it.
+template <typename T, bool LOCAL>
+struct Sink;
+
 template <typename T>
-__device__ void esirkepov(const Params& p, const Sm<T>& s, int ix, int iy, T X0, T Y0, T X1,
-                          T Y1, T w, T dyo, int me) {
+struct Sink<T, true> {
+  uint32_t fbase, ibase;     // address of (comp 0, particle row, col 0): float / fixed point
+  uint32_t cstride, rstride; // bytes per component, per row
+  T jref, jscale;
+  __device__ __forceinline__ Sink(const Params& p, const Sm<T>& s, int yrow0) {
+    const uint32_t off = (uint32_t)((yrow0 + p.JOFF) * p.nx) * (uint32_t)sizeof(T);
+    fbase = sh_addr(s.J) + off;
+    ibase = sh_addr(s.Jint) + (uint32_t)((yrow0 + p.JOFF) * p.nx) * 4u;
+    cstride = (uint32_t)(p.JR * p.nx) * (uint32_t)sizeof(T);
+    rstride = (uint32_t)p.nx * (uint32_t)sizeof(T);
+    jref = s.cst[K_JREF];
+    jscale = s.cst[K_JSCALE];
+  }
+  __device__ __forceinline__ void add(int comp, int yrow, int x, T v) const {
+    if (v == T(0)) return;
+    const uint32_t off = (uint32_t)comp * cstride + (uint32_t)(yrow * (int)rstride) +
+                         (uint32_t)x * (uint32_t)sizeof(T);
+    if constexpr (sizeof(T) == 4) {
+      if (fabsf(v) < jref) {
+        red_local_u32(ibase + off, __float2int_rn(v * jscale));
+        return;
+      }
+    }
+    red_local(fbase + off, v);
+  }
+};
+
+template <typename T>
+struct Sink<T, false> {
+  const Params& p;
+  const T* J;
+  int me, y0;                // global row of the particle
+  __device__ __forceinline__ void add(int comp, int yrow, int x, T v) const {
+    if (v == T(0)) return;
+    const int y = (yrow + y0) & (p.ny - 1);
+    const RowRef<T> rr = row_ref(p, J, p.JR, p.JOFF, y, me);
+    row_red(rr, (uint32_t)(comp * p.JR * p.nx + x), v);
+  }
+};
+
+// Esirkepov (Comput. Phys. Commun. 135, 2001) transverse current of a move (X0,Y0)->(X1,Y1)
+// in cell units relative to node (ix, row 0 of the sink); w is the (rho - j_z) weight.  With
+// D = w S the deposit satisfies (D_new - D_old) + h div J = 0 on every node.
+template <typename T, bool LOCAL>
+__device__ void esirkepov(const Params& p, const Sm<T>& s, const Sink<T, LOCAL>& sk, int ix,
+                          T X0, T Y0, T X1, T Y1, T w, T dyo) {
   const T invh = s.cst[K_INVH];
   const T dX = X1 - X0;
   const T dY = Y1 - Y0;
@@ -623,7 +870,7 @@ __device__ void esirkepov(const Params& p, const Sm<T>& s, int ix, int iy, T X0,
   const int nsub = m > T(1) ? (int)ceil(m) : 1;
   const T cx_ = -(w * s.cst[K_CX]);
   const T cy_ = -(w * s.cst[K_CY]);
-  const int mx = p.nx - 1, my = p.ny - 1;
+  const int mx = p.nx - 1;
   for (int sb = 0; sb < nsub; ++sb) {
     const T xa = X0 + dX * (T(sb) / T(nsub));
     const T xb = X0 + dX * (T(sb + 1) / T(nsub));
@@ -640,12 +887,12 @@ __device__ void esirkepov(const Params& p, const Sm<T>& s, int ix, int iy, T X0,
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         cum = cum + (S1x[a] - S0x[a]);
-        jadd(p, s.J, 0, 0, (gx + a) & mx, cx_ * cum, me);
+        sk.add(0, 0, (gx + a) & mx, cx_ * cum);
       }
       const T dyv = dyo / T(nsub);
 #pragma unroll
       for (int a = 0; a < 3; ++a)
-        jadd(p, s.J, 1, 0, (gx + a) & mx, w * (dyv * invh) * T(0.5) * (S0x[a] + S1x[a]), me);
+        sk.add(1, 0, (gx + a) & mx, w * (dyv * invh) * T(0.5) * (S0x[a] + S1x[a]));
       continue;
     }
     const T ya = Y0 + dY * (T(sb) / T(nsub));
@@ -657,63 +904,51 @@ __device__ void esirkepov(const Params& p, const Sm<T>& s, int ix, int iy, T X0,
       S0y[b] = fmax(T(0), T(1) - fabs(ya - (by + T(b))));
       S1y[b] = fmax(T(0), T(1) - fabs(yb - (by + T(b))));
     }
-    const int gy = iy + (int)by;
+    const int gy = (int)by;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-      const int yy = (gy + b) & my;
       const T hy2 = T(0.5) * (S0y[b] + S1y[b]);
       if (hy2 == T(0)) continue;
-      const RowRef<T> rr = row_ref(p, s.J, yy, me);
       T cum = T(0);
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         cum = cum + (S1x[a] - S0x[a]) * hy2;
-        const T v = cx_ * cum;
-        if (v != T(0)) row_red(rr, (uint32_t)((gx + a) & mx), v);
+        sk.add(0, gy + b, (gx + a) & mx, cx_ * cum);
       }
     }
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      const int yy = (gy + b) & my;
-      const RowRef<T> rr = row_ref(p, s.J, yy, me);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
         // cumulative sum over b of (S1y - S0y)(S0x + S1x)/2 at column a
         T cum = (S1y[0] - S0y[0]) * T(0.5) * (S0x[a] + S1x[a]);
         if (b == 1) cum = cum + (S1y[1] - S0y[1]) * T(0.5) * (S0x[a] + S1x[a]);
-        const T v = cy_ * cum;
-        if (v != T(0)) row_red(rr, (uint32_t)(p.RB * p.nx + ((gx + a) & mx)), v);
+        sk.add(1, gy + b, (gx + a) & mx, cy_ * cum);
       }
     }
   }
 }
 
-// CIC deposit of value v at (X, Y) relative to node (ix, iy) into current plane comp
-template <typename T>
-__device__ __forceinline__ void cic_add(const Params& p, const Sm<T>& s, int comp, int ix,
-                                        int iy, T X, T Y, T v, int me) {
+// CIC deposit of value v at (X, Y) relative to node (ix, row 0 of the sink) into comp
+template <typename T, bool LOCAL>
+__device__ __forceinline__ void cic_add(const Params& p, const Sink<T, LOCAL>& sk, int comp,
+                                        int ix, T X, T Y, T v) {
   const T i0 = floor(X);
   const T fx = X - i0;
   const int gx = (ix + (int)i0) & (p.nx - 1);
   const int gx1 = (gx + 1) & (p.nx - 1);
   if (p.ny == 1) {
-    jadd(p, s.J, comp, 0, gx, (T(1) - fx) * v, me);
-    jadd(p, s.J, comp, 0, gx1, fx * v, me);
+    sk.add(comp, 0, gx, (T(1) - fx) * v);
+    sk.add(comp, 0, gx1, fx * v);
     return;
   }
   const T j0 = floor(Y);
   const T fy = Y - j0;
-  const int gy = (iy + (int)j0) & (p.ny - 1);
-  const int gy1 = (gy + 1) & (p.ny - 1);
-  const uint32_t o = (uint32_t)(comp * p.RB * p.nx);
-  const RowRef<T> r0 = row_ref(p, s.J, gy, me);
-  const RowRef<T> r1 = row_ref(p, s.J, gy1, me);
-  T v00 = ((T(1) - fx) * (T(1) - fy)) * v, v10 = (fx * (T(1) - fy)) * v;
-  T v01 = ((T(1) - fx) * fy) * v, v11 = (fx * fy) * v;
-  if (v00 != T(0)) row_red(r0, o + gx, v00);
-  if (v10 != T(0)) row_red(r0, o + gx1, v10);
-  if (v01 != T(0)) row_red(r1, o + gx, v01);
-  if (v11 != T(0)) row_red(r1, o + gx1, v11);
+  const int gy = (int)j0;
+  sk.add(comp, gy, gx, ((T(1) - fx) * (T(1) - fy)) * v);
+  sk.add(comp, gy, gx1, (fx * (T(1) - fy)) * v);
+  sk.add(comp, gy + 1, gx, ((T(1) - fx) * fy) * v);
+  sk.add(comp, gy + 1, gx1, (fx * fy) * v);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -740,8 +975,13 @@ template <typename T>
 __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PState<T>& P, T d,
                             int me, T& fz_trap, SliceAcc<T>& acc, long long* sub) {
   SUB_DECL
+  const int yl = P.iy - (me << p.logRB);
+  const bool own = p.ny == 1 || (yl >= 0 && yl < p.RB);
   T E[6];
-  gather6(p, Fcur, P.ix, P.fx, P.iy, P.fy, me, E);
+  if (own)
+    gather6_l(p, Fcur, P.ix, P.fx, p.ny == 1 ? 0 : yl, P.fy, E);
+  else
+    gather6_g(p, Fcur, P.ix, P.fx, P.iy, P.fy, me, E);
   SUB_MARK(0);
   const T D = s.cst[K_D];
   const T invh = s.cst[K_INVH];
@@ -768,8 +1008,18 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   const T X1 = P.fx + dx * s.cst[K_INVHX];
   const T Y1 = p.ny > 1 ? P.fy + dy * s.cst[K_INVHY] : P.fy;
   SUB_MARK(1);
-  esirkepov(p, s, P.ix, P.iy, P.fx, P.fy, X1, Y1, w, dy, me);
-  cic_add(p, s, 2, P.ix, P.iy, X1, Y1, w * ds * invh, me);
+  // the move stays inside the band's current rows -1 .. RB + 1 -> local reductions only
+  const T lo = floor(fmin(P.fy, Y1)), hi = floor(fmax(P.fy, Y1));
+  const bool local = own && (p.ny == 1 || (yl + (int)lo >= -1 && yl + (int)hi + 2 <= p.RB + 1));
+  if (local) {
+    const Sink<T, true> sk(p, s, p.ny == 1 ? 0 : yl);
+    esirkepov(p, s, sk, P.ix, P.fx, P.fy, X1, Y1, w, dy);
+    cic_add(p, sk, 2, P.ix, X1, Y1, w * ds * invh);
+  } else {
+    const Sink<T, false> sk{p, s.J, me, P.iy};
+    esirkepov(p, s, sk, P.ix, P.fx, P.fy, X1, Y1, w, dy);
+    cic_add(p, sk, 2, P.ix, X1, Y1, w * ds * invh);
+  }
   SUB_MARK(2);
   // diagnostics: kinetic energy N m (gamma-1) dt/Delta, (rho - j_z) flux through plane n
   const T dtl = hc * gn / den;
@@ -826,16 +1076,134 @@ __device__ PState<T> store_read(const PartStore& S, const Params& p, size_t e, T
   return P;
 }
 
+// hand a particle to the CTA that owns its row (its inbox, DSMEM).  An inbox slot is taken only
+// while the owner still has room for it (free slots + unused capacity, less a margin for the
+// stored particles that may rejoin there in the same slice); otherwise the particle stays and
+// is pushed through the generic path.
+template <typename T>
+__device__ bool migrate(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
+                        const PState<T>& P, int owner) {
+  int* rmisc = cl.map_shared_rank(s.misc, owner);
+  const int room = p.pcap + p.gcap - rmisc[M_PCOUNT] + rmisc[M_FTOP] - 64;
+  const int limit = min(p.mig_cap, room);
+  int* cnt = rmisc + M_INBOX;
+  int e = *(volatile int*)cnt;
+  for (;;) {
+    if (e >= limit) return false;
+    const int prev = atomicCAS(cnt, e, e + 1);
+    if (prev == e) break;
+    e = prev;
+  }
+  *cl.map_shared_rank(s.icell + e, owner) = P.ix | (P.iy << 10) | (P.sp << 20);
+  *cl.map_shared_rank(s.ifx + e, owner) = P.fx;
+  *cl.map_shared_rank(s.ify + e, owner) = P.fy;
+  *cl.map_shared_rank(s.iux + e, owner) = P.u.x;
+  *cl.map_shared_rank(s.iuy + e, owner) = P.u.y;
+  *cl.map_shared_rank(s.iuz + e, owner) = P.u.z;
+  *cl.map_shared_rank(s.isig + e, owner) = P.sig;
+  *cl.map_shared_rank(s.iq + e, owner) = P.q;
+  return true;
+}
+
+// Streaming particle slots of a CTA: [0, pcap) in shared memory, [pcap, pcap + gcap) in its
+// overflow arrays in global memory (used only when the band holds more particles than fit).
+template <typename T>
+struct Ovf {
+  int* cell;
+  T *fx, *fy, *ux, *uy, *uz, *sig, *q;
+};
+
+template <typename T>
+__device__ __forceinline__ Ovf<T> ovf_view(const Params& p, int cid, int me) {
+  Ovf<T> o;
+  const size_t g = (size_t)p.gcap;
+  char* b = (char*)p.pover + ((size_t)cid * p.C + me) * g * (4 + 7 * sizeof(T));
+  o.cell = (int*)b;
+  T* t = (T*)(b + 4 * g);
+  o.fx = t;
+  o.fy = t + g;
+  o.ux = t + 2 * g;
+  o.uy = t + 3 * g;
+  o.uz = t + 4 * g;
+  o.sig = t + 5 * g;
+  o.q = t + 6 * g;
+  return o;
+}
+
+template <typename T>
+__device__ __forceinline__ int get_cell(const Params& p, const Sm<T>& s, const Ovf<T>& o, int i) {
+  return i < p.pcap ? s.pcell[i] : o.cell[i - p.pcap];
+}
+
+template <typename T>
+__device__ __forceinline__ void set_cell(const Params& p, const Sm<T>& s, const Ovf<T>& o, int i,
+                                         int v) {
+  if (i < p.pcap)
+    s.pcell[i] = v;
+  else
+    o.cell[i - p.pcap] = v;
+}
+
+template <typename T>
+__device__ __forceinline__ PState<T> get_particle(const Params& p, const Sm<T>& s,
+                                                  const Ovf<T>& o, int i, int cw) {
+  PState<T> P;
+  P.ix = cw & 1023;
+  P.iy = (cw >> 10) & 1023;
+  P.sp = (cw >> 20) & 3;
+  if (i < p.pcap) {
+    P.fx = s.pfx[i];
+    P.fy = s.pfy[i];
+    P.u = V3<T>{s.pux[i], s.puy[i], s.puz[i]};
+    P.sig = s.psig[i];
+    P.q = s.pq[i];
+  } else {
+    const int j = i - p.pcap;
+    P.fx = o.fx[j];
+    P.fy = o.fy[j];
+    P.u = V3<T>{o.ux[j], o.uy[j], o.uz[j]};
+    P.sig = o.sig[j];
+    P.q = o.q[j];
+  }
+  return P;
+}
+
+template <typename T>
+__device__ __forceinline__ void put_particle(const Params& p, const Sm<T>& s, const Ovf<T>& o,
+                                             int i, const PState<T>& P) {
+  const int cw = P.ix | (P.iy << 10) | (P.sp << 20);
+  if (i < p.pcap) {
+    s.pcell[i] = cw;
+    s.pfx[i] = P.fx;
+    s.pfy[i] = P.fy;
+    s.pux[i] = P.u.x;
+    s.puy[i] = P.u.y;
+    s.puz[i] = P.u.z;
+    s.psig[i] = P.sig;
+    s.pq[i] = P.q;
+  } else {
+    const int j = i - p.pcap;
+    o.cell[j] = cw;
+    o.fx[j] = P.fx;
+    o.fy[j] = P.fy;
+    o.ux[j] = P.u.x;
+    o.uy[j] = P.u.y;
+    o.uz[j] = P.u.z;
+    o.sig[j] = P.sig;
+    o.q[j] = P.q;
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // Stored particle along s (Sec. 4.1: trapped / beam particles are integrated along s):
 // bucket n of level k+1, fields of slices n (Fn) and n+1 (Fn1) of that level.
 // ------------------------------------------------------------------------------------------
 template <typename T>
 __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const T* Fn1,
-                             long long k, int n, int me, double* acc) {
+                             long long k, int n, int me, double* acc, int cnt_raw) {
   const int s1 = (int)(((k + 1) % p.ring + p.ring) % p.ring);
   const int s2 = (int)(((k + 2) % p.ring + p.ring) % p.ring);
-  const int cnt = min(ldcg(p.st.cnt + (size_t)s1 * p.nz + n), p.bcap);
+  const int cnt = min(cnt_raw, p.bcap);
   const T D = s.cst[K_D], h = s.cst[K_H], invh = s.cst[K_INVH];
   const int mx = p.nx - 1, my = p.ny - 1;
   for (int e0 = me * blockDim.x + threadIdx.x; e0 < cnt; e0 += p.C * blockDim.x) {
@@ -852,8 +1220,8 @@ __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const
       continue;
     }
     T lo[6], hi[6], E[6];
-    gather6(p, Fn, P.ix, P.fx, P.iy, P.fy, me, lo);
-    gather6(p, Fn1, P.ix, P.fx, P.iy, P.fy, me, hi);
+    gather6_g(p, Fn, P.ix, P.fx, P.iy, P.fy, me, lo);
+    gather6_g(p, Fn1, P.ix, P.fx, P.iy, P.fy, me, hi);
 #pragma unroll
     for (int c = 0; c < 6; ++c) E[c] = (T(1) - fz) * lo[c] + fz * hi[c];
     const T dt = D * g / P.u.z;
@@ -1007,7 +1375,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   const int s2 = (int)(((k + 2) % p.ring + p.ring) % p.ring);
   const T h = s.cst[K_H], Dl = s.cst[K_DF];
   const long long sl = k - p.k0;                    // step index within this launch
-  const int plane = p.RB * p.nx;                    // elements of one component's rows
+  const Ovf<T> ov = ovf_view<T>(p, cid, me);        // overflow particle slots of this CTA
+  const int fplane = p.FR * p.nx;                   // elements of one field component
+  const int jplane = p.JR * p.nx;                   // elements of one current component
   long long g_sub[3] = {0, 0, 0};
   TIMER_DECL
 
@@ -1023,7 +1393,11 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     p.rq.cnt[(size_t)s2 * nz + b] = 0;
   }
   // fresh particles at the front ghost plane (Sec. 4.1: Q_f = q n hx hy Delta / ppc)
-  if (tid == 0) s.misc[0] = 0;
+  if (tid == 0) {
+    s.misc[M_PCOUNT] = 0;
+    s.misc[M_FTOP] = 0;
+    s.misc[M_INBOX] = 0;
+  }
   __syncthreads();
   if (p.inject) {
     const int per_row = p.nlayer >> p.logny;        // particles per transverse row
@@ -1056,13 +1430,15 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       s.psig[i] = T(0);
       s.pq[i] = s.cst[K_QF + sp];
     }
-    if (tid == 0) s.misc[0] = nmine;
+    if (tid == 0) s.misc[M_PCOUNT] = nmine;
   }
   // ghost slice: field-free
   T* Fcur = s.F[0];
   T* Fnew = s.F[1];
-  for (int i = tid; i < 6 * plane; i += NT) Fcur[i] = T(0);
-  for (int i = tid; i < 3 * plane; i += NT) s.J[i] = T(0);
+  for (int i = tid; i < 6 * fplane; i += NT) Fcur[i] = T(0);
+  for (int i = tid; i < 3 * jplane; i += NT) s.J[i] = T(0);
+  if constexpr (sizeof(T) == 4)
+    for (int i = tid; i < 3 * jplane; i += NT) s.Jint[i] = 0;
 
   // per-mode carried state (one mode per thread)
   const int m = tid;
@@ -1106,65 +1482,71 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     for (int c = 0; c < 6; ++c) o[c] = ldcg(st + blk(nz - 1, c));
   }
   const bool snap_step = p.snapshot && k == p.k0 + p.nsteps - 1;
+  // per-slice counters of other marches, read once per CTA and broadcast in shared memory
+  if (tid == 0) {
+    s.misc[M_RQN] = ldcg(p.rq.cnt + (size_t)s1 * nz + (nz - 1));
+    s.misc[M_JFLAG] = ldcg(p.jflag + (size_t)s1 * nz + (nz - 1));
+  }
+  __syncthreads();
 
   for (int n = nz - 1; n >= 0; --n) {
     // ---------------- A: streaming push from plane n+1 to plane n -----------------------
     SliceAcc<T> sa{T(0), T(0), 0};
     {
-      const int cnt0 = s.misc[0];
+      const int cnt0 = s.misc[M_PCOUNT];
       for (int i = tid; i < cnt0; i += NT) {
-        const int cw = s.pcell[i];
+        const int cw = get_cell(p, s, ov, i);
         if (cw < 0) continue;
-        PState<T> P;
-        P.ix = cw & 1023;
-        P.iy = (cw >> 10) & 1023;
-        P.sp = (cw >> 20) & 3;
-        P.fx = s.pfx[i];
-        P.fy = s.pfy[i];
-        P.u = V3<T>{s.pux[i], s.puy[i], s.puz[i]};
-        P.sig = s.psig[i];
-        P.q = s.pq[i];
+        PState<T> P = get_particle(p, s, ov, i, cw);
         T fzt;
         const bool trap = stream_push(p, s, Fcur, P, h, me, fzt, sa, g_sub);
+        bool gone = trap;
         if (trap) {
-          s.pcell[i] = -1;
           acc[DG_TRAP] += 1.0;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
         } else {
-          s.pcell[i] = P.ix | (P.iy << 10) | (P.sp << 20);
-          s.pfx[i] = P.fx;
-          s.pfy[i] = P.fy;
-          s.pux[i] = P.u.x;
-          s.puy[i] = P.u.y;
-          s.puz[i] = P.u.z;
-          s.psig[i] = P.sig;
+          const int owner = P.iy >> p.logRB;
+          // a particle that left the band moves to the owner of its row (kept here if the
+          // owner's inbox is full: it then takes the generic path)
+          if (owner != me && migrate(cl, p, s, P, owner)) gone = true;
+        }
+        if (gone) {
+          set_cell(p, s, ov, i, -1);
+          // shared-memory slots are reused; a dead overflow slot stays unused this s-step
+          if (i < p.pcap) s.fstack[atomicAdd(s.misc + M_FTOP, 1)] = i;
+        } else {
+          put_particle(p, s, ov, i, P);
         }
       }
-      // stored particles that rejoin the march at this slice: partial first step
-      const int nq = min(ldcg(p.rq.cnt + (size_t)s1 * nz + n), p.bcap);
-      for (int e = me + p.C * tid; e < nq; e += p.C * NT) {
+      // stored particles that rejoin the march at this slice (partial first step), taken by
+      // the CTA that owns their row
+      const int nq = min(s.misc[M_RQN], p.bcap);
+      for (int e = tid; e < nq; e += NT) {
+        const size_t ge = ((size_t)s1 * nz + n) * p.bcap + e;
+        if ((((ldcg(p.rq.cell + ge) >> 10) & 1023) >> p.logRB) != me) continue;
         T fz;
-        PState<T> P = store_read<T>(p.rq, p, ((size_t)s1 * nz + n) * p.bcap + e, fz);
+        PState<T> P = store_read<T>(p.rq, p, ge, fz);
         acc[DG_REJOIN] += 1.0;
         T fzt;
         const bool trap = stream_push(p, s, Fcur, P, fz * h, me, fzt, sa, g_sub);
         if (trap) {
           acc[DG_TRAP] += 1.0;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
+          continue;
+        }
+        const int owner = P.iy >> p.logRB;
+        if (owner != me && migrate(cl, p, s, P, owner)) continue;
+        const int slot = atomicAdd(s.misc + M_PCOUNT, 1);
+        if (slot < p.pcap + p.gcap) {
+          put_particle(p, s, ov, slot, P);
         } else {
-          const int slot = atomicAdd(s.misc, 1);
-          if (slot < p.pcap) {
-            s.pcell[slot] = P.ix | (P.iy << 10) | (P.sp << 20);
-            s.pfx[slot] = P.fx;
-            s.pfy[slot] = P.fy;
-            s.pux[slot] = P.u.x;
-            s.puy[slot] = P.u.y;
-            s.puz[slot] = P.u.z;
-            s.psig[slot] = P.sig;
-            s.pq[slot] = P.q;
-          } else {
-            atomicOr(p.err, ERR_PCAP);
+          atomicOr(p.err, ERR_PCAP);
+#ifdef GEMPIC_PHASE_TIMERS
+          if (p.timers && atomicCAS(p.timers + 20, 0ull, 2ull) == 0ull) {
+            p.timers[21] = n; p.timers[22] = nq; p.timers[24] = slot; p.timers[26] = me;
+            p.timers[27] = (unsigned long long)k;
           }
+#endif
         }
       }
     }
@@ -1172,34 +1554,100 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     acc[DG_FLUX] += (double)sa.flux;
     acc[DG_PUSH] += (double)sa.push;
     TIMER_MARK(PH_A);
-    // publish: iteration n+1 complete (its stored phase and this push have been issued)
     __syncthreads();
+    if constexpr (sizeof(T) == 4) {
+      const T jinv = s.cst[K_JINV];
+      for (int i = tid; i < 3 * jplane; i += NT) s.J[i] += T(s.Jint[i]) * jinv;
+      __syncthreads();
+    }
+    // halo currents (band rows -1, RB, RB+1) to the owners' receive buffers (plain stores)
+    if (p.ny > 1) {
+      const int rb = (me + p.C - 1) & (p.C - 1), ra = (me + 1) & (p.C - 1);
+      for (int i = tid; i < 9 * p.nx; i += NT) {
+        const int c = i / (3 * p.nx);
+        const int rem = i - c * 3 * p.nx;
+        const int which = rem / p.nx, x = rem - which * p.nx;
+        // which 0: band row -1 -> row RB-1 of the CTA below (recv slot 2)
+        // which 1, 2: band rows RB, RB+1 -> rows 0, 1 of the CTA above (recv slots 0, 1)
+        const int jrow = which == 0 ? 0 : p.RB + p.JOFF + (which - 1);
+        const T v = s.J[((size_t)c * p.JR + jrow) * p.nx + x];
+        const int dst = which == 0 ? rb : ra;
+        const int slot = which == 0 ? 2 : which - 1;
+        T* q = s.recv + ((size_t)c * 3 + slot) * p.nx + x;
+        *(dst == me ? q : cl.map_shared_rank(q, dst)) = v;
+      }
+    }
     if (tid == 0) {
-      if (s.misc[0] > p.pcap) s.misc[0] = p.pcap;
+      if (s.misc[M_PCOUNT] > p.pcap + p.gcap) s.misc[M_PCOUNT] = p.pcap + p.gcap;
       __threadfence();
     }
     cl.sync();                                                      // B1: deposits done
+    // publish: iteration n+1 complete (its stored phase and this push have been issued)
     if (p.P > 1 && me == 0 && tid == 0 && n + 1 <= nz - 1)
       st_release_u64(p.progress + cid, prog_value(k, nz, nz - (n + 1)));
+    // stored particles of cell n at this level (traps of this push included), for phase E
+    if (tid == 32) s.misc[M_STN] = ldcg(p.st.cnt + (size_t)s1 * nz + n);
     TIMER_MARK(PH_B1);
+    // received halo currents into own rows; migrating particles into free slots
+    if (p.ny > 1) {
+      for (int i = tid; i < 9 * p.nx; i += NT) {
+        const int c = i / (3 * p.nx);
+        const int rem = i - c * 3 * p.nx;
+        const int slot = rem / p.nx, x = rem - slot * p.nx;
+        const int row = slot == 2 ? p.RB - 1 : slot;
+        s.J[((size_t)c * p.JR + row + p.JOFF) * p.nx + x] +=
+            s.recv[((size_t)c * 3 + slot) * p.nx + x];
+      }
+      const int nin = min(s.misc[M_INBOX], p.mig_cap);
+      const int ftop = s.misc[M_FTOP];
+      const int pc = s.misc[M_PCOUNT];
+      for (int e = tid; e < nin; e += NT) {
+        const int slot = e < ftop ? s.fstack[ftop - 1 - e] : pc + (e - ftop);
+        if (slot >= p.pcap + p.gcap) {
+          atomicOr(p.err, ERR_PCAP);
+#ifdef GEMPIC_PHASE_TIMERS
+          if (p.timers && atomicCAS(p.timers + 20, 0ull, 1ull) == 0ull) {
+            p.timers[21] = n; p.timers[22] = nin; p.timers[23] = ftop; p.timers[24] = pc;
+            p.timers[25] = slot; p.timers[26] = me; p.timers[27] = (unsigned long long)k;
+          }
+#endif
+          continue;
+        }
+        PState<T> P = get_particle(p, s, ov, 0, s.icell[e]);
+        P.fx = s.ifx[e];
+        P.fy = s.ify[e];
+        P.u = V3<T>{s.iux[e], s.iuy[e], s.iuz[e]};
+        P.sig = s.isig[e];
+        P.q = s.iq[e];
+        put_particle(p, s, ov, slot, P);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        s.misc[M_FTOP] = max(0, ftop - nin);
+        s.misc[M_PCOUNT] = min(p.pcap + p.gcap, pc + max(0, nin - ftop));
+        s.misc[M_INBOX] = 0;
+      }
+    }
     // beam current of this level at the half-slice n + 1/2 (own rows); the flag is cleared
     // by CTA 0 after B2, once every CTA has read it
-    if (ldcg(p.jflag + (size_t)s1 * nz + n)) {
+    if (s.misc[M_JFLAG]) {
       T* jb = (T*)p.jbeam + (((size_t)s1 * nz + n) * 3) * (size_t)p.nx * p.ny;
-      for (int i = tid; i < 3 * plane; i += NT) {
-        const int c = i / plane;
-        const int rem = i - c * plane;
+      for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
+        const int c = i / (p.RB * p.nx);
+        const int rem = i - c * p.RB * p.nx;
         const size_t g = (size_t)c * p.nx * p.ny + ((size_t)me << p.logRB) * p.nx + rem;
-        s.J[i] += ldcg(jb + g);
+        s.J[((size_t)c * p.JR + p.JOFF) * p.nx + rem] += ldcg(jb + g);
         jb[g] = T(0);
       }
     }
     if (snap_step) {
+      __syncthreads();
       T* sn = (T*)p.snap;
-      for (int i = tid; i < 3 * plane; i += NT) {
-        const int c = i / plane;
-        const int rem = i - c * plane;
-        sn[(((size_t)(6 + c) * nz + n) * p.ny + (me << p.logRB)) * p.nx + rem] = s.J[i];
+      for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
+        const int c = i / (p.RB * p.nx);
+        const int rem = i - c * p.RB * p.nx;
+        sn[(((size_t)(6 + c) * nz + n) * p.ny + (me << p.logRB)) * p.nx + rem] =
+            s.J[((size_t)c * p.JR + p.JOFF) * p.nx + rem];
       }
     }
     __syncthreads();
@@ -1211,7 +1659,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     if (tid == 0 && me == 0) p.jflag[(size_t)s1 * nz + n] = 0;
     TIMER_MARK(PH_B2);
     // ---------------- C: column FFTs, per-mode solve, inverse column FFTs ------------------
-    for (int i = tid; i < 3 * plane; i += NT) s.J[i] = T(0);
+    for (int i = tid; i < 3 * jplane; i += NT) s.J[i] = T(0);
     column_ffts(p, s, 0, 3, false);
     __syncthreads();
     TIMER_MARK(PH_COLF);
@@ -1280,27 +1728,38 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     if (waits && tid == 0 && me == 0)
       wait_for(p, pcid, prog_value(k - 1, nz, min(nz, nz - n + 3)));   // down to n-3
     cl.sync();                                                      // B3
+    // the predecessor is now known to be done down to slice n-3: counters of slice n-1
+    if (tid == 0 && n > 0) {
+      s.misc[M_RQN] = ldcg(p.rq.cnt + (size_t)s1 * nz + (n - 1));
+      s.misc[M_JFLAG] = ldcg(p.jflag + (size_t)s1 * nz + (n - 1));
+    }
     TIMER_MARK(PH_B3);
     // ---------------- D: inverse rows -> real-space fields of slice n ----------------------
     inverse_rows(p, s, Fnew, fe);
     TIMER_MARK(PH_INV);
+    if constexpr (sizeof(T) == 4) {
+      // SR has been consumed: it holds the fixed-point accumulators of the next push
+      __syncthreads();
+      for (int i = tid; i < 3 * jplane; i += NT) s.Jint[i] = 0;
+    }
     cl.sync();                                                      // B4: fields of slice n
     TIMER_MARK(PH_B4);
     if (p.diag) {
       const int yc = p.ny / 2;
       if (tid == 0 && (yc >> p.logRB) == me)
-        p.onaxis[sl * nz + n] = (double)Fnew[((size_t)2 * p.RB + (yc & (p.RB - 1))) * p.nx + nxh];
+        p.onaxis[sl * nz + n] = (double)Fnew[((size_t)2 * p.FR + (yc & (p.RB - 1))) * p.nx + nxh];
     }
     if (snap_step) {
       T* sn = (T*)p.snap;
-      for (int i = tid; i < 6 * plane; i += NT) {
-        const int c = i / plane;
-        const int rem = i - c * plane;
-        sn[(((size_t)c * nz + n) * p.ny + (me << p.logRB)) * p.nx + rem] = Fnew[i];
+      for (int i = tid; i < 6 * p.RB * p.nx; i += NT) {
+        const int c = i / (p.RB * p.nx);
+        const int rem = i - c * p.RB * p.nx;
+        sn[(((size_t)c * nz + n) * p.ny + (me << p.logRB)) * p.nx + rem] =
+            Fnew[(size_t)c * fplane + rem];
       }
     }
     // ---------------- E: stored particles of cell (zeta_n, zeta_{n+1}] along s -------------
-    stored_phase(p, s, Fnew, Fcur, k, n, me, acc);
+    stored_phase(p, s, Fnew, Fcur, k, n, me, acc, s.misc[M_STN]);
     TIMER_MARK(PH_E);
     T* t = Fcur;
     Fcur = Fnew;
@@ -1399,7 +1858,7 @@ __global__ void __launch_bounds__(512, 1)
       const double dx = x * p.hx - xc;
       const double dy = p.ny > 1 ? ((me << p.logRB) + yl) * p.hy - yc : 0.0;
       const double E = env * exp(-(dy * dy + dx * dx) / (waist * waist));
-      s.J[i] = (c == 2) ? T(2.0 * E) : T(0);
+      s.J[((size_t)c * p.JR + yl + p.JOFF) * p.nx + x] = (c == 2) ? T(2.0 * E) : T(0);
     }
     __syncthreads();
     forward_rows(cl, p, s, me, false);
@@ -1447,27 +1906,43 @@ __global__ void export_kernel(const Params p, Cx<T>* dst, const Cx<T>* src, int 
 static int align16(int v) { return (v + 15) / 16 * 16; }
 
 int smem_layout(Params& p, int eb) {
+  // halo geometry: fields own rows + 1 above, currents rows -1 .. RB + 1 (3-D only)
+  p.FR = p.ny > 1 ? p.RB + 1 : 1;
+  p.JR = p.ny > 1 ? p.RB + 3 : 1;
+  p.JOFF = p.ny > 1 ? 1 : 0;
+  p.mig_cap = p.ny > 1 ? 128 : 0;
+  p.nwork = std::min(p.nthreads / 32, 3 * p.FR);
   const int nxh = p.nx / 2;
   const int nyh = p.ny > 1 ? p.ny / 2 : 1;
   int o = 0;
   p.o_f0 = o;
-  o += align16(6 * p.RB * p.nx * eb);
+  o += align16(6 * p.FR * p.nx * eb);
   p.o_f1 = o;
-  o += align16(6 * p.RB * p.nx * eb);
+  o += align16(6 * p.FR * p.nx * eb);
   p.o_j = o;
-  o += align16(3 * p.RB * p.nx * eb);
+  o += align16(3 * p.JR * p.nx * eb);
+  p.o_recv = o;
+  o += align16((p.ny > 1 ? 9 : 1) * p.nx * eb);
   p.o_sr = o;
-  o += align16(6 * p.RB * nxh * 2 * eb);
+  const int sr_bytes = align16(6 * p.FR * nxh * 2 * eb);
+  o += sr_bytes;
   p.o_sc = o;
-  o += align16(6 * p.KB * p.ny * 2 * eb);
-  p.o_work = o;
-  o += align16(p.nwork * p.nx * 2 * eb);
+  const int sc_bytes = align16(6 * p.KB * p.ny * 2 * eb);
+  o += sc_bytes;
+  // row-FFT work rows live in SR (forward transform) and SC (inverse) when they fit
+  const int work = align16(p.nwork * p.nx * 2 * eb);
+  p.o_workB = work <= sr_bytes ? p.o_sr : o;
+  if (work > sr_bytes) o += work;
+  p.o_workD = work <= sc_bytes ? p.o_sc : o;
+  if (work > sc_bytes) o += work;
   p.o_tw = o;
   o += align16((nxh + nyh + nxh + p.ny) * 2 * eb + (nxh + p.ny + 32) * eb);
+  p.o_inbox = o;
+  o += align16(p.mig_cap * 4) + align16(7 * p.mig_cap * eb);
   p.o_part = o;
-  o += align16(p.pcap * 4) + 7 * align16(p.pcap * eb) + 16 * 7;
+  o += align16(p.pcap * 4) + align16(7 * p.pcap * eb + p.pcap * 4);
   p.o_misc = o;
-  o += 16 + kNDiag * 8;
+  o += 32 + kNDiag * 8;
   p.smem_bytes = align16(o);
   return p.smem_bytes;
 }

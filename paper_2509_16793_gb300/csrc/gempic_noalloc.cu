@@ -102,6 +102,16 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
   p.delta_field = cfg->delta;
   p.nspecies = cfg->nspecies;
   p.nlayer = off;
+  {
+    // fixed-point range of the FP32 deposit: 4 x the largest (rho - j_z) weight times the
+    // largest transverse cell-to-slice ratio; a larger contribution takes the float path
+    double wmax = 0.0;
+    for (int i = 0; i < cfg->nspecies; ++i)
+      wmax = std::max(wmax, std::fabs(cfg->species[i].charge * cfg->species[i].density /
+                                      cfg->species[i].ppc));
+    const double ratio = std::max(1.0, std::max(g.hx, g.hy) / g.h);
+    p.jref = wmax > 0 ? 4.0 * wmax * ratio : 1.0;
+  }
   p.ppc_sum = ppc_sum;
   p.seed = cfg->seed;
 
@@ -118,6 +128,8 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
   for (int cand = (C0 > 0 ? C0 : 1); cand <= (C0 > 0 ? C0 : kMaxCluster); cand *= 2) {
     if (g.ny % cand || nxh % cand || cand > kMaxCluster) continue;
     if (g.ny == 1 && cand != 1) continue;
+    // 3-D bands need two rows or more (the current halo reaches two rows above the band)
+    if (g.ny > 1 && g.ny / cand < 2) continue;
     const int RB = g.ny / cand, KB = nxh / cand, M = KB * g.ny;
     if (M > 512) continue;
     const int fresh = RB * g.nx * ppc_sum;
@@ -130,7 +142,6 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
     p.logRB = ilog2(RB);
     p.logKB = ilog2(KB);
     p.nthreads = NT;
-    p.nwork = std::min(NT / 32, 3 * RB);
     p.pcap = fresh + 32;
     if (gempic::smem_layout(p, eb) <= smem_optin) {
       chosen = true;
@@ -169,6 +180,10 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
     S->fx = S->fy = S->fz = S->ux = S->uy = S->uz = S->q = b + kOffJflag;
   }
   p.jbeam = b + kOffJflag;
+  // no overflow slots: a band that outgrows its shared memory keeps the extra particles in
+  // their old band (generic path) and, if even that fails, reports an overflow
+  p.gcap = 0;
+  p.pover = b + kOffJflag;
   p.snap = nullptr;
   p.timers = nullptr;
   p.state = state;

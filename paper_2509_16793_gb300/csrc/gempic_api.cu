@@ -395,7 +395,7 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     ALLOC(p.pover, (size_t)std::max(s->pmax, 1) * p.C * p.gcap * (4 + 7 * eb));
     if (p.snapshot) ALLOC(p.snap, (size_t)9 * g.nzeta * nperp * eb);
 #ifdef GEMPIC_PHASE_TIMERS
-    ALLOC(p.timers, 64 * sizeof(unsigned long long));
+    ALLOC(p.timers, 256 * sizeof(unsigned long long));
 #endif
   }
 #undef ALLOC
@@ -639,9 +639,9 @@ int gempic_debug_error_word(gempic_sim* s) {
 // profiling builds only: accumulated clock64 cycles per march phase (thread 0 of each CTA)
 gempic_status gempic_phase_timers(gempic_sim* s, unsigned long long* out, int32_t n) {
   if (!s || !out || n < 1) return GEMPIC_EINVAL;
-  cudaError_t e = cudaMemcpyAsync(out, s->p.timers, std::min(n, 64) * sizeof(unsigned long long),
+  cudaError_t e = cudaMemcpyAsync(out, s->p.timers, std::min(n, 256) * sizeof(unsigned long long),
                                   cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->p.timers, 0, 64 * sizeof(unsigned long long), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->p.timers, 0, 256 * sizeof(unsigned long long), s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return cuda_fail(s, e);
 }

@@ -224,34 +224,39 @@ __device__ __forceinline__ Cx<T> shfl_xor_cx(Cx<T> v, int m) {
   return cx<T>(__shfl_xor_sync(0xffffffffu, v.re, m), __shfl_xor_sync(0xffffffffu, v.im, m));
 }
 
-// N = 32 R: lane l holds x[l + 32 r]; R-point DFT in registers, twiddle W_N^{l k2}, then a
-// 32-point decimation-in-frequency DFT across the lanes (shuffles); X[k2 + R k1] ends in
-// lane bitrev5(k1).
+// Register FFTs of length N = 32 R (R = 1, 2, 4, 8), one transform per warp.  With
+// n = l + 32 r and k = k2 + R k1 the DFT factors as
+//   X[k2 + R k1] = sum_l W_32^{l k1} W_N^{l k2} sum_r W_R^{r k2} x[l + 32 r]:
+// an R-point DFT in the registers of each lane, a twiddle, and a 32-point DFT across the
+// lanes (shuffles).  Two register layouts occur:
+//   natural:   lane l, register r holds element l + 32 r;
+//   lane order: lane l, register k2 holds element k2 + R bitrev5(l).
+// fft_dif_lanes maps natural -> lane order (decimation in frequency across the lanes),
+// fft_dit_lanes maps lane order -> natural (decimation in time); both are unnormalised and
+// take conjugate twiddles when inverse is set.  Stored with register j of lane l at
+// position l + 32 j, both layouts give conflict-free shared-memory rows.
+
+// R-point DFT over the registers of one lane, natural order in and out
 template <typename T, int R>
-__device__ void warp_fft_reg(Cx<T>* d, const Cx<T>* tw, bool inverse) {
-  constexpr int N = 32 * R;
-  const int l = threadIdx.x & 31;
-  Cx<T> a[R];
-#pragma unroll
-  for (int r = 0; r < R; ++r) a[r] = d[l + 32 * r];
-  // R-point DFT over r (radix-2, decimation in time on bit-reversed inputs)
-  if (R > 1) {
+__device__ __forceinline__ void reg_dft(Cx<T> (&a)[R], const Cx<T>* tw, bool inverse) {
+  if constexpr (R > 1) {
+    constexpr int N = 32 * R;
     constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : 3;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int rr = (int)(__brev((unsigned)r) >> (32 - LR));
       if (r < rr) {
-        Cx<T> t = a[r];
+        const Cx<T> t = a[r];
         a[r] = a[rr];
         a[rr] = t;
       }
     }
 #pragma unroll
-    for (int s = 1; s <= LR; ++s) {
-      const int half = 1 << (s - 1);
+    for (int st = 1; st <= LR; ++st) {
+      const int half = 1 << (st - 1);
 #pragma unroll
-      for (int b = 0; b < R / 2; ++b) {
-        const int grp = b >> (s - 1), j = b & (half - 1);
+      for (int q = 0; q < R / 2; ++q) {
+        const int grp = q >> (st - 1), j = q & (half - 1);
         const int i0 = grp * (half << 1) + j, i1 = i0 + half;
         const Cx<T> w = twiddle(tw, N, j * (N / (half << 1)), inverse);
         const Cx<T> t = w * a[i1];
@@ -260,10 +265,16 @@ __device__ void warp_fft_reg(Cx<T>* d, const Cx<T>* tw, bool inverse) {
         a[i1] = u - t;
       }
     }
-#pragma unroll
-    for (int k2 = 1; k2 < R; ++k2) a[k2] = twiddle(tw, N, l * k2, inverse) * a[k2];
   }
-  // 32-point DFT across lanes
+}
+
+template <typename T, int R>
+__device__ __forceinline__ void fft_dif_lanes(Cx<T> (&a)[R], const Cx<T>* tw, bool inverse) {
+  constexpr int N = 32 * R;
+  const int l = threadIdx.x & 31;
+  reg_dft<T, R>(a, tw, inverse);
+#pragma unroll
+  for (int k2 = 1; k2 < R; ++k2) a[k2] = twiddle(tw, N, l * k2, inverse) * a[k2];
 #pragma unroll
   for (int half = 16; half >= 1; half >>= 1) {
     const bool bottom = (l & half) != 0;
@@ -274,112 +285,62 @@ __device__ void warp_fft_reg(Cx<T>* d, const Cx<T>* tw, bool inverse) {
       a[k2] = bottom ? w * (o - a[k2]) : a[k2] + o;
     }
   }
-  __syncwarp();
-  const int k1 = (int)(__brev((unsigned)l) >> 27);
-#pragma unroll
-  for (int k2 = 0; k2 < R; ++k2) d[k2 + R * k1] = a[k2];
-  __syncwarp();
 }
 
-// One or two transforms per warp with the layout of warp_fft_reg, reading element j of
-// transform t through ld(t, j) and writing element k through st(t, k, value); the second
-// transform (t1 >= 0) runs interleaved with the first for instruction-level parallelism.
-template <typename T, int R, bool PAIR, typename LD, typename ST>
-__device__ __forceinline__ void wfft2(const LD& ld, const ST& st, int t0, int t1,
-                                      const Cx<T>* tw, bool inverse) {
+template <typename T, int R>
+__device__ __forceinline__ void fft_dit_lanes(Cx<T> (&a)[R], const Cx<T>* tw, bool inverse) {
   constexpr int N = 32 * R;
   const int l = threadIdx.x & 31;
-  const bool two = PAIR && t1 >= 0;
-  Cx<T> a[R], b[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    a[r] = ld(t0, l + 32 * r);
-    b[r] = two ? ld(t1, l + 32 * r) : a[r];
-  }
-  if (R > 1) {
-    constexpr int LR = R == 2 ? 1 : R == 4 ? 2 : 3;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int rr = (int)(__brev((unsigned)r) >> (32 - LR));
-      if (r < rr) {
-        Cx<T> t = a[r];
-        a[r] = a[rr];
-        a[rr] = t;
-        t = b[r];
-        b[r] = b[rr];
-        b[rr] = t;
-      }
-    }
-#pragma unroll
-    for (int s = 1; s <= LR; ++s) {
-      const int half = 1 << (s - 1);
-#pragma unroll
-      for (int q = 0; q < R / 2; ++q) {
-        const int grp = q >> (s - 1), j = q & (half - 1);
-        const int i0 = grp * (half << 1) + j, i1 = i0 + half;
-        const Cx<T> w = twiddle(tw, N, j * (N / (half << 1)), inverse);
-        const Cx<T> ta = w * a[i1], tb = w * b[i1];
-        const Cx<T> ua = a[i0], ub = b[i0];
-        a[i0] = ua + ta;
-        a[i1] = ua - ta;
-        b[i0] = ub + tb;
-        b[i1] = ub - tb;
-      }
-    }
-#pragma unroll
-    for (int k2 = 1; k2 < R; ++k2) {
-      const Cx<T> w = twiddle(tw, N, l * k2, inverse);
-      a[k2] = w * a[k2];
-      b[k2] = w * b[k2];
-    }
-  }
-#pragma unroll
-  for (int half = 16; half >= 1; half >>= 1) {
+  for (int half = 1; half <= 16; half <<= 1) {
     const bool bottom = (l & half) != 0;
     const Cx<T> w = twiddle(tw, N, (l & (half - 1)) * (16 / half) * R, inverse);
 #pragma unroll
     for (int k2 = 0; k2 < R; ++k2) {
-      const Cx<T> oa = shfl_xor_cx(a[k2], half);
-      const Cx<T> ob = shfl_xor_cx(b[k2], half);
-      a[k2] = bottom ? w * (oa - a[k2]) : a[k2] + oa;
-      b[k2] = bottom ? w * (ob - b[k2]) : b[k2] + ob;
+      const Cx<T> t = bottom ? w * a[k2] : a[k2];
+      const Cx<T> o = shfl_xor_cx(t, half);
+      a[k2] = bottom ? o - t : t + o;
     }
   }
-  __syncwarp();
-  const int k1 = (int)(__brev((unsigned)l) >> 27);
 #pragma unroll
-  for (int k2 = 0; k2 < R; ++k2) {
-    st(t0, k2 + R * k1, a[k2]);
-    if (two) st(t1, k2 + R * k1, b[k2]);
-  }
-  __syncwarp();
+  for (int k2 = 1; k2 < R; ++k2) a[k2] = twiddle(tw, N, l * k2, inverse) * a[k2];
+  reg_dft<T, R>(a, tw, inverse);
 }
 
-// dispatch on the transform length; false if it has no register version (caller falls back)
-template <typename T, typename LD, typename ST>
-__device__ __forceinline__ bool wfft2_dispatch(int logN, const LD& ld, const ST& st, int t0, int t1,
-                                               const Cx<T>* tw, bool inverse) {
-  // two transforms per warp up to length 128; longer ones run one at a time (registers)
-  switch (logN) {
-    case 5: wfft2<T, 1, false>(ld, st, t0, -1, tw, inverse); break;
-    case 6: wfft2<T, 2, false>(ld, st, t0, -1, tw, inverse); break;
-    case 7: wfft2<T, 4, false>(ld, st, t0, -1, tw, inverse); break;
-    case 8: wfft2<T, 8, false>(ld, st, t0, -1, tw, inverse); break;
-    default: return false;
-  }
-  if (t1 >= 0) wfft2_dispatch<T>(logN, ld, st, t1, -1, tw, inverse);
-  return true;
+// lengths with a register FFT
+__host__ __device__ __forceinline__ bool reg_fft_len(int logN) { return logN >= 5 && logN <= 8; }
+
+// Column spectra are kept in lane order: position q of a column of length ny holds
+// ky index ky_of_pos(q).  Identity for lengths without a register FFT.
+__host__ __device__ __forceinline__ int bitrev5(int v) {
+  return ((v & 1) << 4) | ((v & 2) << 2) | (v & 4) | ((v & 8) >> 2) | ((v & 16) >> 4);
+}
+__host__ __device__ __forceinline__ int ky_of_pos(int logny, int q) {
+  if (!reg_fft_len(logny)) return q;
+  const int R = 1 << (logny - 5);
+  return (q >> 5) + R * bitrev5(q & 31);
+}
+__host__ __device__ __forceinline__ int pos_of_ky(int logny, int ky) {
+  if (!reg_fft_len(logny)) return ky;
+  const int R = 1 << (logny - 5);
+  return bitrev5(ky / R) + 32 * (ky % R);
 }
 
-template <typename T>
-__device__ void warp_fft(Cx<T>* d, int logN, const Cx<T>* tw, bool inverse) {
-  switch (logN) {
-    case 0: return;
-    case 5: warp_fft_reg<T, 1>(d, tw, inverse); return;
-    case 6: warp_fft_reg<T, 2>(d, tw, inverse); return;
-    case 7: warp_fft_reg<T, 4>(d, tw, inverse); return;
-    case 8: warp_fft_reg<T, 8>(d, tw, inverse); return;
-    default: warp_fft_r2(d, logN, tw, inverse); return;
+// store R consecutive reals (16-byte vectors where the run allows)
+template <typename T, int R>
+__device__ __forceinline__ void st_run(T* dst, const T (&v)[R]) {
+  if constexpr (sizeof(T) == 4 && R >= 4) {
+#pragma unroll
+    for (int i = 0; i < R; i += 4)
+      *reinterpret_cast<float4*>(dst + i) = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+  } else if constexpr (sizeof(T) == 4 && R == 2) {
+    *reinterpret_cast<float2*>(dst) = make_float2(v[0], v[1]);
+  } else if constexpr (sizeof(T) == 8 && R >= 2) {
+#pragma unroll
+    for (int i = 0; i < R; i += 2) *reinterpret_cast<double2*>(dst + i) = make_double2(v[i], v[i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < R; ++i) dst[i] = v[i];
   }
 }
 
@@ -559,9 +520,70 @@ __device__ __forceinline__ void st_cx(const cg::cluster_group& cl, Cx<T>* local,
   *q = v;
 }
 
+// Register path (nx = 32 R): task (row yl, pair pr) transforms u + i v of two real rows; the
+// spectra split as U(k) = (Z(k) + conj Z(N-k))/2, V(k) = i (conj Z(N-k) - Z(k))/2.  With Z
+// in lane order the partner N - k of register k2 > 0 is register R - k2 of lane l ^ 31, that
+// of register 0 is register 0 of lane bitrev5(-bitrev5(l) mod 32); the lanes holding
+// k < N/2 are the even ones.  Values go from registers straight to the kx owners.
+template <typename T, int R>
+__device__ void forward_rows_reg(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
+                                 int me, bool stagger) {
+  constexpr int N = 32 * R;
+  const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const int ntask = 2 * p.RB;
+  const int k1 = bitrev5(l);
+  const int src0 = bitrev5((32 - k1) & 31);
+  for (int task = warp; task < ntask; task += nwarps) {
+    const int yl = task >> 1, pr = task & 1;
+    const T* A = s.J + ((size_t)(pr == 0 ? 0 : 2) * p.JR + yl + p.JOFF) * N;
+    const T* B = s.J + ((size_t)1 * p.JR + yl + p.JOFF) * N;
+    Cx<T> a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) a[r] = cx<T>(A[l + 32 * r], pr == 0 ? B[l + 32 * r] : T(0));
+    fft_dif_lanes<T, R>(a, s.twx, false);
+    Cx<T> zm[R];
+    zm[0] = cx<T>(__shfl_sync(0xffffffffu, a[0].re, src0), __shfl_sync(0xffffffffu, a[0].im, src0));
+#pragma unroll
+    for (int k2 = 1; k2 < R; ++k2) zm[k2] = shfl_xor_cx(a[R - k2], 31);
+    if (l & 1) continue;
+    const int y = (me << p.logRB) + yl;
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) {
+      const int k = k2 + R * k1;
+      const Cx<T> zc = conjg(zm[k2]);
+      Cx<T> X = T(0.5) * (a[k2] + zc);                  // spectrum of the real part
+      const Cx<T> Y = T(0.5) * mul_i(zc - a[k2]);       // spectrum of the imaginary part
+      const int rd = k >> p.logKB, kxl = k & (p.KB - 1);
+      if (pr == 0) {
+        if (stagger) X = X * s.shx[k];
+        st_cx(cl, s.SC + ((size_t)0 * p.KB + kxl) * p.ny + y, rd, me, X);
+        st_cx(cl, s.SC + ((size_t)1 * p.KB + kxl) * p.ny + y, rd, me, Y);
+      } else {
+        st_cx(cl, s.SC + ((size_t)2 * p.KB + kxl) * p.ny + y, rd, me, X);
+      }
+    }
+  }
+}
+
+// the length-256 variants run out of line: inlined, their registers would spill the march's
+// carried per-mode state at every length
+template <typename T>
+__device__ __noinline__ void forward_rows_r8(const cg::cluster_group& cl, const Params& p,
+                                             const Sm<T>& s, int me, bool stagger) {
+  forward_rows_reg<T, 8>(cl, p, s, me, stagger);
+}
+
 template <typename T>
 __device__ void forward_rows(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
                              int me, bool stagger) {
+  switch (p.lognx) {
+    case 5: forward_rows_reg<T, 1>(cl, p, s, me, stagger); return;
+    case 6: forward_rows_reg<T, 2>(cl, p, s, me, stagger); return;
+    case 7: forward_rows_reg<T, 4>(cl, p, s, me, stagger); return;
+    case 8: forward_rows_r8<T>(cl, p, s, me, stagger); return;
+    default: break;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nxh = p.nx / 2;
   const int ntask = 2 * p.RB;                 // (row, pair): pair 0 = jx + i jy, 1 = jz
@@ -573,7 +595,7 @@ __device__ void forward_rows(const cg::cluster_group& cl, const Params& p, const
     const T* b = s.J + ((size_t)1 * p.JR + yl + p.JOFF) * p.nx;
     for (int x = lane; x < p.nx; x += 32) w[x] = cx<T>(a[x], pr == 0 ? b[x] : T(0));
     __syncwarp();
-    warp_fft(w, p.lognx, s.twx, false);
+    warp_fft_r2(w, p.lognx, s.twx, false);
     const int y = (me << p.logRB) + yl;
     for (int k = lane; k < nxh; k += 32) {
       const Cx<T> zk = w[k];
@@ -593,7 +615,29 @@ __device__ void forward_rows(const cg::cluster_group& cl, const Params& p, const
   }
 }
 
-// column FFTs of SC[c0..c1) (in place), forward or inverse
+// one column of length 32 R: forward from natural order to lane order, inverse from lane
+// order to natural order; every lane rewrites the positions it read
+template <typename T, int R>
+__device__ __forceinline__ void col_fft_reg(Cx<T>* d, const Cx<T>* tw, bool inverse) {
+  const int l = threadIdx.x & 31;
+  Cx<T> a[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) a[r] = d[l + 32 * r];
+  if (inverse)
+    fft_dit_lanes<T, R>(a, tw, true);
+  else
+    fft_dif_lanes<T, R>(a, tw, false);
+#pragma unroll
+  for (int r = 0; r < R; ++r) d[l + 32 * r] = a[r];
+}
+
+template <typename T>
+__device__ __noinline__ void col_fft_r8(Cx<T>* d, const Cx<T>* tw, bool inverse) {
+  col_fft_reg<T, 8>(d, tw, inverse);
+}
+
+// column FFTs of SC[c0..c1) (in place), forward or inverse; with a register FFT the
+// spectra stay in lane order (position q holds ky_of_pos(q))
 template <typename T>
 __device__ void column_ffts(const Params& p, const Sm<T>& s, int c0, int c1, bool inverse) {
   if (p.ny == 1) return;
@@ -602,7 +646,14 @@ __device__ void column_ffts(const Params& p, const Sm<T>& s, int c0, int c1, boo
   const int ntask = (c1 - c0) << p.logKB;
   for (int task = warp; task < ntask; task += nwarps) {
     const int c = c0 + (task >> p.logKB), kxl = task & (p.KB - 1);
-    warp_fft(s.SC + ((size_t)c * p.KB + kxl) * p.ny, p.logny, s.twy, inverse);
+    Cx<T>* d = s.SC + ((size_t)c * p.KB + kxl) * p.ny;
+    switch (p.logny) {
+      case 5: col_fft_reg<T, 1>(d, s.twy, inverse); break;
+      case 6: col_fft_reg<T, 2>(d, s.twy, inverse); break;
+      case 7: col_fft_reg<T, 4>(d, s.twy, inverse); break;
+      case 8: col_fft_r8<T>(d, s.twy, inverse); break;
+      default: warp_fft_r2(d, p.logny, s.twy, inverse); break;
+    }
   }
 }
 
@@ -644,43 +695,74 @@ __device__ void scatter_to_rows(const cg::cluster_group& cl, const Params& p, co
 }
 
 // inverse row transforms: SR pairs (Ex,Ey), (Ez,Bx), (By,Bz) -> real rows of Fdst (own rows
-// and the halo row); the field energy counts own rows only.  For lengths with a register FFT
-// the spectrum X + iY (with X(-k) = conj X(k)) is formed while loading and the real and
-// imaginary parts are written straight to the two field rows, two transforms per warp.
+// and the halo row); the field energy counts own rows only.  The spectrum X + iY (with
+// X(-k) = conj X(k)) is formed while loading; the real and imaginary parts of the result
+// are the two field rows.  Register path (nx = 32 R): each lane ends with R consecutive
+// outputs and stores them as vectors.
+template <typename T, int R>
+__device__ void inverse_rows_reg(const Params& p, const Sm<T>& s, T* Fdst, T& fe) {
+  constexpr int N = 32 * R;
+  constexpr int nxh = N / 2;
+  const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  const T scale = T(1.0 / ((double)p.nx * (double)p.ny));
+  const int ntask = 3 * p.FR;
+  const int k1 = bitrev5(l);
+  T acc = T(0);
+  for (int t = warp; t < ntask; t += nwarps) {
+    const int yl = t / 3, pr = t - 3 * (t / 3);
+    const Cx<T>* X = s.SR + ((size_t)(2 * pr) * p.FR + yl) * nxh;
+    const Cx<T>* Y = s.SR + ((size_t)(2 * pr + 1) * p.FR + yl) * nxh;
+    Cx<T> a[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int j = l + 32 * r;
+      Cx<T> v = cx<T>(T(0), T(0));                        // Nyquist projected out
+      if (j < nxh) {
+        const Cx<T> x = X[j], y = Y[j];
+        v = j == 0 ? cx<T>(x.re, y.re)                     // real DC of each field
+                   : cx<T>(x.re - y.im, x.im + y.re);      // X + i Y
+      } else if (j > nxh) {
+        const Cx<T> x = X[N - j], y = Y[N - j];
+        v = cx<T>(x.re + y.im, y.re - x.im);               // conj(X) + i conj(Y)
+      }
+      a[r] = v;
+    }
+    fft_dif_lanes<T, R>(a, s.twx, true);
+    T va[R], vb[R];
+#pragma unroll
+    for (int k2 = 0; k2 < R; ++k2) {
+      va[k2] = a[k2].re * scale;
+      vb[k2] = a[k2].im * scale;
+    }
+    st_run<T, R>(Fdst + ((size_t)(2 * pr) * p.FR + yl) * N + R * k1, va);
+    st_run<T, R>(Fdst + ((size_t)(2 * pr + 1) * p.FR + yl) * N + R * k1, vb);
+    if (yl < p.RB) {
+#pragma unroll
+      for (int k2 = 0; k2 < R; ++k2) acc += va[k2] * va[k2] + vb[k2] * vb[k2];
+    }
+  }
+  fe += acc;
+}
+
+template <typename T>
+__device__ __noinline__ void inverse_rows_r8(const Params& p, const Sm<T>& s, T* Fdst, T& fe) {
+  inverse_rows_reg<T, 8>(p, s, Fdst, fe);
+}
+
 template <typename T>
 __device__ void inverse_rows(const Params& p, const Sm<T>& s, T* Fdst, T& fe) {
+  switch (p.lognx) {
+    case 5: inverse_rows_reg<T, 1>(p, s, Fdst, fe); return;
+    case 6: inverse_rows_reg<T, 2>(p, s, Fdst, fe); return;
+    case 7: inverse_rows_reg<T, 4>(p, s, Fdst, fe); return;
+    case 8: inverse_rows_r8<T>(p, s, Fdst, fe); return;
+    default: break;
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nwarps = blockDim.x >> 5;
   const int nxh = p.nx / 2;
   const T scale = T(1.0 / ((double)p.nx * (double)p.ny));
   const int ntask = 3 * p.FR;
-  if (p.lognx >= 5 && p.lognx <= 8) {
-    // task t: row yl = t / 3, pair pr = t % 3
-    const auto ld = [&](int t, int j) -> Cx<T> {
-      const int yl = t / 3, pr = t - 3 * (t / 3);
-      const Cx<T>* X = s.SR + ((size_t)(2 * pr) * p.FR + yl) * nxh;
-      const Cx<T>* Y = s.SR + ((size_t)(2 * pr + 1) * p.FR + yl) * nxh;
-      if (j == 0) return cx<T>(X[0].re, Y[0].re);             // real DC of each field
-      if (j == nxh) return cx<T>(T(0), T(0));                 // Nyquist projected out
-      if (j < nxh) {
-        const Cx<T> x = X[j], y = Y[j];
-        return cx<T>(x.re - y.im, x.im + y.re);               // X + i Y
-      }
-      const Cx<T> x = X[p.nx - j], y = Y[p.nx - j];
-      return cx<T>(x.re + y.im, y.re - x.im);                 // conj(X) + i conj(Y)
-    };
-    T acc = T(0);
-    const auto st = [&](int t, int k, Cx<T> v) {
-      const int yl = t / 3, pr = t - 3 * (t / 3);
-      const T va = v.re * scale, vb = v.im * scale;
-      Fdst[((size_t)(2 * pr) * p.FR + yl) * p.nx + k] = va;
-      Fdst[((size_t)(2 * pr + 1) * p.FR + yl) * p.nx + k] = vb;
-      if (yl < p.RB) acc += va * va + vb * vb;
-    };
-    for (int t = warp; t < ntask; t += nwarps) wfft2_dispatch<T>(p.lognx, ld, st, t, -1, s.twx, true);
-    fe += acc;
-    return;
-  }
   for (int task = (warp < p.nwork ? warp : ntask); task < ntask; task += p.nwork) {
     Cx<T>* w = s.workD + (size_t)warp * p.nx;
     const int yl = task / 3, pr = task - 3 * yl;
@@ -1440,10 +1522,12 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   if constexpr (sizeof(T) == 4)
     for (int i = tid; i < 3 * jplane; i += NT) s.Jint[i] = 0;
 
-  // per-mode carried state (one mode per thread)
+  // per-mode carried state (one mode per thread): thread m owns column position q of kx
+  // column kxl, i.e. the mode (kxl, ky_of_pos(q))
   const int m = tid;
   const bool has_mode = m < p.M;
-  const int kxl = has_mode ? m >> p.logny : 0, kyi = has_mode ? m & (p.ny - 1) : 0;
+  const int kxl = has_mode ? m >> p.logny : 0, q = has_mode ? m & (p.ny - 1) : 0;
+  const int kyi = ky_of_pos(p.logny, q);
   const T kx = has_mode ? s.kx[(me << p.logKB) + kxl] : T(0);
   const T ky = has_mode ? s.ky[kyi] : T(0);
   const bool masked = p.ny > 1 && kyi == p.ny / 2;
@@ -1664,9 +1748,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     __syncthreads();
     TIMER_MARK(PH_COLF);
     if (has_mode) {
-      Cx<T> Jx = s.SC[((size_t)0 * p.KB + kxl) * p.ny + kyi];
-      Cx<T> Jy = s.SC[((size_t)1 * p.KB + kxl) * p.ny + kyi];
-      Cx<T> Jz = s.SC[((size_t)2 * p.KB + kxl) * p.ny + kyi];
+      Cx<T> Jx = s.SC[((size_t)0 * p.KB + kxl) * p.ny + q];
+      Cx<T> Jy = s.SC[((size_t)1 * p.KB + kxl) * p.ny + q];
+      Cx<T> Jz = s.SC[((size_t)2 * p.KB + kxl) * p.ny + q];
       if (p.ny > 1) Jy = Jy * s.shy[kyi];
       if (masked) Jx = Jy = Jz = cx<T>(T(0), T(0));
       // corrector: R at slice n+1 was built with j_{n+1/2} := j_{n+3/2}
@@ -1694,7 +1778,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
                          Jy, Jz);
       }
       // fields E, B (Eqs. Rx..Ly) for the inverse transform
-      Cx<T>* sc = s.SC + (size_t)kxl * p.ny + kyi;
+      Cx<T>* sc = s.SC + (size_t)kxl * p.ny + q;
       const size_t cs = (size_t)p.KB * p.ny;
       sc[0 * cs] = T(0.5) * (S0.Rx + S0.Lx);
       sc[1 * cs] = T(0.5) * (S0.Ry + S0.Ly);
@@ -1866,9 +1950,9 @@ __global__ void __launch_bounds__(512, 1)
     column_ffts(p, s, 2, 3, false);
     __syncthreads();
     for (int m = threadIdx.x; m < p.M; m += blockDim.x) {
-      const int kxl = m >> p.logny, kyi = m & (p.ny - 1);
-      Cx<T> v = s.SC[((size_t)2 * p.KB + kxl) * p.ny + kyi];
-      if (p.ny > 1 && kyi == p.ny / 2) v = cx<T>(T(0), T(0));
+      const int kxl = m >> p.logny, q = m & (p.ny - 1);
+      Cx<T> v = s.SC[((size_t)2 * p.KB + kxl) * p.ny + q];
+      if (p.ny > 1 && ky_of_pos(p.logny, q) == p.ny / 2) v = cx<T>(T(0), T(0));
       const Cx<T> z = cx<T>(T(0), T(0));
       for (int c = 0; c < 6; ++c)
         stw[(((size_t)n * p.C + me) * 6 + c) * p.M + m] = (c == pol) ? v : z;
@@ -1892,7 +1976,8 @@ __global__ void export_kernel(const Params p, Cx<T>* dst, const Cx<T>* src, int 
     const int c = (int)(i / (nxh * p.ny * p.nz));
     const int b = c >= 4 ? n + 1 : n;
     const int r = kx / p.KB, kxl = kx % p.KB;
-    const size_t e = (((size_t)b * p.C + r) * 6 + c) * p.M + (size_t)kxl * p.ny + ky;
+    const size_t e = (((size_t)b * p.C + r) * 6 + c) * p.M + (size_t)kxl * p.ny +
+                     pos_of_ky(p.logny, ky);
     if (dir == 0)
       dst[i] = src[e];
     else

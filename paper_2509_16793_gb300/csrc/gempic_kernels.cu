@@ -524,16 +524,20 @@ __device__ __forceinline__ void st_cx(const cg::cluster_group& cl, Cx<T>* local,
 // spectra split as U(k) = (Z(k) + conj Z(N-k))/2, V(k) = i (conj Z(N-k) - Z(k))/2.  With Z
 // in lane order the partner N - k of register k2 > 0 is register R - k2 of lane l ^ 31, that
 // of register 0 is register 0 of lane bitrev5(-bitrev5(l) mod 32); the lanes holding
-// k < N/2 are the even ones.  Values go from registers straight to the kx owners.
+// k < N/2 are the even ones.  Their values are staged in SR (free until the inverse
+// transform) as rows [comp][k2][yl] of 16 + 1 entries (conflict-free both ways), then each
+// element (comp, k, yl), yl fastest, goes to its kx owner: a warp's 32 stores go to one CTA.
 template <typename T, int R>
 __device__ void forward_rows_reg(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
                                  int me, bool stagger) {
-  constexpr int N = 32 * R;
+  constexpr int N = 32 * R, NH = N / 2, SP = 17;
+  constexpr int LR = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3;
   const int warp = threadIdx.x >> 5, l = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
   const int ntask = 2 * p.RB;
   const int k1 = bitrev5(l);
   const int src0 = bitrev5((32 - k1) & 31);
+  Cx<T>* stg = s.SR;      // [3][R][RB][SP]
   for (int task = warp; task < ntask; task += nwarps) {
     const int yl = task >> 1, pr = task & 1;
     const T* A = s.J + ((size_t)(pr == 0 ? 0 : 2) * p.JR + yl + p.JOFF) * N;
@@ -547,22 +551,30 @@ __device__ void forward_rows_reg(const cg::cluster_group& cl, const Params& p, c
 #pragma unroll
     for (int k2 = 1; k2 < R; ++k2) zm[k2] = shfl_xor_cx(a[R - k2], 31);
     if (l & 1) continue;
-    const int y = (me << p.logRB) + yl;
 #pragma unroll
     for (int k2 = 0; k2 < R; ++k2) {
       const int k = k2 + R * k1;
       const Cx<T> zc = conjg(zm[k2]);
       Cx<T> X = T(0.5) * (a[k2] + zc);                  // spectrum of the real part
       const Cx<T> Y = T(0.5) * mul_i(zc - a[k2]);       // spectrum of the imaginary part
-      const int rd = k >> p.logKB, kxl = k & (p.KB - 1);
       if (pr == 0) {
         if (stagger) X = X * s.shx[k];
-        st_cx(cl, s.SC + ((size_t)0 * p.KB + kxl) * p.ny + y, rd, me, X);
-        st_cx(cl, s.SC + ((size_t)1 * p.KB + kxl) * p.ny + y, rd, me, Y);
+        stg[((0 * R + k2) * p.RB + yl) * SP + (l >> 1)] = X;
+        stg[((1 * R + k2) * p.RB + yl) * SP + (l >> 1)] = Y;
       } else {
-        st_cx(cl, s.SC + ((size_t)2 * p.KB + kxl) * p.ny + y, rd, me, X);
+        stg[((2 * R + k2) * p.RB + yl) * SP + (l >> 1)] = X;
       }
     }
+  }
+  __syncthreads();
+  const int total = 3 * NH * p.RB;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int yl = i & (p.RB - 1);
+    const int rest = i >> p.logRB;
+    const int k = rest & (NH - 1), c = rest / NH;
+    const Cx<T> v = stg[((c * R + (k & (R - 1))) * p.RB + yl) * SP + (bitrev5(k >> LR) >> 1)];
+    const int rd = k >> p.logKB, kxl = k & (p.KB - 1);
+    st_cx(cl, s.SC + ((size_t)c * p.KB + kxl) * p.ny + (me << p.logRB) + yl, rd, me, v);
   }
 }
 
@@ -658,38 +670,26 @@ __device__ void column_ffts(const Params& p, const Sm<T>& s, int c0, int c1, boo
 }
 
 // scatter the 6 inverse-column-transformed field spectra to the row owners' SR; the first row
-// of each band also goes to the band below as its halo row FR - 1 = RB.  One thread per
-// (component, row) moves the CTA's KB consecutive kx values, 16 bytes per store.
+// of each band also goes to the band below as its halo row FR - 1 = RB.  Element
+// (comp, y, kxl), kxl fastest: with KB RB >= 32 a warp's stores go to one owner CTA.
 template <typename T>
 __device__ void scatter_to_rows(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
                                 int me) {
   const int nxh = p.nx / 2;
-  const int n = 6 * p.ny;
-  const size_t cs = (size_t)p.KB * p.ny;
   const int kx0 = me << p.logKB;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const int c = i >> p.logny, y = i & (p.ny - 1);
+  const int total = 6 * p.ny * p.KB;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int kxl = i & (p.KB - 1);
+    const int y = (i >> p.logKB) & (p.ny - 1);
+    const int c = i >> (p.logKB + p.logny);
     const int ro = y >> p.logRB, yl = y & (p.RB - 1);
-    const bool halo = p.ny > 1 && yl == 0;
-    const int rb = (ro + p.C - 1) & (p.C - 1);
-    Cx<T>* d0 = s.SR + ((size_t)c * p.FR + yl) * nxh + kx0;
-    Cx<T>* d1 = s.SR + ((size_t)c * p.FR + p.RB) * nxh + kx0;
-    Cx<T>* q0 = ro == me ? d0 : cl.map_shared_rank(d0, ro);
-    Cx<T>* q1 = rb == me ? d1 : cl.map_shared_rank(d1, rb);
-    const Cx<T>* src = s.SC + c * cs + y;
-    if (sizeof(Cx<T>) == 8 && (p.KB & 1) == 0) {
-      for (int kxl = 0; kxl < p.KB; kxl += 2) {
-        const Cx<T> a = src[(size_t)kxl * p.ny], b = src[(size_t)(kxl + 1) * p.ny];
-        const float4 v = make_float4((float)a.re, (float)a.im, (float)b.re, (float)b.im);
-        *reinterpret_cast<float4*>(q0 + kxl) = v;
-        if (halo) *reinterpret_cast<float4*>(q1 + kxl) = v;
-      }
-    } else {
-      for (int kxl = 0; kxl < p.KB; ++kxl) {
-        const Cx<T> a = src[(size_t)kxl * p.ny];
-        q0[kxl] = a;
-        if (halo) q1[kxl] = a;
-      }
+    const Cx<T> v = s.SC[((size_t)c * p.KB + kxl) * p.ny + y];
+    Cx<T>* d0 = s.SR + ((size_t)c * p.FR + yl) * nxh + kx0 + kxl;
+    *(ro == me ? d0 : cl.map_shared_rank(d0, ro)) = v;
+    if (p.ny > 1 && yl == 0) {
+      const int rb = (ro + p.C - 1) & (p.C - 1);
+      Cx<T>* d1 = s.SR + ((size_t)c * p.FR + p.RB) * nxh + kx0 + kxl;
+      *(rb == me ? d1 : cl.map_shared_rank(d1, rb)) = v;
     }
   }
 }

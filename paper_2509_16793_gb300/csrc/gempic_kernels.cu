@@ -941,7 +941,10 @@ struct Sink<T, false> {
 
 // Esirkepov (Comput. Phys. Commun. 135, 2001) transverse current of a move (X0,Y0)->(X1,Y1)
 // in cell units relative to node (ix, row 0 of the sink); w is the (rho - j_z) weight.  With
-// D = w S the deposit satisfies (D_new - D_old) + h div J = 0 on every node.
+// D = w S the deposit satisfies (D_new - D_old) + h div J = 0 on every node.  A sub-step that
+// stays inside one cell column (row) has no current on its second x-edge (y-edge row): those
+// sums vanish exactly and are set to zero rather than left to rounding, so they deposit
+// nothing.
 template <typename T, bool LOCAL>
 __device__ void esirkepov(const Params& p, const Sm<T>& s, const Sink<T, LOCAL>& sk, int ix,
                           T X0, T Y0, T X1, T Y1, T w, T dyo) {
@@ -964,12 +967,13 @@ __device__ void esirkepov(const Params& p, const Sm<T>& s, const Sink<T, LOCAL>&
       S1x[a] = fmax(T(0), T(1) - fabs(xb - (bx + T(a))));
     }
     const int gx = ix + (int)bx;
+    const bool crossx = floor(fmax(xa, xb)) != bx;
     if (p.ny == 1) {
       T cum = T(0);
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         cum = cum + (S1x[a] - S0x[a]);
-        sk.add(0, 0, (gx + a) & mx, cx_ * cum);
+        sk.add(0, 0, (gx + a) & mx, (a == 0 || crossx) ? cx_ * cum : T(0));
       }
       const T dyv = dyo / T(nsub);
 #pragma unroll
@@ -987,6 +991,7 @@ __device__ void esirkepov(const Params& p, const Sm<T>& s, const Sink<T, LOCAL>&
       S1y[b] = fmax(T(0), T(1) - fabs(yb - (by + T(b))));
     }
     const int gy = (int)by;
+    const bool crossy = floor(fmax(ya, yb)) != by;
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
       const T hy2 = T(0.5) * (S0y[b] + S1y[b]);
@@ -995,7 +1000,7 @@ __device__ void esirkepov(const Params& p, const Sm<T>& s, const Sink<T, LOCAL>&
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         cum = cum + (S1x[a] - S0x[a]) * hy2;
-        sk.add(0, gy + b, (gx + a) & mx, cx_ * cum);
+        sk.add(0, gy + b, (gx + a) & mx, (a == 0 || crossx) ? cx_ * cum : T(0));
       }
     }
 #pragma unroll
@@ -1005,7 +1010,7 @@ __device__ void esirkepov(const Params& p, const Sm<T>& s, const Sink<T, LOCAL>&
         // cumulative sum over b of (S1y - S0y)(S0x + S1x)/2 at column a
         T cum = (S1y[0] - S0y[0]) * T(0.5) * (S0x[a] + S1x[a]);
         if (b == 1) cum = cum + (S1y[1] - S0y[1]) * T(0.5) * (S0x[a] + S1x[a]);
-        sk.add(1, gy + b, (gx + a) & mx, cy_ * cum);
+        sk.add(1, gy + b, (gx + a) & mx, (b == 0 || crossy) ? cy_ * cum : T(0));
       }
     }
   }

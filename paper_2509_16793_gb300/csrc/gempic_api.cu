@@ -52,6 +52,12 @@ gempic_status cuda_fail(gempic_sim* s, cudaError_t e) {
   return GEMPIC_ECUDA;
 }
 
+#ifdef GEMPIC_PHASE_TIMERS
+// profiling builds: 256 words of phase sums, then per (slice, CTA) of the first march of a
+// launch the cycles from the slice start to the arrival at and the release from barrier B1
+static int timer_words(const gempic::Params& p) { return 256 + 2 * p.nz * p.C; }
+#endif
+
 template <typename Tp>
 cudaError_t dalloc(gempic_sim* s, Tp** ptr, size_t bytes) {
   void* v = nullptr;
@@ -395,7 +401,7 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     ALLOC(p.pover, (size_t)std::max(s->pmax, 1) * p.C * p.gcap * (4 + 7 * eb));
     if (p.snapshot) ALLOC(p.snap, (size_t)9 * g.nzeta * nperp * eb);
 #ifdef GEMPIC_PHASE_TIMERS
-    ALLOC(p.timers, 256 * sizeof(unsigned long long));
+    ALLOC(p.timers, timer_words(p) * sizeof(unsigned long long));
 #endif
   }
 #undef ALLOC
@@ -639,9 +645,10 @@ int gempic_debug_error_word(gempic_sim* s) {
 // profiling builds only: accumulated clock64 cycles per march phase (thread 0 of each CTA)
 gempic_status gempic_phase_timers(gempic_sim* s, unsigned long long* out, int32_t n) {
   if (!s || !out || n < 1) return GEMPIC_EINVAL;
-  cudaError_t e = cudaMemcpyAsync(out, s->p.timers, std::min(n, 256) * sizeof(unsigned long long),
+  const int tw = timer_words(s->p);
+  cudaError_t e = cudaMemcpyAsync(out, s->p.timers, std::min(n, tw) * sizeof(unsigned long long),
                                   cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(s->p.timers, 0, 256 * sizeof(unsigned long long), s->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s->p.timers, 0, tw * sizeof(unsigned long long), s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return cuda_fail(s, e);
 }

@@ -160,6 +160,9 @@ __device__ __forceinline__ void red_cluster(uint32_t a, float v) {
 __device__ __forceinline__ void red_cluster(uint32_t a, double v) {
   asm volatile("red.shared::cluster.add.f64 [%0], %1;" ::"r"(a), "d"(v));
 }
+__device__ __forceinline__ void red_cluster_u32(uint32_t a, int v) {
+  asm volatile("red.shared::cluster.add.u32 [%0], %1;" ::"r"(a), "r"(v));
+}
 
 // Counter-based SplitMix64 (Steele, Lea, Flood 2014): output c of the stream seeded with s.
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long s,
@@ -470,7 +473,7 @@ __device__ void load_tables(const Params& p, const Sm<T>& s) {
 // phase timers (profiling builds only)
 // ------------------------------------------------------------------------------------------
 enum Phase { PH_A = 0, PH_B1, PH_BEAM, PH_FWD, PH_B2, PH_COLF, PH_SOLVE, PH_COLI, PH_SCAT, PH_B3,
-             PH_INV, PH_B4, PH_E, PH_AG, PH_AM, PH_AD, PH_N };
+             PH_INV, PH_B4, PH_E, PH_AG, PH_AM, PH_AD, PH_AW, PH_AR, PH_N };
 #ifdef GEMPIC_PHASE_TIMERS
 #define TIMER_DECL long long t_last = clock64(); long long t_acc[PH_N] = {0};
 #define TIMER_MARK(ph)                      \
@@ -484,8 +487,10 @@ enum Phase { PH_A = 0, PH_B1, PH_BEAM, PH_FWD, PH_B2, PH_COLF, PH_SOLVE, PH_COLI
     if (threadIdx.x == 0 && p.timers) {                                                  \
       for (int i_ = 0; i_ < PH_AG; ++i_)                                                 \
         atomicAdd(p.timers + i_, (unsigned long long)t_acc[i_]);                         \
-      for (int i_ = PH_AG; i_ < PH_N; ++i_)                                              \
+      for (int i_ = PH_AG; i_ < PH_AW; ++i_)                                             \
         atomicAdd(p.timers + i_, (unsigned long long)g_sub[i_ - PH_AG]);                 \
+      for (int i_ = PH_AW; i_ < PH_N; ++i_)                                              \
+        atomicAdd(p.timers + 32 + i_, (unsigned long long)t_acc[i_]);                    \
     }                                                                                    \
   } while (0)
 #define SUB_DECL long long s_t0 = clock64();
@@ -894,7 +899,9 @@ __device__ __forceinline__ void gather6_l(const Params& p, const T* Fb, int ix, 
 // row, band rows -1 .. RB + 1), local shared reductions with precomputed addresses; in FP32
 // a contribution below jref goes to the 32-bit fixed-point accumulators (native integer
 // reductions, exact sums, at most 2^9 such contributions per node), a larger one to the float
-// accumulators.  Sink<T, false>: any global row, through the CTA that owns it.
+// accumulators.  Sink<T, false>: any global row, into the own rows of the CTA that owns it; in
+// FP32 below jref through the owner's fixed-point accumulators (a native distributed-shared
+// integer reduction; the float one is a compare-and-swap loop some 40 times slower).
 template <typename T, bool LOCAL>
 struct Sink;
 
@@ -930,10 +937,25 @@ template <typename T>
 struct Sink<T, false> {
   const Params& p;
   const T* J;
+  const int* Jint;
   int me, y0;                // global row of the particle
+  T jref, jscale;
   __device__ __forceinline__ void add(int comp, int yrow, int x, T v) const {
     if (v == T(0)) return;
     const int y = (yrow + y0) & (p.ny - 1);
+    if constexpr (sizeof(T) == 4) {
+      if (fabsf(v) < jref) {
+        const int r = y >> p.logRB;
+        const uint32_t a =
+            sh_addr(Jint + ((size_t)comp * p.JR + (y & (p.RB - 1)) + p.JOFF) * p.nx + x);
+        const int q = __float2int_rn(v * jscale);
+        if (r == me)
+          red_local_u32(a, q);
+        else
+          red_cluster_u32(cluster_addr(a, r), q);
+        return;
+      }
+    }
     const RowRef<T> rr = row_ref(p, J, p.JR, p.JOFF, y, me);
     row_red(rr, (uint32_t)(comp * p.JR * p.nx + x), v);
   }
@@ -1103,7 +1125,7 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
     esirkepov(p, s, sk, P.ix, P.fx, P.fy, X1, Y1, w, dy);
     cic_add(p, sk, 2, P.ix, X1, Y1, w * ds * invh);
   } else {
-    const Sink<T, false> sk{p, s.J, me, P.iy};
+    const Sink<T, false> sk{p, s.J, s.Jint, me, P.iy, s.cst[K_JREF], s.cst[K_JSCALE]};
     esirkepov(p, s, sk, P.ix, P.fx, P.fy, X1, Y1, w, dy);
     cic_add(p, sk, 2, P.ix, X1, Y1, w * ds * invh);
   }
@@ -1579,6 +1601,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   __syncthreads();
 
   for (int n = nz - 1; n >= 0; --n) {
+#ifdef GEMPIC_PHASE_TIMERS
+    const long long t_slice = clock64();
+#endif
     // ---------------- A: streaming push from plane n+1 to plane n -----------------------
     SliceAcc<T> sa{T(0), T(0), 0};
     {
@@ -1607,6 +1632,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
           put_particle(p, s, ov, i, P);
         }
       }
+      TIMER_MARK(PH_AR);
       // stored particles that rejoin the march at this slice (partial first step), taken by
       // the CTA that owns their row
       const int nq = min(s.misc[M_RQN], p.bcap);
@@ -1644,10 +1670,23 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     acc[DG_PUSH] += (double)sa.push;
     TIMER_MARK(PH_A);
     __syncthreads();
+    TIMER_MARK(PH_AW);
+    // FP32: fold the fixed-point accumulators of the halo rows now (only this CTA's pushes
+    // deposit there); own rows also receive other CTAs' fixed-point deposits and are folded
+    // after the barrier
     if constexpr (sizeof(T) == 4) {
-      const T jinv = s.cst[K_JINV];
-      for (int i = tid; i < 3 * jplane; i += NT) s.J[i] += T(s.Jint[i]) * jinv;
-      __syncthreads();
+      if (p.ny > 1) {
+        const T jinv = s.cst[K_JINV];
+        for (int i = tid; i < 9 * p.nx; i += NT) {
+          const int c = i / (3 * p.nx);
+          const int rem = i - c * 3 * p.nx;
+          const int which = rem / p.nx, x = rem - which * p.nx;
+          const int jrow = which == 0 ? 0 : p.RB + p.JOFF + (which - 1);
+          const size_t j = ((size_t)c * p.JR + jrow) * p.nx + x;
+          s.J[j] += T(s.Jint[j]) * jinv;
+        }
+        __syncthreads();
+      }
     }
     // halo currents (band rows -1, RB, RB+1) to the owners' receive buffers (plain stores)
     if (p.ny > 1) {
@@ -1670,23 +1709,46 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       if (s.misc[M_PCOUNT] > p.pcap + p.gcap) s.misc[M_PCOUNT] = p.pcap + p.gcap;
       __threadfence();
     }
+#ifdef GEMPIC_PHASE_TIMERS
+    // per CTA: cycles from the slice start to the arrival at B1 (words 64 + rank); per slice of
+    // the launch's first march, arrival and release (words 256 + 2 (n C + rank))
+    const long long t_arr = clock64() - t_slice;
+    if (tid == 0 && p.timers) atomicAdd(p.timers + 64 + me, (unsigned long long)t_arr);
+#endif
     cl.sync();                                                      // B1: deposits done
+#ifdef GEMPIC_PHASE_TIMERS
+    if (tid == 0 && p.timers && k == p.k0) {
+      p.timers[256 + 2 * ((size_t)n * p.C + me)] = (unsigned long long)t_arr;
+      p.timers[256 + 2 * ((size_t)n * p.C + me) + 1] = (unsigned long long)(clock64() - t_slice);
+    }
+#endif
     // publish: iteration n+1 complete (its stored phase and this push have been issued)
     if (p.P > 1 && me == 0 && tid == 0 && n + 1 <= nz - 1)
       st_release_u64(p.progress + cid, prog_value(k, nz, nz - (n + 1)));
     // stored particles of cell n at this level (traps of this push included), for phase E
     if (tid == 32) s.misc[M_STN] = ldcg(p.st.cnt + (size_t)s1 * nz + n);
     TIMER_MARK(PH_B1);
-    // received halo currents into own rows; migrating particles into free slots
-    if (p.ny > 1) {
-      for (int i = tid; i < 9 * p.nx; i += NT) {
-        const int c = i / (3 * p.nx);
-        const int rem = i - c * 3 * p.nx;
-        const int slot = rem / p.nx, x = rem - slot * p.nx;
-        const int row = slot == 2 ? p.RB - 1 : slot;
-        s.J[((size_t)c * p.JR + row + p.JOFF) * p.nx + x] +=
-            s.recv[((size_t)c * 3 + slot) * p.nx + x];
+    // own rows: fixed-point accumulators (FP32) and the received halo currents (rows 0, 1
+    // from the band below, RB - 1 from the band above); element mapping as in the beam add
+    {
+      const T jinv = s.cst[K_JINV];
+      for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
+        const int c = i / (p.RB * p.nx);
+        const int rem = i - c * p.RB * p.nx;
+        const int row = rem >> p.lognx, x = rem & (p.nx - 1);
+        const size_t j = ((size_t)c * p.JR + p.JOFF) * p.nx + rem;
+        T v = s.J[j];
+        if constexpr (sizeof(T) == 4) v += T(s.Jint[j]) * jinv;
+        if (p.ny > 1) {
+          if (row == 0) v += s.recv[((size_t)c * 3 + 0) * p.nx + x];
+          if (row == 1) v += s.recv[((size_t)c * 3 + 1) * p.nx + x];
+          if (row == p.RB - 1) v += s.recv[((size_t)c * 3 + 2) * p.nx + x];
+        }
+        s.J[j] = v;
       }
+    }
+    // migrating particles into free slots
+    if (p.ny > 1) {
       const int nin = min(s.misc[M_INBOX], p.mig_cap);
       const int ftop = s.misc[M_FTOP];
       const int pc = s.misc[M_PCOUNT];

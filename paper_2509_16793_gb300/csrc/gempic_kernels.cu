@@ -154,6 +154,12 @@ __device__ __forceinline__ void red_local(uint32_t a, double v) {
 __device__ __forceinline__ void red_local_u32(uint32_t a, int v) {
   asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(a), "r"(v));
 }
+// the same, predicated on v != 0 (no branch)
+__device__ __forceinline__ void red_local_u32_nz(uint32_t a, int v) {
+  asm volatile(
+      "{\n\t.reg .pred nz;\n\tsetp.ne.s32 nz, %1, 0;\n\t@nz red.shared.add.u32 [%0], %1;\n\t}" ::"r"(a),
+      "r"(v));
+}
 __device__ __forceinline__ void red_cluster(uint32_t a, float v) {
   asm volatile("red.shared::cluster.add.f32 [%0], %1;" ::"r"(a), "f"(v));
 }
@@ -474,40 +480,36 @@ __device__ void load_tables(const Params& p, const Sm<T>& s) {
 // ------------------------------------------------------------------------------------------
 enum Phase { PH_A = 0, PH_B1, PH_BEAM, PH_FWD, PH_B2, PH_COLF, PH_SOLVE, PH_COLI, PH_SCAT, PH_B3,
              PH_INV, PH_B4, PH_E, PH_AG, PH_AM, PH_AD, PH_AW, PH_AR, PH_N };
+// Thread 0 of each CTA adds the cycles of each phase straight into global memory (phase ph at
+// word ph, PH_AW and PH_AR at 32 + ph): no per-phase registers are carried through the march.
 #ifdef GEMPIC_PHASE_TIMERS
-#define TIMER_DECL long long t_last = clock64(); long long t_acc[PH_N] = {0};
-#define TIMER_MARK(ph)                      \
-  do {                                      \
-    const long long t_now = clock64();      \
-    t_acc[ph] += t_now - t_last;            \
-    t_last = t_now;                         \
-  } while (0)
-#define TIMER_FLUSH                                                                      \
-  do {                                                                                   \
-    if (threadIdx.x == 0 && p.timers) {                                                  \
-      for (int i_ = 0; i_ < PH_AG; ++i_)                                                 \
-        atomicAdd(p.timers + i_, (unsigned long long)t_acc[i_]);                         \
-      for (int i_ = PH_AG; i_ < PH_AW; ++i_)                                             \
-        atomicAdd(p.timers + i_, (unsigned long long)g_sub[i_ - PH_AG]);                 \
-      for (int i_ = PH_AW; i_ < PH_N; ++i_)                                              \
-        atomicAdd(p.timers + 32 + i_, (unsigned long long)t_acc[i_]);                    \
-    }                                                                                    \
-  } while (0)
-#define SUB_DECL long long s_t0 = clock64();
-#define SUB_MARK(i)                                   \
-  do {                                                \
-    const long long s_t1 = clock64();                 \
-    if (threadIdx.x == 0) sub[i] += s_t1 - s_t0;      \
-    s_t0 = s_t1;                                      \
+__device__ __forceinline__ int timer_word(int ph) { return ph >= PH_AW ? 32 + ph : ph; }
+#define TIMER_DECL long long t_last = clock64();
+#define TIMER_MARK(ph)                                                                \
+  do {                                                                                \
+    const long long t_now = clock64();                                                \
+    if (threadIdx.x == 0 && p.timers)                                                 \
+      atomicAdd(p.timers + timer_word(ph), (unsigned long long)(t_now - t_last));     \
+    t_last = t_now;                                                                   \
   } while (0)
 #else
 #define TIMER_DECL
 #define TIMER_MARK(ph) \
   do {                 \
   } while (0)
-#define TIMER_FLUSH \
-  do {              \
+#endif
+// timers inside the push (gather / arithmetic / deposit): their clock reads keep the compiler
+// from interleaving the stages, so they are a separate profiling option
+#if defined(GEMPIC_PHASE_TIMERS) && defined(GEMPIC_SUB_TIMERS)
+#define SUB_DECL long long s_t0 = clock64();
+#define SUB_MARK(i)                                                                 \
+  do {                                                                              \
+    const long long s_t1 = clock64();                                               \
+    if (threadIdx.x == 0 && p.timers)                                               \
+      atomicAdd(p.timers + PH_AG + (i), (unsigned long long)(s_t1 - s_t0));         \
+    s_t0 = s_t1;                                                                    \
   } while (0)
+#else
 #define SUB_DECL
 #define SUB_MARK(i) \
   do {              \
@@ -981,60 +983,140 @@ __device__ void esirkepov(const Params& p, const Sm<T>& s, const Sink<T, LOCAL>&
   for (int sb = 0; sb < nsub; ++sb) {
     const T xa = X0 + dX * (T(sb) / T(nsub));
     const T xb = X0 + dX * (T(sb + 1) / T(nsub));
+    // 3-node window from bx = floor(min(xa, xb)); with u = x - bx in [0, 2) the linear shape
+    // S(u, a) = max(0, 1 - |u - a|) is (1 - u, u, 0) on [0, 1) and (0, 2 - u, u - 1) on [1, 2)
     const T bx = floor(fmin(xa, xb));
-    T S0x[3], S1x[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      S0x[a] = fmax(T(0), T(1) - fabs(xa - (bx + T(a))));
-      S1x[a] = fmax(T(0), T(1) - fabs(xb - (bx + T(a))));
-    }
-    const int gx = ix + (int)bx;
+    const T ua = xa - bx, ub = xb - bx;
+    const T S0x0 = fmax(T(0), T(1) - ua), S0x1 = T(1) - fabs(ua - T(1)), S0x2 = fmax(T(0), ua - T(1));
+    const T S1x0 = fmax(T(0), T(1) - ub), S1x1 = T(1) - fabs(ub - T(1)), S1x2 = fmax(T(0), ub - T(1));
     const bool crossx = floor(fmax(xa, xb)) != bx;
+    // x-edge currents: cumulative sums of S1x - S0x; the second edge carries current only
+    // when the sub-step crosses into the third node (else its sum vanishes exactly)
+    const T dS0 = S1x0 - S0x0;
+    const T ex0 = cx_ * dS0;
+    const T ex1 = crossx ? cx_ * (dS0 + (S1x1 - S0x1)) : T(0);
+    const T hx0 = T(0.5) * (S0x0 + S1x0), hx1 = T(0.5) * (S0x1 + S1x1), hx2 = T(0.5) * (S0x2 + S1x2);
+    const int gx = ix + (int)bx;
+    const int x0 = gx & mx, x1 = (gx + 1) & mx, x2 = (gx + 2) & mx;
     if (p.ny == 1) {
-      T cum = T(0);
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        cum = cum + (S1x[a] - S0x[a]);
-        sk.add(0, 0, (gx + a) & mx, (a == 0 || crossx) ? cx_ * cum : T(0));
-      }
-      const T dyv = dyo / T(nsub);
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        sk.add(1, 0, (gx + a) & mx, w * (dyv * invh) * T(0.5) * (S0x[a] + S1x[a]));
+      sk.add(0, 0, x0, ex0);
+      sk.add(0, 0, x1, ex1);
+      const T vy = w * ((dyo / T(nsub)) * invh);
+      sk.add(1, 0, x0, vy * hx0);
+      sk.add(1, 0, x1, vy * hx1);
+      sk.add(1, 0, x2, vy * hx2);
       continue;
     }
     const T ya = Y0 + dY * (T(sb) / T(nsub));
     const T yb = Y0 + dY * (T(sb + 1) / T(nsub));
     const T by = floor(fmin(ya, yb));
-    T S0y[3], S1y[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      S0y[b] = fmax(T(0), T(1) - fabs(ya - (by + T(b))));
-      S1y[b] = fmax(T(0), T(1) - fabs(yb - (by + T(b))));
-    }
-    const int gy = (int)by;
+    const T va = ya - by, vb = yb - by;
+    const T S0y0 = fmax(T(0), T(1) - va), S0y1 = T(1) - fabs(va - T(1)), S0y2 = fmax(T(0), va - T(1));
+    const T S1y0 = fmax(T(0), T(1) - vb), S1y1 = T(1) - fabs(vb - T(1)), S1y2 = fmax(T(0), vb - T(1));
     const bool crossy = floor(fmax(ya, yb)) != by;
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const T hy2 = T(0.5) * (S0y[b] + S1y[b]);
-      if (hy2 == T(0)) continue;
-      T cum = T(0);
-#pragma unroll
-      for (int a = 0; a < 2; ++a) {
-        cum = cum + (S1x[a] - S0x[a]) * hy2;
-        sk.add(0, gy + b, (gx + a) & mx, (a == 0 || crossx) ? cx_ * cum : T(0));
-      }
+    const T dT0 = S1y0 - S0y0;
+    const T ey0 = cy_ * dT0;
+    const T ey1 = crossy ? cy_ * (dT0 + (S1y1 - S0y1)) : T(0);
+    const T hy0 = T(0.5) * (S0y0 + S1y0), hy1 = T(0.5) * (S0y1 + S1y1), hy2 = T(0.5) * (S0y2 + S1y2);
+    const int gy = (int)by;
+    // j_x on x-edges (a = 0, 1) of rows b = 0, 1, 2; j_y on y-edges (b = 0, 1) of columns
+    // a = 0, 1, 2 (Esirkepov's W = (S1 - S0) along the current times the mean shape across)
+    sk.add(0, gy, x0, ex0 * hy0);
+    sk.add(0, gy, x1, ex1 * hy0);
+    sk.add(0, gy + 1, x0, ex0 * hy1);
+    sk.add(0, gy + 1, x1, ex1 * hy1);
+    sk.add(0, gy + 2, x0, ex0 * hy2);
+    sk.add(0, gy + 2, x1, ex1 * hy2);
+    sk.add(1, gy, x0, ey0 * hx0);
+    sk.add(1, gy, x1, ey0 * hx1);
+    sk.add(1, gy, x2, ey0 * hx2);
+    sk.add(1, gy + 1, x0, ey1 * hx0);
+    sk.add(1, gy + 1, x1, ey1 * hx1);
+    sk.add(1, gy + 1, x2, ey1 * hx2);
+  }
+}
+
+// FP32 deposit of a move that needs no sub-steps (|dX|, |dY| <= 1) and whose contributions are
+// all below jref: the Esirkepov and CIC values of the general path, added to the fixed-point
+// accumulators by reductions predicated on a nonzero quantum (no branches).  Every value is a
+// shape weight <= 1 times one of ex0, ex1, ey0, ey1 (vy in 2-D) or vz, which bounds them all.
+// Returns false (nothing deposited) where it does not apply.
+template <typename T>
+__device__ __forceinline__ bool deposit_fixed(const Params& p, const Sm<T>& s,
+                                              const Sink<T, true>& sk, int ix, T X0, T Y0, T X1,
+                                              T Y1, T w, T dyo, T vz) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    const T dX = X1 - X0, dY = Y1 - Y0;
+    if (!(fmax(fabs(dX), fabs(dY)) <= T(1))) return false;
+    const int mx = p.nx - 1;
+    const T bx = floor(fmin(X0, X1));
+    const T ua = X0 - bx, ub = X1 - bx;
+    const T S0x0 = fmax(T(0), T(1) - ua), S0x1 = T(1) - fabs(ua - T(1)), S0x2 = fmax(T(0), ua - T(1));
+    const T S1x0 = fmax(T(0), T(1) - ub), S1x1 = T(1) - fabs(ub - T(1)), S1x2 = fmax(T(0), ub - T(1));
+    const bool crossx = floor(fmax(X0, X1)) != bx;
+    const T dS0 = S1x0 - S0x0;
+    const T cx_ = -(w * s.cst[K_CX]);
+    const T ex0 = cx_ * dS0;
+    const T ex1 = crossx ? cx_ * (dS0 + (S1x1 - S0x1)) : T(0);
+    const T hx0 = T(0.5) * (S0x0 + S1x0), hx1 = T(0.5) * (S0x1 + S1x1), hx2 = T(0.5) * (S0x2 + S1x2);
+    const int gx = ix + (int)bx;
+    const uint32_t o0 = (uint32_t)(gx & mx) * 4u, o1 = (uint32_t)((gx + 1) & mx) * 4u,
+                   o2 = (uint32_t)((gx + 2) & mx) * 4u;
+    // CIC of j_z at the end point
+    const T fX1 = floor(X1), fx = X1 - fX1;
+    const int cz = ix + (int)fX1;
+    const uint32_t z0 = (uint32_t)(cz & mx) * 4u, z1 = (uint32_t)((cz + 1) & mx) * 4u;
+    const T js = sk.jscale;
+    const uint32_t cs = sk.cstride, rs = sk.rstride;
+    if (p.ny == 1) {
+      const T vy = w * (dyo * s.cst[K_INVH]);
+      const T bnd = fmax(fmax(fabs(ex0), fabs(ex1)), fmax(fabs(vy), fabs(vz)));
+      if (!(bnd < sk.jref)) return false;
+      const uint32_t b = sk.ibase;
+      red_local_u32_nz(b + o0, __float2int_rn(ex0 * js));
+      red_local_u32_nz(b + o1, __float2int_rn(ex1 * js));
+      red_local_u32_nz(b + cs + o0, __float2int_rn((vy * hx0) * js));
+      red_local_u32_nz(b + cs + o1, __float2int_rn((vy * hx1) * js));
+      red_local_u32_nz(b + cs + o2, __float2int_rn((vy * hx2) * js));
+      red_local_u32_nz(b + 2 * cs + z0, __float2int_rn(((T(1) - fx) * vz) * js));
+      red_local_u32_nz(b + 2 * cs + z1, __float2int_rn((fx * vz) * js));
+      return true;
     }
-#pragma unroll
-    for (int b = 0; b < 2; ++b) {
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        // cumulative sum over b of (S1y - S0y)(S0x + S1x)/2 at column a
-        T cum = (S1y[0] - S0y[0]) * T(0.5) * (S0x[a] + S1x[a]);
-        if (b == 1) cum = cum + (S1y[1] - S0y[1]) * T(0.5) * (S0x[a] + S1x[a]);
-        sk.add(1, gy + b, (gx + a) & mx, (b == 0 || crossy) ? cy_ * cum : T(0));
-      }
-    }
+    const T by = floor(fmin(Y0, Y1));
+    const T va = Y0 - by, vb = Y1 - by;
+    const T S0y0 = fmax(T(0), T(1) - va), S0y1 = T(1) - fabs(va - T(1)), S0y2 = fmax(T(0), va - T(1));
+    const T S1y0 = fmax(T(0), T(1) - vb), S1y1 = T(1) - fabs(vb - T(1)), S1y2 = fmax(T(0), vb - T(1));
+    const bool crossy = floor(fmax(Y0, Y1)) != by;
+    const T dT0 = S1y0 - S0y0;
+    const T cy_ = -(w * s.cst[K_CY]);
+    const T ey0 = cy_ * dT0;
+    const T ey1 = crossy ? cy_ * (dT0 + (S1y1 - S0y1)) : T(0);
+    const T hy0 = T(0.5) * (S0y0 + S1y0), hy1 = T(0.5) * (S0y1 + S1y1), hy2 = T(0.5) * (S0y2 + S1y2);
+    const T bnd = fmax(fmax(fmax(fabs(ex0), fabs(ex1)), fmax(fabs(ey0), fabs(ey1))), fabs(vz));
+    if (!(bnd < sk.jref)) return false;
+    const T fY1 = floor(Y1), fy = Y1 - fY1;
+    const uint32_t r0 = sk.ibase + (uint32_t)((int)by * (int)rs);
+    const uint32_t r1 = r0 + rs, r2 = r1 + rs;
+    red_local_u32_nz(r0 + o0, __float2int_rn((ex0 * hy0) * js));
+    red_local_u32_nz(r0 + o1, __float2int_rn((ex1 * hy0) * js));
+    red_local_u32_nz(r1 + o0, __float2int_rn((ex0 * hy1) * js));
+    red_local_u32_nz(r1 + o1, __float2int_rn((ex1 * hy1) * js));
+    red_local_u32_nz(r2 + o0, __float2int_rn((ex0 * hy2) * js));
+    red_local_u32_nz(r2 + o1, __float2int_rn((ex1 * hy2) * js));
+    red_local_u32_nz(r0 + cs + o0, __float2int_rn((ey0 * hx0) * js));
+    red_local_u32_nz(r0 + cs + o1, __float2int_rn((ey0 * hx1) * js));
+    red_local_u32_nz(r0 + cs + o2, __float2int_rn((ey0 * hx2) * js));
+    red_local_u32_nz(r1 + cs + o0, __float2int_rn((ey1 * hx0) * js));
+    red_local_u32_nz(r1 + cs + o1, __float2int_rn((ey1 * hx1) * js));
+    red_local_u32_nz(r1 + cs + o2, __float2int_rn((ey1 * hx2) * js));
+    const uint32_t q0 = sk.ibase + 2 * cs + (uint32_t)((int)fY1 * (int)rs), q1 = q0 + rs;
+    red_local_u32_nz(q0 + z0, __float2int_rn((((T(1) - fx) * (T(1) - fy)) * vz) * js));
+    red_local_u32_nz(q0 + z1, __float2int_rn(((fx * (T(1) - fy)) * vz) * js));
+    red_local_u32_nz(q1 + z0, __float2int_rn((((T(1) - fx) * fy) * vz) * js));
+    red_local_u32_nz(q1 + z1, __float2int_rn(((fx * fy) * vz) * js));
+    return true;
   }
 }
 
@@ -1082,7 +1164,7 @@ struct SliceAcc {     // per-thread, per-slice diagnostics in the working precis
 
 template <typename T>
 __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PState<T>& P, T d,
-                            int me, T& fz_trap, SliceAcc<T>& acc, long long* sub) {
+                            int me, T& fz_trap, SliceAcc<T>& acc) {
   SUB_DECL
   const int yl = P.iy - (me << p.logRB);
   const bool own = p.ny == 1 || (yl >= 0 && yl < p.RB);
@@ -1122,8 +1204,11 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   const bool local = own && (p.ny == 1 || (yl + (int)lo >= -1 && yl + (int)hi + 2 <= p.RB + 1));
   if (local) {
     const Sink<T, true> sk(p, s, p.ny == 1 ? 0 : yl);
-    esirkepov(p, s, sk, P.ix, P.fx, P.fy, X1, Y1, w, dy);
-    cic_add(p, sk, 2, P.ix, X1, Y1, w * ds * invh);
+    const T vz = w * ds * invh;
+    if (!deposit_fixed(p, s, sk, P.ix, P.fx, P.fy, X1, Y1, w, dy, vz)) {
+      esirkepov(p, s, sk, P.ix, P.fx, P.fy, X1, Y1, w, dy);
+      cic_add(p, sk, 2, P.ix, X1, Y1, vz);
+    }
   } else {
     const Sink<T, false> sk{p, s.J, s.Jint, me, P.iy, s.cst[K_JREF], s.cst[K_JSCALE]};
     esirkepov(p, s, sk, P.ix, P.fx, P.fy, X1, Y1, w, dy);
@@ -1487,7 +1572,6 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   const Ovf<T> ov = ovf_view<T>(p, cid, me);        // overflow particle slots of this CTA
   const int fplane = p.FR * p.nx;                   // elements of one field component
   const int jplane = p.JR * p.nx;                   // elements of one current component
-  long long g_sub[3] = {0, 0, 0};
   TIMER_DECL
 
   double acc[kNDiag];
@@ -1613,7 +1697,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         if (cw < 0) continue;
         PState<T> P = get_particle(p, s, ov, i, cw);
         T fzt;
-        const bool trap = stream_push(p, s, Fcur, P, h, me, fzt, sa, g_sub);
+        const bool trap = stream_push(p, s, Fcur, P, h, me, fzt, sa);
         bool gone = trap;
         if (trap) {
           acc[DG_TRAP] += 1.0;
@@ -1643,7 +1727,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         PState<T> P = store_read<T>(p.rq, p, ge, fz);
         acc[DG_REJOIN] += 1.0;
         T fzt;
-        const bool trap = stream_push(p, s, Fcur, P, fz * h, me, fzt, sa, g_sub);
+        const bool trap = stream_push(p, s, Fcur, P, fz * h, me, fzt, sa);
         if (trap) {
           acc[DG_TRAP] += 1.0;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
@@ -1921,7 +2005,6 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   if (tid == 0) __threadfence();
   cl.sync();
   if (p.P > 1 && me == 0 && tid == 0) st_release_u64(p.progress + cid, prog_value(k, nz, nz));
-  TIMER_FLUSH;
 
   // diagnostics: per-CTA FP64 partials
   if (p.diag) {

@@ -75,17 +75,34 @@ __device__ __forceinline__ T gamma_minus_uz(V3<T> u, T g) {
   return u.z > T(0) ? ((T(1) + u.x * u.x) + u.y * u.y) / (g + u.z) : g - u.z;
 }
 
+// reciprocal and reciprocal square root: hardware approximations (a few ulp) in FP32, exact
+// division in FP64
+template <typename T>
+__device__ __forceinline__ T rcp(T x) {
+  if constexpr (sizeof(T) == 4)
+    return __fdividef(1.0f, x);
+  else
+    return T(1) / x;
+}
+template <typename T>
+__device__ __forceinline__ T rsq(T x) {
+  if constexpr (sizeof(T) == 4)
+    return rsqrtf(x);
+  else
+    return T(1) / sqrt(x);
+}
+
 // Relativistic Boris rotation over lab time dt: du/dt = (q/m)(E + u x B / gamma).
 template <typename T>
 __device__ __forceinline__ V3<T> boris(V3<T> u, const T* E, const T* B, T qm, T dt) {
   const T a = T(0.5) * qm * dt;
   V3<T> um{u.x + a * E[0], u.y + a * E[1], u.z + a * E[2]};
-  const T gm = sqrt(T(1) + ((um.x * um.x + um.y * um.y) + um.z * um.z));
-  const T tx = a * B[0] / gm, ty = a * B[1] / gm, tz = a * B[2] / gm;
+  const T ag = a * rsq(T(1) + ((um.x * um.x + um.y * um.y) + um.z * um.z));   // a / gamma
+  const T tx = ag * B[0], ty = ag * B[1], tz = ag * B[2];
   V3<T> up{um.x + (um.y * tz - um.z * ty), um.y + (um.z * tx - um.x * tz),
            um.z + (um.x * ty - um.y * tx)};
-  const T den = T(1) + ((tx * tx + ty * ty) + tz * tz);
-  const T sx = T(2) * tx / den, sy = T(2) * ty / den, sz = T(2) * tz / den;
+  const T f = T(2) * rcp(T(1) + ((tx * tx + ty * ty) + tz * tz));
+  const T sx = f * tx, sy = f * ty, sz = f * tz;
   V3<T> upl{um.x + (up.y * sz - up.z * sy), um.y + (up.z * sx - up.x * sz),
             um.z + (up.x * sy - up.y * sx)};
   return V3<T>{upl.x + a * E[0], upl.y + a * E[1], upl.z + a * E[2]};
@@ -1192,8 +1209,8 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   const T dt2 = hc * gb / gamma_minus_uz(ub, gb);
   const V3<T> un = boris(u, E, E + 3, qm, dt2);
   const T gn = gamma_of(un);
-  const T den = gamma_minus_uz(un, gn);
-  const T dx = hc * un.x / den, dy = hc * un.y / den, ds = hc * un.z / den;
+  const T hden = hc * rcp(gamma_minus_uz(un, gn));    // h / (gamma - u_z)
+  const T dx = hden * un.x, dy = hden * un.y, ds = hden * un.z;
   // deposit: w = Q/(hx hy Delta) is the particle's (rho - j_z) density weight (Sec. 4.1)
   const T w = P.q * s.cst[K_WSCALE];
   const T X1 = P.fx + dx * s.cst[K_INVHX];
@@ -1216,7 +1233,7 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   }
   SUB_MARK(2);
   // diagnostics: kinetic energy N m (gamma-1) dt/Delta, (rho - j_z) flux through plane n
-  const T dtl = hc * gn / den;
+  const T dtl = hden * gn;
   acc.kin += P.q * s.cst[K_MOQ + P.sp] * (gn - T(1)) * dtl / D;
   if (!trap) acc.flux += w;
   acc.push += 1;

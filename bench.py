@@ -284,15 +284,7 @@ def main():
     flops = algorithmic_flops(w) * args.steps
     achieved = flops / (ms / 1e3) / 1e12
     hbm = algorithmic_bytes(w) * args.steps / (ms / 1e3) / 1e9
-    traffic = None
-    tf = os.path.join(ROOT, "profiles", "march_traffic.json")
-    if os.path.exists(tf):
-        try:
-            tj = json.load(open(tf))
-            if tj.get("kernel_hash") == kernel_hash():
-                traffic = tj["bytes_per_step"] * args.steps
-        except Exception:
-            traffic = None
+    traffic = measured_traffic(w) * args.steps if measured_traffic(w) else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
             "frac": achieved / peak_alu, "traffic": traffic,
             "peak_source": "152 SM x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)",
@@ -311,7 +303,8 @@ def main():
             "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": config_dict(w, shape), "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "pushes/s", "h2d_bytes_per_step": nb,
+            "e2e": {"value": e2e_value if math.isfinite(e2e_value) else None,
+                    "unit": "pushes/s", "h2d_bytes_per_step": nb,
                     "d2h_bytes_per_step": nb + 64},
             "gpu_launches": launches, "clocks": clocks,
             "diag": {k: diag[k] for k in ("field_energy", "kinetic_energy", "n_stored", "pushes")}}
@@ -321,6 +314,19 @@ def main():
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def measured_traffic(w):
+    """DRAM bytes per s-step of the march kernel from the committed ncu summary, if it was
+    taken on this kernel source and this workload's grid (else None)."""
+    import re
+    f = os.path.join(ROOT, "profiles", "march_kernel_lwfa3d_128x128x1024.md")
+    if not os.path.exists(f) or (w.nx, w.ny, w.nzeta) != (128, 128, 1024) or w.precision != 32:
+        return None
+    m = re.search(r"traffic_bytes_per_step: (\d+) kernel_hash: (\w+)", open(f).read())
+    if not m or m.group(2) != kernel_hash():
+        return None
+    return int(m.group(1))
 
 
 def kernel_hash() -> str:

@@ -4,9 +4,9 @@
  *
  * One simulation = one persistent spectral field state on the device plus its particle
  * stores.  Each s-step (slow coordinate, step Delta) marches the zeta-slices from the front
- * of the window to the back (Sec. 4.1): fresh plasma is injected at the front (Sec. 4.1,
- * "Current Deposition", Q_f = q n h_x h_y Delta), particles are gathered, pushed along zeta
- * with the GT2 characteristics (Sec. 4, Eqs. after Vlasov2, trap2) and deposited, and the
+ * of the window to the back (Sec. 4.1): fresh plasma is injected at the front (Sec. 5.1,
+ * Q_f = q n h_x h_y Delta), particles are gathered, pushed along zeta with the GT2
+ * characteristics (Sec. 5, Eqs. after Vlasov2, trap2) and deposited, and the
  * universal reduced Maxwell system (Eqs. RxGu..EzGu) is advanced slice by slice with the
  * semi-implicit scheme of Sec. 4.1 (Eqs. RxN..eqall, closed form of App. B).  Particles that
  * pass the back boundary are removed; particles whose slow-coordinate budget is used up stay
@@ -55,7 +55,7 @@ typedef struct {
 } gempic_grid;
 
 /* A background species swept by the window and injected fresh at the front each s-step
- * (Sec. 4.1, Q_f = q n h_x h_y Delta, split over ppc macroparticles per transverse cell,
+ * (Sec. 5.1, Q_f = q n h_x h_y Delta, split over ppc macroparticles per transverse cell,
  * cold, at uniform random in-cell offsets drawn from a counter-based SplitMix64 stream keyed
  * by (seed, s-step, particle)). */
 typedef struct {
@@ -114,7 +114,7 @@ typedef struct {
 gempic_status gempic_create(const gempic_config* cfg, struct gempic_sim** out);
 
 /* Place macroparticles inside the box at the current level (beam / driver particles,
- * Sec. 4.1 Q_b): absolute positions, momenta u = p/(m c) and charge Q (host FP64 arrays of
+ * Sec. 5.1 Q_b): absolute positions, momenta u = p/(m c) and charge Q (host FP64 arrays of
  * length n, species[i] < nspecies).  Valid only before the first gempic_step. */
 gempic_status gempic_add_particles(struct gempic_sim* sim, int64_t n, const double* x,
                                    const double* y, const double* zeta, const double* ux,

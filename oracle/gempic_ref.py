@@ -13,15 +13,15 @@ The paper is silent or garbled in places; the readings taken here are:
     -(Delta/4)(j_true - j_pred) (Sec. 4.1, predictor-corrector).  At slice 0, j_{-1/2} := j_{+1/2}.
   * Transverse boundaries are periodic; the x- and y-Nyquist modes are projected out.
   * The front ghost slice zeta_{N} has R = L = E_z = B_z = 0 and E = B = 0.
-  * Particles (GT2, Sec. 4): u on half-slices, r_perp and s~ on slices; a deterministic
+  * Particles (GT2, Sec. 5): u on half-slices, r_perp and s~ on slices; a deterministic
     two-pass Boris step resolves the implicit dependence of dt = h/(1 - v_z) on v_z.
   * Step length: -dzeta = min(d, (Delta - sigma)(1 - v_z)/v_z) with v_z taken before the
     step (Eq. trap2); a particle whose step is cut short is trapped and kept in the box with
     its weight unchanged.
   * Transverse shape: cloud-in-cell; j_perp by the 2-D Esirkepov decomposition of the
     transverse move across one slice, so that (rho - j_z) is conserved through the planes.
-  * Stored (trapped / beam) particles are pushed along s (Sec. 4.1, "integrate the trapped
-    particles along the slow s coordinate") with the fields of the last completed level; a
+  * Stored (trapped / beam) particles are pushed along the slow coordinate s (Sec. 5.1, last
+    paragraph) with the fields of the last completed level; a
     stored particle with Delta(1-v_z)/v_z >= h rejoins the zeta march at its slice.
 """
 from __future__ import annotations
@@ -414,7 +414,7 @@ class RefSim:
     def _zero_jbeam(self):
         return np.zeros((self.nz, 3, self.ny, self.nx))
 
-    # -- fresh particles at the front ghost slice (Sec. 4.1, Q_f = q n hx hy Delta) -----------
+    # -- fresh particles at the front ghost slice (Sec. 5.1, Q_f = q n hx hy Delta) -----------
     def _inject(self):
         w = self.w
         ncell = self.nx * self.ny
@@ -449,7 +449,7 @@ class RefSim:
     def _charge(self, sp):
         return np.array([s.charge for s in self.w.species])[sp]
 
-    # -- stored set along s (Sec. 4.1, last paragraph) --------------------------------------
+    # -- stored set along s (Sec. 5.1, last paragraph) --------------------------------------
     def _stored_push(self):
         """Advance the stored particles from s^k to s^{k+1} with the fields of level k.
         Returns (particles that rejoin the zeta march, beam current j^{k+1} on half-slices)."""
@@ -500,7 +500,7 @@ class RefSim:
         S = S.select(keep)
         fwd = fwd[keep]
         gn = gn[keep]
-        # beam current j = Q v / (hx hy h) on half-slice nodes (Sec. 4.1, j = q n v)
+        # beam current j = Q v / (hx hy h) on half-slice nodes (Sec. 5.1, j = q n v)
         if S.n:
             D3 = S.select(fwd)
             gd = gn[fwd]
@@ -523,7 +523,7 @@ class RefSim:
         self.stored = S
         return R, jbeam, nremoved
 
-    # -- the zeta march at level s^1 (Sec. 4.1: march from the right boundary leftwards) -------
+    # -- the zeta march at level s^1 (Sec. 4.1: from the front of the window towards the back) -------
     def _march(self, delta_field, inject, joiners, jbeam):
         nx, ny, nz, h = self.nx, self.ny, self.nz, self.h
         old = {k: v.copy() for k, v in self.S.items()}
@@ -560,7 +560,7 @@ class RefSim:
                 trap = hlim < P.dist
                 hc = np.where(trap, hlim, P.dist)
                 un, dx, dy, ds = zeta_push(P.u, E, B, self._qm(P.sp), hc)
-                wgt = P.Q / (self.hx * self.hy * D)            # D-weight q n / ppc of Sec. 4.1
+                wgt = P.Q / (self.hx * self.hy * D)            # D-weight q n / ppc of Sec. 5.1
                 X1 = X0 + dx / self.hx
                 Y1 = Y0 + dy / self.hy if ny > 1 else Y0
                 esirkepov_deposit(jx, jy, X0, Y0, X1, Y1, wgt, h, self.hx, self.hy,
@@ -616,7 +616,7 @@ class RefSim:
             new1 = sol
             F1 = F0
             jprev = (Jx, Jy)
-        # particles that reached the back plane leave the box (Sec. 4, left boundary)
+        # particles that reached the back plane leave the box (Sec. 5, left boundary)
         T = Particles.concat(trapped)
         self.stored = Particles.concat([self.stored, T])
         stored_ke = 0.0

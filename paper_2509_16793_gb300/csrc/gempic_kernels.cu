@@ -1,8 +1,8 @@
 // GEM-PIC hot path on sm_103a: the zeta march of one s-step as a persistent kernel run by a
 // thread-block cluster, and (optionally) several s-steps in flight as a wavefront.
 //
-// One cluster of C CTAs marches one s-step (Sec. 4.1: "we start marching along zeta from the
-// right boundary").  CTA r owns
+// One cluster of C CTAs marches one s-step (Sec. 4.1: the fields of the next s-level are found
+// slice by slice, starting at the front edge of the window).  CTA r owns
 //   * real-space rows y in [r RB, (r+1) RB) of every slice plane (fields for the gather,
 //     current accumulators for the deposit), and the fresh particles injected into them;
 //   * spectral columns kx in [r KB, (r+1) KB) for all ky (per-mode slice solve, App. B),
@@ -18,7 +18,7 @@
 //      n+1 to HBM, App. B solve at slice n, fields E,B; inverse column FFTs, transposed back.
 //   D  inverse row FFTs: real-space E,B of slice n into shared memory (next gather).
 //   E  stored particles in cell (zeta_n, zeta_{n+1}] are pushed along s with the fields of
-//      slices n and n+1 (Sec. 4.1, last paragraph), depositing the next level's beam current.
+//      slices n and n+1 (Sec. 5.1, last paragraph), depositing the next level's beam current.
 //
 // Wavefront: the march of s-step k+1 on another cluster needs, at slice n, only what the march
 // of step k produced at slices >= n-1.  Marches publish per-slice progress in global memory
@@ -1211,7 +1211,7 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   const T gn = gamma_of(un);
   const T hden = hc * rcp(gamma_minus_uz(un, gn));    // h / (gamma - u_z)
   const T dx = hden * un.x, dy = hden * un.y, ds = hden * un.z;
-  // deposit: w = Q/(hx hy Delta) is the particle's (rho - j_z) density weight (Sec. 4.1)
+  // deposit: w = Q/(hx hy Delta) is the particle's (rho - j_z) density weight (Sec. 5.1)
   const T w = P.q * s.cst[K_WSCALE];
   const T X1 = P.fx + dx * s.cst[K_INVHX];
   const T Y1 = p.ny > 1 ? P.fy + dy * s.cst[K_INVHY] : P.fy;
@@ -1406,7 +1406,7 @@ __device__ __forceinline__ void put_particle(const Params& p, const Sm<T>& s, co
 }
 
 // ------------------------------------------------------------------------------------------
-// Stored particle along s (Sec. 4.1: trapped / beam particles are integrated along s):
+// Stored particle along s (Sec. 5.1: trapped / beam particles are integrated along s):
 // bucket n of level k+1, fields of slices n (Fn) and n+1 (Fn1) of that level.
 // ------------------------------------------------------------------------------------------
 template <typename T>
@@ -1602,7 +1602,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     p.st.cnt[(size_t)s2 * nz + b] = 0;
     p.rq.cnt[(size_t)s2 * nz + b] = 0;
   }
-  // fresh particles at the front ghost plane (Sec. 4.1: Q_f = q n hx hy Delta / ppc)
+  // fresh particles at the front ghost plane (Sec. 5.1: Q_f = q n hx hy Delta / ppc)
   if (tid == 0) {
     s.misc[M_PCOUNT] = 0;
     s.misc[M_FTOP] = 0;

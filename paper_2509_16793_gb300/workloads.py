@@ -8,9 +8,9 @@ Units are the paper's normalised units (Sec. 3): lengths in c/omega_0, time in 1
 fields in m c omega_0 / e, densities in n_cr.  With omega_0 = omega_L the laser wavelength is
 lambda_L = 2*pi and an electron plasma of density n has omega_p^2 = n.
 
-The stand-in workloads follow the paper's LWFA set-up (Sec. 5: Gaussian x-polarised laser
+The stand-in workloads follow the paper's LWFA set-up (Sec. 6: Gaussian x-polarised laser
 driver, Eq. E_laser; cold uniform background plasma swept by the moving window; fresh
-macroparticles injected at the front every s-step, Sec. 4.1 "Current Deposition").  The
+macroparticles injected at the front every s-step, Sec. 5.1).  The
 paper's own run (150x150x180 um, 12 h on 432 cores) is not a dataset; these seeded configs
 stand in for it.
 """
@@ -54,7 +54,7 @@ class Laser:
 
 @dataclass
 class StoredParticles:
-    """Macroparticles placed inside the box at creation (beam / driver bunch, Sec. 4.1 Q_b).
+    """Macroparticles placed inside the box at creation (beam / driver bunch, Sec. 5.1 Q_b).
 
     Positions are absolute (x, y, zeta), momenta u = p/(m c), weight is the macroparticle
     charge Q (sign included), species indexes the workload's species list for q/m.

@@ -230,7 +230,7 @@ def test_p6_esirkepov_continuity(ny):
 
 
 # ---------------------------------------------------------------------------------------
-# P7: deposit weights.  Streaming: j = q n v/(1 - v_z) (Sec. 4.1); beam: j = Q v/(hx hy h).
+# P7: deposit weights.  Streaming: j = q n v/(1 - v_z) (Sec. 5.1); beam: j = Q v/(hx hy h).
 # ---------------------------------------------------------------------------------------
 def test_p7_streaming_current_identity():
     rng = np.random.default_rng(5)
@@ -332,7 +332,7 @@ def test_p9_vacuum_diffraction():
 
 # ---------------------------------------------------------------------------------------
 # P10: uniform cold plasma, no driver: fields and currents stay exactly zero; every plane
-# carries (rho - j_z) = q n (Sec. 4.1: a fresh particle has rho - j_z = q n / ppc per cell).
+# carries (rho - j_z) = q n (Sec. 5.1: a fresh particle has rho - j_z = q n / ppc per cell).
 # ---------------------------------------------------------------------------------------
 def test_p10_uniform_plasma_stays_quiet():
     w = W.small_3d(nx=8, ny=8, nzeta=12).with_(laser=None)
@@ -388,7 +388,7 @@ def test_trap_position_in_plane_wave():
     assert np.abs(sim.stored.zeta - zt).max() < 4 * h
     # trapped with v_z well below 1: Delta (1 - v_z)/v_z >= h, so at the next s-step they
     # rejoin the zeta march at their slice (stored particles are pushed along s only when they
-    # move less than one cell per s-step, Sec. 4.1)
+    # move less than one cell per s-step, Sec. 5.1)
     d2 = sim.step()
     assert d2["n_rejoined"] == w.nx * 2
 

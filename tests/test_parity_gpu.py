@@ -157,6 +157,37 @@ def test_fp32_matches_fp64_oracle():
                 assert abs(gd[key] - od[key]) <= 1e-4 * abs(od[key]), key
 
 
+def test_fp32_bench_grid_matches_oracle():
+    """The bench workload's transverse grid and launch shape -- 128 x 128, clusters of 16 CTAs
+    x 512 threads, transforms of length 128, several s-steps marched concurrently in one
+    launch -- on a window short enough for the oracle."""
+    w = W.small_3d(nx=128, ny=128, nzeta=48, ppc=2, precision=32)
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        shape = g.launch_shape()
+        assert shape["cluster_ctas"] == 16 and shape["threads"] == 512
+        for n in (1, 3):
+            g.step(n)                                   # n s-steps in one launch
+            for _ in range(n):
+                od = o.step()
+            gd = g.diagnostics()
+            ez, oez = g.onaxis_ez(), od["onaxis_ez"]
+            print("bench-grid FP32 on-axis Ez error", np.abs(ez - oez).max() / np.abs(oez).max(),
+                  {k: abs(gd[k] - od[k]) / abs(od[k]) for k in ("field_energy", "kinetic_energy")})
+            assert np.abs(ez - oez).max() <= 1e-4 * np.abs(oez).max()
+            for key in ("field_energy", "kinetic_energy"):
+                assert abs(gd[key] - od[key]) <= 1e-4 * abs(od[key]), key
+        # every mode: fields against the largest field component, currents against the
+        # largest current (a near-zero component, R_y of an x-polarised laser, is not its own
+        # scale); a misplaced mode or row would be an O(1) error
+        gs, os_ = g.state(), o.state()
+        fs = max(np.abs(os_[c]).max() for c in range(4))
+        js = max(np.abs(os_[c]).max() for c in (4, 5))
+        for c, name in enumerate(COMPS):
+            scale = fs if c < 4 else js
+            assert np.abs(gs[c] - os_[c]).max() <= 1e-4 * scale, name
+
+
 def test_pipelined_equals_sequential():
     w = W.small_3d(nx=16, ny=16, nzeta=40, ppc=2, precision=64)
     with gpu_sim(w, cluster_ctas=2, pipeline_depth=1) as a, \

@@ -336,18 +336,22 @@ __device__ __forceinline__ void fft_dit_lanes(Cx<T> (&a)[R], const Cx<T>* tw, bo
 // lengths with a register FFT
 __host__ __device__ __forceinline__ bool reg_fft_len(int logN) { return logN >= 5 && logN <= 8; }
 
-// Column spectra are kept in lane order: position q of a column of length ny holds
-// ky index ky_of_pos(q).  Identity for lengths without a register FFT.
+// Column spectra of the lane-order register FFTs (ny = 32, 64, 256) are kept in lane order:
+// position q of a column holds ky index ky_of_pos(q); natural order for other lengths.
 __host__ __device__ __forceinline__ int bitrev5(int v) {
   return ((v & 1) << 4) | ((v & 2) << 2) | (v & 4) | ((v & 8) >> 2) | ((v & 16) >> 4);
 }
+// columns of length 128 use the natural-order transform fft128_h16
+__host__ __device__ __forceinline__ bool col_lane_order(int logny) {
+  return reg_fft_len(logny) && logny != 7;
+}
 __host__ __device__ __forceinline__ int ky_of_pos(int logny, int q) {
-  if (!reg_fft_len(logny)) return q;
+  if (!col_lane_order(logny)) return q;
   const int R = 1 << (logny - 5);
   return (q >> 5) + R * bitrev5(q & 31);
 }
 __host__ __device__ __forceinline__ int pos_of_ky(int logny, int ky) {
-  if (!reg_fft_len(logny)) return ky;
+  if (!col_lane_order(logny)) return ky;
   const int R = 1 << (logny - 5);
   return bitrev5(ky / R) + 32 * (ky % R);
 }
@@ -368,6 +372,117 @@ __device__ __forceinline__ void st_run(T* dst, const T (&v)[R]) {
 #pragma unroll
     for (int i = 0; i < R; ++i) dst[i] = v[i];
   }
+}
+
+// Transforms of length 128 (the 128-cell transverse grids): 16 lanes per transform, 8 values
+// per lane, one swizzled transpose through shared memory, compile-time twiddles for the small
+// DFTs.  With n = j + 16 r and k = k2 + 8 k1:
+//   X[k2 + 8 k1] = sum_j W_16^{j k1} W_128^{j k2} sum_r W_8^{r k2} x[j + 16 r];
+// each lane does the 8-point DFT over r and the twiddle W_128^{j k2}; after the transpose lane
+// (k2, j0) does the 8-point DFT over j1 of the terms j = 2 j1 + j0, and the pair (j0 = 0, 1)
+// finishes the 16-point DFT over j with one radix-2 step across the two lanes.
+
+// a (c - i s) forward, a (c + i s) inverse
+template <typename T>
+__device__ __forceinline__ Cx<T> cmul_w(Cx<T> a, T c, T s, bool inverse) {
+  const T sn = inverse ? s : -s;
+  return cx<T>(a.re * c - a.im * sn, a.re * sn + a.im * c);
+}
+
+// cos and sin of 2 pi m / 16, m = 0..7
+template <typename T>
+__device__ __forceinline__ T cos16(int m) {
+  return m == 0 ? T(1) : m == 1 ? T(0.92387953251128675613) : m == 2 ? T(0.70710678118654752440)
+       : m == 3 ? T(0.38268343236508977173) : m == 4 ? T(0) : m == 5 ? T(-0.38268343236508977173)
+       : m == 6 ? T(-0.70710678118654752440) : T(-0.92387953251128675613);
+}
+template <typename T>
+__device__ __forceinline__ T sin16(int m) {
+  return m == 0 ? T(0) : m == 1 || m == 7 ? T(0.38268343236508977173)
+       : m == 2 || m == 6 ? T(0.70710678118654752440) : m == 3 || m == 5 ? T(0.92387953251128675613)
+       : T(1);
+}
+
+// 8-point DFT in registers (radix 2, decimation in time on bit-reversed inputs), natural order
+// in and out, unnormalised; conjugate twiddles when inverse
+template <typename T>
+__device__ __forceinline__ void dft8_reg(Cx<T> (&a)[8], bool inverse) {
+  { Cx<T> t = a[1]; a[1] = a[4]; a[4] = t; t = a[3]; a[3] = a[6]; a[6] = t; }
+#pragma unroll
+  for (int st = 1; st <= 3; ++st) {
+    const int half = 1 << (st - 1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int grp = q >> (st - 1), j = q & (half - 1);
+      const int i0 = grp * (half << 1) + j, i1 = i0 + half;
+      const int m16 = j * (16 / (half << 1));           // W_{2 half}^j = W_16^{m16}
+      Cx<T> t;
+      if (m16 == 0)
+        t = a[i1];
+      else if (m16 == 4)
+        t = inverse ? cx<T>(-a[i1].im, a[i1].re) : cx<T>(a[i1].im, -a[i1].re);
+      else
+        t = cmul_w(a[i1], cos16<T>(m16), sin16<T>(m16), inverse);
+      const Cx<T> u = a[i0];
+      a[i0] = u + t;
+      a[i1] = u - t;
+    }
+  }
+}
+
+// In: lane i = j (i = lane mod 16) holds a[r] = x[j + 16 r].  Out: lane i = 2 k2 + j0 holds
+// b[m] = X[k2 + 8 m + 64 j0], m = 0..7.  bufA / bufB: positions 0..63 / 64..127 of 128 entries
+// of scratch private to this half-warp; the transpose puts (k2, j) at 16 k2 + (j ^ 2 k2)
+// (conflict-free for the writing and the reading lanes).  tw[j] = W_128^j (j < 16).  Every lane
+// of the warp calls it (it synchronises the warp); a half with active == false touches no
+// memory.
+template <typename T>
+__device__ __forceinline__ void fft128_h16(Cx<T> (&a)[8], Cx<T>* bufA, Cx<T>* bufB,
+                                           const Cx<T>* tw, bool inverse, bool active,
+                                           Cx<T> (&b)[8]) {
+  const int i = threadIdx.x & 15;
+  dft8_reg<T>(a, inverse);
+  {
+    // W_128^{j k2}, k2 = 1..7, as powers of W_128^j
+    Cx<T> w1 = tw[i];
+    if (inverse) w1.im = -w1.im;
+    const Cx<T> w2 = w1 * w1, w4 = w2 * w2;
+    const Cx<T> w3 = w2 * w1, w5 = w4 * w1, w6 = w4 * w2, w7 = w4 * w3;
+    a[1] = w1 * a[1];
+    a[2] = w2 * a[2];
+    a[3] = w3 * a[3];
+    a[4] = w4 * a[4];
+    a[5] = w5 * a[5];
+    a[6] = w6 * a[6];
+    a[7] = w7 * a[7];
+  }
+  __syncwarp();
+  if (active) {
+#pragma unroll
+    for (int k2 = 0; k2 < 8; ++k2) {
+      const int pos = 16 * k2 + (i ^ (2 * k2));
+      if (k2 < 4)
+        bufA[pos] = a[k2];
+      else
+        bufB[pos - 64] = a[k2];
+    }
+  }
+  __syncwarp();
+  const int k2 = i >> 1, j0 = i & 1;
+#pragma unroll
+  for (int j1 = 0; j1 < 8; ++j1) {
+    const int pos = 16 * k2 + ((2 * j1 + j0) ^ (2 * k2));
+    b[j1] = active ? (pos < 64 ? bufA[pos] : bufB[pos - 64]) : cx<T>(T(0), T(0));
+  }
+  dft8_reg<T>(b, inverse);
+  // X[k2 + 8 k1] = E[k1] + W_16^{k1} O[k1], X[k2 + 8 (k1 + 8)] = E[k1] - W_16^{k1} O[k1]
+#pragma unroll
+  for (int m = 0; m < 8; ++m) {
+    const Cx<T> mine = j0 ? cmul_w(b[m], cos16<T>(m), sin16<T>(m), inverse) : b[m];
+    const Cx<T> other = shfl_xor_cx(mine, 1);
+    b[m] = j0 ? other - mine : mine + other;
+  }
+  __syncwarp();
 }
 
 // ------------------------------------------------------------------------------------------
@@ -602,6 +717,76 @@ __device__ void forward_rows_reg(const cg::cluster_group& cl, const Params& p, c
   }
 }
 
+// Length 128 with an even number of rows per band: the tasks pair the rows (j_x, j_y) of one
+// y and the j_z rows of two y, each as u + i v of one transform, two tasks per warp.  A task's
+// two current rows (dead after this phase) are its transform scratch; the split spectra
+// U(k) = (Z(k) + conj Z(N-k))/2, V(k) = i (conj Z(N-k) - Z(k))/2 are staged in SR (free
+// until the inverse transform) as [3][64][RB + 1] and sent with y fastest, so that a warp's
+// distributed-shared stores go to one kx owner.
+template <typename T>
+__device__ void forward_rows_128(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
+                                 int me, bool stagger) {
+  constexpr int N = 128, NH = 64;
+  const int warp = threadIdx.x >> 5, hf = (threadIdx.x >> 4) & 1, i = threadIdx.x & 15;
+  const int nwarps = blockDim.x >> 5;
+  const int ntask = p.RB + p.RB / 2;
+  const int SP = p.RB + 1;
+  Cx<T>* stg = s.SR;
+  for (int t0 = 2 * warp; t0 < ntask; t0 += 2 * nwarps) {
+    const int t = min(t0 + hf, ntask - 1);
+    const bool live = t0 + hf < ntask;
+    // rows of the pair and their (comp, y) destinations
+    int ca, ya, cb, yb;
+    if (t < p.RB) {
+      ca = 0; ya = t; cb = 1; yb = t;
+    } else {
+      ca = 2; ya = 2 * (t - p.RB); cb = 2; yb = ya + 1;
+    }
+    T* A = s.J + ((size_t)ca * p.JR + ya + p.JOFF) * N;
+    T* B = s.J + ((size_t)cb * p.JR + yb + p.JOFF) * N;
+    Cx<T> a[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] = cx<T>(A[i + 16 * r], B[i + 16 * r]);
+    Cx<T> z[8];
+    Cx<T>* bufA = reinterpret_cast<Cx<T>*>(A);
+    Cx<T>* bufB = reinterpret_cast<Cx<T>*>(B);
+    fft128_h16<T>(a, bufA, bufB, s.twx, false, live, z);
+    if (live) {
+      const int k2 = i >> 1, j0 = i & 1;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int k = k2 + 8 * m + 64 * j0;
+        if (k < 64) bufA[k] = z[m]; else bufB[k - 64] = z[m];
+      }
+    }
+    __syncwarp();
+    if (live) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int k = i + 16 * q;
+        const Cx<T> zk = bufA[k];
+        const Cx<T> zc = conjg(k == 0 ? bufA[0] : bufB[64 - k]);        // conj Z(N - k)
+        Cx<T> X = T(0.5) * (zk + zc);
+        const Cx<T> Y = T(0.5) * mul_i(zc - zk);
+        if (ca == 0 && stagger) X = X * s.shx[k];
+        stg[((size_t)ca * NH + k) * SP + ya] = X;
+        stg[((size_t)cb * NH + k) * SP + yb] = Y;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  const int total = 3 * NH * p.RB;
+  for (int e = threadIdx.x; e < total; e += blockDim.x) {
+    const int yl = e & (p.RB - 1);
+    const int rest = e >> p.logRB;
+    const int k = rest & (NH - 1), c = rest >> 6;
+    const Cx<T> v = stg[((size_t)c * NH + k) * SP + yl];
+    const int rd = k >> p.logKB, kxl = k & (p.KB - 1);
+    st_cx(cl, s.SC + ((size_t)c * p.KB + kxl) * p.ny + (me << p.logRB) + yl, rd, me, v);
+  }
+}
+
 // the length-256 variants run out of line: inlined, their registers would spill the march's
 // carried per-mode state at every length
 template <typename T>
@@ -613,6 +798,10 @@ __device__ __noinline__ void forward_rows_r8(const cg::cluster_group& cl, const 
 template <typename T>
 __device__ void forward_rows(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
                              int me, bool stagger) {
+  if (p.lognx == 7 && p.ny > 1 && (p.RB & 1) == 0) {
+    forward_rows_128(cl, p, s, me, stagger);
+    return;
+  }
   switch (p.lognx) {
     case 5: forward_rows_reg<T, 1>(cl, p, s, me, stagger); return;
     case 6: forward_rows_reg<T, 2>(cl, p, s, me, stagger); return;
@@ -672,11 +861,39 @@ __device__ __noinline__ void col_fft_r8(Cx<T>* d, const Cx<T>* tw, bool inverse)
   col_fft_reg<T, 8>(d, tw, inverse);
 }
 
-// column FFTs of SC[c0..c1) (in place), forward or inverse; with a register FFT the
-// spectra stay in lane order (position q holds ky_of_pos(q))
+// columns of length 128: two per warp, in place, natural order in and out
+template <typename T>
+__device__ void column_ffts_128(const Params& p, const Sm<T>& s, int c0, int c1, bool inverse) {
+  const int warp = threadIdx.x >> 5, hf = (threadIdx.x >> 4) & 1, i = threadIdx.x & 15;
+  const int nwarps = blockDim.x >> 5;
+  const int ntask = (c1 - c0) << p.logKB;
+  for (int t0 = 2 * warp; t0 < ntask; t0 += 2 * nwarps) {
+    const int t = min(t0 + hf, ntask - 1);
+    const bool live = t0 + hf < ntask;
+    const int c = c0 + (t >> p.logKB), kxl = t & (p.KB - 1);
+    Cx<T>* d = s.SC + ((size_t)c * p.KB + kxl) * 128;
+    Cx<T> a[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) a[r] = d[i + 16 * r];
+    Cx<T> b[8];
+    fft128_h16<T>(a, d, d + 64, s.twy, inverse, live, b);
+    if (live) {
+      const int k2 = i >> 1, j0 = i & 1;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) d[k2 + 8 * m + 64 * j0] = b[m];
+    }
+  }
+}
+
+// column FFTs of SC[c0..c1) (in place), forward or inverse; with a lane-order register FFT
+// the spectra stay in lane order (position q holds ky_of_pos(q))
 template <typename T>
 __device__ void column_ffts(const Params& p, const Sm<T>& s, int c0, int c1, bool inverse) {
   if (p.ny == 1) return;
+  if (p.logny == 7) {
+    column_ffts_128(p, s, c0, c1, inverse);
+    return;
+  }
   const int warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   const int ntask = (c1 - c0) << p.logKB;
@@ -769,6 +986,56 @@ __device__ void inverse_rows_reg(const Params& p, const Sm<T>& s, T* Fdst, T& fe
   fe += acc;
 }
 
+// Length 128: two tasks per warp (all 3 FR tasks in one round on 16 warps); a task's two
+// spectrum rows X, Y are its transform scratch once read.
+template <typename T>
+__device__ void inverse_rows_128(const Params& p, const Sm<T>& s, T* Fdst, T& fe) {
+  constexpr int N = 128, nxh = 64;
+  const int warp = threadIdx.x >> 5, hf = (threadIdx.x >> 4) & 1, i = threadIdx.x & 15;
+  const int nwarps = blockDim.x >> 5;
+  const T scale = T(1.0 / ((double)p.nx * (double)p.ny));
+  const int ntask = 3 * p.FR;
+  T acc = T(0);
+  for (int t0 = 2 * warp; t0 < ntask; t0 += 2 * nwarps) {
+    const int t = min(t0 + hf, ntask - 1);
+    const bool live = t0 + hf < ntask;
+    const int yl = t / 3, pr = t - 3 * (t / 3);
+    Cx<T>* X = s.SR + ((size_t)(2 * pr) * p.FR + yl) * nxh;
+    Cx<T>* Y = s.SR + ((size_t)(2 * pr + 1) * p.FR + yl) * nxh;
+    Cx<T> a[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int n = i + 16 * r;
+      Cx<T> v = cx<T>(T(0), T(0));                          // Nyquist projected out
+      if (n < nxh) {
+        const Cx<T> x = X[n], y = Y[n];
+        v = n == 0 ? cx<T>(x.re, y.re)                       // real DC of each field
+                   : cx<T>(x.re - y.im, x.im + y.re);        // X + i Y
+      } else if (n > nxh) {
+        const Cx<T> x = X[N - n], y = Y[N - n];
+        v = cx<T>(x.re + y.im, y.re - x.im);                 // conj(X) + i conj(Y)
+      }
+      a[r] = v;
+    }
+    Cx<T> b[8];
+    fft128_h16<T>(a, X, Y, s.twx, true, live, b);
+    if (live) {
+      const int k2 = i >> 1, j0 = i & 1;
+      T* A = Fdst + ((size_t)(2 * pr) * p.FR + yl) * N;
+      T* B = Fdst + ((size_t)(2 * pr + 1) * p.FR + yl) * N;
+#pragma unroll
+      for (int m = 0; m < 8; ++m) {
+        const int k = k2 + 8 * m + 64 * j0;
+        const T va = b[m].re * scale, vb = b[m].im * scale;
+        A[k] = va;
+        B[k] = vb;
+        if (yl < p.RB) acc += va * va + vb * vb;
+      }
+    }
+  }
+  fe += acc;
+}
+
 template <typename T>
 __device__ __noinline__ void inverse_rows_r8(const Params& p, const Sm<T>& s, T* Fdst, T& fe) {
   inverse_rows_reg<T, 8>(p, s, Fdst, fe);
@@ -779,7 +1046,7 @@ __device__ void inverse_rows(const Params& p, const Sm<T>& s, T* Fdst, T& fe) {
   switch (p.lognx) {
     case 5: inverse_rows_reg<T, 1>(p, s, Fdst, fe); return;
     case 6: inverse_rows_reg<T, 2>(p, s, Fdst, fe); return;
-    case 7: inverse_rows_reg<T, 4>(p, s, Fdst, fe); return;
+    case 7: inverse_rows_128<T>(p, s, Fdst, fe); return;
     case 8: inverse_rows_r8<T>(p, s, Fdst, fe); return;
     default: break;
   }

@@ -84,6 +84,18 @@ def test_2d_fp64_state_matches_oracle(steps):
         assert gd["pushes"] == w.pushes_per_step
 
 
+def test_2d_fp64_nx128_matches_oracle():
+    """FP64 2-D slab at the transform length of the bench workloads (nx = 128)."""
+    w = W.small_2d(nx=128, nzeta=48, ppc=2, precision=64)
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        for _ in range(2):
+            od = o.step()
+            g.step()
+            check_state(g.state(), o.state(), 1e-10)
+            check_diag(g.diagnostics(), od, 1e-10)
+
+
 @pytest.mark.parametrize("C", [1, 2, 4])
 def test_3d_fp64_state_matches_oracle_cluster(C):
     w = W.small_3d(nx=16, ny=16, nzeta=40, ppc=2, precision=64)

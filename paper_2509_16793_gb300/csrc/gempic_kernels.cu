@@ -795,9 +795,15 @@ __device__ __noinline__ void forward_rows_r8(const cg::cluster_group& cl, const 
   forward_rows_reg<T, 8>(cl, p, s, me, stagger);
 }
 
-template <typename T>
+// SH = 1: the kernel instantiated for 128 x 128 grids with an even band (only the length-128
+// transforms are compiled in; with the other lengths present the compiler schedules them
+// markedly worse)
+template <typename T, int SH>
 __device__ void forward_rows(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
                              int me, bool stagger) {
+  if constexpr (SH == 1) {
+    forward_rows_128(cl, p, s, me, stagger);
+  } else {
   if (p.lognx == 7 && p.ny > 1 && (p.RB & 1) == 0) {
     forward_rows_128(cl, p, s, me, stagger);
     return;
@@ -837,6 +843,7 @@ __device__ void forward_rows(const cg::cluster_group& cl, const Params& p, const
       }
     }
     __syncwarp();
+  }
   }
 }
 
@@ -887,25 +894,28 @@ __device__ void column_ffts_128(const Params& p, const Sm<T>& s, int c0, int c1,
 
 // column FFTs of SC[c0..c1) (in place), forward or inverse; with a lane-order register FFT
 // the spectra stay in lane order (position q holds ky_of_pos(q))
-template <typename T>
+template <typename T, int SH>
 __device__ void column_ffts(const Params& p, const Sm<T>& s, int c0, int c1, bool inverse) {
-  if (p.ny == 1) return;
-  if (p.logny == 7) {
+  if constexpr (SH == 1) {
     column_ffts_128(p, s, c0, c1, inverse);
-    return;
-  }
-  const int warp = threadIdx.x >> 5;
-  const int nwarps = blockDim.x >> 5;
-  const int ntask = (c1 - c0) << p.logKB;
-  for (int task = warp; task < ntask; task += nwarps) {
-    const int c = c0 + (task >> p.logKB), kxl = task & (p.KB - 1);
-    Cx<T>* d = s.SC + ((size_t)c * p.KB + kxl) * p.ny;
-    switch (p.logny) {
-      case 5: col_fft_reg<T, 1>(d, s.twy, inverse); break;
-      case 6: col_fft_reg<T, 2>(d, s.twy, inverse); break;
-      case 7: col_fft_reg<T, 4>(d, s.twy, inverse); break;
-      case 8: col_fft_r8<T>(d, s.twy, inverse); break;
-      default: warp_fft_r2(d, p.logny, s.twy, inverse); break;
+  } else {
+    if (p.ny == 1) return;
+    if (p.logny == 7) {
+      column_ffts_128(p, s, c0, c1, inverse);
+      return;
+    }
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int ntask = (c1 - c0) << p.logKB;
+    for (int task = warp; task < ntask; task += nwarps) {
+      const int c = c0 + (task >> p.logKB), kxl = task & (p.KB - 1);
+      Cx<T>* d = s.SC + ((size_t)c * p.KB + kxl) * p.ny;
+      switch (p.logny) {
+        case 5: col_fft_reg<T, 1>(d, s.twy, inverse); break;
+        case 6: col_fft_reg<T, 2>(d, s.twy, inverse); break;
+        case 8: col_fft_r8<T>(d, s.twy, inverse); break;
+        default: warp_fft_r2(d, p.logny, s.twy, inverse); break;
+      }
     }
   }
 }
@@ -1041,46 +1051,50 @@ __device__ __noinline__ void inverse_rows_r8(const Params& p, const Sm<T>& s, T*
   inverse_rows_reg<T, 8>(p, s, Fdst, fe);
 }
 
-template <typename T>
+template <typename T, int SH>
 __device__ void inverse_rows(const Params& p, const Sm<T>& s, T* Fdst, T& fe) {
-  switch (p.lognx) {
-    case 5: inverse_rows_reg<T, 1>(p, s, Fdst, fe); return;
-    case 6: inverse_rows_reg<T, 2>(p, s, Fdst, fe); return;
-    case 7: inverse_rows_128<T>(p, s, Fdst, fe); return;
-    case 8: inverse_rows_r8<T>(p, s, Fdst, fe); return;
-    default: break;
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nxh = p.nx / 2;
-  const T scale = T(1.0 / ((double)p.nx * (double)p.ny));
-  const int ntask = 3 * p.FR;
-  for (int task = (warp < p.nwork ? warp : ntask); task < ntask; task += p.nwork) {
-    Cx<T>* w = s.workD + (size_t)warp * p.nx;
-    const int yl = task / 3, pr = task - 3 * yl;
-    const Cx<T>* X = s.SR + ((size_t)(2 * pr) * p.FR + yl) * nxh;
-    const Cx<T>* Y = s.SR + ((size_t)(2 * pr + 1) * p.FR + yl) * nxh;
-    for (int k = lane; k < nxh; k += 32) {
-      Cx<T> x = X[k], y = Y[k];
-      if (k == 0) {
-        w[0] = cx<T>(x.re, y.re);                         // real DC of each field
-      } else {
-        w[k] = cx<T>(x.re - y.im, x.im + y.re);           // X + i Y
-        w[p.nx - k] = cx<T>(x.re + y.im, y.re - x.im);    // conj(X) + i conj(Y)
+  if constexpr (SH == 1) {
+    inverse_rows_128<T>(p, s, Fdst, fe);
+  } else {
+    switch (p.lognx) {
+      case 5: inverse_rows_reg<T, 1>(p, s, Fdst, fe); return;
+      case 6: inverse_rows_reg<T, 2>(p, s, Fdst, fe); return;
+      case 7: inverse_rows_128<T>(p, s, Fdst, fe); return;
+      case 8: inverse_rows_r8<T>(p, s, Fdst, fe); return;
+      default: break;
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nxh = p.nx / 2;
+    const T scale = T(1.0 / ((double)p.nx * (double)p.ny));
+    const int ntask = 3 * p.FR;
+    for (int task = (warp < p.nwork ? warp : ntask); task < ntask; task += p.nwork) {
+      Cx<T>* w = s.workD + (size_t)warp * p.nx;
+      const int yl = task / 3, pr = task - 3 * yl;
+      const Cx<T>* X = s.SR + ((size_t)(2 * pr) * p.FR + yl) * nxh;
+      const Cx<T>* Y = s.SR + ((size_t)(2 * pr + 1) * p.FR + yl) * nxh;
+      for (int k = lane; k < nxh; k += 32) {
+        Cx<T> x = X[k], y = Y[k];
+        if (k == 0) {
+          w[0] = cx<T>(x.re, y.re);                         // real DC of each field
+        } else {
+          w[k] = cx<T>(x.re - y.im, x.im + y.re);           // X + i Y
+          w[p.nx - k] = cx<T>(x.re + y.im, y.re - x.im);    // conj(X) + i conj(Y)
+        }
       }
+      if (lane == 0) w[nxh] = cx<T>(T(0), T(0));            // Nyquist projected out
+      __syncwarp();
+      warp_fft_r2(w, p.lognx, s.twx, true);
+      T* a = Fdst + ((size_t)(2 * pr) * p.FR + yl) * p.nx;
+      T* b = Fdst + ((size_t)(2 * pr + 1) * p.FR + yl) * p.nx;
+      const bool own = yl < p.RB;
+      for (int x = lane; x < p.nx; x += 32) {
+        const T va = w[x].re * scale, vb = w[x].im * scale;
+        a[x] = va;
+        b[x] = vb;
+        if (own) fe += va * va + vb * vb;
+      }
+      __syncwarp();
     }
-    if (lane == 0) w[nxh] = cx<T>(T(0), T(0));            // Nyquist projected out
-    __syncwarp();
-    warp_fft_r2(w, p.lognx, s.twx, true);
-    T* a = Fdst + ((size_t)(2 * pr) * p.FR + yl) * p.nx;
-    T* b = Fdst + ((size_t)(2 * pr + 1) * p.FR + yl) * p.nx;
-    const bool own = yl < p.RB;
-    for (int x = lane; x < p.nx; x += 32) {
-      const T va = w[x].re * scale, vb = w[x].im * scale;
-      a[x] = va;
-      b[x] = vb;
-      if (own) fe += va * va + vb * vb;
-    }
-    __syncwarp();
   }
 }
 
@@ -1839,7 +1853,7 @@ __device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
 // CANON = false: the library's block layout [nz+1][C][6][M].  CANON = true: the public layout
 // of gempic_get_state ([6][nz][ny][nx/2]; j at half-slice index n <-> block n+1), used by the
 // allocation-free entry point on a caller's buffer.
-template <typename T, bool CANON = false>
+template <typename T, bool CANON = false, int SH = 0>
 __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& cl, long long k,
                       int cid) {
   const int me = (int)cl.block_rank();
@@ -2172,14 +2186,14 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     __syncthreads();
     TIMER_MARK(PH_BEAM);
     // ---------------- B: row FFTs of the currents, transposed to the kx owners ------------
-    forward_rows(cl, p, s, me, true);
+    forward_rows<T, SH>(cl, p, s, me, true);
     TIMER_MARK(PH_FWD);
     cl.sync();                                                      // B2
     if (tid == 0 && me == 0) p.jflag[(size_t)s1 * nz + n] = 0;
     TIMER_MARK(PH_B2);
     // ---------------- C: column FFTs, per-mode solve, inverse column FFTs ------------------
     for (int i = tid; i < 3 * jplane; i += NT) s.J[i] = T(0);
-    column_ffts(p, s, 0, 3, false);
+    column_ffts<T, SH>(p, s, 0, 3, false);
     __syncthreads();
     TIMER_MARK(PH_COLF);
     if (has_mode) {
@@ -2239,7 +2253,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     }
     __syncthreads();
     TIMER_MARK(PH_SOLVE);
-    column_ffts(p, s, 0, 6, true);
+    column_ffts<T, SH>(p, s, 0, 6, true);
     __syncthreads();
     TIMER_MARK(PH_COLI);
     scatter_to_rows(cl, p, s, me);
@@ -2254,7 +2268,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     }
     TIMER_MARK(PH_B3);
     // ---------------- D: inverse rows -> real-space fields of slice n ----------------------
-    inverse_rows(p, s, Fnew, fe);
+    inverse_rows<T, SH>(p, s, Fnew, fe);
     TIMER_MARK(PH_INV);
     if constexpr (sizeof(T) == 4) {
       // SR has been consumed: it holds the fixed-point accumulators of the next push
@@ -2310,7 +2324,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   }
 }
 
-template <typename T, bool CANON = false>
+template <typename T, bool CANON = false, int SH = 0>
 __global__ void __launch_bounds__(512, 1) march_kernel(const Params p) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -2319,7 +2333,7 @@ __global__ void __launch_bounds__(512, 1) march_kernel(const Params p) {
   if (threadIdx.x < kNDiag) s.dacc[threadIdx.x] = 0.0;
   __syncthreads();
   const int cid = (int)(blockIdx.x / p.C);
-  for (long long k = p.k0 + cid; k < p.k0 + p.nsteps; k += p.P) march<T, CANON>(p, s, cl, k, cid);
+  for (long long k = p.k0 + cid; k < p.k0 + p.nsteps; k += p.P) march<T, CANON, SH>(p, s, cl, k, cid);
 }
 
 // tables of the allocation-free entry point, built on the device (same formulas as the host
@@ -2352,7 +2366,7 @@ __global__ void tables_kernel(const Params p, void* dst) {
 // ------------------------------------------------------------------------------------------
 // laser initial condition (Eq. E_laser): R = 2E (forward wave) on every slice, spectral
 // ------------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, int SH = 0>
 __global__ void __launch_bounds__(512, 1)
     laser_kernel(const Params p, double a0, double waist, double dur, double zc, int pol) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -2379,9 +2393,9 @@ __global__ void __launch_bounds__(512, 1)
       s.J[((size_t)c * p.JR + yl + p.JOFF) * p.nx + x] = (c == 2) ? T(2.0 * E) : T(0);
     }
     __syncthreads();
-    forward_rows(cl, p, s, me, false);
+    forward_rows<T, SH>(cl, p, s, me, false);
     cl.sync();
-    column_ffts(p, s, 2, 3, false);
+    column_ffts<T, SH>(p, s, 2, 3, false);
     __syncthreads();
     for (int m = threadIdx.x; m < p.M; m += blockDim.x) {
       const int kxl = m >> p.logny, q = m & (p.ny - 1);
@@ -2466,19 +2480,29 @@ int smem_layout(Params& p, int eb) {
   return p.smem_bytes;
 }
 
-template <typename T>
-static cudaError_t cfg_one(int smem) {
-  cudaError_t e = cudaFuncSetAttribute(march_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+// kernel instantiation for the grid: 1 = FP32 128 x 128 with an even band (length-128
+// transforms only), 0 = any size
+static int shape_class(int precision, const Params& p) {
+  return precision == 32 && p.nx == 128 && p.ny == 128 && (p.RB & 1) == 0 ? 1 : 0;
+}
+
+template <typename K>
+static cudaError_t cfg_kernel(K* k, int smem) {
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(march_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(laser_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(laser_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
 cudaError_t configure_kernels(int precision, int smem, int) {
-  return precision == 64 ? cfg_one<double>(smem) : cfg_one<float>(smem);
+  if (precision == 64) {
+    cudaError_t e = cfg_kernel(march_kernel<double>, smem);
+    return e == cudaSuccess ? cfg_kernel(laser_kernel<double>, smem) : e;
+  }
+  cudaError_t e = cfg_kernel(march_kernel<float>, smem);
+  if (e == cudaSuccess) e = cfg_kernel(laser_kernel<float>, smem);
+  if (e == cudaSuccess) e = cfg_kernel(march_kernel<float, false, 1>, smem);
+  if (e == cudaSuccess) e = cfg_kernel(laser_kernel<float, 1>, smem);
+  return e;
 }
 
 static cudaLaunchConfig_t make_cfg(const Params& p, int nclusters, cudaStream_t s,
@@ -2501,6 +2525,7 @@ cudaError_t launch_march(int precision, const Params& p, cudaStream_t s) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t c = make_cfg(p, p.P, s, attr);
   if (precision == 64) return cudaLaunchKernelEx(&c, march_kernel<double>, p);
+  if (shape_class(precision, p) == 1) return cudaLaunchKernelEx(&c, march_kernel<float, false, 1>, p);
   return cudaLaunchKernelEx(&c, march_kernel<float>, p);
 }
 
@@ -2513,6 +2538,8 @@ cudaError_t launch_laser_init(int precision, const Params& p, double a0, double 
   if (ncl > p.nz) ncl = p.nz;
   cudaLaunchConfig_t c = make_cfg(p, ncl, s, attr);
   if (precision == 64) return cudaLaunchKernelEx(&c, laser_kernel<double>, p, a0, waist, dur, zc, pol);
+  if (shape_class(precision, p) == 1)
+    return cudaLaunchKernelEx(&c, laser_kernel<float, 1>, p, a0, waist, dur, zc, pol);
   return cudaLaunchKernelEx(&c, laser_kernel<float>, p, a0, waist, dur, zc, pol);
 }
 
@@ -2540,17 +2567,15 @@ cudaError_t configure_march_canon(int precision, int smem) {
     return cudaFuncSetAttribute(march_kernel<double, true>,
                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   }
-  cudaError_t e = cudaFuncSetAttribute(march_kernel<float, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(march_kernel<float, true>,
-                              cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaError_t e = cfg_kernel(march_kernel<float, true>, smem);
+  return e == cudaSuccess ? cfg_kernel(march_kernel<float, true, 1>, smem) : e;
 }
 
 cudaError_t launch_march_canon(int precision, const Params& p, cudaStream_t s) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t c = make_cfg(p, 1, s, attr);
   if (precision == 64) return cudaLaunchKernelEx(&c, march_kernel<double, true>, p);
+  if (shape_class(precision, p) == 1) return cudaLaunchKernelEx(&c, march_kernel<float, true, 1>, p);
   return cudaLaunchKernelEx(&c, march_kernel<float, true>, p);
 }
 
@@ -2566,6 +2591,8 @@ cudaError_t max_active_clusters(int precision, const Params& p, int* n) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t c = make_cfg(p, 1, 0, attr);
   if (precision == 64) return cudaOccupancyMaxActiveClusters(n, march_kernel<double>, &c);
+  if (shape_class(precision, p) == 1)
+    return cudaOccupancyMaxActiveClusters(n, march_kernel<float, false, 1>, &c);
   return cudaOccupancyMaxActiveClusters(n, march_kernel<float>, &c);
 }
 

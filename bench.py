@@ -194,7 +194,12 @@ def main():
                     help="profiling only: shorter window of the same workload")
     ap.add_argument("--pipeline", type=int, default=0, help="s-steps marched concurrently (0 = auto)")
     ap.add_argument("--bucket-capacity", type=int, default=0)
+    ap.add_argument("--workload", default="lwfa3d", choices=["lwfa3d", "scan"],
+                    help="lwfa3d: the 3-D LWFA (default); scan: the batched 2-D parameter scan")
+    ap.add_argument("--instances", type=int, default=64, help="scan: number of instances")
     args = ap.parse_args()
+    if args.workload == "scan" and args.impl == "gempic":
+        return run_scan(args)
 
     from paper_2509_16793_gb300 import workloads as W
     w = W.lwfa_3d_128x128x1024()
@@ -327,6 +332,73 @@ def measured_traffic(w):
     if not m or m.group(2) != kernel_hash():
         return None
     return int(m.group(1))
+
+
+def run_scan(args):
+    """Batched parameter scan: independent 2-D instances of uneven size stepped side by side,
+    one persistent launch per instance per call, each on its own stream.  Timed with CUDA
+    events recorded on every instance's stream: latest end minus earliest start."""
+    import torch
+    from paper_2509_16793_gb300 import build, gempic, workloads as W
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    ws = W.scan_2d(n=args.instances, seed=W.SEED + 1000 * rank)
+    pushes = sum(w.pushes_per_step for w in ws)
+    with gempic.Batch(ws) as b:
+        b.step(args.warmup)
+        launches0 = sum(v.launch_count() for v in b.sims)
+        streams = [torch.cuda.ExternalStream(b.stream(i)) for i in range(len(ws))]
+        ref = torch.cuda.Event(enable_timing=True)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in ws]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in ws]
+        torch.cuda.synchronize()
+        ref.record(streams[0])
+        with ClockSampler(local) as clk:
+            for e, st in zip(starts, streams):
+                e.record(st)
+            b.step_async(args.steps)
+            for e, st in zip(ends, streams):
+                e.record(st)
+            b.sync()
+            torch.cuda.synchronize()
+        t0 = min(ref.elapsed_time(e) for e in starts)
+        t1 = max(ref.elapsed_time(e) for e in ends)
+        ms = t1 - t0
+        per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        launches = sum(v.launch_count() for v in b.sims) - launches0
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * pushes * args.steps / (ms / 1e3)
+    if rank == 0:
+        peaks = measured_peaks()
+        peak_alu = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+        flops = sum(algorithmic_flops(w) for w in ws) * args.steps
+        achieved = flops / (ms / 1e3) / 1e12
+        sizes = sorted({(w.nx, w.nzeta) for w in ws})
+        line = {"metric": "particle-pushes/s", "value": value, "unit": "pushes/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"scan_2d_{len(ws)}", "instances": len(ws),
+                           "sizes_nx_nzeta": sizes, "ppc": 4, "pushes_per_step": pushes,
+                           "per_instance_ms": {"min": min(per), "max": max(per)},
+                           "l2": "every instance's state and particles are resident; no L2 flush"},
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu,
+                             "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": None,
+                             "kernel": "march_kernel<float> (one per instance)"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": launches,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
 
 
 def kernel_hash() -> str:

@@ -181,6 +181,43 @@ int64_t gempic_launch_count(const struct gempic_sim* sim);
 gempic_status gempic_launch_shape(const struct gempic_sim* sim, int32_t* cluster_ctas,
                                   int32_t* threads, int32_t* smem_bytes, int32_t* pipeline);
 
+/* ---- Batched parameter scan ------------------------------------------------------------
+ * Independent simulations stepped side by side on one GPU (the paper has no counterpart: a
+ * scan over grids, drivers and densities).  Each instance is an ordinary gempic_sim with its
+ * own CUDA stream and one s-step in flight -- no wavefront between clusters of an instance,
+ * so no instance ever waits on another's residency; a step call submits one persistent
+ * launch per instance and the GPU runs them concurrently. */
+typedef struct gempic_batch gempic_batch;
+
+/* Create n >= 1 instances from cfgs[0..n-1], each validated like gempic_create;
+ * cuda_stream and pipeline_depth of the configs are ignored (the batch creates a
+ * non-blocking stream per instance).  On a failure nothing is kept and the first failing
+ * status is returned. */
+gempic_status gempic_batch_create(const gempic_config* cfgs, int32_t n, gempic_batch** out);
+
+/* Launch n s-steps on every instance (one launch each, on its stream) and return. */
+gempic_status gempic_batch_step_async(gempic_batch* b, int32_t n);
+
+/* Wait for every instance and check its device status word; the first error is returned
+ * (the other instances are still waited for). */
+gempic_status gempic_batch_sync(gempic_batch* b);
+
+/* gempic_batch_step_async then gempic_batch_sync. */
+gempic_status gempic_batch_step(gempic_batch* b, int32_t n);
+
+/* Number of instances (0 for NULL). */
+int32_t gempic_batch_size(const gempic_batch* b);
+
+/* Instance i, owned by the batch: use it with the gempic_get_* and gempic_add_particles
+ * calls, never with gempic_destroy.  NULL if i is out of range. */
+struct gempic_sim* gempic_batch_sim(gempic_batch* b, int32_t i);
+
+/* The cudaStream_t of instance i (for events and interoperation); NULL if out of range. */
+void* gempic_batch_stream(gempic_batch* b, int32_t i);
+
+/* Destroy every instance and the batch's streams (waits for them first). */
+void gempic_batch_destroy(gempic_batch* b);
+
 /* Allocation-free s-step.  The paper has no counterpart: this entry point is for callers that
  * cannot allocate device memory -- for example code whose host application owns every device
  * allocation under a fixed budget, or a plug-in that is not allowed to call cudaMalloc.

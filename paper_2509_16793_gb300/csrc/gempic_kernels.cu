@@ -2486,9 +2486,17 @@ static int shape_class(int precision, const Params& p) {
   return precision == 32 && p.nx == 128 && p.ny == 128 && (p.RB & 1) == 0 ? 1 : 0;
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel function, shared by every
+// simulation of the process: it is raised to the device's opt-in maximum (each launch asks
+// for its own size), never set to one simulation's size, which would break the launches of a
+// larger simulation alive at the same time.
 template <typename K>
 static cudaError_t cfg_kernel(K* k, int smem) {
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, std::max(smem, optin));
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
@@ -2560,13 +2568,7 @@ cudaError_t launch_import_state(int precision, const Params& p, const void* src,
 }
 
 cudaError_t configure_march_canon(int precision, int smem) {
-  if (precision == 64) {
-    cudaError_t e = cudaFuncSetAttribute(march_kernel<double, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(march_kernel<double, true>,
-                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  }
+  if (precision == 64) return cfg_kernel(march_kernel<double, true>, smem);
   cudaError_t e = cfg_kernel(march_kernel<float, true>, smem);
   return e == cudaSuccess ? cfg_kernel(march_kernel<float, true, 1>, smem) : e;
 }

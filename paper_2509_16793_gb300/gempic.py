@@ -84,6 +84,14 @@ SIGNATURES = {
     "gempic_launch_shape": (c_int32, [c_void_p] + [POINTER(c_int32)] * 4),
     "gempic_step_noalloc": (c_int32, [POINTER(gempic_config), c_int64, c_void_p, c_size_t,
                                        POINTER(gempic_diag), c_void_p]),
+    "gempic_batch_create": (c_int32, [POINTER(gempic_config), c_int32, POINTER(c_void_p)]),
+    "gempic_batch_step_async": (c_int32, [c_void_p, c_int32]),
+    "gempic_batch_sync": (c_int32, [c_void_p]),
+    "gempic_batch_step": (c_int32, [c_void_p, c_int32]),
+    "gempic_batch_size": (c_int32, [c_void_p]),
+    "gempic_batch_sim": (c_void_p, [c_void_p, c_int32]),
+    "gempic_batch_stream": (c_void_p, [c_void_p, c_int32]),
+    "gempic_batch_destroy": (None, [c_void_p]),
     "gempic_strerror": (c_char_p, [c_int32]),
     "gempic_destroy": (None, [c_void_p]),
 }
@@ -167,12 +175,23 @@ class Sim:
 
     def __init__(self, w, **kw):
         lib = load()
-        self.w = w
-        self.lib = lib
         cfg, self._keep = config_from_workload(w, **kw)
         h = c_void_p()
         _check(lib.gempic_create(byref(cfg), byref(h)), "gempic_create")
+        self._attach(lib, w, h, owned=True)
+
+    @classmethod
+    def borrowed(cls, w, handle):
+        """A view of a simulation owned elsewhere (an instance of a Batch)."""
+        self = cls.__new__(cls)
+        self._attach(load(), w, c_void_p(handle), owned=False)
+        return self
+
+    def _attach(self, lib, w, h, owned):
+        self.w = w
+        self.lib = lib
         self.h = h
+        self.owned = owned
         self.dtype = np.complex128 if w.precision == 64 else np.complex64
         self.rdtype = np.float64 if w.precision == 64 else np.float32
         if w.stored is not None and w.stored.n > 0:
@@ -282,7 +301,71 @@ class Sim:
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
-            self.lib.gempic_destroy(self.h)
+            if getattr(self, "owned", True):
+                self.lib.gempic_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Independent simulations stepped side by side (gempic_batch_create ...
+    gempic_batch_destroy); `sims[i]` is a view of instance i for the query calls."""
+
+    def __init__(self, workloads, **kw):
+        lib = load()
+        n = len(workloads)
+        cfgs = (gempic_config * n)()
+        self._keep = []
+        for i, w in enumerate(workloads):
+            c, k = config_from_workload(w, **kw)
+            cfgs[i] = c
+            self._keep.append(k)
+        h = c_void_p()
+        _check(lib.gempic_batch_create(cfgs, n, byref(h)), "gempic_batch_create")
+        self.lib = lib
+        self.h = h
+        self.workloads = list(workloads)
+        self.sims = [Sim.borrowed(w, lib.gempic_batch_sim(h, i)) for i, w in enumerate(workloads)]
+
+    def __len__(self):
+        return int(self.lib.gempic_batch_size(self.h))
+
+    def gempic_batch_step(self, n: int = 1):
+        _check(self.lib.gempic_batch_step(self.h, n), "gempic_batch_step")
+
+    step = gempic_batch_step
+
+    def gempic_batch_step_async(self, n: int = 1):
+        _check(self.lib.gempic_batch_step_async(self.h, n), "gempic_batch_step_async")
+
+    step_async = gempic_batch_step_async
+
+    def gempic_batch_sync(self):
+        _check(self.lib.gempic_batch_sync(self.h), "gempic_batch_sync")
+
+    sync = gempic_batch_sync
+
+    def gempic_batch_stream(self, i: int) -> int:
+        return int(self.lib.gempic_batch_stream(self.h, i) or 0)
+
+    stream = gempic_batch_stream
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            for v in self.sims:
+                v.h = c_void_p()
+            self.lib.gempic_batch_destroy(self.h)
             self.h = c_void_p()
 
     def __del__(self):

@@ -129,6 +129,31 @@ def lwfa_2d_128x256(precision: int = 64, steps: int = 200) -> Workload:
         precision=precision, steps=steps)
 
 
+def scan_2d(n: int = 64, seed: int = SEED, precision: int = 32, steps: int = 500) -> List[Workload]:
+    """Batched parameter scan: n independent 2-D (x, zeta) instances with nx drawn from
+    {128, 256, 512} and nzeta from {256, 512, 1024, 2048}, a0 ~ U[0.5, 3], n0 log-uniform on
+    [1e-3, 1e-2] n_cr, 4 ppc, dzeta = lambda/20, dx = lambda/2, Delta at each instance's
+    stability limit Delta h omega_p^2 = 4, and the laser of the 2-D workload (10 lambda/c
+    FWHM, waist 8 lambda) centred at 0.6 of the window.  Draws from a seeded generator;
+    instance i uses seed + i for its injection offsets."""
+    rng = np.random.default_rng(seed)
+    h = LAMBDA_L / 20.0
+    out = []
+    for i in range(n):
+        nx = int(rng.choice([128, 256, 512]))
+        nz = int(rng.choice([256, 512, 1024, 2048]))
+        a0 = float(rng.uniform(0.5, 3.0))
+        n0 = float(10.0 ** rng.uniform(-3.0, -2.0))
+        L = nz * h
+        out.append(Workload(
+            name=f"scan{i}_{nx}x{nz}", nx=nx, ny=1, nzeta=nz, hx=LAMBDA_L / 2.0, hy=1.0, h=h,
+            delta=4.0 / (n0 * h), species=[Species(-1.0, 1.0, n0, 4)],
+            laser=Laser(a0=a0, waist=8.0 * LAMBDA_L, duration=fwhm_to_T(10.0 * LAMBDA_L),
+                        zeta_center=0.6 * L),
+            seed=seed + i, precision=precision, steps=steps))
+    return out
+
+
 def lwfa_3d_128x128x1024(precision: int = 32, steps: int = 2000) -> Workload:
     """3-D LWFA: 128 x 128 x 1024, dzeta = lambda/20, dx = dy = lambda/4, n0 = 0.002 n_cr,
     2 ppc (33.5 M pushes per s-step), a0 = 2.5, 8 lambda/c FWHM, waist 10 lambda.

@@ -154,6 +154,29 @@ def test_beam_particles_fp64():
         compare_particles(g.particles(0), oc.stored_particles(), 1e-10)
 
 
+def test_pwfa_mobile_ions_and_drive_bunch_fp64():
+    """Beam-driven set-up (the PWFA configuration's physics at a grid the oracle handles):
+    background electrons and mobile protons (m = 1836) injected at the front, no laser, and a
+    relativistic electron drive bunch (n_b = 2 n0, gamma = 2000, 1e-3 spread) in the stored
+    set; background electrons may be trapped and stored like any other particle."""
+    n0 = 0.01
+    w = W.small_3d(nx=16, ny=16, nzeta=48, ppc=1, precision=64, a0=0.0, n0=n0)
+    w = w.with_(species=[W.Species(-1.0, 1.0, n0, 1), W.Species(1.0, 1836.0, n0, 1)])
+    beam = W.gaussian_bunch(w, n_macro=2000, n_peak=2.0 * n0, sigma_r=1.5, sigma_z=2.0,
+                            zeta_center=0.6 * w.nzeta * w.h, gamma=2000.0, rel_spread=1e-3)
+    w = w.with_(stored=beam)
+    o = RefSim(w)
+    with gpu_sim(w, cluster_ctas=2) as g:
+        for _ in range(3):
+            od = o.step()
+            g.step()
+            check_diag(g.diagnostics(), od, 1e-10)
+            check_state(g.state(), o.state(), 1e-10)
+        oc = copy.deepcopy(o)
+        oc._stored_push()
+        compare_particles(g.particles(0), oc.stored_particles(), 1e-10)
+
+
 def test_fp32_matches_fp64_oracle():
     w = W.small_3d(nx=32, ny=32, nzeta=64, ppc=2, precision=32)
     o = RefSim(w)
@@ -208,6 +231,29 @@ def test_pipelined_equals_sequential():
         a.step(6)
         b.step(6)
         check_state(b.state(), a.state(), 1e-12)
+
+
+def test_simulations_of_different_sizes_alive_together():
+    """Kernel attributes are shared by the process: creating a smaller simulation must not
+    break the launches of a larger one that is still alive."""
+    big = W.small_3d(nx=32, ny=32, nzeta=32, ppc=2, precision=64)
+    small = W.small_2d(nx=16, nzeta=32, ppc=1, precision=64)
+    with gpu_sim(big) as a:
+        ref_state = None
+        with gpu_sim(big) as r:
+            r.step(2)
+            ref_state = r.state()
+        with gpu_sim(small) as b:
+            a.step(1)
+            b.step(1)
+            a.step(1)
+            b.step(1)
+        # FP64 current reductions sum in a varying order: equal to rounding
+        g = a.state()
+        fs = max(np.abs(ref_state[c]).max() for c in range(4))
+        js = max(np.abs(ref_state[c]).max() for c in (4, 5))
+        for c in range(6):
+            assert np.abs(g[c] - ref_state[c]).max() <= 1e-12 * (fs if c < 4 else js), c
 
 
 def test_vacuum_and_degenerate_sizes():

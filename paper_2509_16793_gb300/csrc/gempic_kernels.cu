@@ -611,7 +611,7 @@ __device__ void load_tables(const Params& p, const Sm<T>& s) {
 // phase timers (profiling builds only)
 // ------------------------------------------------------------------------------------------
 enum Phase { PH_A = 0, PH_B1, PH_BEAM, PH_FWD, PH_B2, PH_COLF, PH_SOLVE, PH_COLI, PH_SCAT, PH_B3,
-             PH_INV, PH_B4, PH_E, PH_AG, PH_AM, PH_AD, PH_AW, PH_AR, PH_N };
+             PH_INV, PH_B4, PH_E, PH_AG, PH_AM, PH_AD, PH_AW, PH_AR, PH_BF, PH_BI, PH_N };
 // Thread 0 of each CTA adds the cycles of each phase straight into global memory (phase ph at
 // word ph, PH_AW and PH_AR at 32 + ph): no per-phase registers are carried through the march.
 #ifdef GEMPIC_PHASE_TIMERS
@@ -2060,9 +2060,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       if (p.ny > 1) {
         const T jinv = s.cst[K_JINV];
         for (int i = tid; i < 9 * p.nx; i += NT) {
-          const int c = i / (3 * p.nx);
-          const int rem = i - c * 3 * p.nx;
-          const int which = rem / p.nx, x = rem - which * p.nx;
+          const int rowi = i >> p.lognx, x = i & (p.nx - 1);
+          const int c = rowi / 3, which = rowi - 3 * c;
           const int jrow = which == 0 ? 0 : p.RB + p.JOFF + (which - 1);
           const size_t j = ((size_t)c * p.JR + jrow) * p.nx + x;
           s.J[j] += T(s.Jint[j]) * jinv;
@@ -2074,9 +2073,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     if (p.ny > 1) {
       const int rb = (me + p.C - 1) & (p.C - 1), ra = (me + 1) & (p.C - 1);
       for (int i = tid; i < 9 * p.nx; i += NT) {
-        const int c = i / (3 * p.nx);
-        const int rem = i - c * 3 * p.nx;
-        const int which = rem / p.nx, x = rem - which * p.nx;
+        const int rowi = i >> p.lognx, x = i & (p.nx - 1);
+        const int c = rowi / 3, which = rowi - 3 * c;
         // which 0: band row -1 -> row RB-1 of the CTA below (recv slot 2)
         // which 1, 2: band rows RB, RB+1 -> rows 0, 1 of the CTA above (recv slots 0, 1)
         const int jrow = which == 0 ? 0 : p.RB + p.JOFF + (which - 1);
@@ -2115,8 +2113,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     {
       const T jinv = s.cst[K_JINV];
       for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
-        const int c = i / (p.RB * p.nx);
-        const int rem = i - c * p.RB * p.nx;
+        const int c = i >> (p.logRB + p.lognx);
+        const int rem = i & ((p.RB << p.lognx) - 1);
         const int row = rem >> p.lognx, x = rem & (p.nx - 1);
         const size_t j = ((size_t)c * p.JR + p.JOFF) * p.nx + rem;
         T v = s.J[j];
@@ -2129,6 +2127,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         s.J[j] = v;
       }
     }
+    TIMER_MARK(PH_BF);
     // migrating particles into free slots
     if (p.ny > 1) {
       const int nin = min(s.misc[M_INBOX], p.mig_cap);
@@ -2161,13 +2160,14 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         s.misc[M_INBOX] = 0;
       }
     }
+    TIMER_MARK(PH_BI);
     // beam current of this level at the half-slice n + 1/2 (own rows); the flag is cleared
     // by CTA 0 after B2, once every CTA has read it
     if (s.misc[M_JFLAG]) {
       T* jb = (T*)p.jbeam + (((size_t)s1 * nz + n) * 3) * (size_t)p.nx * p.ny;
       for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
-        const int c = i / (p.RB * p.nx);
-        const int rem = i - c * p.RB * p.nx;
+        const int c = i >> (p.logRB + p.lognx);
+        const int rem = i & ((p.RB << p.lognx) - 1);
         const size_t g = (size_t)c * p.nx * p.ny + ((size_t)me << p.logRB) * p.nx + rem;
         s.J[((size_t)c * p.JR + p.JOFF) * p.nx + rem] += ldcg(jb + g);
         jb[g] = T(0);
@@ -2177,8 +2177,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       __syncthreads();
       T* sn = (T*)p.snap;
       for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
-        const int c = i / (p.RB * p.nx);
-        const int rem = i - c * p.RB * p.nx;
+        const int c = i >> (p.logRB + p.lognx);
+        const int rem = i & ((p.RB << p.lognx) - 1);
         sn[(((size_t)(6 + c) * nz + n) * p.ny + (me << p.logRB)) * p.nx + rem] =
             s.J[((size_t)c * p.JR + p.JOFF) * p.nx + rem];
       }
@@ -2285,8 +2285,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     if (snap_step) {
       T* sn = (T*)p.snap;
       for (int i = tid; i < 6 * p.RB * p.nx; i += NT) {
-        const int c = i / (p.RB * p.nx);
-        const int rem = i - c * p.RB * p.nx;
+        const int c = i >> (p.logRB + p.lognx);
+        const int rem = i & ((p.RB << p.lognx) - 1);
         sn[(((size_t)c * nz + n) * p.ny + (me << p.logRB)) * p.nx + rem] =
             Fnew[(size_t)c * fplane + rem];
       }

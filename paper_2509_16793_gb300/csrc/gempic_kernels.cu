@@ -2056,33 +2056,41 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     // FP32: fold the fixed-point accumulators of the halo rows now (only this CTA's pushes
     // deposit there); own rows also receive other CTAs' fixed-point deposits and are folded
     // after the barrier
-    if constexpr (sizeof(T) == 4) {
-      if (p.ny > 1) {
+    // (FP32: four consecutive elements per thread, 16-byte accesses; rows are nx >= 32 long)
+    if (p.ny > 1) {
+      const int rb = (me + p.C - 1) & (p.C - 1), ra = (me + 1) & (p.C - 1);
+      if constexpr (sizeof(T) == 4) {
         const T jinv = s.cst[K_JINV];
-        for (int i = tid; i < 9 * p.nx; i += NT) {
+        for (int i = 4 * tid; i < 9 * p.nx; i += 4 * NT) {
           const int rowi = i >> p.lognx, x = i & (p.nx - 1);
           const int c = rowi / 3, which = rowi - 3 * c;
           const int jrow = which == 0 ? 0 : p.RB + p.JOFF + (which - 1);
           const size_t j = ((size_t)c * p.JR + jrow) * p.nx + x;
-          s.J[j] += T(s.Jint[j]) * jinv;
+          float4 v = *reinterpret_cast<const float4*>(s.J + j);
+          const int4 q = *reinterpret_cast<const int4*>(s.Jint + j);
+          v.x += T(q.x) * jinv;
+          v.y += T(q.y) * jinv;
+          v.z += T(q.z) * jinv;
+          v.w += T(q.w) * jinv;
+          // which 0: band row -1 -> row RB-1 of the CTA below (recv slot 2)
+          // which 1, 2: band rows RB, RB+1 -> rows 0, 1 of the CTA above (recv slots 0, 1)
+          const int dst = which == 0 ? rb : ra;
+          const int slot = which == 0 ? 2 : which - 1;
+          float4* d = reinterpret_cast<float4*>(s.recv + ((size_t)c * 3 + slot) * p.nx + x);
+          *(dst == me ? d : cl.map_shared_rank(d, dst)) = v;
         }
-        __syncthreads();
-      }
-    }
-    // halo currents (band rows -1, RB, RB+1) to the owners' receive buffers (plain stores)
-    if (p.ny > 1) {
-      const int rb = (me + p.C - 1) & (p.C - 1), ra = (me + 1) & (p.C - 1);
-      for (int i = tid; i < 9 * p.nx; i += NT) {
-        const int rowi = i >> p.lognx, x = i & (p.nx - 1);
-        const int c = rowi / 3, which = rowi - 3 * c;
-        // which 0: band row -1 -> row RB-1 of the CTA below (recv slot 2)
-        // which 1, 2: band rows RB, RB+1 -> rows 0, 1 of the CTA above (recv slots 0, 1)
-        const int jrow = which == 0 ? 0 : p.RB + p.JOFF + (which - 1);
-        const T v = s.J[((size_t)c * p.JR + jrow) * p.nx + x];
-        const int dst = which == 0 ? rb : ra;
-        const int slot = which == 0 ? 2 : which - 1;
-        T* q = s.recv + ((size_t)c * 3 + slot) * p.nx + x;
-        *(dst == me ? q : cl.map_shared_rank(q, dst)) = v;
+      } else {
+        // halo currents (band rows -1, RB, RB+1) to the owners' receive buffers (plain stores)
+        for (int i = tid; i < 9 * p.nx; i += NT) {
+          const int rowi = i >> p.lognx, x = i & (p.nx - 1);
+          const int c = rowi / 3, which = rowi - 3 * c;
+          const int jrow = which == 0 ? 0 : p.RB + p.JOFF + (which - 1);
+          const T v = s.J[((size_t)c * p.JR + jrow) * p.nx + x];
+          const int dst = which == 0 ? rb : ra;
+          const int slot = which == 0 ? 2 : which - 1;
+          T* q = s.recv + ((size_t)c * 3 + slot) * p.nx + x;
+          *(dst == me ? q : cl.map_shared_rank(q, dst)) = v;
+        }
       }
     }
     if (tid == 0) {
@@ -2110,15 +2118,45 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     TIMER_MARK(PH_B1);
     // own rows: fixed-point accumulators (FP32) and the received halo currents (rows 0, 1
     // from the band below, RB - 1 from the band above); element mapping as in the beam add
-    {
+    if constexpr (sizeof(T) == 4) {
       const T jinv = s.cst[K_JINV];
+      for (int i = 4 * tid; i < 3 * p.RB * p.nx; i += 4 * NT) {
+        const int c = i >> (p.logRB + p.lognx);
+        const int rem = i & ((p.RB << p.lognx) - 1);
+        const int row = rem >> p.lognx, x = rem & (p.nx - 1);
+        const size_t j = ((size_t)c * p.JR + p.JOFF) * p.nx + rem;
+        float4 v = *reinterpret_cast<const float4*>(s.J + j);
+        const int4 q = *reinterpret_cast<const int4*>(s.Jint + j);
+        v.x += T(q.x) * jinv;
+        v.y += T(q.y) * jinv;
+        v.z += T(q.z) * jinv;
+        v.w += T(q.w) * jinv;
+        if (p.ny > 1) {
+          const int slot = row == 0 ? 0 : row == 1 ? 1 : row == p.RB - 1 ? 2 : -1;
+          if (slot >= 0) {
+            const float4 r = *reinterpret_cast<const float4*>(s.recv + ((size_t)c * 3 + slot) * p.nx + x);
+            v.x += r.x;
+            v.y += r.y;
+            v.z += r.z;
+            v.w += r.w;
+            if (slot == 1 && p.RB == 2) {     // RB = 2: row 1 is also row RB - 1
+              const float4 r2 = *reinterpret_cast<const float4*>(s.recv + ((size_t)c * 3 + 2) * p.nx + x);
+              v.x += r2.x;
+              v.y += r2.y;
+              v.z += r2.z;
+              v.w += r2.w;
+            }
+          }
+        }
+        *reinterpret_cast<float4*>(s.J + j) = v;
+      }
+    } else {
       for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
         const int c = i >> (p.logRB + p.lognx);
         const int rem = i & ((p.RB << p.lognx) - 1);
         const int row = rem >> p.lognx, x = rem & (p.nx - 1);
         const size_t j = ((size_t)c * p.JR + p.JOFF) * p.nx + rem;
         T v = s.J[j];
-        if constexpr (sizeof(T) == 4) v += T(s.Jint[j]) * jinv;
         if (p.ny > 1) {
           if (row == 0) v += s.recv[((size_t)c * 3 + 0) * p.nx + x];
           if (row == 1) v += s.recv[((size_t)c * 3 + 1) * p.nx + x];
@@ -2161,6 +2199,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       }
     }
     TIMER_MARK(PH_BI);
+    __syncthreads();
     // beam current of this level at the half-slice n + 1/2 (own rows); the flag is cleared
     // by CTA 0 after B2, once every CTA has read it
     if (s.misc[M_JFLAG]) {
@@ -2192,7 +2231,12 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     if (tid == 0 && me == 0) p.jflag[(size_t)s1 * nz + n] = 0;
     TIMER_MARK(PH_B2);
     // ---------------- C: column FFTs, per-mode solve, inverse column FFTs ------------------
-    for (int i = tid; i < 3 * jplane; i += NT) s.J[i] = T(0);
+    if constexpr (sizeof(T) == 4) {
+      for (int i = 4 * tid; i < 3 * jplane; i += 4 * NT)
+        *reinterpret_cast<float4*>(s.J + i) = make_float4(0.f, 0.f, 0.f, 0.f);
+    } else {
+      for (int i = tid; i < 3 * jplane; i += NT) s.J[i] = T(0);
+    }
     column_ffts<T, SH>(p, s, 0, 3, false);
     __syncthreads();
     TIMER_MARK(PH_COLF);
@@ -2273,7 +2317,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     if constexpr (sizeof(T) == 4) {
       // SR has been consumed: it holds the fixed-point accumulators of the next push
       __syncthreads();
-      for (int i = tid; i < 3 * jplane; i += NT) s.Jint[i] = 0;
+      for (int i = 4 * tid; i < 3 * jplane; i += 4 * NT)
+        *reinterpret_cast<int4*>(s.Jint + i) = make_int4(0, 0, 0, 0);
     }
     cl.sync();                                                      // B4: fields of slice n
     TIMER_MARK(PH_B4);

@@ -32,6 +32,7 @@ struct gempic_sim {
   long long last_launch_k0 = 0;
   int last_launch_n = 0;
   std::vector<void*> allocs;
+  void* stage = nullptr;           // device staging of the public state layout (host copies)
   // particles placed before the first step: absolute positions
   std::vector<double> px, py, pz, pux, puy, puz, pq;
   std::vector<int> psp;
@@ -487,21 +488,27 @@ static gempic_status copy_state(gempic_sim* s, void* ptr, size_t bytes, int is_d
   if (st != GEMPIC_OK) return st;
   const size_t nb = gempic_state_bytes(s);
   void* dev = ptr;
-  void* tmp = nullptr;
   cudaError_t e = cudaSuccess;
   if (!is_device) {
-    e = cudaMallocAsync(&tmp, nb, s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e);
-    dev = tmp;
-    if (!out) e = cudaMemcpyAsync(tmp, ptr, nb, cudaMemcpyHostToDevice, s->stream);
+    // one staging buffer per simulation, kept for its lifetime: a host copy every s-step
+    // (the end-to-end path) then costs no allocation
+    if (!s->stage) {
+      e = cudaMalloc(&s->stage, nb);
+      if (e != cudaSuccess) {
+        s->stage = nullptr;
+        return cuda_fail(s, e);
+      }
+      s->allocs.push_back(s->stage);
+    }
+    dev = s->stage;
+    if (!out) e = cudaMemcpyAsync(dev, ptr, nb, cudaMemcpyHostToDevice, s->stream);
   }
   if (e == cudaSuccess)
     e = out ? gempic::launch_export_state(s->cfg.precision, s->p, dev, s->stream)
             : gempic::launch_import_state(s->cfg.precision, s->p, dev, s->stream);
   s->launches++;
   if (e == cudaSuccess && !is_device && out)
-    e = cudaMemcpyAsync(ptr, tmp, nb, cudaMemcpyDeviceToHost, s->stream);
-  if (tmp) cudaFreeAsync(tmp, s->stream);
+    e = cudaMemcpyAsync(ptr, dev, nb, cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
   return cuda_fail(s, e);
 }

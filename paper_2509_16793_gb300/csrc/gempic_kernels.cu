@@ -2113,8 +2113,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     // publish: iteration n+1 complete (its stored phase and this push have been issued)
     if (p.P > 1 && me == 0 && tid == 0 && n + 1 <= nz - 1)
       st_release_u64(p.progress + cid, prog_value(k, nz, nz - (n + 1)));
-    // stored particles of cell n at this level (traps of this push included), for phase E
-    if (tid == 32) s.misc[M_STN] = ldcg(p.st.cnt + (size_t)s1 * nz + n);
+    // stored particles of cell n at this level (traps of this push included), for phase E;
+    // loaded by the last warp, which has no forward-transform task
+    if (tid == NT - 32) s.misc[M_STN] = ldcg(p.st.cnt + (size_t)s1 * nz + n);
     TIMER_MARK(PH_B1);
     // own rows: fixed-point accumulators (FP32) and the received halo currents (rows 0, 1
     // from the band below, RB - 1 from the band above); element mapping as in the beam add
@@ -2305,8 +2306,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     if (waits && tid == 0 && me == 0)
       wait_for(p, pcid, prog_value(k - 1, nz, min(nz, nz - n + 3)));   // down to n-3
     cl.sync();                                                      // B3
-    // the predecessor is now known to be done down to slice n-3: counters of slice n-1
-    if (tid == 0 && n > 0) {
+    // the predecessor is now known to be done down to slice n-3: counters of slice n-1,
+    // loaded by the last warp (no inverse-transform task) so that no transform waits on them
+    if (tid == NT - 32 && n > 0) {
       s.misc[M_RQN] = ldcg(p.rq.cnt + (size_t)s1 * nz + (n - 1));
       s.misc[M_JFLAG] = ldcg(p.jflag + (size_t)s1 * nz + (n - 1));
     }

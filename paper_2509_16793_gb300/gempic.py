@@ -226,9 +226,15 @@ class Sim:
 
     def gempic_get_state(self, out=None) -> np.ndarray:
         """Spectral state [6, nzeta, ny, nx/2] (Rx, Ry, Ez, Bz, jx, jy) on the host, or into
-        a device tensor `out`."""
+        `out`: a device tensor, or a C-contiguous host buffer of state_bytes() bytes (any
+        dtype; its bytes are written)."""
         if out is not None and hasattr(out, "data_ptr") and out.is_cuda:
             _check(self.lib.gempic_get_state(self.h, out.data_ptr(), self.state_bytes(), 1), "gempic_get_state")
+            return out
+        if out is not None:
+            if out.nbytes < self.state_bytes() or not out.flags["C_CONTIGUOUS"]:
+                raise ValueError("out must be C-contiguous with state_bytes() bytes")
+            _check(self.lib.gempic_get_state(self.h, out.ctypes.data, out.nbytes, 0), "gempic_get_state")
             return out
         a = np.empty(self.state_shape(), self.dtype)
         _check(self.lib.gempic_get_state(self.h, a.ctypes.data, a.nbytes, 0), "gempic_get_state")
@@ -237,10 +243,13 @@ class Sim:
     state = gempic_get_state
 
     def gempic_set_state(self, a):
+        """From a device tensor, a host array of the state (converted to its dtype), or a raw
+        C-contiguous host buffer of exactly state_bytes() bytes in another dtype."""
         if hasattr(a, "data_ptr") and a.is_cuda:
             _check(self.lib.gempic_set_state(self.h, a.data_ptr(), self.state_bytes(), 1), "gempic_set_state")
             return
-        a = np.ascontiguousarray(a, self.dtype)
+        if not (a.dtype != self.dtype and a.nbytes == self.state_bytes() and a.flags["C_CONTIGUOUS"]):
+            a = np.ascontiguousarray(a, self.dtype)
         _check(self.lib.gempic_set_state(self.h, a.ctypes.data, a.nbytes, 0), "gempic_set_state")
 
     def gempic_step_host(self, n: int, state_in: Optional[np.ndarray], state_out: Optional[np.ndarray]):

@@ -223,6 +223,49 @@ def test_fp32_bench_grid_matches_oracle():
             assert np.abs(gs[c] - os_[c]).max() <= 1e-4 * scale, name
 
 
+def test_config1_full_size_fp64_matches_oracle():
+    """The 2-D FP64 workload at its full size (128 x 256, 4 ppc, Delta at the stability
+    limit), three s-steps."""
+    w = W.lwfa_2d_128x256(precision=64)
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        for _ in range(3):
+            od = o.step()
+            g.step()
+            check_diag(g.diagnostics(), od, 1e-10)
+        gs, os_ = g.state(), o.state()
+        fs = max(np.abs(os_[c]).max() for c in range(4))
+        js = max(np.abs(os_[c]).max() for c in (4, 5))
+        for c, name in enumerate(COMPS):
+            assert np.abs(gs[c] - os_[c]).max() <= 1e-10 * (fs if c < 4 else js), name
+
+
+def test_bench_workload_full_size_properties():
+    """The bench workload at its full size and launch configuration (128 x 128 x 1024 FP32,
+    several s-steps in flight), too large for the oracle: the pipelined launch equals one
+    march at a time (FP32 currents are exact fixed-point sums but for the few contributions
+    above jref, which add as floats), the energies are finite, and the crossings are those of
+    the fresh layer through every slice, less the few trapped on the way."""
+    w = W.lwfa_3d_128x128x1024()
+    with gpu_sim(w) as a, gpu_sim(w, pipeline_depth=1) as b:
+        assert a.launch_shape()["pipeline"] > 1
+        a.step(3)
+        for _ in range(3):
+            b.step(1)
+        da, db = a.diagnostics(), b.diagnostics()
+        for k in ("field_energy", "kinetic_energy"):
+            assert np.isfinite(da[k]) and da[k] > 0
+            assert abs(da[k] - db[k]) <= 1e-6 * abs(db[k]), k
+        for k in ("n_trapped", "n_stored", "n_rejoined"):
+            assert abs(da[k] - db[k]) <= max(2, 1e-3 * db[k]), k
+        # trapped particles stop streaming; rejoining ones add partial crossings
+        assert abs(da["pushes"] - db["pushes"]) <= max(2, 1e-6 * db["pushes"])
+        assert abs(da["pushes"] - w.pushes_per_step) <= 0.01 * w.pushes_per_step
+        sa, sb = a.state(), b.state()
+        scale = max(np.abs(sb[c]).max() for c in range(4))
+        assert np.abs(sa[:4] - sb[:4]).max() <= 1e-6 * scale
+
+
 def test_pipelined_equals_sequential():
     w = W.small_3d(nx=16, ny=16, nzeta=40, ppc=2, precision=64)
     with gpu_sim(w, cluster_ctas=2, pipeline_depth=1) as a, \

@@ -309,7 +309,7 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
         break;
       }
       if (cfg->particle_headroom > 0 || head <= 32) break;
-      head = head * 3 / 4;
+      head -= 32;
     }
     if (chosen) break;
   }

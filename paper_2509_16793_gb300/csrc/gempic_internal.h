@@ -54,6 +54,8 @@ struct Params {
   int P;                          // concurrent marches (clusters)
   int inject, diag, snapshot;
   int pcap;                       // streaming particle slots per CTA in shared memory
+  int fcap;                       // entries of the free-slot stack (slots freed and not yet
+                                  // reused; further freed slots stay empty this s-step)
   int gcap;                       // further slots per CTA in global memory (overflow)
   int bcap, ring;                 // stored bucket capacity, ring of s-levels
   int wait_spin_limit;            // bounded wait: polls before giving up

@@ -518,7 +518,7 @@ struct Sm {
   T *ifx, *ify, *iux, *iuy, *iuz, *isig, *iq;
   int* pcell;       // [pcap] ix | iy << 10 | sp << 20, -1 = empty
   T *pfx, *pfy, *pux, *puy, *puz, *psig, *pq;
-  int* fstack;      // [pcap] free particle slots
+  int* fstack;      // [fcap] free particle slots
   int* misc;        // MiscSlot
   double* dacc;     // [kNDiag]
 };
@@ -1576,7 +1576,7 @@ template <typename T>
 __device__ bool migrate(const cg::cluster_group& cl, const Params& p, const Sm<T>& s,
                         const PState<T>& P, int owner) {
   int* rmisc = cl.map_shared_rank(s.misc, owner);
-  const int room = p.pcap + p.gcap - rmisc[M_PCOUNT] + rmisc[M_FTOP] - 64;
+  const int room = p.pcap + p.gcap - rmisc[M_PCOUNT] + min(rmisc[M_FTOP], p.fcap) - 64;
   const int limit = min(p.mig_cap, room);
   int* cnt = rmisc + M_INBOX;
   int e = *(volatile int*)cnt;
@@ -2009,7 +2009,10 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         if (gone) {
           set_cell(p, s, ov, i, -1);
           // shared-memory slots are reused; a dead overflow slot stays unused this s-step
-          if (i < p.pcap) s.fstack[atomicAdd(s.misc + M_FTOP, 1)] = i;
+          if (i < p.pcap) {
+            const int f = atomicAdd(s.misc + M_FTOP, 1);
+            if (f < p.fcap) s.fstack[f] = i;
+          }
         } else {
           put_particle(p, s, ov, i, P);
         }
@@ -2170,7 +2173,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     // migrating particles into free slots
     if (p.ny > 1) {
       const int nin = min(s.misc[M_INBOX], p.mig_cap);
-      const int ftop = s.misc[M_FTOP];
+      const int ftop = min(s.misc[M_FTOP], p.fcap);
       const int pc = s.misc[M_PCOUNT];
       for (int e = tid; e < nin; e += NT) {
         const int slot = e < ftop ? s.fstack[ftop - 1 - e] : pc + (e - ftop);
@@ -2520,7 +2523,10 @@ int smem_layout(Params& p, int eb) {
   p.o_inbox = o;
   o += align16(p.mig_cap * 4) + align16(7 * p.mig_cap * eb);
   p.o_part = o;
-  o += align16(p.pcap * 4) + align16(7 * p.pcap * eb + p.pcap * 4);
+  // free-slot stack: bounded (a slot freed beyond it stays empty until the next s-step), so
+  // that a particle slot costs 4 + 7 reals of shared memory
+  p.fcap = std::min(p.pcap, 512);
+  o += align16(p.pcap * 4) + align16(7 * p.pcap * eb + p.fcap * 4);
   p.o_misc = o;
   o += 32 + kNDiag * 8;
   p.smem_bytes = align16(o);

@@ -62,7 +62,7 @@ struct Params {
   int nwork;                      // FFT work rows per CTA
   int mig_cap;                    // migrating particles a CTA can receive per slice
   // shared-memory layout (byte offsets)
-  int o_f0, o_f1, o_j, o_recv, o_sr, o_sc, o_workB, o_workD, o_tw, o_inbox, o_part, o_misc,
+  int o_f0, o_f1, o_j, o_recv, o_sr, o_sc, o_workB, o_workD, o_tw, o_inbox, o_outbox, o_part, o_misc,
       smem_bytes;
   // device memory
   void* state;                    // blocks [nz+1][C][6][M] complex

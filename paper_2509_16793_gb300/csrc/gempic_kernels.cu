@@ -492,7 +492,9 @@ enum CstSlot {
   K_H = 0, K_INVH, K_HX, K_HY, K_D, K_DF, K_WSCALE, K_CX, K_CY, K_INVHX, K_INVHY, K_FLUX,
   K_BEAM, K_JREF, K_JSCALE, K_JINV, K_QM = 16, K_MOQ = 20, K_QF = 24, K_N = 28
 };
-enum MiscSlot { M_PCOUNT = 0, M_FTOP, M_INBOX, M_RQN, M_JFLAG, M_STN, M_PAD0, M_PAD1 };
+enum MiscSlot { M_PCOUNT = 0, M_FTOP, M_INBOX, M_RQN, M_JFLAG, M_STN, M_OUTN, M_PAD1 };
+// particles leaving the band during a push wait in a local outbox of this many entries
+constexpr int kOutCap = 64;
 
 // Shared memory of one CTA.  Plane sets are [comp][rows][nx]: the fields F keep the CTA's RB
 // rows plus one halo row above (FR = RB + 1); the currents J keep rows -1 .. RB + 1 of the
@@ -516,6 +518,8 @@ struct Sm {
   T* cst;           // [K_N] constants in the working precision
   int* icell;       // [mig_cap] inbox of particles migrating in
   T *ifx, *ify, *iux, *iuy, *iuz, *isig, *iq;
+  int *ocell, *odst;  // [kOutCap] outbox of particles leaving the band (3-D), owner CTA
+  T *ofx, *ofy, *oux, *ouy, *ouz, *osig, *oq;
   int* pcell;       // [pcap] ix | iy << 10 | sp << 20, -1 = empty
   T *pfx, *pfy, *pux, *puy, *puz, *psig, *pq;
   int* fstack;      // [fcap] free particle slots
@@ -555,6 +559,17 @@ __device__ Sm<T> carve(const Params& p, unsigned char* base) {
   s.iuz = it + 4 * mcap;
   s.isig = it + 5 * mcap;
   s.iq = it + 6 * mcap;
+  unsigned char* ob = base + p.o_outbox;
+  s.ocell = (int*)ob;
+  s.odst = s.ocell + kOutCap;
+  T* ot = (T*)(ob + 2 * kOutCap * 4);
+  s.ofx = ot;
+  s.ofy = ot + kOutCap;
+  s.oux = ot + 2 * kOutCap;
+  s.ouy = ot + 3 * kOutCap;
+  s.ouz = ot + 4 * kOutCap;
+  s.osig = ot + 5 * kOutCap;
+  s.oq = ot + 6 * kOutCap;
   unsigned char* pp = base + p.o_part;
   s.pcell = (int*)pp;
   T* pt = (T*)(pp + ((p.pcap * 4 + 15) / 16) * 16);
@@ -1888,6 +1903,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     s.misc[M_PCOUNT] = 0;
     s.misc[M_FTOP] = 0;
     s.misc[M_INBOX] = 0;
+    s.misc[M_OUTN] = 0;
   }
   __syncthreads();
   if (p.inject) {
@@ -2002,9 +2018,26 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
         } else {
           const int owner = P.iy >> p.logRB;
-          // a particle that left the band moves to the owner of its row (kept here if the
+          // a particle that left the band moves to the owner of its row: queued in the local
+          // outbox and sent after the push (directly if the outbox is full; kept here if the
           // owner's inbox is full: it then takes the generic path)
-          if (owner != me && migrate(cl, p, s, P, owner)) gone = true;
+          if (owner != me) {
+            const int o = atomicAdd(s.misc + M_OUTN, 1);
+            if (o < kOutCap) {
+              s.ocell[o] = P.ix | (P.iy << 10) | (P.sp << 20);
+              s.odst[o] = owner;
+              s.ofx[o] = P.fx;
+              s.ofy[o] = P.fy;
+              s.oux[o] = P.u.x;
+              s.ouy[o] = P.u.y;
+              s.ouz[o] = P.u.z;
+              s.osig[o] = P.sig;
+              s.oq[o] = P.q;
+              gone = true;
+            } else if (migrate(cl, p, s, P, owner)) {
+              gone = true;
+            }
+          }
         }
         if (gone) {
           set_cell(p, s, ov, i, -1);
@@ -2056,6 +2089,68 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     TIMER_MARK(PH_A);
     __syncthreads();
     TIMER_MARK(PH_AW);
+    // outbox: the lanes of the first warps group their particles by owner; per owner one lane
+    // reserves inbox entries (as many as fit) and the lanes write them remotely; a particle
+    // that does not fit returns to a slot of this CTA
+    if (p.ny > 1) {
+      const int nout = min(s.misc[M_OUTN], kOutCap);
+      if (tid < ((nout + 31) & ~31)) {
+        const int lane = tid & 31;
+        const bool have = tid < nout;
+        const int dst = have ? s.odst[tid] : -1;
+        const unsigned grp = __match_any_sync(0xffffffffu, dst);
+        const int leader = __ffs(grp) - 1;
+        const int rank = __popc(grp & ((1u << lane) - 1u));
+        int base = 0, take = 0;
+        if (lane == leader && dst >= 0) {
+          const int want = __popc(grp);
+          int* rmisc = cl.map_shared_rank(s.misc, dst);
+          const int room = p.pcap + p.gcap - rmisc[M_PCOUNT] + min(rmisc[M_FTOP], p.fcap) - 64;
+          const int limit = min(p.mig_cap, room);
+          int* cnt = rmisc + M_INBOX;
+          int e = *(volatile int*)cnt;
+          for (;;) {
+            take = max(0, min(want, limit - e));
+            if (take == 0) break;
+            const int prev = atomicCAS(cnt, e, e + take);
+            if (prev == e) break;
+            e = prev;
+          }
+          base = e;
+        }
+        base = __shfl_sync(0xffffffffu, base, leader);
+        take = __shfl_sync(0xffffffffu, take, leader);
+        if (have) {
+          PState<T> P;
+          const int cw = s.ocell[tid];
+          P.ix = cw & 1023;
+          P.iy = (cw >> 10) & 1023;
+          P.sp = (cw >> 20) & 3;
+          P.fx = s.ofx[tid];
+          P.fy = s.ofy[tid];
+          P.u = V3<T>{s.oux[tid], s.ouy[tid], s.ouz[tid]};
+          P.sig = s.osig[tid];
+          P.q = s.oq[tid];
+          if (rank < take) {
+            const int e = base + rank;
+            *cl.map_shared_rank(s.icell + e, dst) = cw;
+            *cl.map_shared_rank(s.ifx + e, dst) = P.fx;
+            *cl.map_shared_rank(s.ify + e, dst) = P.fy;
+            *cl.map_shared_rank(s.iux + e, dst) = P.u.x;
+            *cl.map_shared_rank(s.iuy + e, dst) = P.u.y;
+            *cl.map_shared_rank(s.iuz + e, dst) = P.u.z;
+            *cl.map_shared_rank(s.isig + e, dst) = P.sig;
+            *cl.map_shared_rank(s.iq + e, dst) = P.q;
+          } else {
+            const int slot = atomicAdd(s.misc + M_PCOUNT, 1);
+            if (slot < p.pcap + p.gcap)
+              put_particle(p, s, ov, slot, P);
+            else
+              atomicOr(p.err, ERR_PCAP);
+          }
+        }
+      }
+    }
     // FP32: fold the fixed-point accumulators of the halo rows now (only this CTA's pushes
     // deposit there); own rows also receive other CTAs' fixed-point deposits and are folded
     // after the barrier
@@ -2200,6 +2295,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         s.misc[M_FTOP] = max(0, ftop - nin);
         s.misc[M_PCOUNT] = min(p.pcap + p.gcap, pc + max(0, nin - ftop));
         s.misc[M_INBOX] = 0;
+        s.misc[M_OUTN] = 0;
       }
     }
     TIMER_MARK(PH_BI);
@@ -2522,6 +2618,8 @@ int smem_layout(Params& p, int eb) {
   o += align16((nxh + nyh + nxh + p.ny) * 2 * eb + (nxh + p.ny + 32) * eb);
   p.o_inbox = o;
   o += align16(p.mig_cap * 4) + align16(7 * p.mig_cap * eb);
+  p.o_outbox = o;
+  if (p.ny > 1) o += align16(2 * kOutCap * 4) + align16(7 * kOutCap * eb);
   p.o_part = o;
   // free-slot stack: bounded (a slot freed beyond it stays empty until the next s-step), so
   // that a particle slot costs 4 + 7 reals of shared memory

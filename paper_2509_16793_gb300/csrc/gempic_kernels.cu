@@ -525,6 +525,7 @@ struct Sm {
   int* fstack;      // [fcap] free particle slots
   int* misc;        // MiscSlot
   double* dacc;     // [kNDiag]
+  double* dwarp;    // [nthreads / 32][kNDiag] per-warp FP64 diagnostic sums of this march
 };
 
 template <typename T>
@@ -583,6 +584,7 @@ __device__ Sm<T> carve(const Params& p, unsigned char* base) {
   s.fstack = (int*)(pt + 7 * p.pcap);
   s.misc = (int*)(base + p.o_misc);
   s.dacc = (double*)(base + p.o_misc + 32);
+  s.dwarp = s.dacc + kNDiag;
   return s;
 }
 
@@ -1705,9 +1707,21 @@ __device__ __forceinline__ void put_particle(const Params& p, const Sm<T>& s, co
 // Stored particle along s (Sec. 5.1: trapped / beam particles are integrated along s):
 // bucket n of level k+1, fields of slices n (Fn) and n+1 (Fn1) of that level.
 // ------------------------------------------------------------------------------------------
+// Adds the warp's sum of v into the warp's row of FP64 diagnostics.  The sum runs in the
+// type of v (FP32 sums in FP32: FP64 arithmetic is a small fraction of the FP32 rate), and lane
+// 0 adds it in FP64.  Every lane of the warp calls it.
+template <typename V>
+__device__ __forceinline__ void warp_diag_add(double* dwarp, int slot, V v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) dwarp[(threadIdx.x >> 5) * kNDiag + slot] += (double)v;
+}
+
 template <typename T>
 __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const T* Fn1,
-                             long long k, int n, int me, double* acc, int cnt_raw) {
+                             long long k, int n, int me, int cnt_raw) {
+  T dkin = T(0);
+  int dsto = 0, dlost = 0;
   const int s1 = (int)(((k + 1) % p.ring + p.ring) % p.ring);
   const int s2 = (int)(((k + 2) % p.ring + p.ring) % p.ring);
   const int cnt = min(cnt_raw, p.bcap);
@@ -1717,8 +1731,8 @@ __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const
     T fz;
     PState<T> P = store_read<T>(p.st, p, ((size_t)s1 * p.nz + n) * p.bcap + e0, fz);
     const T g = gamma_of(P.u);
-    acc[DG_KIN] += (double)(P.q * s.cst[K_MOQ + P.sp] * (g - T(1)));
-    acc[DG_STORED] += 1.0;
+    dkin += P.q * s.cst[K_MOQ + P.sp] * (g - T(1));
+    ++dsto;
     const T gmu = gamma_minus_uz(P.u, g);
     const bool spush = (P.u.z > T(0)) && (D * gmu < h * fmax(P.u.z, T(0)));
     if (!spush) {
@@ -1752,7 +1766,7 @@ __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const
       m = n + (int)cZ;
       fz = Z - cZ;
       if (m < 0) {                              // left the box at the back
-        acc[DG_LOST] += 1.0;
+        ++dlost;
         continue;
       }
       // beam current of the next level j = Q u/(gamma hx hy h), CIC across, linear in zeta
@@ -1791,6 +1805,13 @@ __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const
       }
     }
     if (!store_append(p.st, p, s2, m, P, fz)) atomicOr(p.err, ERR_BCAP);
+  }
+  if (p.diag) {
+    if (__any_sync(0xffffffffu, (dsto | dlost) != 0)) {
+      warp_diag_add(s.dwarp, DG_KIN, dkin);
+      warp_diag_add(s.dwarp, DG_STORED, dsto);
+      warp_diag_add(s.dwarp, DG_LOST, dlost);
+    }
   }
 }
 
@@ -1862,6 +1883,9 @@ __device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
   }
 }
 
+// FP64 diagnostics: each warp adds its lanes' sums to its own row (no atomics); the rows are
+// summed once at the end of the march.  Every lane of the warp calls it.
+
 // ------------------------------------------------------------------------------------------
 // the march of one s-step k (computes level k+1)
 // ------------------------------------------------------------------------------------------
@@ -1887,9 +1911,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   const int jplane = p.JR * p.nx;                   // elements of one current component
   TIMER_DECL
 
-  double acc[kNDiag];
-#pragma unroll
-  for (int i = 0; i < kNDiag; ++i) acc[i] = 0.0;
+  // FP64 diagnostics go to per-warp rows in shared memory (section below), not registers
   T fe = T(0);
 
   // reset the next level's stored buckets and rejoin queues (free: their last reader, the
@@ -1905,6 +1927,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     s.misc[M_INBOX] = 0;
     s.misc[M_OUTN] = 0;
   }
+  for (int i = tid; i < (NT >> 5) * kNDiag; i += NT) s.dwarp[i] = 0.0;
   __syncthreads();
   if (p.inject) {
     const int per_row = p.nlayer >> p.logny;        // particles per transverse row
@@ -2004,6 +2027,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
 #endif
     // ---------------- A: streaming push from plane n+1 to plane n -----------------------
     SliceAcc<T> sa{T(0), T(0), 0};
+    int ntrap = 0, nrej = 0;
     {
       const int cnt0 = s.misc[M_PCOUNT];
       for (int i = tid; i < cnt0; i += NT) {
@@ -2014,7 +2038,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         const bool trap = stream_push(p, s, Fcur, P, h, me, fzt, sa);
         bool gone = trap;
         if (trap) {
-          acc[DG_TRAP] += 1.0;
+          ++ntrap;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
         } else {
           const int owner = P.iy >> p.logRB;
@@ -2059,11 +2083,11 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         if ((((ldcg(p.rq.cell + ge) >> 10) & 1023) >> p.logRB) != me) continue;
         T fz;
         PState<T> P = store_read<T>(p.rq, p, ge, fz);
-        acc[DG_REJOIN] += 1.0;
+        ++nrej;
         T fzt;
         const bool trap = stream_push(p, s, Fcur, P, fz * h, me, fzt, sa);
         if (trap) {
-          acc[DG_TRAP] += 1.0;
+          ++ntrap;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
           continue;
         }
@@ -2083,9 +2107,20 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         }
       }
     }
-    acc[DG_KIN] += (double)sa.kin;
-    acc[DG_FLUX] += (double)sa.flux;
-    acc[DG_PUSH] += (double)sa.push;
+    if (p.diag) {
+      warp_diag_add(s.dwarp, DG_KIN, sa.kin);
+      warp_diag_add(s.dwarp, DG_FLUX, sa.flux);
+      int cnts[3] = {sa.push, ntrap, nrej};
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        for (int off = 16; off > 0; off >>= 1) cnts[c] += __shfl_down_sync(0xffffffffu, cnts[c], off);
+      if ((tid & 31) == 0) {
+        double* row = s.dwarp + (tid >> 5) * kNDiag;
+        row[DG_PUSH] += (double)cnts[0];
+        row[DG_TRAP] += (double)cnts[1];
+        row[DG_REJOIN] += (double)cnts[2];
+      }
+    }
     TIMER_MARK(PH_A);
     __syncthreads();
     TIMER_MARK(PH_AW);
@@ -2438,7 +2473,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       }
     }
     // ---------------- E: stored particles of cell (zeta_n, zeta_{n+1}] along s -------------
-    stored_phase(p, s, Fnew, Fcur, k, n, me, acc, s.misc[M_STN]);
+    stored_phase(p, s, Fnew, Fcur, k, n, me, s.misc[M_STN]);
     TIMER_MARK(PH_E);
     T* t = Fcur;
     Fcur = Fnew;
@@ -2452,19 +2487,15 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
 
   // diagnostics: per-CTA FP64 partials
   if (p.diag) {
-    acc[DG_FIELD] = (double)fe;
-    for (int i = 0; i < kNDiag; ++i) {
-      double v = acc[i];
-      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-      if ((tid & 31) == 0) atomicAdd(s.dacc + i, v);
-    }
+    warp_diag_add(s.dwarp, DG_FIELD, fe);
     __syncthreads();
     if (tid < kNDiag) {
+      double v = 0.0;
+      for (int w = 0; w < (NT >> 5); ++w) v += s.dwarp[w * kNDiag + tid];
       const double hv = tid == DG_FIELD ? 0.5 * p.hx * p.hy * p.h
                         : tid == DG_FLUX ? p.hx * p.hy * p.h
                                          : 1.0;
-      p.diag_out[((size_t)sl * kNDiag + tid) * p.C + me] = s.dacc[tid] * hv;
-      s.dacc[tid] = 0.0;
+      p.diag_out[((size_t)sl * kNDiag + tid) * p.C + me] = v * hv;
     }
     __syncthreads();
   }
@@ -2626,7 +2657,7 @@ int smem_layout(Params& p, int eb) {
   p.fcap = std::min(p.pcap, 512);
   o += align16(p.pcap * 4) + align16(7 * p.pcap * eb + p.fcap * 4);
   p.o_misc = o;
-  o += 32 + kNDiag * 8;
+  o += 32 + kNDiag * 8 + (p.nthreads / 32) * kNDiag * 8;
   p.smem_bytes = align16(o);
   return p.smem_bytes;
 }

@@ -74,6 +74,17 @@ typedef struct {
   int32_t reserved;
 } gempic_laser;
 
+/* Transverse plasma channel (Sec. 6, Eq. n_plasma): the density of every species is
+ * n(r) = n [1 + (n1/n0 - 1) exp(-r^2 / R_ch^2)], r the transverse distance from the window's
+ * middle node (x_c, y_c) = (nx hx / 2, ny hy / 2); in 2-D r = |x - x_c|.  A fresh
+ * macroparticle takes the charge Q_f n(r)/n at its injection position.  n1_over_n0 >= 0 and
+ * radius > 0, else gempic_create returns GEMPIC_EINVAL.  Immobile ions carry no current in
+ * the slice equations, so the profile enters through the injected charge alone. */
+typedef struct {
+  double n1_over_n0;      /* density on the axis over the density far from it */
+  double radius;          /* R_ch */
+} gempic_channel;
+
 /* Flags */
 #define GEMPIC_FLAG_DIAG      1u  /* FP64 diagnostics every s-step (default on)           */
 #define GEMPIC_FLAG_SNAPSHOT  2u  /* keep real-space E, B, j of the last s-step of a call */
@@ -93,6 +104,7 @@ typedef struct {
   int32_t pipeline_depth;        /* s-steps marched concurrently (wavefront); 0 = auto, 1 = none */
   int32_t reserved;
   void* cuda_stream;             /* cudaStream_t; NULL = legacy default stream */
+  const gempic_channel* channel; /* NULL: uniform density; copied at create */
 } gempic_config;
 
 /* Per-s-step diagnostics, accumulated on the device in FP64. */

@@ -20,6 +20,10 @@ The paper is silent or garbled in places; the readings taken here are:
     its weight unchanged.
   * Transverse shape: cloud-in-cell; j_perp by the 2-D Esirkepov decomposition of the
     transverse move across one slice, so that (rho - j_z) is conserved through the planes.
+  * Plasma channel (Sec. 6, Eq. n_plasma): its axis is the grid's middle node (x_c, y_c) =
+    (nx hx/2, ny hy/2), as for the laser; immobile ions carry no current in the slice
+    equations, so the profile enters only through each fresh macroparticle's charge, taken
+    at its injection position.
   * Stored (trapped / beam) particles are pushed along the slow coordinate s (Sec. 5.1, last
     paragraph) with the fields of the last completed level; a
     stored particle with Delta(1-v_z)/v_z >= h rejoins the zeta march at its slice.
@@ -320,6 +324,19 @@ def cic_deposit(plane, X, Y, val):
 
 
 # ----------------------------------------------------------------------------------------
+# Plasma channel, Sec. 6 Eq. n_plasma.
+# ----------------------------------------------------------------------------------------
+def channel_profile(ch, dx, dy):
+    """n(r_perp) / n0 of the Gaussian channel: n = n0 [1 + (n1 - n0)/n0 exp(-r^2/R_ch^2)],
+    with r^2 = dx^2 + dy^2 measured from the channel axis; ch.n1_over_n0 = n1/n0,
+    ch.radius = R_ch."""
+    n0 = 1.0
+    n1 = ch.n1_over_n0 * n0
+    r2 = np.asarray(dx) ** 2 + np.asarray(dy) ** 2
+    return (n0 * (1.0 + (n1 - n0) / n0 * np.exp(-r2 / ch.radius ** 2))) / n0
+
+
+# ----------------------------------------------------------------------------------------
 # The simulation.
 # ----------------------------------------------------------------------------------------
 @dataclass
@@ -381,7 +398,8 @@ class RefSim:
         self.fields_rs = np.zeros((self.nz, 6, self.ny, self.nx))
         self.step_index = 0
         self.diag: Dict = {}
-        if w.omega_p2 * self.delta * self.h > 4.0 * (1.0 + 1e-12):
+        densest = max(1.0, w.channel.n1_over_n0) if w.channel is not None else 1.0
+        if w.omega_p2 * densest * self.delta * self.h > 4.0 * (1.0 + 1e-12):
             raise ValueError("Delta h omega_p^2 > 4: outside the stability bound (Sec. 4.2)")
         self.stored = Particles.empty()
         if w.stored is not None and w.stored.n > 0:
@@ -434,8 +452,12 @@ class RefSim:
             y = (j + oy) * self.hy if self.ny > 1 else np.zeros(cell.size)
             n = cell.size
             Q = s.charge * s.density * self.hx * self.hy * self.delta / s.ppc
+            if w.channel is not None:
+                Q = Q * channel_profile(w.channel, x - 0.5 * self.nx * self.hx,
+                                        y - 0.5 * self.ny * self.hy if self.ny > 1 else y)
             parts.append(Particles(x, y, np.full(n, self.nz * self.h), np.zeros((3, n)),
-                                   np.zeros(n), np.full(n, Q), np.full(n, si, np.int64),
+                                   np.zeros(n), np.broadcast_to(Q, (n,)).copy(),
+                                   np.full(n, si, np.int64),
                                    np.full(n, self.h)))
             off += ncell * s.ppc
         return Particles.concat(parts)

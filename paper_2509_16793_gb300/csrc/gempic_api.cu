@@ -12,6 +12,7 @@
 
 #include "../../include/gempic.h"
 #include "gempic_internal.h"
+#include "gempic_setup.h"
 
 using gempic::Params;
 
@@ -206,18 +207,11 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
   if (g.nzeta < 2 || !(g.hx > 0) || !(g.hy > 0) || !(g.h > 0) || !(cfg->delta >= 0))
     return GEMPIC_EINVAL;
   if (cfg->precision != 32 && cfg->precision != 64) return GEMPIC_EINVAL;
-  if (cfg->nspecies < 0 || cfg->nspecies > gempic::kMaxSpecies) return GEMPIC_EINVAL;
-  if (cfg->nspecies > 0 && !cfg->species) return GEMPIC_EINVAL;
-  double wp2 = 0.0;
-  int ppc_sum = 0;
-  for (int i = 0; i < cfg->nspecies; ++i) {
-    const gempic_species& sp = cfg->species[i];
-    if (sp.ppc < 1 || !(sp.mass > 0) || !(sp.density >= 0)) return GEMPIC_EINVAL;
-    if (sp.density > 0 && sp.charge == 0) return GEMPIC_EINVAL;
-    wp2 += sp.charge * sp.charge * sp.density / sp.mass;
-    ppc_sum += sp.ppc;
+  gempic::Params chk{};
+  {
+    const gempic_status st = gempic::setup_species(cfg, chk);
+    if (st != GEMPIC_OK) return st;
   }
-  if (cfg->delta * g.h * wp2 > 4.0 * (1.0 + 1e-12)) return GEMPIC_EUNSTABLE;
 
   gempic_sim* s = new (std::nothrow) gempic_sim();
   if (!s) return GEMPIC_ENOMEM;
@@ -229,6 +223,7 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     s->has_laser = true;
   }
   s->cfg.laser = nullptr;
+  s->cfg.channel = nullptr;
   s->stream = (cudaStream_t)cfg->cuda_stream;
   s->eb = cfg->precision == 64 ? 8 : 4;
 
@@ -243,31 +238,9 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
   p.h = g.h;
   p.delta = cfg->delta;
   p.delta_field = cfg->delta;
-  p.nspecies = cfg->nspecies;
   p.seed = cfg->seed;
-  int off = 0;
-  for (int i = 0; i < cfg->nspecies; ++i) {
-    const gempic_species& sp = s->species[i];
-    p.qm[i] = sp.charge / sp.mass;
-    p.Qf[i] = sp.charge * sp.density * g.hx * g.hy * cfg->delta / sp.ppc;
-    p.wd[i] = p.Qf[i] / (g.hx * g.hy * cfg->delta);
-    p.m_over_q[i] = sp.charge != 0 ? sp.mass / sp.charge : 0.0;
-    p.ppc[i] = sp.ppc;
-    p.poff[i] = off;
-    off += g.nx * g.ny * sp.ppc;
-  }
-  p.nlayer = off;
-  {
-    // fixed-point range of the FP32 deposit: 4 x the largest (rho - j_z) weight times the
-    // largest transverse cell-to-slice ratio; a larger contribution takes the float path
-    double wmax = 0.0;
-    for (int i = 0; i < cfg->nspecies; ++i)
-      wmax = std::max(wmax, std::fabs(cfg->species[i].charge * cfg->species[i].density /
-                                      cfg->species[i].ppc));
-    const double ratio = std::max(1.0, std::max(g.hx, g.hy) / g.h);
-    p.jref = wmax > 0 ? 4.0 * wmax * ratio : 1.0;
-  }
-  p.ppc_sum = ppc_sum;
+  gempic::setup_species(cfg, p);
+  const int ppc_sum = p.ppc_sum;
 
   // launch shape: C CTAs per cluster own ny/C rows and (nx/2)/C kx columns; one spectral
   // mode per thread (M <= 512).

@@ -47,6 +47,8 @@ struct Params {
   double Qf[kMaxSpecies];         // fresh macroparticle charge q n hx hy Delta/ppc
   double m_over_q[kMaxSpecies];   // m/q: kinetic energy of N = Q/q particles is Q (m/q)(gamma-1)
   int ppc[kMaxSpecies], poff[kMaxSpecies];
+  double chan_a, chan_ir2;        // density channel f(r) = 1 + chan_a exp(-r^2 chan_ir2)
+                                  // (Eq. n_plasma); chan_a = 0: uniform
   unsigned long long seed;
   // launch
   long long k0;                   // s-step index of the first march of this launch (-1: init)

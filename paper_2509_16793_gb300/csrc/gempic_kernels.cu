@@ -1951,14 +1951,23 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
           (unsigned long long)(p.poff[sp] + cell * p.ppc[sp] + kk);
       const unsigned long long c =
           ((unsigned long long)k * (unsigned long long)p.nlayer + g) * 2ull;
+      const T fx = T(uniform24(p.seed, c));
+      const T fy = p.ny > 1 ? T(uniform24(p.seed, c + 1)) : T(0);
+      T q = s.cst[K_QF + sp];
+      if (p.chan_a != 0.0) {
+        // density channel (Eq. n_plasma) at the particle's distance from the middle node
+        const T dx = (T(ix - (p.nx >> 1)) + fx) * s.cst[K_HX];
+        const T dy = p.ny > 1 ? (T(iy - (p.ny >> 1)) + fy) * s.cst[K_HY] : T(0);
+        q *= T(1) + T(p.chan_a) * exp(-(dx * dx + dy * dy) * T(p.chan_ir2));
+      }
       s.pcell[i] = ix | (iy << 10) | (sp << 20);
-      s.pfx[i] = T(uniform24(p.seed, c));
-      s.pfy[i] = p.ny > 1 ? T(uniform24(p.seed, c + 1)) : T(0);
+      s.pfx[i] = fx;
+      s.pfy[i] = fy;
       s.pux[i] = T(0);
       s.puy[i] = T(0);
       s.puz[i] = T(0);
       s.psig[i] = T(0);
-      s.pq[i] = s.cst[K_QF + sp];
+      s.pq[i] = q;
     }
     if (tid == 0) s.misc[M_PCOUNT] = nmine;
   }

@@ -16,6 +16,7 @@
 
 #include "../../include/gempic.h"
 #include "gempic_internal.h"
+#include "gempic_setup.h"
 
 namespace {
 
@@ -66,30 +67,16 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
   if (g.nzeta < 2 || g.nzeta > kMaxNzeta) return GEMPIC_EINVAL;
   if (!(g.hx > 0) || !(g.hy > 0) || !(g.h > 0) || !(cfg->delta >= 0)) return GEMPIC_EINVAL;
   if (cfg->precision != 32 && cfg->precision != 64) return GEMPIC_EINVAL;
-  if (cfg->nspecies < 0 || cfg->nspecies > gempic::kMaxSpecies) return GEMPIC_EINVAL;
-  if (cfg->nspecies > 0 && !cfg->species) return GEMPIC_EINVAL;
   const int eb = cfg->precision == 64 ? 8 : 4;
   const size_t need = (size_t)6 * g.nzeta * g.ny * (g.nx / 2) * 2 * eb;
   if (state_bytes < need) return GEMPIC_EINVAL;
 
   Params p{};
-  double wp2 = 0.0;
-  int ppc_sum = 0, off = 0;
-  for (int i = 0; i < cfg->nspecies; ++i) {
-    const gempic_species& sp = cfg->species[i];
-    if (sp.ppc < 1 || !(sp.mass > 0) || !(sp.density >= 0)) return GEMPIC_EINVAL;
-    if (sp.density > 0 && sp.charge == 0) return GEMPIC_EINVAL;
-    wp2 += sp.charge * sp.charge * sp.density / sp.mass;
-    ppc_sum += sp.ppc;
-    p.qm[i] = sp.charge / sp.mass;
-    p.Qf[i] = sp.charge * sp.density * g.hx * g.hy * cfg->delta / sp.ppc;
-    p.wd[i] = p.Qf[i] / (g.hx * g.hy * cfg->delta);
-    p.m_over_q[i] = sp.charge != 0 ? sp.mass / sp.charge : 0.0;
-    p.ppc[i] = sp.ppc;
-    p.poff[i] = off;
-    off += g.nx * g.ny * sp.ppc;
+  {
+    const gempic_status st = gempic::setup_species(cfg, p);
+    if (st != GEMPIC_OK) return st;
   }
-  if (cfg->delta * g.h * wp2 > 4.0 * (1.0 + 1e-12)) return GEMPIC_EUNSTABLE;
+  const int ppc_sum = p.ppc_sum;
   p.nx = g.nx;
   p.ny = g.ny;
   p.nz = g.nzeta;
@@ -100,19 +87,6 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
   p.h = g.h;
   p.delta = cfg->delta;
   p.delta_field = cfg->delta;
-  p.nspecies = cfg->nspecies;
-  p.nlayer = off;
-  {
-    // fixed-point range of the FP32 deposit: 4 x the largest (rho - j_z) weight times the
-    // largest transverse cell-to-slice ratio; a larger contribution takes the float path
-    double wmax = 0.0;
-    for (int i = 0; i < cfg->nspecies; ++i)
-      wmax = std::max(wmax, std::fabs(cfg->species[i].charge * cfg->species[i].density /
-                                      cfg->species[i].ppc));
-    const double ratio = std::max(1.0, std::max(g.hx, g.hy) / g.h);
-    p.jref = wmax > 0 ? 4.0 * wmax * ratio : 1.0;
-  }
-  p.ppc_sum = ppc_sum;
   p.seed = cfg->seed;
 
   int dev = 0;

@@ -47,13 +47,18 @@ class gempic_laser(Structure):
                 ("zeta_center", c_double), ("pol", c_int32), ("reserved", c_int32)]
 
 
+class gempic_channel(Structure):
+    _fields_ = [("n1_over_n0", c_double), ("radius", c_double)]
+
+
 class gempic_config(Structure):
     _fields_ = [("grid", gempic_grid), ("delta", c_double), ("precision", c_int32),
                 ("flags", c_uint32), ("seed", c_uint64), ("nspecies", c_int32),
                 ("cluster_ctas", c_int32), ("species", POINTER(gempic_species)),
                 ("laser", POINTER(gempic_laser)), ("stored_bucket_capacity", c_int32),
                 ("particle_headroom", c_int32), ("pipeline_depth", c_int32),
-                ("reserved", c_int32), ("cuda_stream", c_void_p)]
+                ("reserved", c_int32), ("cuda_stream", c_void_p),
+                ("channel", POINTER(gempic_channel))]
 
 
 class gempic_diag(Structure):
@@ -143,6 +148,9 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
     if w.laser is not None:
         L = w.laser
         las = gempic_laser(L.a0, L.waist, L.duration, L.zeta_center, L.pol, 0)
+    ch = None
+    if w.channel is not None:
+        ch = gempic_channel(w.channel.n1_over_n0, w.channel.radius)
     if w.snapshot:
         flags |= GEMPIC_FLAG_SNAPSHOT
     cfg = gempic_config(
@@ -151,8 +159,9 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
         species=ctypes.cast(sp, POINTER(gempic_species)),
         laser=ctypes.pointer(las) if las is not None else None,
         stored_bucket_capacity=bucket_capacity, particle_headroom=headroom,
-        pipeline_depth=pipeline_depth, reserved=0, cuda_stream=stream)
-    return cfg, (sp, las)
+        pipeline_depth=pipeline_depth, reserved=0, cuda_stream=stream,
+        channel=ctypes.pointer(ch) if ch is not None else None)
+    return cfg, (sp, las, ch)
 
 
 def gempic_step_noalloc(w, step: int, state, onaxis: bool = False, stream: Optional[int] = None,

@@ -53,6 +53,15 @@ class Laser:
 
 
 @dataclass
+class Channel:
+    """Transverse plasma channel (Sec. 6, Eq. n_plasma): every species' density is scaled by
+    1 + (n1/n0 - 1) exp(-r^2/R_ch^2), r the transverse distance from the grid's middle node
+    (2-D: |x - x_c|)."""
+    n1_over_n0: float = 0.25            # Sec. 6: n1 = n0 / 4
+    radius: float = 95.5 * LAMBDA_L     # Sec. 6: R_ch = 76.4 um at lambda = 0.8 um
+
+
+@dataclass
 class StoredParticles:
     """Macroparticles placed inside the box at creation (beam / driver bunch, Sec. 5.1 Q_b).
 
@@ -91,6 +100,7 @@ class Workload:
     steps: int = 1
     stored: Optional[StoredParticles] = None
     snapshot: bool = False       # keep real-space fields of the last s-step
+    channel: Optional[Channel] = None   # None: uniform density
 
     @property
     def ncells(self) -> int:

@@ -417,3 +417,76 @@ def test_splitmix_uniform():
     raw = R.splitmix64(20250916, c)
     assert np.unique(raw).size == raw.size
     assert not np.array_equal(R.splitmix64(1, c[:10]), R.splitmix64(2, c[:10]))
+
+
+# ---- plasma channel (Sec. 6, Eq. n_plasma) --------------------------------------------------
+def _channel_layer(ny, ratio=0.25, radius_cells=10.0, n=64, ppc=16):
+    w = (W.small_3d(nx=n, ny=n, nzeta=8, ppc=ppc) if ny > 1 else
+         W.small_2d(nx=n, nzeta=8, ppc=ppc))
+    w = w.with_(channel=W.Channel(ratio, radius_cells * w.hx), laser=None)
+    o = R.RefSim(w)
+    P = o._inject()
+    sp = w.species[0]
+    Q0 = sp.charge * sp.density * w.hx * w.hy * w.delta / sp.ppc
+    return w, P, Q0
+
+
+@pytest.mark.parametrize("ny", [1, 64])
+def test_channel_layer_charge_is_the_profile_integral(ny):
+    """The charge of one fresh layer is q Delta times the integral of n(r) over the window:
+    n0 [A + (n1/n0 - 1) pi R^2 erf(Lx/2R) erf(Ly/2R)] in 3-D and, per unit depth,
+    n0 [Lx + (n1/n0 - 1) sqrt(pi) R erf(Lx/2R)] in 2-D (Gaussian integrals over a finite
+    window).  Random in-cell positions (16 per cell) leave a sampling error of 6e-4 (2-D, 64
+    cells) and 2e-5 (3-D); exp(-r^2/2R^2) instead misses by 11 % and 6 %, a flipped sign or
+    n0/n1 swapped by more."""
+    w, P, Q0 = _channel_layer(ny)
+    sp = w.species[0]
+    a, Rc = w.channel.n1_over_n0 - 1.0, w.channel.radius
+    Lx = w.nx * w.hx
+    if ny > 1:
+        Ly = w.ny * w.hy
+        area = Lx * Ly + a * math.pi * Rc ** 2 * math.erf(Lx / (2 * Rc)) * math.erf(Ly / (2 * Rc))
+    else:
+        area = w.hy * (Lx + a * math.sqrt(math.pi) * Rc * math.erf(Lx / (2 * Rc)))
+    exact = sp.charge * sp.density * w.delta * area
+    assert abs(P.Q.sum() - exact) <= (2e-3 if ny == 1 else 1e-4) * abs(exact)
+    deficit = sp.charge * sp.density * w.delta * a * (math.pi * Rc ** 2 if ny > 1 else math.sqrt(math.pi) * Rc * w.hy)
+    assert abs(deficit) > 0.05 * abs(exact)                    # the test can see the profile
+
+
+@pytest.mark.parametrize("ny", [1, 64])
+def test_channel_axis_and_width(ny):
+    """The charge deficit Q0 - Q is a Gaussian centred on the middle node (nx hx/2, ny hy/2)
+    with per-axis second moment R^2/2 (the variance of exp(-x^2/R^2)); a one-cell shift of the
+    axis or R taken as the 1/e radius of the intensity (R/sqrt 2) fails."""
+    w, P, Q0 = _channel_layer(ny)
+    d = Q0 - P.Q
+    assert np.all(d / Q0 >= -1e-15) and np.all(d / Q0 <= 0.75 + 1e-15)
+    Rc = w.channel.radius
+    axes = [(P.x, w.nx * w.hx / 2, w.hx)]
+    if ny > 1:
+        axes.append((P.y, w.ny * w.hy / 2, w.hy))
+    for pos, c, hcell in axes:
+        mean = (d * pos).sum() / d.sum()
+        assert abs(mean - c) <= 0.05 * hcell
+        var = (d * (pos - c) ** 2).sum() / d.sum()
+        assert abs(var - Rc ** 2 / 2) <= 0.01 * Rc ** 2          # sampled: within 0.5 %
+    # the deepest point of the channel: n1/n0 on the axis
+    near = np.hypot(P.x - w.nx * w.hx / 2, P.y - (w.ny * w.hy / 2 if ny > 1 else 0.0)) < 0.1 * Rc
+    assert near.any() and np.all(np.abs(P.Q[near] / Q0 - 0.25) < 0.75 * 0.011)
+
+
+def test_channel_with_n1_equal_n0_is_uniform():
+    w = W.small_2d(nx=16, nzeta=24, ppc=2)
+    a, b = R.RefSim(w), R.RefSim(w.with_(channel=W.Channel(1.0, 3.0)))
+    a.step(2)
+    b.step(2)
+    for x, y in zip(a.state(), b.state()):
+        assert np.array_equal(x, y)
+
+
+def test_channel_stability_uses_the_densest_point():
+    w = W.small_2d(nx=16, nzeta=24, ppc=2)           # Delta at the uniform limit
+    R.RefSim(w.with_(channel=W.Channel(0.25, 3.0)))  # densest far from the axis: n0
+    with pytest.raises(ValueError):
+        R.RefSim(w.with_(channel=W.Channel(1.5, 3.0)))

@@ -318,3 +318,67 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(gempic.GempicError) as e:
         gempic.Sim(w.with_(nx=100))
     assert e.value.status == -1
+
+
+# ---- plasma channel (Sec. 6, Eq. n_plasma) --------------------------------------------------
+def test_channel_2d_fp64_matches_oracle():
+    w = W.small_2d(nx=32, nzeta=64, ppc=3, precision=64)
+    w = w.with_(channel=W.Channel(0.25, 5.0 * w.hx))
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        for _ in range(2):
+            od = o.step()
+            g.step()
+            check_state(g.state(), o.state(), 1e-10)
+            check_diag(g.diagnostics(), od, 1e-10)
+
+
+@pytest.mark.parametrize("C", [1, 2])
+def test_channel_3d_fp64_matches_oracle(C):
+    w = W.small_3d(nx=16, ny=16, nzeta=40, ppc=2, precision=64)
+    w = w.with_(channel=W.Channel(0.25, 3.0 * w.hx))
+    o = RefSim(w)
+    od = o.step(2)
+    with gpu_sim(w, cluster_ctas=C) as g:
+        g.step(2)
+        check_state(g.state(), o.state(), 1e-10)
+        check_diag(g.diagnostics(), od, 1e-10)
+        # the channel changes the run: the uniform plasma gives another current
+        with gpu_sim(w.with_(channel=None), cluster_ctas=C) as u:
+            u.step(2)
+            assert np.abs(u.state()[4] - g.state()[4]).max() > 1e-3 * np.abs(g.state()[4]).max()
+
+
+def test_channel_fp32_bench_grid_matches_oracle():
+    """The 128 x 128 FP32 launch shape of the bench workload with a channel (n1 = n0/4, axis at
+    the middle node, a dense ring outside it)."""
+    w = W.small_3d(nx=128, ny=128, nzeta=48, ppc=2, precision=32)
+    w = w.with_(channel=W.Channel(0.25, 20.0 * w.hx))
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        g.step(2)
+        for _ in range(2):
+            od = o.step()
+        gd = g.diagnostics()
+        ez, oez = g.onaxis_ez(), od["onaxis_ez"]
+        assert np.abs(ez - oez).max() <= 1e-4 * np.abs(oez).max()
+        for key in ("field_energy", "kinetic_energy"):
+            assert abs(gd[key] - od[key]) <= 1e-4 * abs(od[key]), key
+        gs, os_ = g.state(), o.state()
+        fs = max(np.abs(os_[c]).max() for c in range(4))
+        js = max(np.abs(os_[c]).max() for c in (4, 5))
+        for c, name in enumerate(COMPS):
+            scale = fs if c < 4 else js
+            assert np.abs(gs[c] - os_[c]).max() <= 1e-4 * scale, name
+
+
+def test_channel_invalid_arguments_are_rejected():
+    from paper_2509_16793_gb300 import gempic
+    w = W.small_2d(nx=32, nzeta=48, ppc=2, precision=64)       # Delta at the uniform limit
+    for bad in (W.Channel(0.25, 0.0), W.Channel(-0.5, 3.0), W.Channel(float("nan"), 3.0)):
+        with pytest.raises(gempic.GempicError) as e:
+            gempic.Sim(w.with_(channel=bad))
+        assert e.value.status == -1
+    with pytest.raises(gempic.GempicError) as e:               # n1 > n0: densest on the axis
+        gempic.Sim(w.with_(channel=W.Channel(1.5, 3.0)))
+    assert e.value.status == -4

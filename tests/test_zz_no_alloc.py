@@ -13,7 +13,8 @@ from paper_2509_16793_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_matches_gempic_step_twice():
+@pytest.mark.parametrize("channel", [False, True])
+def test_noalloc_matches_gempic_step_twice(channel):
     import torch
     from paper_2509_16793_gb300 import build, gempic
     build.build()
@@ -22,6 +23,8 @@ def test_noalloc_matches_gempic_step_twice():
     # a laser weak enough that no particle is trapped (the allocation-free step keeps no
     # stored particles)
     w = W.small_3d(nx=16, ny=16, nzeta=40, ppc=2, precision=64, a0=0.8)
+    if channel:                            # density channel (Eq. n_plasma) through the config
+        w = w.with_(channel=W.Channel(0.25, 3.0 * w.hx))
     with gempic.Sim(w, cluster_ctas=2, stream=stream) as ref:
         shape = ref.state_shape()
         s0 = torch.empty(shape, dtype=torch.complex128, device="cuda")

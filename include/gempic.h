@@ -88,6 +88,13 @@ typedef struct {
 /* Flags */
 #define GEMPIC_FLAG_DIAG      1u  /* FP64 diagnostics every s-step (default on)           */
 #define GEMPIC_FLAG_SNAPSHOT  2u  /* keep real-space E, B, j of the last s-step of a call */
+/* Particle law GT1 (Sec. 5, Eq. trap1): the s-budget of a particle is the lab time,
+ * ds = |dzeta|/(1 - v_z), a streaming step is at most (Delta - sigma)(1 - v_z), a stored
+ * particle advances by the lab time Delta and rejoins when Delta (1 - v_z) >= h.  Default
+ * (flag clear): GT2 (Eq. trap2), ds~ = v_z |dzeta|/(1 - v_z), the s-step is the propagation
+ * distance Delta.  Under GT1 with Delta shorter than the window every fresh particle stops
+ * inside it (the paper's stitches), so the stored buckets need room for a full layer. */
+#define GEMPIC_FLAG_GT1       4u
 
 typedef struct {
   gempic_grid grid;

@@ -24,6 +24,10 @@ The paper is silent or garbled in places; the readings taken here are:
     (nx hx/2, ny hy/2), as for the laser; immobile ions carry no current in the slice
     equations, so the profile enters only through each fresh macroparticle's charge, taken
     at its injection position.
+  * Particle law GT1 (Sec. 5, Eq. trap1; the default is GT2): the s-budget is the lab time,
+    ds = |dzeta|/(1 - v_z), the step is min(d, (Delta - sigma)(1 - v_z)); a stored particle
+    advances by the lab time Delta (zeta += Delta (v_z - 1)) and rejoins the zeta march when
+    Delta (1 - v_z) >= h.  The current deposit is the same under both laws.
   * Stored (trapped / beam) particles are pushed along the slow coordinate s (Sec. 5.1, last
     paragraph) with the fields of the last completed level; a
     stored particle with Delta(1-v_z)/v_z >= h rejoins the zeta march at its slice.
@@ -390,6 +394,9 @@ class RefSim:
         self.nx, self.ny, self.nz = w.nx, w.ny, w.nzeta
         self.hx, self.hy, self.h = w.hx, w.hy, w.h
         self.delta = w.delta
+        if w.particle_law not in ("GT1", "GT2"):
+            raise ValueError("particle_law is GT1 or GT2 (Sec. 5)")
+        self.gt1 = w.particle_law == "GT1"
         self.sp = Spectral(self.nx, self.ny, self.hx, self.hy)
         self.KX = self.sp.kx[None, :]
         self.KY = self.sp.ky[:, None]
@@ -483,7 +490,12 @@ class RefSim:
         h, D = self.h, self.delta
         g = gamma_of(P.u)
         gmu = gamma_minus_uz(P.u, g)
-        spush = (P.u[2] > 0.0) & (D * gmu < h * np.maximum(P.u[2], 0.0))
+        if self.gt1:
+            # GT1: one s-step is the lab time Delta; the particle stays stored while it moves
+            # less than one cell along zeta in it, Delta (1 - v_z) < h
+            spush = D * gmu < h * g
+        else:
+            spush = (P.u[2] > 0.0) & (D * gmu < h * np.maximum(P.u[2], 0.0))
         # rejoiners: their zeta march starts at their position, budget 0, first step to the
         # plane below them.
         R = P.select(~spush)
@@ -507,16 +519,28 @@ class RefSim:
             Efld[c] = (1.0 - fz) * lo + fz * hi
         u = S.u
         g = gamma_of(u)
-        dt = D * g / u[2]
-        un = boris(u, Efld[:3], Efld[3:], self._qm(S.sp), dt)
-        gn = gamma_of(un)
-        fwd = un[2] > 0.0
-        safe_uz = np.where(fwd, un[2], 1.0)
-        S.u = un
-        S.x = np.where(fwd, (S.x + D * un[0] / safe_uz) % (self.nx * self.hx), S.x)
-        if self.ny > 1:
-            S.y = np.where(fwd, (S.y + D * un[1] / safe_uz) % (self.ny * self.hy), S.y)
-        S.zeta = np.where(fwd, S.zeta - D * gamma_minus_uz(un, gn) / safe_uz, S.zeta)
+        if self.gt1:
+            # GT1: dt = Delta; r_perp += Delta v_perp, zeta += Delta (v_z - 1)
+            un = boris(u, Efld[:3], Efld[3:], self._qm(S.sp), D)
+            gn = gamma_of(un)
+            fwd = np.ones(S.n, bool)
+            S.u = un
+            S.x = (S.x + D * un[0] / gn) % (self.nx * self.hx)
+            if self.ny > 1:
+                S.y = (S.y + D * un[1] / gn) % (self.ny * self.hy)
+            S.zeta = S.zeta - D * gamma_minus_uz(un, gn) / gn
+        else:
+            # GT2: the s-step is the propagation distance Delta, dt = Delta / v_z
+            dt = D * g / u[2]
+            un = boris(u, Efld[:3], Efld[3:], self._qm(S.sp), dt)
+            gn = gamma_of(un)
+            fwd = un[2] > 0.0
+            safe_uz = np.where(fwd, un[2], 1.0)
+            S.u = un
+            S.x = np.where(fwd, (S.x + D * un[0] / safe_uz) % (self.nx * self.hx), S.x)
+            if self.ny > 1:
+                S.y = np.where(fwd, (S.y + D * un[1] / safe_uz) % (self.ny * self.hy), S.y)
+            S.zeta = np.where(fwd, S.zeta - D * gamma_minus_uz(un, gn) / safe_uz, S.zeta)
         keep = S.zeta > 0.0
         nremoved = int((~keep).sum())
         S = S.select(keep)
@@ -576,8 +600,13 @@ class RefSim:
                 g = gamma_of(P.u)
                 gmu = gamma_minus_uz(P.u, g)
                 uzp = np.maximum(P.u[2], 0.0)
-                # Eq. trap2: the step is min(d, (Delta - sigma)(1 - v_z)/v_z) for v_z > 0
-                hlim = np.where(P.u[2] > 0.0, (D - P.sigma) * gmu / np.where(uzp > 0, uzp, 1.0), np.inf)
+                if self.gt1:
+                    # Eq. trap1: s = ct advances by the lab time |dzeta|/(1 - v_z); the step
+                    # is min(d, (Delta - sigma)(1 - v_z)), 1 - v_z = (gamma - u_z)/gamma
+                    hlim = (D - P.sigma) * gmu / g
+                else:
+                    # Eq. trap2: the step is min(d, (Delta - sigma)(1 - v_z)/v_z) for v_z > 0
+                    hlim = np.where(P.u[2] > 0.0, (D - P.sigma) * gmu / np.where(uzp > 0, uzp, 1.0), np.inf)
                 hlim = np.maximum(hlim, 0.0)
                 trap = hlim < P.dist
                 hc = np.where(trap, hlim, P.dist)
@@ -598,7 +627,8 @@ class RefSim:
                 P.x = (X1 * self.hx) % (nx * self.hx)
                 if ny > 1:
                     P.y = (Y1 * self.hy) % (ny * self.hy)
-                P.sigma = P.sigma + ds
+                # the s-budget: s~ = z under GT2 (ds~ = v_z dt), s = ct under GT1 (ds = dt)
+                P.sigma = P.sigma + (dtl if self.gt1 else ds)
                 P.zeta = n * h + (P.dist - hc)
                 if trap.any():
                     T = P.select(trap)

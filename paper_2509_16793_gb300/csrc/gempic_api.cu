@@ -295,6 +295,7 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
   p.wait_spin_limit = 20000000;
   p.diag = (cfg->flags & GEMPIC_FLAG_DIAG) ? 1 : 0;
   p.snapshot = (cfg->flags & GEMPIC_FLAG_SNAPSHOT) ? 1 : 0;
+  p.gt1 = (cfg->flags & GEMPIC_FLAG_GT1) ? 1 : 0;
 
   e = gempic::configure_kernels(cfg->precision, p.smem_bytes, p.C);
   int maxcl = 1;

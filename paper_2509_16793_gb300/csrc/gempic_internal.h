@@ -55,6 +55,7 @@ struct Params {
   int nsteps;                     // marches in this launch
   int P;                          // concurrent marches (clusters)
   int inject, diag, snapshot;
+  int gt1;                        // particle law: 0 = GT2 (Eq. trap2), 1 = GT1 (Eq. trap1)
   int pcap;                       // streaming particle slots per CTA in shared memory
   int fcap;                       // entries of the free-slot stack (slots freed and not yet
                                   // reused; further freed slots stay empty this s-step)

@@ -1495,7 +1495,11 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   V3<T> u = P.u;
   const T g0 = gamma_of(u);
   const T gmu0 = gamma_minus_uz(u, g0);
-  T hlim = u.z > T(0) ? (D - P.sig) * gmu0 / u.z : T(INFINITY);
+  // the step ends where the s-budget reaches Delta: GT2 (Eq. trap2) ds~ = v_z dt, so
+  // -dzeta <= (Delta - sigma)(gamma - u_z)/u_z; GT1 (Eq. trap1) ds = dt, so
+  // -dzeta <= (Delta - sigma)(gamma - u_z)/gamma
+  const T vs = p.gt1 ? g0 : u.z;
+  T hlim = vs > T(0) ? (D - P.sig) * gmu0 / vs : T(INFINITY);
   hlim = fmax(hlim, T(0));
   const bool trap = hlim < d;
   const T hc = trap ? hlim : d;
@@ -1545,7 +1549,7 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
     P.fy = Y1 - fY;
   }
   P.u = un;
-  P.sig = P.sig + ds;
+  P.sig = P.sig + (p.gt1 ? dtl : ds);
   fz_trap = (d - hc) * invh;
   return trap;
 }
@@ -1734,7 +1738,10 @@ __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const
     dkin += P.q * s.cst[K_MOQ + P.sp] * (g - T(1));
     ++dsto;
     const T gmu = gamma_minus_uz(P.u, g);
-    const bool spush = (P.u.z > T(0)) && (D * gmu < h * fmax(P.u.z, T(0)));
+    // stays stored while it moves less than one cell per s-step: GT2 Delta (1 - v_z)/v_z < h,
+    // GT1 Delta (1 - v_z) < h
+    const bool spush = p.gt1 ? D * gmu < h * g
+                             : (P.u.z > T(0)) && (D * gmu < h * fmax(P.u.z, T(0)));
     if (!spush) {
       // moves more than one cell per s-step: rejoins the next zeta march at this slice
       if (!store_append(p.rq, p, s2, n, P, fz)) atomicOr(p.err, ERR_QCAP);
@@ -1745,23 +1752,26 @@ __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const
     gather6_g(p, Fn1, P.ix, P.fx, P.iy, P.fy, me, hi);
 #pragma unroll
     for (int c = 0; c < 6; ++c) E[c] = (T(1) - fz) * lo[c] + fz * hi[c];
-    const T dt = D * g / P.u.z;
+    // GT2: the s-step is the distance Delta along z (dt = Delta/v_z); GT1: the lab time Delta
+    const T dt = p.gt1 ? D : D * g / P.u.z;
     const V3<T> un = boris(P.u, E, E + 3, s.cst[K_QM + P.sp], dt);
     const T gn = gamma_of(un);
     P.u = un;
     int m = n;
-    if (un.z > T(0)) {
-      const T X = P.fx + D * un.x / un.z * s.cst[K_INVHX];
+    // displacement per unit of the new velocity's divisor: dr = Delta u/vd
+    const T vd = p.gt1 ? gn : un.z;
+    if (vd > T(0)) {
+      const T X = P.fx + D * un.x / vd * s.cst[K_INVHX];
       const T fX = floor(X);
       P.ix = (P.ix + (int)fX) & mx;
       P.fx = X - fX;
       if (p.ny > 1) {
-        const T Y = P.fy + D * un.y / un.z * s.cst[K_INVHY];
+        const T Y = P.fy + D * un.y / vd * s.cst[K_INVHY];
         const T fY = floor(Y);
         P.iy = (P.iy + (int)fY) & my;
         P.fy = Y - fY;
       }
-      const T Z = fz - D * gamma_minus_uz(un, gn) / un.z * invh;
+      const T Z = fz - D * gamma_minus_uz(un, gn) / vd * invh;
       const T cZ = ceil(Z) - T(1);
       m = n + (int)cZ;
       fz = Z - cZ;

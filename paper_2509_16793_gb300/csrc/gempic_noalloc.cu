@@ -167,6 +167,7 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
   p.inject = cfg->nspecies > 0 ? 1 : 0;
   p.diag = 1;
   p.snapshot = 0;
+  p.gt1 = (cfg->flags & GEMPIC_FLAG_GT1) ? 1 : 0;
   p.wait_spin_limit = 20000000;
 
   cudaStream_t s = (cudaStream_t)cfg->cuda_stream;

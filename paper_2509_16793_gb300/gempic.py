@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(PKG, "libgempic.so")
 
 GEMPIC_FLAG_DIAG = 1
 GEMPIC_FLAG_SNAPSHOT = 2
+GEMPIC_FLAG_GT1 = 4
 STATUS = {0: "GEMPIC_OK", -1: "GEMPIC_EINVAL", -2: "GEMPIC_ENOMEM", -3: "GEMPIC_ECUDA",
           -4: "GEMPIC_EUNSTABLE", -5: "GEMPIC_ETIMEOUT", -6: "GEMPIC_ESTATE",
           -7: "GEMPIC_EOVERFLOW"}
@@ -153,6 +154,10 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
         ch = gempic_channel(w.channel.n1_over_n0, w.channel.radius)
     if w.snapshot:
         flags |= GEMPIC_FLAG_SNAPSHOT
+    if w.particle_law not in ("GT1", "GT2"):
+        raise ValueError("particle_law is GT1 or GT2")
+    if w.particle_law == "GT1":
+        flags |= GEMPIC_FLAG_GT1
     cfg = gempic_config(
         grid=gempic_grid(w.nx, w.ny, w.nzeta, w.hx, w.hy, w.h), delta=w.delta,
         precision=w.precision, flags=flags, seed=w.seed, nspecies=n, cluster_ctas=cluster_ctas,

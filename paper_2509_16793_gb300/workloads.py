@@ -101,6 +101,7 @@ class Workload:
     stored: Optional[StoredParticles] = None
     snapshot: bool = False       # keep real-space fields of the last s-step
     channel: Optional[Channel] = None   # None: uniform density
+    particle_law: str = "GT2"    # "GT2" (Eq. trap2, s~ = z) or "GT1" (Eq. trap1, s = ct)
 
     @property
     def ncells(self) -> int:

@@ -490,3 +490,53 @@ def test_channel_stability_uses_the_densest_point():
     R.RefSim(w.with_(channel=W.Channel(0.25, 3.0)))  # densest far from the axis: n0
     with pytest.raises(ValueError):
         R.RefSim(w.with_(channel=W.Channel(1.5, 3.0)))
+
+
+# ---- particle law GT1 (Sec. 5, Eq. trap1) ----------------------------------------------------
+def _quiet(law, nzeta=64, steps_per_delta=20):
+    h = W.LAMBDA_L / 16.0
+    w = W.small_2d(nx=16, nzeta=nzeta, ppc=2, delta=steps_per_delta * h)
+    return w.with_(laser=None, particle_law=law)
+
+
+def test_gt1_stitches_in_a_quiet_plasma():
+    """A uniform plasma without a driver stays at rest (v_z = 0), so under GT1 a particle's
+    s = ct advances by |dzeta| per step: it stops after exactly Delta/h = 20 slices, is stored
+    there, rejoins the next s-step (Delta (1 - v_z) >= h) and stops 20 slices further on --
+    the stitches of Sec. 5.  Under GT2 (ds~ = v_z dt = 0) it crosses the window."""
+    w = _quiet("GT1")
+    h, nz, layer = w.h, w.nzeta, w.nx * w.species[0].ppc
+    o = R.RefSim(w)
+    for k in range(1, 5):
+        d = o.step()
+        z = np.sort(o.stored.zeta) / h
+        # every layer in the box (the fresh one and those that rejoined) stops once per s-step
+        stops = [nz - 20 * j for j in range(1, k + 1) if nz - 20 * j > 0]
+        assert d["n_trapped"] == layer * len(stops)
+        assert o.stored.n == layer * len(stops)
+        want = np.repeat(sorted(stops), layer)
+        assert np.abs(z - want).max() < 1e-9
+        assert np.abs(o.stored.u).max() < 1e-12
+    g = R.RefSim(_quiet("GT2"))
+    for _ in range(2):
+        d = g.step()
+        assert d["n_trapped"] == 0 and g.stored.n == 0
+
+
+def test_gt1_budget_is_lab_time():
+    """With a driver: Delta far above the window length stops nobody under either law; Delta
+    of half the window stops the whole fresh layer under GT1 near mid-window (lab time
+    ~ |dzeta| for slow particles), while under GT2 (budget ~ v_z dt) nobody stops."""
+    w = W.small_2d(nx=16, nzeta=48, ppc=2)
+    a = R.RefSim(w)
+    b = R.RefSim(w.with_(particle_law="GT1"))
+    da, db = a.step(), b.step()
+    assert db["n_trapped"] == da["n_trapped"] == 0
+    half = 0.5 * w.nzeta * w.h
+    c = R.RefSim(w.with_(particle_law="GT1", delta=half))
+    dc = c.step()
+    assert dc["n_trapped"] == w.nx * w.species[0].ppc
+    z = c.stored.zeta / w.h
+    assert np.all(z > 0.5 * w.nzeta - 3) and np.all(z < 0.5 * w.nzeta + 3)
+    e = R.RefSim(w.with_(delta=half))
+    assert e.step()["n_trapped"] == 0

@@ -382,3 +382,76 @@ def test_channel_invalid_arguments_are_rejected():
     with pytest.raises(gempic.GempicError) as e:               # n1 > n0: densest on the axis
         gempic.Sim(w.with_(channel=W.Channel(1.5, 3.0)))
     assert e.value.status == -4
+
+
+# ---- particle law GT1 (Sec. 5, Eq. trap1) ----------------------------------------------------
+def _gt1_run(w, steps, tol, **kw):
+    o = RefSim(w)
+    with gpu_sim(w, **kw) as g:
+        for _ in range(steps):
+            od = o.step()
+            g.step()
+            check_diag(g.diagnostics(), od, tol)
+            check_state(g.state(), o.state(), tol)
+        oc = copy.deepcopy(o)
+        rejoin, _, _ = oc._stored_push()
+        compare_particles(g.particles(0), oc.stored_particles(), tol)
+        compare_particles(g.particles(1), dict(x=rejoin.x, y=rejoin.y, zeta=rejoin.zeta,
+                                               ux=rejoin.u[0], uy=rejoin.u[1], uz=rejoin.u[2],
+                                               weight=rejoin.Q), tol)
+    return od
+
+
+def test_gt1_quiet_plasma_stitches_fp64():
+    """Quiet plasma, Delta = 20 h: every layer stops 20 slices on each s-step and rejoins."""
+    h = W.LAMBDA_L / 16.0
+    w = W.small_2d(nx=16, nzeta=64, ppc=2, precision=64, delta=20 * h)
+    w = w.with_(laser=None, particle_law="GT1")
+    od = _gt1_run(w, 4, 1e-10)
+    assert od["n_trapped"] == 3 * 32 and od["n_rejoined"] == 3 * 32
+
+
+def test_gt1_2d_driver_fp64():
+    w = W.small_2d(nx=32, nzeta=64, ppc=3, precision=64, a0=2.0)
+    w = w.with_(particle_law="GT1", delta=0.5 * w.nzeta * w.h)
+    od = _gt1_run(w, 3, 1e-9)
+    assert od["n_trapped"] > 0 and od["n_rejoined"] > 0
+
+
+@pytest.mark.parametrize("C", [1, 2])
+def test_gt1_3d_driver_fp64(C):
+    w = W.small_3d(nx=16, ny=16, nzeta=40, ppc=2, precision=64)
+    w = w.with_(particle_law="GT1", delta=0.6 * w.nzeta * w.h)
+    od = _gt1_run(w, 2, 1e-9, cluster_ctas=C, bucket_capacity=1024)
+    assert od["n_trapped"] >= 16 * 16 * 2
+
+
+def test_gt1_fp32_matches_oracle():
+    w = W.small_3d(nx=32, ny=32, nzeta=64, ppc=2, precision=32)
+    w = w.with_(particle_law="GT1", delta=0.6 * w.nzeta * w.h)
+    o = RefSim(w)
+    with gpu_sim(w, bucket_capacity=4096) as g:
+        for _ in range(2):
+            od = o.step()
+            g.step()
+            gd = g.diagnostics()
+            ez, oez = g.onaxis_ez(), od["onaxis_ez"]
+            assert np.abs(ez - oez).max() <= 1e-4 * np.abs(oez).max()
+            for key in ("field_energy", "kinetic_energy"):
+                assert abs(gd[key] - od[key]) <= 1e-4 * abs(od[key]), key
+            assert gd["n_trapped"] == od["n_trapped"]
+
+
+def test_gt1_without_stops_equals_gt2():
+    """Delta far above the window and no particle fast enough to stop: both laws march the
+    same particles through the same steps (the budget never binds)."""
+    w = W.small_2d(nx=32, nzeta=48, ppc=2, precision=64, a0=0.5)
+    with gpu_sim(w) as a, gpu_sim(w.with_(particle_law="GT1")) as b:
+        a.step(2)
+        b.step(2)
+        sa, sb = a.state(), b.state()
+        fs = max(np.abs(sa[c]).max() for c in range(4))          # fields
+        js = max(np.abs(sa[c]).max() for c in (4, 5))            # currents
+        for c in range(6):
+            assert np.abs(sa[c] - sb[c]).max() <= 1e-12 * (fs if c < 4 else js), c
+        assert a.diagnostics()["n_trapped"] == b.diagnostics()["n_trapped"] == 0

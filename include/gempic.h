@@ -146,6 +146,17 @@ gempic_status gempic_step(struct gempic_sim* sim, int32_t n);
 /* Same, without waiting: launches on the simulation's stream and returns. */
 gempic_status gempic_step_async(struct gempic_sim* sim, int32_t n);
 
+/* Change the s-step Delta for the s-steps launched after this call (Sec. 6 varies Delta along
+ * the run; the field update of Sec. 4.1, the fresh weight Q_f = q n h_x h_y Delta/ppc and the
+ * s-budget of each particle all take the new value; particles already stored keep their
+ * charge).  The stored set is advanced to the next level at the end of each s-step, with
+ * that s-step's fields and Delta, so after a change it lags the new Delta by one s-step.
+ * Initialises the simulation first if no step has run, so that the level-0 set-up uses the
+ * Delta of gempic_create.  GEMPIC_EINVAL for delta < 0 or non-finite,
+ * GEMPIC_EUNSTABLE above the stability bound (the simulation keeps its old Delta), GEMPIC_ESTATE
+ * after a failure.  Launches already issued are not affected. */
+gempic_status gempic_set_delta(struct gempic_sim* sim, double delta);
+
 /* Wait for the stream and check the device status word of the simulation. */
 gempic_status gempic_sync(struct gempic_sim* sim);
 

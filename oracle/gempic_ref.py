@@ -28,6 +28,9 @@ The paper is silent or garbled in places; the readings taken here are:
     ds = |dzeta|/(1 - v_z), the step is min(d, (Delta - sigma)(1 - v_z)); a stored particle
     advances by the lab time Delta (zeta += Delta (v_z - 1)) and rejoins the zeta march when
     Delta (1 - v_z) >= h.  The current deposit is the same under both laws.
+  * Variable Delta (Sec. 6 changes Delta along the run without saying how the change meets
+    the stored set): the stored set's advance from s^k to s^{k+1} uses the Delta of s-step k,
+    the one whose fields it gathers; after a change the stored set lags it by one s-step.
   * Stored (trapped / beam) particles are pushed along the slow coordinate s (Sec. 5.1, last
     paragraph) with the fields of the last completed level; a
     stored particle with Delta(1-v_z)/v_z >= h rejoins the zeta march at its slice.
@@ -397,6 +400,9 @@ class RefSim:
         if w.particle_law not in ("GT1", "GT2"):
             raise ValueError("particle_law is GT1 or GT2 (Sec. 5)")
         self.gt1 = w.particle_law == "GT1"
+        # Delta of the next advance of the stored set: that of the last completed s-step
+        # (the level-0 set-up counts as one, with the Delta of creation)
+        self.delta_stored = self.delta
         self.sp = Spectral(self.nx, self.ny, self.hx, self.hy)
         self.KX = self.sp.kx[None, :]
         self.KY = self.sp.ky[:, None]
@@ -421,6 +427,19 @@ class RefSim:
         # initial laser and the real-space fields of level 0.
         self._march(delta_field=0.0, inject=False, joiners=Particles.empty(),
                     jbeam=self._zero_jbeam())
+
+    def set_delta(self, delta):
+        """Sec. 6: Delta may change along the run.  The s-steps after this call use the new
+        Delta in the slice update (Sec. 4.1), the fresh weight Q_f (Sec. 5.1) and the
+        particles' s-budget (Sec. 5); stored particles keep their charge.  The stored set is
+        advanced to the next level with the Delta of the s-step that produced the fields it
+        uses (the previous one), so after a change it lags the new Delta by one s-step."""
+        densest = max(1.0, self.w.channel.n1_over_n0) if self.w.channel is not None else 1.0
+        if not (delta >= 0.0) or not math.isfinite(delta):
+            raise ValueError("Delta must be finite and >= 0")
+        if self.w.omega_p2 * densest * delta * self.h > 4.0 * (1.0 + 1e-12):
+            raise ValueError("Delta h omega_p^2 > 4: outside the stability bound (Sec. 4.2)")
+        self.delta = float(delta)
 
     # -- initial condition: forward wave R = 2E, L = 0 (Eqs. Rx/Ry, E_laser) ------------------
     def _init_laser(self):
@@ -487,7 +506,7 @@ class RefSim:
         nremoved = 0
         if P.n == 0:
             return Particles.empty(), jbeam, 0
-        h, D = self.h, self.delta
+        h, D = self.h, self.delta_stored
         g = gamma_of(P.u)
         gmu = gamma_minus_uz(P.u, g)
         if self.gt1:
@@ -685,6 +704,7 @@ class RefSim:
         for _ in range(n):
             joiners, jbeam, nrem = self._stored_push()
             d = self._march(delta_field=self.delta, inject=True, joiners=joiners, jbeam=jbeam)
+            self.delta_stored = self.delta
             d["n_rejoined"] = joiners.n
             d["n_stored_removed"] = nrem
             self.step_index += 1

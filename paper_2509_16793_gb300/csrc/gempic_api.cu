@@ -21,6 +21,8 @@ struct gempic_sim {
   gempic_species species[gempic::kMaxSpecies];
   gempic_laser laser;
   bool has_laser = false;
+  gempic_channel channel;
+  bool has_channel = false;
   Params p{};                      // launch template
   int eb = 8;                      // bytes per real
   int pmax = 1;                    // concurrent marches
@@ -223,6 +225,10 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     s->has_laser = true;
   }
   s->cfg.laser = nullptr;
+  if (cfg->channel) {
+    s->channel = *cfg->channel;
+    s->has_channel = true;
+  }
   s->cfg.channel = nullptr;
   s->stream = (cudaStream_t)cfg->cuda_stream;
   s->eb = cfg->precision == 64 ? 8 : 4;
@@ -435,6 +441,25 @@ gempic_status gempic_step_async(gempic_sim* s, int32_t n) {
   s->last_launch_k0 = s->k;
   s->last_launch_n = n;
   s->k += n;
+  return GEMPIC_OK;
+}
+
+gempic_status gempic_set_delta(gempic_sim* s, double delta) {
+  if (!s) return GEMPIC_EINVAL;
+  if (!(delta >= 0) || !std::isfinite(delta)) return GEMPIC_EINVAL;
+  gempic_status st = ensure_initialized(s);
+  if (st != GEMPIC_OK) return st;
+  gempic_config c = s->cfg;
+  c.delta = delta;
+  c.species = s->species;
+  c.channel = s->has_channel ? &s->channel : nullptr;
+  Params t = s->p;
+  st = gempic::setup_species(&c, t);
+  if (st != GEMPIC_OK) return st;
+  s->cfg.delta = delta;
+  s->p = t;
+  s->p.delta = delta;
+  s->p.delta_field = delta;
   return GEMPIC_OK;
 }
 

@@ -78,6 +78,7 @@ SIGNATURES = {
     "gempic_step": (c_int32, [c_void_p, c_int32]),
     "gempic_step_async": (c_int32, [c_void_p, c_int32]),
     "gempic_sync": (c_int32, [c_void_p]),
+    "gempic_set_delta": (c_int32, [c_void_p, c_double]),
     "gempic_step_host": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_size_t, POINTER(gempic_diag)]),
     "gempic_state_bytes": (c_size_t, [c_void_p]),
     "gempic_get_state": (c_int32, [c_void_p, c_void_p, c_size_t, c_int32]),
@@ -230,6 +231,11 @@ class Sim:
         _check(self.lib.gempic_sync(self.h), "gempic_sync")
 
     sync = gempic_sync
+
+    def gempic_set_delta(self, delta: float):
+        _check(self.lib.gempic_set_delta(self.h, float(delta)), "gempic_set_delta")
+
+    set_delta = gempic_set_delta
 
     def state_bytes(self) -> int:
         return int(self.lib.gempic_state_bytes(self.h))

@@ -540,3 +540,47 @@ def test_gt1_budget_is_lab_time():
     assert np.all(z > 0.5 * w.nzeta - 3) and np.all(z < 0.5 * w.nzeta + 3)
     e = R.RefSim(w.with_(delta=half))
     assert e.step()["n_trapped"] == 0
+
+
+# ---- variable Delta (Sec. 6: Delta grows along the run) --------------------------------------
+def test_variable_delta_vacuum_diffraction():
+    """P9 with a Delta schedule: 4 s-steps of Z_R/8 then 3 of Z_R/4 propagate the beam by
+    1.25 Z_R, so its width is w0 sqrt(1 + 1.25^2) (Gaussian-beam closed form), as for a run
+    with constant Delta over the same distance."""
+    lam = 2 * math.pi
+    nx, hx, nz, h = 64, math.pi, 128, lam / 16
+    w0 = 4 * lam
+    zr = math.pi * w0 * w0 / lam
+    w = W.Workload(name="vac2d", nx=nx, ny=1, nzeta=nz, hx=hx, hy=1.0, h=h, delta=zr / 8,
+                   species=[], laser=W.Laser(a0=0.1, waist=w0, duration=8.0, zeta_center=0.5 * nz * h))
+    sim = R.RefSim(w)
+    x = np.arange(nx) * hx - 0.5 * nx * hx
+
+    def width():
+        I = (sim.fields_rs[:, 0, 0, :] ** 2).sum(0)
+        return 2.0 * math.sqrt((I * x * x).sum() / I.sum())
+    sim.step(4)
+    sim.set_delta(zr / 4)
+    sim.step(3)
+    expect = w0 * math.sqrt(1 + 1.25 ** 2)
+    assert abs(width() - expect) / expect < 0.03
+    # a schedule that ignored the change (7 steps of Z_R/8 = 0.875 Z_R) would be 9 % narrower
+    assert abs(w0 * math.sqrt(1 + 0.875 ** 2) - expect) / expect > 0.09
+
+
+@pytest.mark.parametrize("law", ["GT2", "GT1"])
+def test_variable_delta_keeps_the_density(law):
+    """Every plane carries (rho - j_z) = q n: the charge flux of an s-step is q n A L whatever
+    Delta is (Q_f grows with Delta and the deposit weight Q/(hx hy Delta) divides it out);
+    a weight left at the old Delta would change it by the ratio of the two."""
+    w = W.small_2d(nx=16, nzeta=24, ppc=2, a0=0.5).with_(particle_law=law)
+    sim = R.RefSim(w)
+    sp = w.species[0]
+    exact = sp.charge * sp.density * (w.nx * w.hx) * w.hy * (w.nzeta * w.h)
+    for delta in (w.delta, 0.5 * w.delta, 0.25 * w.delta):
+        sim.set_delta(delta)
+        d = sim.step()
+        assert d["n_trapped"] == 0
+        assert abs(d["charge_flux"] - exact) <= 1e-12 * abs(exact)
+    with pytest.raises(ValueError):
+        sim.set_delta(1.01 * w.delta)                 # above the stability bound

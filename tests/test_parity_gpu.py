@@ -455,3 +455,74 @@ def test_gt1_without_stops_equals_gt2():
         for c in range(6):
             assert np.abs(sa[c] - sb[c]).max() <= 1e-12 * (fs if c < 4 else js), c
         assert a.diagnostics()["n_trapped"] == b.diagnostics()["n_trapped"] == 0
+
+
+# ---- variable Delta (Sec. 6) ---------------------------------------------------------------
+def test_delta_schedule_2d_fp64_with_trapping():
+    w = W.small_2d(nx=16, nzeta=96, ppc=2, precision=64, a0=2.0, delta=1.5)
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        for delta in (1.5, 3.0, 0.75, 0.75):
+            o.set_delta(delta)
+            g.set_delta(delta)
+            od = o.step()
+            g.step()
+            check_diag(g.diagnostics(), od, 1e-9)
+            check_state(g.state(), o.state(), 1e-9)
+        assert od["n_trapped"] > 0
+        oc = copy.deepcopy(o)
+        oc._stored_push()
+        compare_particles(g.particles(0), oc.stored_particles(), 1e-9)
+
+
+def test_delta_set_before_first_step_with_beam_fp64():
+    """The level-0 set-up (the beam's first advance) uses the Delta of creation; the new Delta
+    applies to the fields and fresh particles from the first s-step on and to the stored set
+    one s-step later."""
+    w = W.small_3d(nx=16, ny=16, nzeta=48, ppc=1, precision=64, a0=0.5)
+    beam = W.gaussian_bunch(w, n_macro=2000, n_peak=0.05, sigma_r=2.0, sigma_z=2.0,
+                            zeta_center=0.5 * w.nzeta * w.h, gamma=200.0, rel_spread=1e-3)
+    w = w.with_(stored=beam)
+    o = RefSim(w)
+    with gpu_sim(w, cluster_ctas=2) as g:
+        o.set_delta(0.5 * w.delta)
+        g.set_delta(0.5 * w.delta)
+        for _ in range(2):
+            od = o.step()
+            g.step()
+            check_diag(g.diagnostics(), od, 1e-10)
+            check_state(g.state(), o.state(), 1e-10)
+
+
+def test_delta_schedule_fp32_bench_grid_pipelined():
+    """128 x 128 FP32, three s-steps per launch (marched concurrently), Delta changed between
+    launches."""
+    w = W.small_3d(nx=128, ny=128, nzeta=48, ppc=2, precision=32)
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        for delta in (w.delta, 0.5 * w.delta):
+            g.set_delta(delta)
+            o.set_delta(delta)
+            g.step(3)
+            for _ in range(3):
+                od = o.step()
+            gd = g.diagnostics()
+            ez, oez = g.onaxis_ez(), od["onaxis_ez"]
+            assert np.abs(ez - oez).max() <= 1e-4 * np.abs(oez).max()
+            for key in ("field_energy", "kinetic_energy", "charge_flux"):
+                assert abs(gd[key] - od[key]) <= 1e-4 * abs(od[key]), key
+
+
+def test_delta_rejects_bad_values_and_keeps_the_old_one():
+    from paper_2509_16793_gb300 import gempic
+    w = W.small_2d(nx=16, nzeta=32, ppc=2, precision=64)      # Delta at the stability limit
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        for bad, status in ((-1.0, -1), (float("inf"), -1), (1.5 * w.delta, -4)):
+            with pytest.raises(gempic.GempicError) as e:
+                g.set_delta(bad)
+            assert e.value.status == status
+        od = o.step()
+        g.step()
+        check_state(g.state(), o.state(), 1e-10)
+        check_diag(g.diagnostics(), od, 1e-10)

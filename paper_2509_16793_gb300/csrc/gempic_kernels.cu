@@ -1477,7 +1477,8 @@ struct SliceAcc {     // per-thread, per-slice diagnostics in the working precis
   int push;
 };
 
-template <typename T>
+// LAW: 0 = GT2, 1 = GT1, -1 = either (read from p.gt1)
+template <typename T, int LAW>
 __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PState<T>& P, T d,
                             int me, T& fz_trap, SliceAcc<T>& acc) {
   SUB_DECL
@@ -1498,7 +1499,8 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   // the step ends where the s-budget reaches Delta: GT2 (Eq. trap2) ds~ = v_z dt, so
   // -dzeta <= (Delta - sigma)(gamma - u_z)/u_z; GT1 (Eq. trap1) ds = dt, so
   // -dzeta <= (Delta - sigma)(gamma - u_z)/gamma
-  const T vs = p.gt1 ? g0 : u.z;
+  const bool gt1 = LAW < 0 ? p.gt1 != 0 : LAW == 1;
+  const T vs = gt1 ? g0 : u.z;
   T hlim = vs > T(0) ? (D - P.sig) * gmu0 / vs : T(INFINITY);
   hlim = fmax(hlim, T(0));
   const bool trap = hlim < d;
@@ -1549,7 +1551,7 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
     P.fy = Y1 - fY;
   }
   P.u = un;
-  P.sig = P.sig + (p.gt1 ? dtl : ds);
+  P.sig = P.sig + (gt1 ? dtl : ds);
   fz_trap = (d - hc) * invh;
   return trap;
 }
@@ -1905,6 +1907,8 @@ __device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
 template <typename T, bool CANON = false, int SH = 0>
 __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& cl, long long k,
                       int cid) {
+  // the 128 x 128 instantiation is compiled for GT2 only (GT1 runs take the generic one)
+  constexpr int LAW = SH == 1 ? 0 : -1;
   const int me = (int)cl.block_rank();
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
@@ -2054,7 +2058,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         if (cw < 0) continue;
         PState<T> P = get_particle(p, s, ov, i, cw);
         T fzt;
-        const bool trap = stream_push(p, s, Fcur, P, h, me, fzt, sa);
+        const bool trap = stream_push<T, LAW>(p, s, Fcur, P, h, me, fzt, sa);
         bool gone = trap;
         if (trap) {
           ++ntrap;
@@ -2104,7 +2108,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         PState<T> P = store_read<T>(p.rq, p, ge, fz);
         ++nrej;
         T fzt;
-        const bool trap = stream_push(p, s, Fcur, P, fz * h, me, fzt, sa);
+        const bool trap = stream_push<T, LAW>(p, s, Fcur, P, fz * h, me, fzt, sa);
         if (trap) {
           ++ntrap;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
@@ -2684,7 +2688,7 @@ int smem_layout(Params& p, int eb) {
 // kernel instantiation for the grid: 1 = FP32 128 x 128 with an even band (length-128
 // transforms only), 0 = any size
 static int shape_class(int precision, const Params& p) {
-  return precision == 32 && p.nx == 128 && p.ny == 128 && (p.RB & 1) == 0 ? 1 : 0;
+  return precision == 32 && p.nx == 128 && p.ny == 128 && (p.RB & 1) == 0 && !p.gt1 ? 1 : 0;
 }
 
 // The dynamic shared-memory limit is an attribute of the kernel function, shared by every

@@ -526,3 +526,19 @@ def test_delta_rejects_bad_values_and_keeps_the_old_one():
         g.step()
         check_state(g.state(), o.state(), 1e-10)
         check_diag(g.diagnostics(), od, 1e-10)
+
+
+def test_gt1_fp32_bench_grid_takes_the_generic_kernel():
+    """The 128 x 128 FP32 kernel is compiled for GT2 only; a GT1 run of that grid uses the
+    generic instantiation and must still match the oracle."""
+    w = W.small_3d(nx=128, ny=128, nzeta=48, ppc=2, precision=32).with_(particle_law="GT1")
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        g.step(2)
+        for _ in range(2):
+            od = o.step()
+        gd = g.diagnostics()
+        ez, oez = g.onaxis_ez(), od["onaxis_ez"]
+        assert np.abs(ez - oez).max() <= 1e-4 * np.abs(oez).max()
+        for key in ("field_energy", "kinetic_energy"):
+            assert abs(gd[key] - od[key]) <= 1e-4 * abs(od[key]), key

@@ -112,6 +112,14 @@ typedef struct {
   int32_t reserved;
   void* cuda_stream;             /* cudaStream_t; NULL = legacy default stream */
   const gempic_channel* channel; /* NULL: uniform density; copied at create */
+  /* Variable zeta-step (Sec. 6 refines the back of the window): nzeta slab thicknesses, slab
+   * n lying between planes n and n+1, plane 0 at the back; every step-dependent part of the
+   * scheme (slice equations, particle step, deposit normalisation, energies, stored
+   * particles' slabs) takes the thickness of the slab it concerns.  NULL: grid.h everywhere.
+   * The profile should vary smoothly (second order needs h_{n+1} - h_n = O(h^2)).  Copied at
+   * create; GEMPIC_EINVAL for a non-positive or non-finite entry; the stability bound uses
+   * the largest slab.  gempic_step_noalloc does not take a table (GEMPIC_EINVAL). */
+  const double* hz;
 } gempic_config;
 
 /* Per-s-step diagnostics, accumulated on the device in FP64. */

@@ -397,6 +397,18 @@ class RefSim:
         self.nx, self.ny, self.nz = w.nx, w.ny, w.nzeta
         self.hx, self.hy, self.h = w.hx, w.hy, w.h
         self.delta = w.delta
+        # zeta grid: slab n between planes n and n+1 has thickness hz[n]; plane n sits at
+        # zp[n] (plane 0 at the back).  Uniform: hz = h.  Variable (Sec. 6 refines the back
+        # of the window): every use of h below takes the thickness of the slab it concerns.
+        self.varh = w.hz is not None
+        if self.varh:
+            self.hz = np.asarray(w.hz, dtype=float)
+            if self.hz.shape != (self.nz,) or not np.all(self.hz > 0) or not np.all(np.isfinite(self.hz)):
+                raise ValueError("hz holds nzeta positive slab thicknesses")
+            self.zp = np.concatenate([[0.0], np.cumsum(self.hz)])
+        else:
+            self.hz = np.full(self.nz, self.h)
+            self.zp = np.arange(self.nz + 1) * self.h
         if w.particle_law not in ("GT1", "GT2"):
             raise ValueError("particle_law is GT1 or GT2 (Sec. 5)")
         self.gt1 = w.particle_law == "GT1"
@@ -412,7 +424,7 @@ class RefSim:
         self.step_index = 0
         self.diag: Dict = {}
         densest = max(1.0, w.channel.n1_over_n0) if w.channel is not None else 1.0
-        if w.omega_p2 * densest * self.delta * self.h > 4.0 * (1.0 + 1e-12):
+        if w.omega_p2 * densest * self.delta * self.hz.max() > 4.0 * (1.0 + 1e-12):
             raise ValueError("Delta h omega_p^2 > 4: outside the stability bound (Sec. 4.2)")
         self.stored = Particles.empty()
         if w.stored is not None and w.stored.n > 0:
@@ -437,7 +449,7 @@ class RefSim:
         densest = max(1.0, self.w.channel.n1_over_n0) if self.w.channel is not None else 1.0
         if not (delta >= 0.0) or not math.isfinite(delta):
             raise ValueError("Delta must be finite and >= 0")
-        if self.w.omega_p2 * densest * delta * self.h > 4.0 * (1.0 + 1e-12):
+        if self.w.omega_p2 * densest * delta * self.hz.max() > 4.0 * (1.0 + 1e-12):
             raise ValueError("Delta h omega_p^2 > 4: outside the stability bound (Sec. 4.2)")
         self.delta = float(delta)
 
@@ -451,9 +463,18 @@ class RefSim:
         r2 = yj[:, None] ** 2 + xi[None, :] ** 2
         comp = "Rx" if L.pol == 0 else "Ry"
         for n in range(self.nz):
-            phi = n * self.h - L.zeta_center
+            phi = self.zp[n] - L.zeta_center
             E = L.a0 * math.cos(phi) * math.exp(-phi * phi / L.duration ** 2) * np.exp(-r2 / L.waist ** 2)
             self.S[comp][n] = self.sp.forward(2.0 * E)
+
+    def _slab(self, zeta):
+        """Slab m with zp[m] < zeta <= zp[m+1] and the offset (zeta - zp[m]) / hz[m]."""
+        if self.varh:
+            m = np.searchsorted(self.zp, zeta, side="left").astype(np.int64) - 1
+            mc = np.clip(m, 0, self.nz - 1)
+            return m, (zeta - self.zp[mc]) / self.hz[mc]
+        m = np.ceil(zeta / self.h).astype(np.int64) - 1
+        return m, zeta / self.h - m
 
     def _zero_jbeam(self):
         return np.zeros((self.nz, 3, self.ny, self.nx))
@@ -481,10 +502,10 @@ class RefSim:
             if w.channel is not None:
                 Q = Q * channel_profile(w.channel, x - 0.5 * self.nx * self.hx,
                                         y - 0.5 * self.ny * self.hy if self.ny > 1 else y)
-            parts.append(Particles(x, y, np.full(n, self.nz * self.h), np.zeros((3, n)),
+            parts.append(Particles(x, y, np.full(n, self.zp[self.nz]), np.zeros((3, n)),
                                    np.zeros(n), np.broadcast_to(Q, (n,)).copy(),
                                    np.full(n, si, np.int64),
-                                   np.full(n, self.h)))
+                                   np.full(n, self.hz[self.nz - 1])))
             off += ncell * s.ppc
         return Particles.concat(parts)
 
@@ -506,7 +527,9 @@ class RefSim:
         nremoved = 0
         if P.n == 0:
             return Particles.empty(), jbeam, 0
-        h, D = self.h, self.delta_stored
+        D = self.delta_stored
+        ms, _ = self._slab(P.zeta)
+        h = self.hz[np.clip(ms, 0, self.nz - 1)]        # thickness of each particle's slab
         g = gamma_of(P.u)
         gmu = gamma_minus_uz(P.u, g)
         if self.gt1:
@@ -518,13 +541,12 @@ class RefSim:
         # rejoiners: their zeta march starts at their position, budget 0, first step to the
         # plane below them.
         R = P.select(~spush)
-        m = np.ceil(R.zeta / h).astype(np.int64) - 1
-        R.dist = R.zeta - m * h
+        m, _ = self._slab(R.zeta)
+        R.dist = R.zeta - (self.zp[m] if self.varh else m * self.h)
         R.sigma = np.zeros(R.n)
         S = P.select(spush)
         # gather at (x, y, zeta): CIC across, linear in zeta between slices m and m+1
-        m = np.ceil(S.zeta / h).astype(np.int64) - 1
-        fz = S.zeta / h - m
+        m, fz = self._slab(S.zeta)
         X, Y = S.x / self.hx, S.y / self.hy
         Efld = np.zeros((6, S.n))
         for c in range(6):
@@ -569,16 +591,30 @@ class RefSim:
         if S.n:
             D3 = S.select(fwd)
             gd = gn[fwd]
-            t = D3.zeta / h - 0.5
-            i0 = np.floor(t).astype(np.int64)
-            f = t - i0
+            if self.varh:
+                # linear between the half-slice centres c_i = zp[i] + hz[i]/2 (the grid
+                # extended by one slab of the end thickness on either side); the density of
+                # half-slice i is charge / (hx hy hz[i])
+                hpad = np.concatenate([[self.hz[0]], self.hz, [self.hz[-1]]])
+                c = np.concatenate([[-0.5 * self.hz[0]], self.zp[:-1] + 0.5 * self.hz,
+                                    [self.zp[-1] + 0.5 * self.hz[-1]]])
+                k = np.searchsorted(c, D3.zeta, side="right") - 1   # c[k] <= zeta < c[k+1]
+                i0 = k - 1
+                f = (D3.zeta - c[k]) / (c[k + 1] - c[k])
+                amp = D3.Q / (self.hx * self.hy * gd)
+                inv_h = lambda ii: 1.0 / hpad[np.clip(ii + 1, 0, self.nz + 1)]
+            else:
+                t = D3.zeta / self.h - 0.5
+                i0 = np.floor(t).astype(np.int64)
+                f = t - i0
+                amp = D3.Q / (self.hx * self.hy * self.h * gd)
+                inv_h = lambda ii: 1.0
             X, Y = D3.x / self.hx, D3.y / self.hy
-            amp = D3.Q / (self.hx * self.hy * h * gd)
             for ii, wz in ((i0, 1.0 - f), (i0 + 1, f)):
                 ok = (ii >= 0) & (ii < self.nz)
                 for iz in np.unique(ii[ok]):
                     sel = ok & (ii == iz)
-                    a = amp[sel] * wz[sel]
+                    a = amp[sel] * wz[sel] * inv_h(iz)
                     cic_deposit(jbeam[iz, 0], X[sel] - 0.5, Y[sel], a * D3.u[0, sel])
                     if self.ny > 1:
                         cic_deposit(jbeam[iz, 1], X[sel], Y[sel] - 0.5, a * D3.u[1, sel])
@@ -590,7 +626,7 @@ class RefSim:
 
     # -- the zeta march at level s^1 (Sec. 4.1: from the front of the window towards the back) -------
     def _march(self, delta_field, inject, joiners, jbeam):
-        nx, ny, nz, h = self.nx, self.ny, self.nz, self.h
+        nx, ny, nz = self.nx, self.ny, self.nz
         old = {k: v.copy() for k, v in self.S.items()}
         D = self.delta
         zero = np.zeros((ny, nx // 2), complex)
@@ -604,8 +640,9 @@ class RefSim:
         charge_flux = 0.0
         onaxis = np.zeros(nz)
         if joiners.n:
-            jm = np.ceil(joiners.zeta / h).astype(np.int64) - 1
+            jm, _ = self._slab(joiners.zeta)
         for n in range(nz - 1, -1, -1):
+            h = self.hz[n]                                  # slab n: planes n and n+1
             if joiners.n:
                 P = Particles.concat([P, joiners.select(jm == n)])
             jx = np.zeros((ny, nx))
@@ -648,13 +685,13 @@ class RefSim:
                     P.y = (Y1 * self.hy) % (ny * self.hy)
                 # the s-budget: s~ = z under GT2 (ds~ = v_z dt), s = ct under GT1 (ds = dt)
                 P.sigma = P.sigma + (dtl if self.gt1 else ds)
-                P.zeta = n * h + (P.dist - hc)
+                P.zeta = self.zp[n] + (P.dist - hc) if self.varh else n * h + (P.dist - hc)
                 if trap.any():
                     T = P.select(trap)
                     trapped.append(T)
                 P = P.select(~trap)
-                P.dist = np.full(P.n, h)
-                P.zeta = np.full(P.n, n * h)
+                P.dist = np.full(P.n, self.hz[n - 1] if n > 0 else h)
+                P.zeta = np.full(P.n, self.zp[n] if self.varh else n * h)
             jx += jbeam[n, 0]
             jy += jbeam[n, 1]
             jz += jbeam[n, 2]

@@ -23,6 +23,7 @@ struct gempic_sim {
   bool has_laser = false;
   gempic_channel channel;
   bool has_channel = false;
+  std::vector<double> hz, zp;      // variable zeta-step: slab thicknesses, plane positions
   Params p{};                      // launch template
   int eb = 8;                      // bytes per real
   int pmax = 1;                    // concurrent marches
@@ -111,9 +112,18 @@ gempic_status upload_particles(gempic_sim* s) {
   for (auto& v : f) v.assign(cap, 0.0);
   for (size_t i = 0; i < n; ++i) {
     const double X = s->px[i] / p.hx, Y = p.ny > 1 ? s->py[i] / p.hy : 0.0;
-    const double Z = s->pz[i] / p.h;
     const double fX = std::floor(X), fY = std::floor(Y);
-    const int m = (int)std::ceil(Z) - 1;
+    int m;
+    double fz;
+    if (s->zp.empty()) {
+      const double Z = s->pz[i] / p.h;
+      m = (int)std::ceil(Z) - 1;
+      fz = Z - m;
+    } else {
+      // slab m with zeta_m < zeta <= zeta_{m+1}
+      m = (int)(std::lower_bound(s->zp.begin(), s->zp.end(), s->pz[i]) - s->zp.begin()) - 1;
+      fz = m >= 0 && m < p.nz ? (s->pz[i] - s->zp[m]) / s->hz[m] : 0.0;
+    }
     if (m < 0 || m >= p.nz) continue;
     const int ix = ((int)fX % p.nx + p.nx) % p.nx, iy = ((int)fY % p.ny + p.ny) % p.ny;
     if (cnt[m] >= p.bcap) return GEMPIC_EOVERFLOW;
@@ -121,7 +131,7 @@ gempic_status upload_particles(gempic_sim* s) {
     cell[e] = ix | (iy << 10) | (s->psp[i] << 20);
     f[0][e] = X - fX;
     f[1][e] = Y - fY;
-    f[2][e] = Z - m;
+    f[2][e] = fz;
     f[3][e] = s->pux[i];
     f[4][e] = s->puy[i];
     f[5][e] = s->puz[i];
@@ -230,6 +240,12 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     s->has_channel = true;
   }
   s->cfg.channel = nullptr;
+  if (cfg->hz) {
+    s->hz.assign(cfg->hz, cfg->hz + g.nzeta);
+    s->zp.assign(g.nzeta + 1, 0.0);
+    for (int n = 0; n < g.nzeta; ++n) s->zp[n + 1] = s->zp[n] + s->hz[n];
+  }
+  s->cfg.hz = nullptr;
   s->stream = (cudaStream_t)cfg->cuda_stream;
   s->eb = cfg->precision == 64 ? 8 : 4;
 
@@ -333,6 +349,27 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     const size_t ncx = nxh + nyh + nxh + g.ny, nr = nxh + g.ny;
     ALLOC(tab, (ncx * 2 + nr) * eb);
     p.tables = tab;
+    if (!s->hz.empty()) {
+      // variable zeta-step tables: slab thicknesses in the arithmetic type, plane positions
+      void* hzt = nullptr;
+      double* zpd = nullptr;
+      ALLOC(hzt, (size_t)g.nzeta * eb);
+      ALLOC(zpd, (size_t)(g.nzeta + 1) * sizeof(double));
+      std::vector<unsigned char> hb((size_t)g.nzeta * eb);
+      for (int n = 0; n < g.nzeta; ++n) {
+        if (eb == 8) ((double*)hb.data())[n] = s->hz[n];
+        else ((float*)hb.data())[n] = (float)s->hz[n];
+      }
+      e = cudaMemcpyAsync(hzt, hb.data(), hb.size(), cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(zpd, s->zp.data(), s->zp.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, s->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+      if (e != cudaSuccess) goto fail;
+      p.hzt = hzt;
+      p.zpd = zpd;
+      p.varh = 1;
+    }
     // twiddles and shifts in FP64 on the host
     std::vector<double> t(ncx * 2 + nr);
     size_t o = 0;
@@ -407,7 +444,8 @@ gempic_status gempic_add_particles(gempic_sim* s, int64_t n, const double* x, co
   if (s->p.ny > 1 && n > 0 && !y) return GEMPIC_EINVAL;
   for (int64_t i = 0; i < n; ++i) {
     if (species[i] < 0 || species[i] >= std::max(1, s->p.nspecies)) return GEMPIC_EINVAL;
-    if (!(zeta[i] > 0) || !(zeta[i] <= s->p.nz * s->p.h)) return GEMPIC_EINVAL;
+    const double L = s->zp.empty() ? s->p.nz * s->p.h : s->zp.back();
+    if (!(zeta[i] > 0) || !(zeta[i] <= L)) return GEMPIC_EINVAL;
   }
   for (int64_t i = 0; i < n; ++i) {
     s->px.push_back(x[i]);
@@ -453,6 +491,7 @@ gempic_status gempic_set_delta(gempic_sim* s, double delta) {
   c.delta = delta;
   c.species = s->species;
   c.channel = s->has_channel ? &s->channel : nullptr;
+  c.hz = s->hz.empty() ? nullptr : s->hz.data();
   Params t = s->p;
   st = gempic::setup_species(&c, t);
   if (st != GEMPIC_OK) return st;
@@ -587,7 +626,7 @@ gempic_status gempic_get_particles(gempic_sim* s, int32_t kind, int64_t* n_inout
       const int ix = c & 1023, iy = (c >> 10) & 1023, sp = (c >> 20) & 3;
       if (x) x[o] = (ix + val(0, e2)) * p.hx;
       if (y) y[o] = p.ny > 1 ? (iy + val(1, e2)) * p.hy : 0.0;
-      if (zeta) zeta[o] = (b + val(2, e2)) * p.h;
+      if (zeta) zeta[o] = s->zp.empty() ? (b + val(2, e2)) * p.h : s->zp[b] + val(2, e2) * s->hz[b];
       if (ux) ux[o] = val(3, e2);
       if (uy) uy[o] = val(4, e2);
       if (uz) uz[o] = val(5, e2);

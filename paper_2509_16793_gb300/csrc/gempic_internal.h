@@ -56,6 +56,9 @@ struct Params {
   int P;                          // concurrent marches (clusters)
   int inject, diag, snapshot;
   int gt1;                        // particle law: 0 = GT2 (Eq. trap2), 1 = GT1 (Eq. trap1)
+  int varh;                       // 1: slab thicknesses from hzt (variable zeta-step)
+  const void* hzt;                // [nz] slab thickness h_n (slab n: planes n, n+1), real type
+  const double* zpd;              // [nz+1] plane positions zeta_n (plane 0 at the back)
   int pcap;                       // streaming particle slots per CTA in shared memory
   int fcap;                       // entries of the free-slot stack (slots freed and not yet
                                   // reused; further freed slots stay empty this s-step)

@@ -1725,7 +1725,7 @@ __device__ __forceinline__ void warp_diag_add(double* dwarp, int slot, V v) {
 
 template <typename T>
 __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const T* Fn1,
-                             long long k, int n, int me, int cnt_raw) {
+                             long long k, int n, int me, int cnt_raw, bool varh) {
   T dkin = T(0);
   int dsto = 0, dlost = 0;
   const int s1 = (int)(((k + 1) % p.ring + p.ring) % p.ring);
@@ -1774,24 +1774,58 @@ __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const
         P.fy = Y - fY;
       }
       const T Z = fz - D * gamma_minus_uz(un, gn) / vd * invh;
-      const T cZ = ceil(Z) - T(1);
-      m = n + (int)cZ;
-      fz = Z - cZ;
+      const T* hz = (const T*)p.hzt;
+      if (varh) {
+        // variable zeta-step: walk down the slabs from plane n (moves are backwards)
+        T za = Z * h;                           // distance above plane n
+        m = n;
+        while (za <= T(0) && m > 0) {
+          --m;
+          za += hz[m];
+        }
+        while (m < p.nz - 1 && za > hz[m]) {
+          za -= hz[m];
+          ++m;
+        }
+        fz = za / hz[m];
+        if (za <= T(0)) m = -1;
+      } else {
+        const T cZ = ceil(Z) - T(1);
+        m = n + (int)cZ;
+        fz = Z - cZ;
+      }
       if (m < 0) {                              // left the box at the back
         ++dlost;
         continue;
       }
       // beam current of the next level j = Q u/(gamma hx hy h), CIC across, linear in zeta
-      const T amp = P.q * s.cst[K_BEAM] / gn;
-      const T tz = fz - T(0.5);
-      const T ftz = floor(tz);
-      const int i0 = m + (int)ftz;
-      const T f = tz - ftz;
+      // between half-slice centres; with a variable step the centres are zeta_i + h_i/2 and
+      // half-slice i divides by its own thickness
+      const T amp = varh ? P.q / (T(p.hx * p.hy) * gn) : P.q * s.cst[K_BEAM] / gn;
+      int i0;
+      T f;
+      if (varh) {
+        const T hm = hz[m];
+        if (fz >= T(0.5)) {
+          const T hu = m + 1 < p.nz ? hz[m + 1] : hm;
+          i0 = m;
+          f = (fz - T(0.5)) * hm / (T(0.5) * (hm + hu));
+        } else {
+          const T hd = m > 0 ? hz[m - 1] : hm;
+          i0 = m - 1;
+          f = (T(0.5) * hd + fz * hm) / (T(0.5) * (hd + hm));
+        }
+      } else {
+        const T tz = fz - T(0.5);
+        const T ftz = floor(tz);
+        i0 = m + (int)ftz;
+        f = tz - ftz;
+      }
       T* jb = (T*)p.jbeam;
       for (int t = 0; t < 2; ++t) {
         const int iz = i0 + t;
         if (iz < 0 || iz >= p.nz) continue;
-        const T a = amp * (t == 0 ? T(1) - f : f);
+        const T a = amp * (t == 0 ? T(1) - f : f) / (varh ? hz[iz] : T(1));
         T* base = jb + (((size_t)s2 * p.nz + iz) * 3) * (size_t)p.nx * p.ny;
         const T vals[3] = {a * un.x, a * un.y, a * un.z};
         for (int c = 0; c < 3; ++c) {
@@ -1907,8 +1941,11 @@ __device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
 template <typename T, bool CANON = false, int SH = 0>
 __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& cl, long long k,
                       int cid) {
-  // the 128 x 128 instantiation is compiled for GT2 only (GT1 runs take the generic one)
+  // the 128 x 128 instantiation is compiled for GT2 and a uniform zeta-step only (other runs
+  // take the generic one)
   constexpr int LAW = SH == 1 ? 0 : -1;
+  const bool varh = SH != 1 && p.varh != 0;
+  const T* hzt = (const T*)p.hzt;
   const int me = (int)cl.block_rank();
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
@@ -2048,6 +2085,22 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
 #ifdef GEMPIC_PHASE_TIMERS
     const long long t_slice = clock64();
 #endif
+    // variable zeta-step: the slab of this slice (planes n, n+1) sets the step-dependent
+    // constants (the previous slice's stored phase has finished reading them)
+    const T hn = varh ? hzt[n] : h;
+    if (varh) {
+      __syncthreads();
+      if (tid == 0) {
+        T* c = s.cst;
+        c[K_H] = hn;
+        c[K_INVH] = T(1) / hn;
+        c[K_CX] = T(p.hx) / hn;
+        c[K_CY] = T(p.hy) / hn;
+        c[K_FLUX] = T(p.hx * p.hy) * hn;
+        c[K_BEAM] = T(1) / (T(p.hx * p.hy) * hn);
+      }
+      __syncthreads();
+    }
     // ---------------- A: streaming push from plane n+1 to plane n -----------------------
     SliceAcc<T> sa{T(0), T(0), 0};
     int ntrap = 0, nrej = 0;
@@ -2058,7 +2111,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         if (cw < 0) continue;
         PState<T> P = get_particle(p, s, ov, i, cw);
         T fzt;
-        const bool trap = stream_push<T, LAW>(p, s, Fcur, P, h, me, fzt, sa);
+        const bool trap = stream_push<T, LAW>(p, s, Fcur, P, hn, me, fzt, sa);
         bool gone = trap;
         if (trap) {
           ++ntrap;
@@ -2108,7 +2161,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         PState<T> P = store_read<T>(p.rq, p, ge, fz);
         ++nrej;
         T fzt;
-        const bool trap = stream_push<T, LAW>(p, s, Fcur, P, fz * h, me, fzt, sa);
+        const bool trap = stream_push<T, LAW>(p, s, Fcur, P, fz * hn, me, fzt, sa);
         if (trap) {
           ++ntrap;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
@@ -2132,7 +2185,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     }
     if (p.diag) {
       warp_diag_add(s.dwarp, DG_KIN, sa.kin);
-      warp_diag_add(s.dwarp, DG_FLUX, sa.flux);
+      warp_diag_add(s.dwarp, DG_FLUX, varh ? sa.flux * hn : sa.flux);
       int cnts[3] = {sa.push, ntrap, nrej};
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -2425,7 +2478,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       if (masked) {
         S0.Rx = S0.Ry = S0.Lx = S0.Ly = S0.Ez = S0.Bz = cx<T>(T(0), T(0));
       } else {
-        S0 = slice_solve(kx, ky, h, Dl, S1, o[0], o[1], o[2], o[3], j0mx, j0my, j0px, j0py, Jx,
+        S0 = slice_solve(kx, ky, hn, Dl, S1, o[0], o[1], o[2], o[3], j0mx, j0my, j0px, j0py, Jx,
                          Jy, Jz);
       }
       // fields E, B (Eqs. Rx..Ly) for the inverse transform
@@ -2471,7 +2524,11 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     }
     TIMER_MARK(PH_B3);
     // ---------------- D: inverse rows -> real-space fields of slice n ----------------------
-    inverse_rows<T, SH>(p, s, Fnew, fe);
+    {
+      T fs = T(0);
+      inverse_rows<T, SH>(p, s, Fnew, fs);
+      fe += varh ? fs * hn : fs;
+    }
     TIMER_MARK(PH_INV);
     if constexpr (sizeof(T) == 4) {
       // SR has been consumed: it holds the fixed-point accumulators of the next push
@@ -2496,7 +2553,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       }
     }
     // ---------------- E: stored particles of cell (zeta_n, zeta_{n+1}] along s -------------
-    stored_phase(p, s, Fnew, Fcur, k, n, me, s.misc[M_STN]);
+    stored_phase(p, s, Fnew, Fcur, k, n, me, s.misc[M_STN], varh);
     TIMER_MARK(PH_E);
     T* t = Fcur;
     Fcur = Fnew;
@@ -2515,8 +2572,10 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     if (tid < kNDiag) {
       double v = 0.0;
       for (int w = 0; w < (NT >> 5); ++w) v += s.dwarp[w * kNDiag + tid];
-      const double hv = tid == DG_FIELD ? 0.5 * p.hx * p.hy * p.h
-                        : tid == DG_FLUX ? p.hx * p.hy * p.h
+      // variable zeta-step: each slice's sums were weighted by its slab thickness
+      const double hw = p.varh ? 1.0 : p.h;
+      const double hv = tid == DG_FIELD ? 0.5 * p.hx * p.hy * hw
+                        : tid == DG_FLUX ? p.hx * p.hy * hw
                                          : 1.0;
       p.diag_out[((size_t)sl * kNDiag + tid) * p.C + me] = v * hv;
     }
@@ -2581,7 +2640,7 @@ __global__ void __launch_bounds__(512, 1)
   const double xc = 0.5 * p.nx * p.hx, yc = 0.5 * p.ny * p.hy;
   const int plane = p.RB * p.nx;
   for (int n = cid; n < p.nz; n += ncl) {
-    const double phi = n * p.h - zc;
+    const double phi = (p.varh ? p.zpd[n] : n * p.h) - zc;
     const double env = a0 * cos(phi) * exp(-phi * phi / (dur * dur));
     for (int i = threadIdx.x; i < 3 * plane; i += blockDim.x) {
       const int c = i / plane;
@@ -2688,7 +2747,8 @@ int smem_layout(Params& p, int eb) {
 // kernel instantiation for the grid: 1 = FP32 128 x 128 with an even band (length-128
 // transforms only), 0 = any size
 static int shape_class(int precision, const Params& p) {
-  return precision == 32 && p.nx == 128 && p.ny == 128 && (p.RB & 1) == 0 && !p.gt1 ? 1 : 0;
+  return precision == 32 && p.nx == 128 && p.ny == 128 && (p.RB & 1) == 0 && !p.gt1 && !p.varh
+             ? 1 : 0;
 }
 
 // The dynamic shared-memory limit is an attribute of the kernel function, shared by every

@@ -67,6 +67,7 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
   if (g.nzeta < 2 || g.nzeta > kMaxNzeta) return GEMPIC_EINVAL;
   if (!(g.hx > 0) || !(g.hy > 0) || !(g.h > 0) || !(cfg->delta >= 0)) return GEMPIC_EINVAL;
   if (cfg->precision != 32 && cfg->precision != 64) return GEMPIC_EINVAL;
+  if (cfg->hz) return GEMPIC_EINVAL;               // uniform zeta-step only
   const int eb = cfg->precision == 64 ? 8 : 4;
   const size_t need = (size_t)6 * g.nzeta * g.ny * (g.nx / 2) * 2 * eb;
   if (state_bytes < need) return GEMPIC_EINVAL;

@@ -28,6 +28,17 @@ inline gempic_status setup_species(const gempic_config* cfg, Params& p) {
     ir2 = 1.0 / (ch.radius * ch.radius);
   }
   const double fmax = std::max(1.0, 1.0 + a);   // f is largest on the axis or far from it
+  // zeta-step: the largest slab bounds stability, the smallest sets the fixed-point range
+  double hmax = g.h, hmin = g.h;
+  if (cfg->hz) {
+    hmax = 0.0;
+    hmin = INFINITY;
+    for (int n = 0; n < g.nzeta; ++n) {
+      if (!(cfg->hz[n] > 0) || !std::isfinite(cfg->hz[n])) return GEMPIC_EINVAL;
+      hmax = std::max(hmax, cfg->hz[n]);
+      hmin = std::min(hmin, cfg->hz[n]);
+    }
+  }
   double wp2 = 0.0, wmax = 0.0;
   int ppc_sum = 0, off = 0;
   for (int i = 0; i < cfg->nspecies; ++i) {
@@ -45,7 +56,7 @@ inline gempic_status setup_species(const gempic_config* cfg, Params& p) {
     p.poff[i] = off;
     off += g.nx * g.ny * sp.ppc;
   }
-  if (cfg->delta * g.h * wp2 * fmax > 4.0 * (1.0 + 1e-12)) return GEMPIC_EUNSTABLE;
+  if (cfg->delta * hmax * wp2 * fmax > 4.0 * (1.0 + 1e-12)) return GEMPIC_EUNSTABLE;
   p.nspecies = cfg->nspecies;
   p.nlayer = off;
   p.ppc_sum = ppc_sum;
@@ -53,7 +64,7 @@ inline gempic_status setup_species(const gempic_config* cfg, Params& p) {
   p.chan_ir2 = ir2;
   // fixed-point range of the FP32 deposit: 4 x the largest (rho - j_z) weight times the
   // largest transverse cell-to-slice ratio; a larger contribution takes the float path
-  const double ratio = std::max(1.0, std::max(g.hx, g.hy) / g.h);
+  const double ratio = std::max(1.0, std::max(g.hx, g.hy) / hmin);
   p.jref = wmax > 0 ? 4.0 * wmax * fmax * ratio : 1.0;
   return GEMPIC_OK;
 }

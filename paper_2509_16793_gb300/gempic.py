@@ -59,7 +59,7 @@ class gempic_config(Structure):
                 ("laser", POINTER(gempic_laser)), ("stored_bucket_capacity", c_int32),
                 ("particle_headroom", c_int32), ("pipeline_depth", c_int32),
                 ("reserved", c_int32), ("cuda_stream", c_void_p),
-                ("channel", POINTER(gempic_channel))]
+                ("channel", POINTER(gempic_channel)), ("hz", POINTER(c_double))]
 
 
 class gempic_diag(Structure):
@@ -150,6 +150,11 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
     if w.laser is not None:
         L = w.laser
         las = gempic_laser(L.a0, L.waist, L.duration, L.zeta_center, L.pol, 0)
+    hz = None
+    if w.hz is not None:
+        hz = np.ascontiguousarray(w.hz, dtype=np.float64)
+        if hz.shape != (w.nzeta,):
+            raise ValueError("hz holds nzeta slab thicknesses")
     ch = None
     if w.channel is not None:
         ch = gempic_channel(w.channel.n1_over_n0, w.channel.radius)
@@ -166,8 +171,9 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
         laser=ctypes.pointer(las) if las is not None else None,
         stored_bucket_capacity=bucket_capacity, particle_headroom=headroom,
         pipeline_depth=pipeline_depth, reserved=0, cuda_stream=stream,
-        channel=ctypes.pointer(ch) if ch is not None else None)
-    return cfg, (sp, las, ch)
+        channel=ctypes.pointer(ch) if ch is not None else None,
+        hz=hz.ctypes.data_as(POINTER(c_double)) if hz is not None else None)
+    return cfg, (sp, las, ch, hz)
 
 
 def gempic_step_noalloc(w, step: int, state, onaxis: bool = False, stream: Optional[int] = None,

@@ -102,6 +102,7 @@ class Workload:
     snapshot: bool = False       # keep real-space fields of the last s-step
     channel: Optional[Channel] = None   # None: uniform density
     particle_law: str = "GT2"    # "GT2" (Eq. trap2, s~ = z) or "GT1" (Eq. trap1, s = ct)
+    hz: Optional[np.ndarray] = None     # nzeta slab thicknesses (back to front); None: h
 
     @property
     def ncells(self) -> int:
@@ -118,6 +119,16 @@ class Workload:
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
+
+
+def refined_h(nzeta: int, h_front: float, ratio: float, back_fraction: float = 1.0 / 3.0,
+              width: float = 0.1) -> np.ndarray:
+    """Slab thicknesses refined at the back of the window (Sec. 6: 6.3 nm over the back third,
+    where the bubble's back wall sits, 50 nm in front): h_front / ratio behind, h_front in
+    front, joined smoothly by a tanh over `width` of the window.  Index 0 is the back slab."""
+    x = (np.arange(nzeta) + 0.5) / nzeta
+    t = 0.5 * (1.0 + np.tanh((x - back_fraction) / width))
+    return h_front / ratio + (h_front - h_front / ratio) * t
 
 
 def fwhm_to_T(fwhm_intensity: float) -> float:

@@ -584,3 +584,68 @@ def test_variable_delta_keeps_the_density(law):
         assert abs(d["charge_flux"] - exact) <= 1e-12 * abs(exact)
     with pytest.raises(ValueError):
         sim.set_delta(1.01 * w.delta)                 # above the stability bound
+
+
+# ---- variable zeta-step h(zeta) (Sec. 6: refined back of the window) ------------------------
+def test_variable_h_table_of_equal_steps_is_the_uniform_grid():
+    w = W.small_2d(nx=16, nzeta=40, ppc=2, a0=2.0, delta=1.5)
+    a = R.RefSim(w)
+    b = R.RefSim(w.with_(hz=np.full(w.nzeta, w.h)))
+    for _ in range(3):
+        da, db = a.step(), b.step()
+        for k in ("n_trapped", "n_stored", "n_rejoined"):
+            assert da[k] == db[k]
+        for k in ("field_energy", "kinetic_energy", "charge_flux"):
+            assert abs(da[k] - db[k]) <= 1e-12 * abs(da[k])
+    assert da["n_trapped"] > 0
+    sa, sb = a.state(), b.state()
+    for c in range(6):
+        assert np.abs(sa[c] - sb[c]).max() <= 1e-11 * max(np.abs(sa[c]).max(), 1e-300)
+
+
+def test_variable_h_linear_wake():
+    """P8 on a grid refined by 2 over the back third (tanh transition): the wake behind a weak
+    pulse follows 1-D linear theory integrated on the same planes, to 5 % of its amplitude."""
+    n0, hf, a0, T = 0.01, 0.1, 0.05, 8.0
+    nz = 1700
+    hz = W.refined_h(nz, hf, 2.0)
+    zp = np.concatenate([[0.0], np.cumsum(hz)])
+    L = zp[-1]
+    zc = L - 3.2 * T
+    w = W.Workload(name="wake1d_var", nx=4, ny=1, nzeta=nz, hx=1.0, hy=1.0, h=hf, delta=1.0,
+                   species=[W.Species(-1.0, 1.0, n0, 4)],
+                   laser=W.Laser(a0=a0, waist=1e9, duration=T, zeta_center=zc), hz=hz)
+    sim = R.RefSim(w)
+    d = sim.step()
+    ez = d["onaxis_ez"]
+    ex = sim.fields_rs[:, 0, 0, 0]
+    A = -np.cumsum((ex * hz)[::-1])[::-1]                  # A(zeta_n) = -int_{zeta_n}^inf E_x
+    kp2 = n0
+    psi = np.zeros(nz + 1)
+    dpsi = 0.0
+    ezl = np.zeros(nz)
+    for n in range(nz - 1, -1, -1):
+        dpsi += hz[n] * kp2 * (0.5 * A[n] ** 2 - psi[n + 1])
+        psi[n] = psi[n + 1] + hz[n] * dpsi
+        ezl[n] = dpsi
+    behind = zp[:-1] < zc - 2.5 * T
+    scale = np.abs(ezl[behind]).max()
+    assert scale > 1e-5
+    assert np.abs(ez[behind] - ezl[behind]).max() < 0.05 * scale
+    # the same theory on a uniform grid of the front step would misplace the back of the wake
+    assert np.abs(ezl[behind][:200]).max() > 0.2 * scale
+
+
+def test_variable_h_charge_flux_and_stability():
+    """(rho - j_z) = q n on every plane: the charge flux of an s-step is q n A sum(h_n); the
+    stability bound takes the largest slab."""
+    w = W.small_2d(nx=16, nzeta=48, ppc=2, a0=0.5)
+    hz = W.refined_h(w.nzeta, w.h, 3.0)
+    sim = R.RefSim(w.with_(hz=hz))
+    d = sim.step()
+    sp = w.species[0]
+    exact = sp.charge * sp.density * (w.nx * w.hx) * w.hy * hz.sum()
+    assert d["n_trapped"] == 0
+    assert abs(d["charge_flux"] - exact) <= 1e-12 * abs(exact)
+    with pytest.raises(ValueError):
+        R.RefSim(w.with_(hz=hz * 1.01 * w.h / hz.max()))   # largest slab just above the bound

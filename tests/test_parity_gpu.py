@@ -542,3 +542,94 @@ def test_gt1_fp32_bench_grid_takes_the_generic_kernel():
         assert np.abs(ez - oez).max() <= 1e-4 * np.abs(oez).max()
         for key in ("field_energy", "kinetic_energy"):
             assert abs(gd[key] - od[key]) <= 1e-4 * abs(od[key]), key
+
+
+# ---- variable zeta-step h(zeta) (Sec. 6) ------------------------------------------------------
+def test_variable_h_2d_fp64_with_trapping():
+    w = W.small_2d(nx=16, nzeta=96, ppc=2, precision=64, a0=2.0, delta=1.5)
+    w = w.with_(hz=W.refined_h(w.nzeta, w.h, 2.0))
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        for _ in range(3):
+            od = o.step()
+            g.step()
+            check_diag(g.diagnostics(), od, 1e-9)
+            check_state(g.state(), o.state(), 1e-9)
+        assert od["n_trapped"] > 0 and od["n_rejoined"] > 0
+        oc = copy.deepcopy(o)
+        rejoin, _, _ = oc._stored_push()
+        compare_particles(g.particles(0), oc.stored_particles(), 1e-9)
+        compare_particles(g.particles(1), dict(x=rejoin.x, y=rejoin.y, zeta=rejoin.zeta,
+                                               ux=rejoin.u[0], uy=rejoin.u[1], uz=rejoin.u[2],
+                                               weight=rejoin.Q), 1e-9)
+
+
+@pytest.mark.parametrize("C", [1, 2])
+def test_variable_h_3d_fp64_with_beam(C):
+    w = W.small_3d(nx=16, ny=16, nzeta=48, ppc=1, precision=64, a0=0.5)
+    w = w.with_(hz=W.refined_h(w.nzeta, w.h, 3.0))
+    zp = np.concatenate([[0.0], np.cumsum(w.hz)])
+    beam = W.gaussian_bunch(w, n_macro=2000, n_peak=0.05, sigma_r=2.0, sigma_z=2.0,
+                            zeta_center=0.4 * zp[-1], gamma=200.0, rel_spread=1e-3)
+    w = w.with_(stored=beam)
+    o = RefSim(w)
+    with gpu_sim(w, cluster_ctas=C) as g:
+        for _ in range(2):
+            od = o.step()
+            g.step()
+            check_diag(g.diagnostics(), od, 1e-10)
+            check_state(g.state(), o.state(), 1e-10)
+        oc = copy.deepcopy(o)
+        oc._stored_push()
+        compare_particles(g.particles(0), oc.stored_particles(), 1e-10)
+
+
+@pytest.mark.parametrize("n", [32, 128])
+def test_variable_h_fp32_matches_oracle(n):
+    """FP32, generic kernel (the 128 x 128 kernel is compiled for a uniform step)."""
+    w = W.small_3d(nx=n, ny=n, nzeta=48, ppc=2, precision=32)
+    w = w.with_(hz=W.refined_h(w.nzeta, w.h, 2.0))
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        g.step(2)
+        for _ in range(2):
+            od = o.step()
+        gd = g.diagnostics()
+        ez, oez = g.onaxis_ez(), od["onaxis_ez"]
+        assert np.abs(ez - oez).max() <= 1e-4 * np.abs(oez).max()
+        for key in ("field_energy", "kinetic_energy", "charge_flux"):
+            assert abs(gd[key] - od[key]) <= 1e-4 * abs(od[key]), key
+
+
+def test_variable_h_equal_steps_equal_the_uniform_grid():
+    w = W.small_2d(nx=32, nzeta=48, ppc=2, precision=64, a0=1.5, delta=2.0)
+    with gpu_sim(w) as a, gpu_sim(w.with_(hz=np.full(w.nzeta, w.h))) as b:
+        a.step(3)
+        b.step(3)
+        sa, sb = a.state(), b.state()
+        fs = max(np.abs(sa[c]).max() for c in range(4))
+        js = max(np.abs(sa[c]).max() for c in (4, 5))
+        for c in range(6):
+            assert np.abs(sa[c] - sb[c]).max() <= 1e-11 * (fs if c < 4 else js), c
+        da, db = a.diagnostics(), b.diagnostics()
+        for k in ("n_trapped", "n_stored", "n_rejoined", "pushes"):
+            assert da[k] == db[k], k
+
+
+def test_variable_h_invalid_tables_are_rejected():
+    import torch
+    from paper_2509_16793_gb300 import gempic
+    w = W.small_2d(nx=16, nzeta=32, ppc=2, precision=64)
+    bad = np.full(w.nzeta, w.h)
+    bad[5] = 0.0
+    with pytest.raises(gempic.GempicError) as e:
+        gempic.Sim(w.with_(hz=bad))
+    assert e.value.status == -1
+    big = np.full(w.nzeta, w.h)
+    big[-1] = 1.5 * w.h                                   # largest slab above the bound
+    with pytest.raises(gempic.GempicError) as e:
+        gempic.Sim(w.with_(hz=big))
+    assert e.value.status == -4
+    state = torch.zeros(6 * w.nzeta * (w.nx // 2), dtype=torch.complex128, device="cuda")
+    st, _, _ = gempic.gempic_step_noalloc(w.with_(hz=np.full(w.nzeta, w.h)), 0, state)
+    assert st == -1

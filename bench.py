@@ -189,7 +189,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="gempic", choices=["gempic", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3, help="0 skips the end-to-end leg")
+    ap.add_argument("--e2e-steps", type=int, default=10, help="0 skips the end-to-end leg")
     ap.add_argument("--nzeta", type=int, default=0,
                     help="profiling only: shorter window of the same workload")
     ap.add_argument("--pipeline", type=int, default=0, help="s-steps marched concurrently (0 = auto)")
@@ -197,6 +197,8 @@ def main():
     ap.add_argument("--workload", default="lwfa3d", choices=["lwfa3d", "scan"],
                     help="lwfa3d: the 3-D LWFA (default); scan: the batched 2-D parameter scan")
     ap.add_argument("--instances", type=int, default=64, help="scan: number of instances")
+    ap.add_argument("--fp64-steps", type=int, default=40,
+                    help="s-steps of the FP64-plain comparison on the 2-D workload (0 skips it)")
     args = ap.parse_args()
     if args.workload == "scan" and args.impl == "gempic":
         return run_scan(args)
@@ -296,6 +298,18 @@ def main():
             "kernel": "march_kernel<float>",
             "hbm": {"achieved": hbm, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                     "frac": hbm / peaks.get("hbm_gbs", 6800.0), "of": "measured"}}
+    # the metric's FP32-vs-FP64-plain comparison: the 2-D FP64 workload (128 x 256, 4 ppc, Delta
+    # at the stability limit) in FP64 and, on the same grid, in FP32
+    fp64 = None
+    if args.fp64_steps > 0:
+        from paper_2509_16793_gb300 import workloads as W
+        w2 = W.lwfa_2d_128x256(precision=64)
+        v64, ms64 = time_plain(w2, args.fp64_steps, 3, stream)
+        v32, ms32 = time_plain(w2.with_(precision=32), args.fp64_steps, 3, stream)
+        fp64 = {"workload": w2.name, "steps": args.fp64_steps,
+                "fp64": {"value": v64, "ms_per_step": ms64},
+                "fp32": {"value": v32, "ms_per_step": ms32},
+                "unit": "pushes/s", "fp32_over_fp64": v32 / v64}
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -311,7 +325,7 @@ def main():
             "e2e": {"value": e2e_value if math.isfinite(e2e_value) else None,
                     "unit": "pushes/s", "h2d_bytes_per_step": nb,
                     "d2h_bytes_per_step": nb + 64},
-            "gpu_launches": launches, "clocks": clocks,
+            "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64,
             "diag": {k: diag[k] for k in ("field_energy", "kinetic_energy", "n_stored", "pushes")}}
     print(json.dumps(line), flush=True)
     sim.close()
@@ -319,6 +333,25 @@ def main():
         torch.distributed.barrier()
         torch.distributed.destroy_process_group()
     return 0
+
+
+def time_plain(w, steps: int, warmup: int, stream):
+    """Device time of `steps` s-steps of workload w in one call (CUDA events on the stream the
+    library launches on): (pushes/s, ms per step)."""
+    import torch
+    from paper_2509_16793_gb300 import gempic
+    with gempic.Sim(w, stream=stream.cuda_stream) as sim:
+        sim.step(warmup)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step_async(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sim.sync()
+        ms = e0.elapsed_time(e1)
+    return w.pushes_per_step * steps / (ms / 1e3), ms / steps
 
 
 def measured_traffic(w):

@@ -124,6 +124,29 @@ def dist_env():
     return rank, world, local
 
 
+def replica_workload(w, rank: int):
+    """Replicas: rank r simulates its own plasma (seed offset r) on its own GPU; there is no
+    data-path collective, so per-rank work is fixed as ranks are added (weak scaling)."""
+    return w.with_(seed=w.seed + rank)
+
+
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank sets the job's time: max of a per-rank float over the process group
+    (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def oracle_sample(w, seconds: float, max_steps: int):
     """Time the FP64 oracle on a bounded sample of the workload: the same transverse grid and
     particles per cell over a 64-slice window; pushes/s extrapolate per slice."""
@@ -227,7 +250,7 @@ def main():
         torch.distributed.barrier()
     stream = torch.cuda.current_stream()
     # replicas: each rank simulates its own plasma (seed offset), no data-path collective
-    wr = w.with_(seed=w.seed + rank)
+    wr = replica_workload(w, rank)
     sim = gempic.Sim(wr, stream=stream.cuda_stream, pipeline_depth=args.pipeline,
                      bucket_capacity=args.bucket_capacity)
     shape = sim.launch_shape()
@@ -247,13 +270,9 @@ def main():
             torch.distributed.barrier()
     sim.sync()
     launches = sim.launch_count() - launches0
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), "cuda")
     ms_step = ms / args.steps
-    value = world * w.pushes_per_step * args.steps / (ms / 1e3)
+    value = job_rate(w.pushes_per_step * args.steps, world, ms / 1e3)
     diag = sim.diagnostics()
 
     # end to end through the C-ABI with host buffers: the spectral state comes in from pinned
@@ -271,11 +290,8 @@ def main():
             sim.gempic_step_host(1, hin.numpy(), hout.numpy())
             hin, hout = hout, hin
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * w.pushes_per_step / e2e_s
+    e2e_s = max_over_ranks(e2e_s, "cuda")
+    e2e_value = job_rate(w.pushes_per_step, world, e2e_s)
 
     if rank != 0:
         sim.close()
@@ -403,11 +419,8 @@ def run_scan(args):
         ms = t1 - t0
         per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
         launches = sum(v.launch_count() for v in b.sims) - launches0
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * pushes * args.steps / (ms / 1e3)
+    ms = max_over_ranks(ms, "cuda")
+    value = job_rate(pushes * args.steps, world, ms / 1e3)
     if rank == 0:
         peaks = measured_peaks()
         peak_alu = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))

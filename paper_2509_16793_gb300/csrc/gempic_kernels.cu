@@ -2081,6 +2081,11 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   }
   __syncthreads();
 
+  // per-thread diagnostic sums, flushed to the warp rows every 16 slices (a warp reduction
+  // per slice costs more than the push of a particle)
+  SliceAcc<T> sa{T(0), T(0), 0};
+  int ntrap = 0, nrej = 0;
+  T fluxw = T(0);                                  // variable zeta-step: flux weighted by h_n
   for (int n = nz - 1; n >= 0; --n) {
 #ifdef GEMPIC_PHASE_TIMERS
     const long long t_slice = clock64();
@@ -2102,8 +2107,6 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       __syncthreads();
     }
     // ---------------- A: streaming push from plane n+1 to plane n -----------------------
-    SliceAcc<T> sa{T(0), T(0), 0};
-    int ntrap = 0, nrej = 0;
     {
       const int cnt0 = s.misc[M_PCOUNT];
       for (int i = tid; i < cnt0; i += NT) {
@@ -2183,9 +2186,13 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         }
       }
     }
-    if (p.diag) {
+    if (varh) {
+      fluxw += sa.flux * hn;
+      sa.flux = T(0);
+    }
+    if (p.diag && (n & 15) == 0) {
       warp_diag_add(s.dwarp, DG_KIN, sa.kin);
-      warp_diag_add(s.dwarp, DG_FLUX, varh ? sa.flux * hn : sa.flux);
+      warp_diag_add(s.dwarp, DG_FLUX, varh ? fluxw : sa.flux);
       int cnts[3] = {sa.push, ntrap, nrej};
 #pragma unroll
       for (int c = 0; c < 3; ++c)
@@ -2196,6 +2203,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         row[DG_TRAP] += (double)cnts[1];
         row[DG_REJOIN] += (double)cnts[2];
       }
+      sa = SliceAcc<T>{T(0), T(0), 0};
+      ntrap = nrej = 0;
+      fluxw = T(0);
     }
     TIMER_MARK(PH_A);
     __syncthreads();

@@ -1725,11 +1725,10 @@ __device__ __forceinline__ void warp_diag_add(double* dwarp, int slot, V v) {
 
 template <typename T>
 __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const T* Fn1,
-                             long long k, int n, int me, int cnt_raw, bool varh) {
+                             int s1, int s2, int n, int me, int cnt_raw, bool varh) {
+  // s1, s2: ring slots of the stored sets at levels k+1 and k+2
   T dkin = T(0);
   int dsto = 0, dlost = 0;
-  const int s1 = (int)(((k + 1) % p.ring + p.ring) % p.ring);
-  const int s2 = (int)(((k + 2) % p.ring + p.ring) % p.ring);
   const int cnt = min(cnt_raw, p.bcap);
   const T D = s.cst[K_D], h = s.cst[K_H], invh = s.cst[K_INVH];
   const int mx = p.nx - 1, my = p.ny - 1;
@@ -2563,7 +2562,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       }
     }
     // ---------------- E: stored particles of cell (zeta_n, zeta_{n+1}] along s -------------
-    stored_phase(p, s, Fnew, Fcur, k, n, me, s.misc[M_STN], varh);
+    // (most cells hold no stored particle: the call is skipped, uniformly over the CTA)
+    if (s.misc[M_STN] > 0) stored_phase(p, s, Fnew, Fcur, s1, s2, n, me, s.misc[M_STN], varh);
     TIMER_MARK(PH_E);
     T* t = Fcur;
     Fcur = Fnew;

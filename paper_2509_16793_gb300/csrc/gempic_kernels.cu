@@ -2419,10 +2419,13 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       }
     }
     TIMER_MARK(PH_BI);
-    __syncthreads();
+    // the inbox drain ends with a barrier that also orders the own-row fold before the beam
+    // add and the row transforms; 2-D runs have no inbox
+    if (p.ny == 1) __syncthreads();
     // beam current of this level at the half-slice n + 1/2 (own rows); the flag is cleared
     // by CTA 0 after B2, once every CTA has read it
-    if (s.misc[M_JFLAG]) {
+    const bool beam_slice = s.misc[M_JFLAG] != 0;
+    if (beam_slice) {
       T* jb = (T*)p.jbeam + (((size_t)s1 * nz + n) * 3) * (size_t)p.nx * p.ny;
       for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
         const int c = i >> (p.logRB + p.lognx);
@@ -2442,7 +2445,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
             s.J[((size_t)c * p.JR + p.JOFF) * p.nx + rem];
       }
     }
-    __syncthreads();
+    if (beam_slice || snap_step) __syncthreads();
     TIMER_MARK(PH_BEAM);
     // ---------------- B: row FFTs of the currents, transposed to the kx owners ------------
     forward_rows<T, SH>(cl, p, s, me, true);

@@ -69,6 +69,15 @@ template <typename T>
 __device__ __forceinline__ T gamma_of(V3<T> u) {   // sqrt(1 + ux^2 + uy^2 + uz^2)
   return sqrt(((T(1) + u.x * u.x) + u.y * u.y) + u.z * u.z);
 }
+// gamma - 1 for the kinetic energy: in FP32 as u^2/(gamma + 1) (sqrt(1 + u^2) - 1 cancels for
+// slow particles); in FP64 as gamma - 1, the form the FP64 reference evaluates
+template <typename T>
+__device__ __forceinline__ T gamma_minus_one(V3<T> u, T g) {
+  if constexpr (sizeof(T) == 4)
+    return ((u.x * u.x + u.y * u.y) + u.z * u.z) / (g + T(1));
+  else
+    return g - T(1);
+}
 // gamma - u_z, as (1 + u_perp^2)/(gamma + u_z) where u_z > 0 (no cancellation).
 template <typename T>
 __device__ __forceinline__ T gamma_minus_uz(V3<T> u, T g) {
@@ -1538,7 +1547,7 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   SUB_MARK(2);
   // diagnostics: kinetic energy N m (gamma-1) dt/Delta, (rho - j_z) flux through plane n
   const T dtl = hden * gn;
-  acc.kin += P.q * s.cst[K_MOQ + P.sp] * (gn - T(1)) * dtl / D;
+  acc.kin += P.q * s.cst[K_MOQ + P.sp] * gamma_minus_one(un, gn) * dtl / D;
   if (!trap) acc.flux += w;
   acc.push += 1;
   // new cell-relative position
@@ -1736,7 +1745,7 @@ __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const
     T fz;
     PState<T> P = store_read<T>(p.st, p, ((size_t)s1 * p.nz + n) * p.bcap + e0, fz);
     const T g = gamma_of(P.u);
-    dkin += P.q * s.cst[K_MOQ + P.sp] * (g - T(1));
+    dkin += P.q * s.cst[K_MOQ + P.sp] * gamma_minus_one(P.u, g);
     ++dsto;
     const T gmu = gamma_minus_uz(P.u, g);
     // stays stored while it moves less than one cell per s-step: GT2 Delta (1 - v_z)/v_z < h,

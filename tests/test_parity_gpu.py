@@ -633,3 +633,38 @@ def test_variable_h_invalid_tables_are_rejected():
     state = torch.zeros(6 * w.nzeta * (w.nx // 2), dtype=torch.complex128, device="cuda")
     st, _, _ = gempic.gempic_step_noalloc(w.with_(hz=np.full(w.nzeta, w.h)), 0, state)
     assert st == -1
+
+
+# ---- maximum sizes -----------------------------------------------------------------------
+@pytest.mark.parametrize("precision,nx", [(64, 512), (32, 1024)])
+def test_largest_transverse_size_2d(precision, nx):
+    """The widest 2-D grids one CTA's shared memory holds: nx = 512 in FP64, 1024 in FP32
+    (radix-2 transforms of that length)."""
+    w = W.small_2d(nx=nx, nzeta=24, ppc=1, precision=precision)
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        for _ in range(2):
+            od = o.step()
+            g.step()
+            gd = g.diagnostics()
+            assert gd["pushes"] == w.pushes_per_step
+            if precision == 64:
+                check_state(g.state(), o.state(), 1e-10)
+                check_diag(gd, od, 1e-10)
+            else:
+                # the on-axis wake of this wide, short window is ~1e-4 of the laser field:
+                # E_z is held to 1e-4 of the field scale a0, the energies to 1e-4 relative
+                ez, oez = g.onaxis_ez(), od["onaxis_ez"]
+                assert np.abs(ez - oez).max() <= 1e-4 * w.laser.a0
+                for key in ("field_energy", "kinetic_energy"):
+                    assert abs(gd[key] - od[key]) <= 1e-4 * abs(od[key]), key
+
+
+def test_beyond_the_largest_sizes_is_rejected():
+    from paper_2509_16793_gb300 import gempic
+    for w in (W.small_3d(nx=256, ny=256, nzeta=16, ppc=1, precision=32),   # 2048 modes per CTA
+              W.small_2d(nx=2048, nzeta=16, ppc=1, precision=32),         # nx above 1024
+              W.small_2d(nx=1024, nzeta=16, ppc=1, precision=64)):        # FP64 planes too big
+        with pytest.raises(gempic.GempicError) as e:
+            gempic.Sim(w)
+        assert e.value.status == -1

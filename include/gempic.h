@@ -37,6 +37,9 @@
 extern "C" {
 #endif
 
+/* Opaque handle of one simulation (created by gempic_create, released by gempic_destroy). */
+struct gempic_sim;
+
 typedef enum {
   GEMPIC_OK = 0,
   GEMPIC_EINVAL = -1,     /* bad argument or unsupported size                              */

@@ -56,6 +56,8 @@ def test_ctypes_layout_matches_c():
              sizeof(gempic_laser), sizeof(gempic_config), sizeof(gempic_diag));
       printf("%zu %zu %zu %zu\n", offsetof(gempic_config, species), offsetof(gempic_config, laser),
              offsetof(gempic_config, pipeline_depth), offsetof(gempic_config, cuda_stream));
+      printf("%zu %zu %zu\n", sizeof(gempic_channel), offsetof(gempic_config, channel),
+             offsetof(gempic_config, hz));
       return 0;
     }
     """
@@ -71,5 +73,43 @@ def test_ctypes_layout_matches_c():
     sizes = [int(v) for v in out]
     assert sizes[:5] == [ctypes.sizeof(t) for t in (G.gempic_grid, G.gempic_species, G.gempic_laser,
                                                      G.gempic_config, G.gempic_diag)]
-    assert sizes[5:] == [G.gempic_config.species.offset, G.gempic_config.laser.offset,
-                         G.gempic_config.pipeline_depth.offset, G.gempic_config.cuda_stream.offset]
+    assert sizes[5:9] == [G.gempic_config.species.offset, G.gempic_config.laser.offset,
+                          G.gempic_config.pipeline_depth.offset, G.gempic_config.cuda_stream.offset]
+    assert sizes[9:] == [ctypes.sizeof(G.gempic_channel), G.gempic_config.channel.offset,
+                         G.gempic_config.hz.offset]
+
+
+def test_plain_c_caller_links_and_runs(built):
+    """The boundary is usable from C alone: a C99 program compiled against include/gempic.h
+    with warnings as errors links libgempic.so and makes calls that need no GPU (argument
+    checks happen before any CUDA call)."""
+    src = r"""
+    #include <stdio.h>
+    #include <string.h>
+    #include "gempic.h"
+    int main(void) {
+      struct gempic_sim* sim = NULL;
+      gempic_config c;
+      gempic_status st;
+      memset(&c, 0, sizeof c);
+      c.grid.nx = 100; c.grid.ny = 1; c.grid.nzeta = 16;     /* nx not a power of two */
+      c.grid.hx = 1.0; c.grid.hy = 1.0; c.grid.h = 0.1; c.precision = 32;
+      st = gempic_create(&c, &sim);
+      printf("%d %d %s\n", (int)st, sim == NULL, gempic_strerror(st));
+      gempic_destroy(NULL);
+      return 0;
+    }
+    """
+    libdir = os.path.dirname(built)
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "caller.c")
+        exe = os.path.join(d, "caller")
+        open(c, "w").write(src)
+        r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                            "-I", os.path.join(ROOT, "include"), c, "-o", exe,
+                            built, "-Wl,-rpath," + libdir], capture_output=True, text=True)
+        assert r.returncode == 0, r.stderr
+        out = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert out.returncode == 0, out.stderr
+    st, null, msg = out.stdout.split(maxsplit=2)
+    assert st == "-1" and null == "1" and "invalid argument" in msg

@@ -668,3 +668,25 @@ def test_beyond_the_largest_sizes_is_rejected():
         with pytest.raises(gempic.GempicError) as e:
             gempic.Sim(w)
         assert e.value.status == -1
+
+
+def test_bench_workload_full_size_initial_state_matches_oracle():
+    """The bench workload at its full size (128 x 128 x 1024, FP32) in the launch shape the
+    bench times: the level-0 set-up (laser laid as a forward wave, then a Delta = 0 march over
+    all 1024 slices through the row/column transforms and the per-mode solve) against the
+    oracle's, every mode of every slice."""
+    w = W.lwfa_3d_128x128x1024()
+    o = RefSim(w)
+    ref = o.state()
+    with gpu_sim(w) as g:
+        shape = g.launch_shape()
+        assert shape["cluster_ctas"] == 16 and shape["threads"] == 512 and shape["pipeline"] == 7
+        st = g.state()
+    fs = max(np.abs(ref[c]).max() for c in range(4))
+    for c, name in enumerate(COMPS):
+        scale = np.abs(ref[c]).max()
+        err = np.abs(st[c] - ref[c]).max()
+        if scale > 0:
+            assert err <= 1e-4 * scale, (name, err, scale)
+        else:
+            assert err <= 1e-4 * fs, (name, err)

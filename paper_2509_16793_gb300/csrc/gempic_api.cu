@@ -261,7 +261,7 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
   p.delta = cfg->delta;
   p.delta_field = cfg->delta;
   p.seed = cfg->seed;
-  gempic::setup_species(cfg, p);
+  (void)gempic::setup_species(cfg, p);            // validated at the top of this function
   const int ppc_sum = p.ppc_sum;
 
   // launch shape: C CTAs per cluster own ny/C rows and (nx/2)/C kx columns; one spectral

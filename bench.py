@@ -208,7 +208,8 @@ def config_dict(w, shape=None):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=48)
+    # 49 = 7 x 7: every cluster of the 7-deep wavefront marches the same number of s-steps
+    ap.add_argument("--steps", type=int, default=49)
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="gempic", choices=["gempic", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -98,6 +98,9 @@ typedef struct {
  * distance Delta.  Under GT1 with Delta shorter than the window every fresh particle stops
  * inside it (the paper's stitches), so the stored buckets need room for a full layer. */
 #define GEMPIC_FLAG_GT1       4u
+/* Discrete continuity residual of the deposit (gempic_diag.continuity_residual), 2-D grids
+ * only: one more shared-memory row and two CIC reductions per push (a verification mode). */
+#define GEMPIC_FLAG_RESIDUAL  8u
 
 typedef struct {
   gempic_grid grid;
@@ -136,6 +139,11 @@ typedef struct {
   int64_t n_stored;             /* stored particles at the new level                         */
   int64_t n_rejoined;           /* stored particles that rejoined the zeta march this step   */
   int64_t pushes;               /* streaming crossings performed this step                   */
+  double continuity_residual;   /* with GEMPIC_FLAG_RESIDUAL on a 2-D grid: max over slabs and
+                                   nodes of |(D_start - D_end)/h - d j_x/dx|, D the CIC density
+                                   of the weights at the start and end of every move of the
+                                   step (Sec. 5.1: rho - j_z is carried through the planes);
+                                   round-off for the charge-conserving deposit.  -1 otherwise */
 } gempic_diag;
 
 /* Create a simulation: validates the config (GEMPIC_EUNSTABLE if Delta h omega_p^2 > 4),

@@ -638,6 +638,7 @@ class RefSim:
         field_energy = 0.0
         kinetic = 0.0
         charge_flux = 0.0
+        continuity = 0.0          # max over slabs and nodes of the discrete continuity residual
         onaxis = np.zeros(nz)
         if joiners.n:
             jm, _ = self._slab(joiners.zeta)
@@ -675,6 +676,16 @@ class RefSim:
                 cic_deposit(jz, X1, Y1, wgt * ds / h)
                 reach = ~trap
                 cic_deposit(Dn, X1[reach], Y1[reach], wgt[reach])
+                # discrete continuity of this slab's deposit (Sec. 5.1; rho - j_z conserved
+                # through the planes): (D(start) - D(end))/h = div j_perp on every node, with D
+                # the CIC density of w at the start and end of each particle's move
+                Dd = np.zeros((ny, nx))
+                cic_deposit(Dd, X0, Y0, wgt)
+                cic_deposit(Dd, X1 % nx, (Y1 % ny) if ny > 1 else Y1, -wgt)
+                div = (jx - np.roll(jx, 1, axis=1)) / self.hx
+                if ny > 1:
+                    div = div + (jy - np.roll(jy, 1, axis=0)) / self.hy
+                continuity = max(continuity, float(np.abs(Dd / h - div).max()))
                 gn = gamma_of(un)
                 dtl = hc * gn / gamma_minus_uz(un, gn)
                 kinetic += float(np.sum((P.Q / self._charge(P.sp)) * self._mass(P.sp) * (gn - 1.0) * dtl / D))
@@ -733,7 +744,8 @@ class RefSim:
             stored_ke = float(np.sum((self.stored.Q / self._charge(self.stored.sp))
                                      * self._mass(self.stored.sp) * (g - 1.0)))
         return dict(field_energy=field_energy, kinetic_energy=kinetic + stored_ke,
-                    charge_flux=charge_flux, onaxis_ez=onaxis, n_trapped=T.n,
+                    charge_flux=charge_flux, continuity_residual=continuity,
+                    onaxis_ez=onaxis, n_trapped=T.n,
                     n_stored=self.stored.n)
 
     # -- one s-step ---------------------------------------------------------------------

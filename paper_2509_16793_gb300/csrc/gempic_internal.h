@@ -57,6 +57,8 @@ struct Params {
   int inject, diag, snapshot;
   int gt1;                        // particle law: 0 = GT2 (Eq. trap2), 1 = GT1 (Eq. trap1)
   int varh;                       // 1: slab thicknesses from hzt (variable zeta-step)
+  int resid;                      // 1: continuity residual of the deposit (2-D only)
+  double* resid_out;              // [nsteps] its maximum per s-step
   const void* hzt;                // [nz] slab thickness h_n (slab n: planes n, n+1), real type
   const double* zpd;              // [nz+1] plane positions zeta_n (plane 0 at the back)
   int pcap;                       // streaming particle slots per CTA in shared memory
@@ -68,7 +70,7 @@ struct Params {
   int nwork;                      // FFT work rows per CTA
   int mig_cap;                    // migrating particles a CTA can receive per slice
   // shared-memory layout (byte offsets)
-  int o_f0, o_f1, o_j, o_recv, o_sr, o_sc, o_workB, o_workD, o_tw, o_inbox, o_outbox, o_part, o_misc,
+  int o_f0, o_f1, o_j, o_recv, o_sr, o_sc, o_workB, o_workD, o_tw, o_inbox, o_outbox, o_part, o_misc, o_dd,
       smem_bytes;
   // device memory
   void* state;                    // blocks [nz+1][C][6][M] complex

@@ -533,7 +533,8 @@ struct Sm {
   T *pfx, *pfy, *pux, *puy, *puz, *psig, *pq;
   int* fstack;      // [fcap] free particle slots
   int* misc;        // MiscSlot
-  double* dacc;     // [kNDiag]
+  double* dacc;     // [kNDiag]; dacc[0] holds the march's continuity-residual maximum
+  T* dd;            // [nx] continuity residual (2-D): w CIC(start) - w CIC(end) of the slice
   double* dwarp;    // [nthreads / 32][kNDiag] per-warp FP64 diagnostic sums of this march
 };
 
@@ -594,6 +595,7 @@ __device__ Sm<T> carve(const Params& p, unsigned char* base) {
   s.misc = (int*)(base + p.o_misc);
   s.dacc = (double*)(base + p.o_misc + 32);
   s.dwarp = s.dacc + kNDiag;
+  s.dd = (T*)(base + p.o_dd);
   return s;
 }
 
@@ -1486,8 +1488,9 @@ struct SliceAcc {     // per-thread, per-slice diagnostics in the working precis
   int push;
 };
 
-// LAW: 0 = GT2, 1 = GT1, -1 = either (read from p.gt1)
-template <typename T, int LAW>
+// LAW: 0 = GT2, 1 = GT1, -1 = either (read from p.gt1); RES: the continuity-residual
+// deposit may be compiled in (taken when p.resid)
+template <typename T, int LAW, bool RES>
 __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PState<T>& P, T d,
                             int me, T& fz_trap, SliceAcc<T>& acc) {
   SUB_DECL
@@ -1545,6 +1548,19 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
     cic_add(p, sk, 2, P.ix, X1, Y1, w * ds * invh);
   }
   SUB_MARK(2);
+  if constexpr (RES) {
+    if (p.resid) {
+      // 2-D continuity residual: +w at the start of the move, -w at its end (CIC)
+      const uint32_t b = sh_addr(s.dd);
+      const int mx = p.nx - 1;
+      const T fXe = floor(X1), fe = X1 - fXe;
+      const int ie = (P.ix + (int)fXe) & mx;
+      red_local(b + (uint32_t)(P.ix * sizeof(T)), w * (T(1) - P.fx));
+      red_local(b + (uint32_t)(((P.ix + 1) & mx) * sizeof(T)), w * P.fx);
+      red_local(b + (uint32_t)(ie * sizeof(T)), -(w * (T(1) - fe)));
+      red_local(b + (uint32_t)(((ie + 1) & mx) * sizeof(T)), -(w * fe));
+    }
+  }
   // diagnostics: kinetic energy N m (gamma-1) dt/Delta, (rho - j_z) flux through plane n
   const T dtl = hden * gn;
   acc.kin += P.q * s.cst[K_MOQ + P.sp] * gamma_minus_one(un, gn) * dtl / D;
@@ -1953,6 +1969,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   // take the generic one)
   constexpr int LAW = SH == 1 ? 0 : -1;
   const bool varh = SH != 1 && p.varh != 0;
+  const bool resid = SH != 1 && p.resid != 0;     // 2-D continuity residual (p.resid: ny == 1)
+  T rmax = T(0);
   const T* hzt = (const T*)p.hzt;
   const int me = (int)cl.block_rank();
   const int tid = threadIdx.x;
@@ -1987,6 +2005,10 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     s.misc[M_OUTN] = 0;
   }
   for (int i = tid; i < (NT >> 5) * kNDiag; i += NT) s.dwarp[i] = 0.0;
+  if (resid) {
+    for (int i = tid; i < p.nx; i += NT) s.dd[i] = T(0);
+    if (tid == 0) s.dacc[0] = 0.0;
+  }
   __syncthreads();
   if (p.inject) {
     const int per_row = p.nlayer >> p.logny;        // particles per transverse row
@@ -2122,7 +2144,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         if (cw < 0) continue;
         PState<T> P = get_particle(p, s, ov, i, cw);
         T fzt;
-        const bool trap = stream_push<T, LAW>(p, s, Fcur, P, hn, me, fzt, sa);
+        const bool trap = stream_push<T, LAW, SH != 1>(p, s, Fcur, P, hn, me, fzt, sa);
         bool gone = trap;
         if (trap) {
           ++ntrap;
@@ -2172,7 +2194,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         PState<T> P = store_read<T>(p.rq, p, ge, fz);
         ++nrej;
         T fzt;
-        const bool trap = stream_push<T, LAW>(p, s, Fcur, P, fz * hn, me, fzt, sa);
+        const bool trap = stream_push<T, LAW, SH != 1>(p, s, Fcur, P, fz * hn, me, fzt, sa);
         if (trap) {
           ++ntrap;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
@@ -2431,6 +2453,18 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     // the inbox drain ends with a barrier that also orders the own-row fold before the beam
     // add and the row transforms; 2-D runs have no inbox
     if (p.ny == 1) __syncthreads();
+    if (resid) {
+      // (D(start) - D(end))/h_n - (j_x(i) - j_x(i-1))/hx on every node of the row, before the
+      // beam current joins j; each thread clears the entries it read
+      const T* jx = s.J + (size_t)p.JOFF * p.nx;
+      const T ihx = T(1.0 / p.hx), ih = T(1) / hn;
+      for (int i = tid; i < p.nx; i += NT) {
+        const T r = s.dd[i] * ih - (jx[i] - jx[(i - 1) & (p.nx - 1)]) * ihx;
+        rmax = fmax(rmax, fabs(r));
+        s.dd[i] = T(0);
+      }
+      __syncthreads();
+    }
     // beam current of this level at the half-slice n + 1/2 (own rows); the flag is cleared
     // by CTA 0 after B2, once every CTA has read it
     const bool beam_slice = s.misc[M_JFLAG] != 0;
@@ -2587,6 +2621,16 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   cl.sync();
   if (p.P > 1 && me == 0 && tid == 0) st_release_u64(p.progress + cid, prog_value(k, nz, nz));
 
+  if (resid) {
+    // the march's largest residual: non-negative doubles order like their bit patterns
+    double v = (double)rmax;
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    if ((tid & 31) == 0)
+      atomicMax(reinterpret_cast<unsigned long long*>(s.dacc),
+                (unsigned long long)__double_as_longlong(v));
+    __syncthreads();
+    if (tid == 0) p.resid_out[sl] = s.dacc[0];
+  }
   // diagnostics: per-CTA FP64 partials
   if (p.diag) {
     warp_diag_add(s.dwarp, DG_FIELD, fe);
@@ -2760,6 +2804,9 @@ int smem_layout(Params& p, int eb) {
   // that a particle slot costs 4 + 7 reals of shared memory
   p.fcap = std::min(p.pcap, 512);
   o += align16(p.pcap * 4) + align16(7 * p.pcap * eb + p.fcap * 4);
+  // continuity residual (2-D): one row of start-minus-end CIC densities
+  p.o_dd = o;
+  if (p.resid && p.ny == 1) o += align16(p.nx * eb);
   p.o_misc = o;
   o += 32 + kNDiag * 8 + (p.nthreads / 32) * kNDiag * 8;
   p.smem_bytes = align16(o);

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(PKG, "libgempic.so")
 GEMPIC_FLAG_DIAG = 1
 GEMPIC_FLAG_SNAPSHOT = 2
 GEMPIC_FLAG_GT1 = 4
+GEMPIC_FLAG_RESIDUAL = 8
 STATUS = {0: "GEMPIC_OK", -1: "GEMPIC_EINVAL", -2: "GEMPIC_ENOMEM", -3: "GEMPIC_ECUDA",
           -4: "GEMPIC_EUNSTABLE", -5: "GEMPIC_ETIMEOUT", -6: "GEMPIC_ESTATE",
           -7: "GEMPIC_EOVERFLOW"}
@@ -65,7 +66,8 @@ class gempic_config(Structure):
 class gempic_diag(Structure):
     _fields_ = [("step", c_int64), ("field_energy", c_double), ("kinetic_energy", c_double),
                 ("charge_flux", c_double), ("n_trapped", c_int64), ("n_stored", c_int64),
-                ("n_rejoined", c_int64), ("pushes", c_int64)]
+                ("n_rejoined", c_int64), ("pushes", c_int64),
+                ("continuity_residual", c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -164,6 +166,8 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
         raise ValueError("particle_law is GT1 or GT2")
     if w.particle_law == "GT1":
         flags |= GEMPIC_FLAG_GT1
+    if w.residual:
+        flags |= GEMPIC_FLAG_RESIDUAL
     cfg = gempic_config(
         grid=gempic_grid(w.nx, w.ny, w.nzeta, w.hx, w.hy, w.h), delta=w.delta,
         precision=w.precision, flags=flags, seed=w.seed, nspecies=n, cluster_ctas=cluster_ctas,

@@ -103,6 +103,7 @@ class Workload:
     channel: Optional[Channel] = None   # None: uniform density
     particle_law: str = "GT2"    # "GT2" (Eq. trap2, s~ = z) or "GT1" (Eq. trap1, s = ct)
     hz: Optional[np.ndarray] = None     # nzeta slab thicknesses (back to front); None: h
+    residual: bool = False       # report the deposit's continuity residual (2-D)
 
     @property
     def ncells(self) -> int:

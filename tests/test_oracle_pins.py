@@ -649,3 +649,36 @@ def test_variable_h_charge_flux_and_stability():
     assert abs(d["charge_flux"] - exact) <= 1e-12 * abs(exact)
     with pytest.raises(ValueError):
         R.RefSim(w.with_(hz=hz * 1.01 * w.h / hz.max()))   # largest slab just above the bound
+
+
+# ---- continuity residual of the deposit (the discrete continuity of P6, in the march) -------
+@pytest.mark.parametrize("ny", [1, 16])
+def test_continuity_residual_is_round_off(ny):
+    """Every move's Esirkepov currents carry its start-minus-end CIC density: the residual
+    (D_start - D_end)/h - div j_perp stays at round-off of q n / h, trapped particles
+    included."""
+    w = (W.small_2d(nx=16, nzeta=96, ppc=2, a0=2.0, delta=1.5) if ny == 1 else
+         W.small_3d(nx=16, ny=16, nzeta=40, ppc=2, a0=2.0, delta=2.0))
+    o = R.RefSim(w)
+    scale = abs(w.species[0].charge * w.species[0].density) / w.h
+    trapped = 0
+    for _ in range(3):
+        d = o.step()
+        trapped += d["n_trapped"]
+        assert d["continuity_residual"] <= 1e-13 * scale
+    assert trapped > 0
+
+
+def test_continuity_residual_sees_a_wrong_current(monkeypatch):
+    """A mistake planted in the oracle's deposit (currents 0.1 % too large) shows up in the
+    residual at the level of the mistake."""
+    w = W.small_2d(nx=16, nzeta=48, ppc=2, a0=1.0)
+    good = R.RefSim(w).step()["continuity_residual"]
+    orig = R.esirkepov_deposit
+
+    def scaled(jx, jy, X0, Y0, X1, Y1, wgt, *a, **k):
+        return orig(jx, jy, X0, Y0, X1, Y1, 1.001 * wgt, *a, **k)
+    monkeypatch.setattr(R, "esirkepov_deposit", scaled)
+    bad = R.RefSim(w).step()["continuity_residual"]
+    scale = abs(w.species[0].charge * w.species[0].density) / w.h
+    assert good <= 1e-13 * scale and bad >= 1e3 * good and bad >= 1e-6 * scale

@@ -690,3 +690,38 @@ def test_bench_workload_full_size_initial_state_matches_oracle():
             assert err <= 1e-4 * scale, (name, err, scale)
         else:
             assert err <= 1e-4 * fs, (name, err)
+
+
+# ---- continuity residual of the deposit (2-D) -------------------------------------------------
+@pytest.mark.parametrize("precision,bound", [(64, 1e-12), (32, 1e-4)])
+def test_continuity_residual_2d(precision, bound):
+    """GEMPIC_FLAG_RESIDUAL on a 2-D run with trapping: the device's residual is round-off of
+    q n / h (FP64) or within the FP32 fixed-point resolution of the currents, and the mode
+    leaves the results as they are."""
+    w = W.small_2d(nx=16, nzeta=96, ppc=2, precision=precision, a0=2.0, delta=1.5)
+    scale = abs(w.species[0].charge * w.species[0].density) / w.h
+    o = RefSim(w)
+    with gpu_sim(w.with_(residual=True)) as g, gpu_sim(w) as plain:
+        for _ in range(3):
+            od = o.step()
+            g.step()
+            plain.step()
+            d = g.diagnostics()
+            assert 0.0 <= d["continuity_residual"] <= bound * scale, d["continuity_residual"]
+            assert od["continuity_residual"] <= 1e-13 * scale
+            assert plain.diagnostics()["continuity_residual"] == -1.0
+        assert od["n_trapped"] > 0
+        if precision == 64:
+            check_state(g.state(), o.state(), 1e-9)
+        a, b = g.state(), plain.state()
+        fs = max(np.abs(b[c]).max() for c in range(4))
+        js = max(np.abs(b[c]).max() for c in (4, 5))
+        for c in range(6):
+            assert np.abs(a[c] - b[c]).max() <= (1e-12 if precision == 64 else 1e-5) * (fs if c < 4 else js)
+
+
+def test_continuity_residual_is_not_reported_in_3d():
+    w = W.small_3d(nx=16, ny=16, nzeta=24, ppc=1, precision=64).with_(residual=True)
+    with gpu_sim(w) as g:
+        g.step()
+        assert g.diagnostics()["continuity_residual"] == -1.0

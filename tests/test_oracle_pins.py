@@ -682,3 +682,25 @@ def test_continuity_residual_sees_a_wrong_current(monkeypatch):
     bad = R.RefSim(w).step()["continuity_residual"]
     scale = abs(w.species[0].charge * w.species[0].density) / w.h
     assert good <= 1e-13 * scale and bad >= 1e3 * good and bad >= 1e-6 * scale
+
+
+def test_variable_h_beam_current_integral():
+    """Beam current on a refined zeta grid (Sec. 5.1, j = Q v/(hx hy h)): linear between
+    half-slice centres and divided by each receiving half-slice's thickness, so its integral
+    over the window, sum_i j_i hx hy h_i, is sum Q v over the pushed beam particles exactly
+    (particles a half-slice or more inside the window)."""
+    w = W.small_3d(nx=16, ny=16, nzeta=48, ppc=1, a0=0.5)
+    w = w.with_(hz=W.refined_h(w.nzeta, w.h, 3.0))
+    zp = np.concatenate([[0.0], np.cumsum(w.hz)])
+    beam = W.gaussian_bunch(w, n_macro=500, n_peak=0.05, sigma_r=2.0, sigma_z=1.0,
+                            zeta_center=0.4 * zp[-1], gamma=200.0, rel_spread=1e-3)
+    o = R.RefSim(w.with_(stored=beam))
+    rejoin, jbeam, lost = o._stored_push()
+    S = o.stored
+    assert rejoin.n == 0 and lost == 0 and S.n == 500
+    assert S.zeta.min() > zp[1] and S.zeta.max() < zp[-2]
+    g = R.gamma_of(S.u)
+    for c in range(3):
+        got = (jbeam[:, c].sum(axis=(1, 2)) * w.hx * w.hy * w.hz).sum()
+        want = (S.Q * S.u[c] / g).sum()
+        assert abs(got - want) <= 1e-12 * np.abs(S.Q * S.u[c] / g).sum(), c

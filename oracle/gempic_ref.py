@@ -519,6 +519,38 @@ class RefSim:
         return np.array([s.charge for s in self.w.species])[sp]
 
     # -- stored set along s (Sec. 5.1, last paragraph) --------------------------------------
+    def _gather_stored(self, x, y, zeta):
+        """E, B [6, N] at the absolute positions (x, y, zeta) from the real-space fields of the
+        last completed level: CIC across, linear in zeta between the slices m and m + 1 of the
+        slab holding zeta (the ghost slice in front of the window is field-free)."""
+        m, fz = self._slab(zeta)
+        X, Y = x / self.hx, y / self.hy
+        Efld = np.zeros((6, x.size))
+        for c in range(6):
+            lo = np.zeros(x.size)
+            hi = np.zeros(x.size)
+            for mm in np.unique(m):
+                sel = m == mm
+                lo[sel] = cic_gather(self.fields_rs[mm, c], X[sel], Y[sel])
+                if mm + 1 < self.nz:
+                    hi[sel] = cic_gather(self.fields_rs[mm + 1, c], X[sel], Y[sel])
+            Efld[c] = (1.0 - fz) * lo + fz * hi
+        return Efld
+
+    def _beam_cells(self, zeta):
+        """Half-slices receiving the beam current of a particle at zeta (Sec. 5.1, j = Q v/
+        (hx hy h)): i0 with weight 1 - f and i0 + 1 with weight f, linear between the
+        half-slice centres zeta_{i+1/2} = zp[i] + hz[i]/2 (the grid extended by one slab of
+        the end thickness on either side)."""
+        if self.varh:
+            c = np.concatenate([[-0.5 * self.hz[0]], self.zp[:-1] + 0.5 * self.hz,
+                                [self.zp[-1] + 0.5 * self.hz[-1]]])
+            k = np.searchsorted(c, zeta, side="right") - 1   # c[k] <= zeta < c[k+1]
+            return k - 1, (zeta - c[k]) / (c[k + 1] - c[k])
+        t = zeta / self.h - 0.5
+        i0 = np.floor(t).astype(np.int64)
+        return i0, t - i0
+
     def _stored_push(self):
         """Advance the stored particles from s^k to s^{k+1} with the fields of level k.
         Returns (particles that rejoin the zeta march, beam current j^{k+1} on half-slices)."""
@@ -545,19 +577,7 @@ class RefSim:
         R.dist = R.zeta - (self.zp[m] if self.varh else m * self.h)
         R.sigma = np.zeros(R.n)
         S = P.select(spush)
-        # gather at (x, y, zeta): CIC across, linear in zeta between slices m and m+1
-        m, fz = self._slab(S.zeta)
-        X, Y = S.x / self.hx, S.y / self.hy
-        Efld = np.zeros((6, S.n))
-        for c in range(6):
-            lo = np.zeros(S.n)
-            hi = np.zeros(S.n)
-            for mm in np.unique(m):
-                sel = m == mm
-                lo[sel] = cic_gather(self.fields_rs[mm, c], X[sel], Y[sel])
-                if mm + 1 < self.nz:
-                    hi[sel] = cic_gather(self.fields_rs[mm + 1, c], X[sel], Y[sel])
-            Efld[c] = (1.0 - fz) * lo + fz * hi
+        Efld = self._gather_stored(S.x, S.y, S.zeta)
         u = S.u
         g = gamma_of(u)
         if self.gt1:
@@ -591,22 +611,14 @@ class RefSim:
         if S.n:
             D3 = S.select(fwd)
             gd = gn[fwd]
+            i0, f = self._beam_cells(D3.zeta)
             if self.varh:
-                # linear between the half-slice centres c_i = zp[i] + hz[i]/2 (the grid
-                # extended by one slab of the end thickness on either side); the density of
-                # half-slice i is charge / (hx hy hz[i])
+                # the density of half-slice i is charge / (hx hy hz[i]) (the grid extended by
+                # one slab of the end thickness on either side)
                 hpad = np.concatenate([[self.hz[0]], self.hz, [self.hz[-1]]])
-                c = np.concatenate([[-0.5 * self.hz[0]], self.zp[:-1] + 0.5 * self.hz,
-                                    [self.zp[-1] + 0.5 * self.hz[-1]]])
-                k = np.searchsorted(c, D3.zeta, side="right") - 1   # c[k] <= zeta < c[k+1]
-                i0 = k - 1
-                f = (D3.zeta - c[k]) / (c[k + 1] - c[k])
                 amp = D3.Q / (self.hx * self.hy * gd)
                 inv_h = lambda ii: 1.0 / hpad[np.clip(ii + 1, 0, self.nz + 1)]
             else:
-                t = D3.zeta / self.h - 0.5
-                i0 = np.floor(t).astype(np.int64)
-                f = t - i0
                 amp = D3.Q / (self.hx * self.hy * self.h * gd)
                 inv_h = lambda ii: 1.0
             X, Y = D3.x / self.hx, D3.y / self.hy

@@ -704,3 +704,278 @@ def test_variable_h_beam_current_integral():
         got = (jbeam[:, c].sum(axis=(1, 2)) * w.hx * w.hy * w.hz).sum()
         want = (S.Q * S.u[c] / g).sum()
         assert abs(got - want) <= 1e-12 * np.abs(S.Q * S.u[c] / g).sum(), c
+
+
+# ---------------------------------------------------------------------------------------
+# cic_gather (the transverse gather of Sec. 5's particle equations, cloud-in-cell): exact for
+# node values linear across the plane, invariant under shifts by whole cells (periodic wrap
+# included), and the adjoint of cic_deposit (pinned by P6): sum_p w_p F(X_p) = <F, D(w)>.
+# ---------------------------------------------------------------------------------------
+def _cic_gather_errors(gather):
+    rng = np.random.default_rng(21)
+    nx, ny = 12, 10
+    a, b, c = 0.7, -1.3, 2.1
+    jj, ii = np.mgrid[0:ny, 0:nx].astype(float)
+    lin = a + b * ii + c * jj
+    # interior positions: the stencil of (X, Y) does not reach the wrap
+    X = rng.uniform(0.0, nx - 1.0, 500)
+    Y = rng.uniform(0.0, ny - 1.0, 500)
+    e_lin3 = np.abs(gather(lin, X, Y) - (a + b * X + c * Y)).max()
+    e_lin2 = np.abs(gather(lin[:1], X, np.zeros_like(X)) - (a + b * X)).max()
+    # any node values: shifting the plane by whole cells and the positions with it changes
+    # nothing, so the wrap cells behave like interior ones
+    F = rng.normal(size=(ny, nx))
+    Xa = rng.uniform(0.0, nx, 500)
+    Ya = rng.uniform(0.0, ny, 500)
+    e_wrap = 0.0
+    for sx, sy in ((1, 0), (0, 1), (5, 3), (nx - 1, ny - 1)):
+        shifted = np.roll(np.roll(F, sy, axis=0), sx, axis=1)
+        e_wrap = max(e_wrap, np.abs(gather(shifted, (Xa + sx) % nx, (Ya + sy) % ny)
+                                    - gather(F, Xa, Ya)).max())
+    e_wrap = max(e_wrap, np.abs(gather(F, Xa + nx, Ya - ny) - gather(F, Xa, Ya)).max())
+    # adjoint of the CIC deposit
+    wts = rng.uniform(0.5, 1.5, 500)
+    D = np.zeros((ny, nx))
+    R.cic_deposit(D, Xa, Ya, wts)
+    e_adj = abs((gather(F, Xa, Ya) * wts).sum() - (F * D).sum())
+    D1 = np.zeros((1, nx))
+    R.cic_deposit(D1, Xa, np.zeros_like(Xa), wts)
+    e_adj = max(e_adj, abs((gather(F[:1], Xa, np.zeros_like(Xa)) * wts).sum() - (F[:1] * D1).sum()))
+    return dict(lin3=e_lin3, lin2=e_lin2, wrap=e_wrap, adjoint=e_adj)
+
+
+def test_cic_gather_linear_periodic_adjoint():
+    e = _cic_gather_errors(R.cic_gather)
+    assert e["lin3"] < 1e-12 and e["lin2"] < 1e-12
+    assert e["wrap"] < 1e-12
+    assert e["adjoint"] < 1e-11
+
+
+@pytest.mark.parametrize("mistake", ["swapped_fx", "one_node_shift", "swapped_fy"])
+def test_cic_gather_pins_catch_a_planted_mistake(mistake):
+    def gather(F, X, Y):
+        i0, j0 = np.floor(X), np.floor(Y)
+        if mistake == "swapped_fx":     # weights (fx, 1 - fx) on (i0, i0 + 1)
+            return R.cic_gather(F, i0 + 1.0 - (X - i0), Y)
+        if mistake == "swapped_fy":
+            return R.cic_gather(F, X, j0 + 1.0 - (Y - j0) if F.shape[0] > 1 else Y)
+        return R.cic_gather(F, X + 1.0, Y)
+    e = _cic_gather_errors(gather)
+    assert max(e["lin3"], e["lin2"], e["adjoint"]) > 1e-3
+
+
+# ---------------------------------------------------------------------------------------
+# Stored-set gather and push (Sec. 5.1, last paragraph): prescribed fields linear in x, y and
+# zeta, no magnetic field.  The Boris step then reduces to u += (q/m) E dt exactly, with
+# dt = Delta gamma/u_z (GT2: the s-step is the propagation distance Delta), and CIC across
+# plus linear interpolation in zeta reproduce a linear field exactly.
+# ---------------------------------------------------------------------------------------
+def _stored_gather_case():
+    w = W.small_3d(nx=16, ny=16, nzeta=24, ppc=1).with_(
+        species=[W.Species(-1.0, 1.0, 0.0, 1), W.Species(1.0, 1836.0, 0.0, 1)],
+        laser=None, delta=5.0)
+    rng = np.random.default_rng(8)
+    n = 64
+    g0 = 200.0
+    st = W.StoredParticles(
+        x=rng.uniform(2.0, 13.0, n) * w.hx, y=rng.uniform(2.0, 13.0, n) * w.hy,
+        zeta=rng.uniform(2.0, 20.0, n) * w.h, ux=rng.normal(0, 0.3, n), uy=rng.normal(0, 0.3, n),
+        uz=np.full(n, math.sqrt(g0 * g0 - 1.0)), weight=rng.uniform(-0.5, 0.5, n),
+        species=(np.arange(n) % 2).astype(np.int32))
+    return w, st
+
+
+def _prescribe_linear_fields(sim, coef):
+    """fields_rs[m, c] = coef[c] . (1, x, y, zeta_m) on the nodes (E only; B = 0)."""
+    x = np.arange(sim.nx) * sim.hx
+    y = np.arange(sim.ny) * sim.hy
+    sim.fields_rs[:] = 0.0
+    for m in range(sim.nz):
+        z = m * sim.h
+        for c in range(3):
+            a, bx, by, bz = coef[c]
+            sim.fields_rs[m, c] = a + bx * x[None, :] + by * y[:, None] + bz * z
+
+
+def _stored_push_error(sim_cls=R.RefSim):
+    w, st = _stored_gather_case()
+    coef = [(0.02, 0.003, -0.002, 0.01), (-0.01, -0.001, 0.004, -0.02), (0.05, 0.002, 0.001, -0.03)]
+    sim = sim_cls(w.with_(stored=st))
+    _prescribe_linear_fields(sim, coef)
+    u0 = np.stack([st.ux, st.uy, st.uz])
+    rejoin, jbeam, lost = sim._stored_push()
+    assert rejoin.n == 0 and lost == 0 and sim.stored.n == st.n
+    g = np.sqrt(1.0 + (u0 ** 2).sum(0))
+    qm = np.where(st.species == 0, -1.0, 1.0 / 1836.0)
+    dt = w.delta * g / u0[2]
+    err = 0.0
+    for c in range(3):
+        a, bx, by, bz = coef[c]
+        E = a + bx * st.x + by * st.y + bz * st.zeta
+        want = u0[c] + qm * E * dt
+        err = max(err, np.abs(sim.stored.u[c] - want).max() / np.abs(qm * E * dt).max())
+    return err
+
+
+def test_stored_gather_is_linear_in_zeta_and_push_is_the_closed_form():
+    assert _stored_push_error() < 1e-10
+
+
+def test_stored_gather_pin_catches_swapped_zeta_weights():
+    class Swapped(R.RefSim):
+        def _gather_stored(self, x, y, zeta):
+            m, fz = self._slab(zeta)
+            # fz -> 1 - fz, same slab: the weights of slices m and m + 1 exchanged
+            mirrored = np.where(self.varh, zeta, (m + 1.0 - fz) * self.h)
+            return super()._gather_stored(x, y, mirrored)
+    assert _stored_push_error(Swapped) > 1e-3
+
+
+# ---------------------------------------------------------------------------------------
+# Beam current placement (Sec. 5.1, j = Q v/(hx hy h) on half-slices): besides its integral,
+# the deposit keeps the first moments of each particle's current: along zeta, with the
+# half-slice centres zeta_{i+1/2}, and across, with the nodes (j_z), the x-edges (j_x) and
+# the y-edges (j_y).  An off-by-half-slice placement moves the zeta moment by h/2 sum Q v.
+# ---------------------------------------------------------------------------------------
+def _beam_moment_errors(refined, sim_cls=R.RefSim):
+    w = W.small_3d(nx=16, ny=16, nzeta=48, ppc=1, a0=0.5).with_(laser=None)
+    if refined:
+        w = w.with_(hz=W.refined_h(w.nzeta, w.h, 3.0))
+    hz = w.hz if refined else np.full(w.nzeta, w.h)
+    zp = np.concatenate([[0.0], np.cumsum(hz)])
+    rng = np.random.default_rng(12)
+    n = 300
+    st = W.StoredParticles(
+        x=rng.uniform(3.0, 12.0, n) * w.hx, y=rng.uniform(3.0, 12.0, n) * w.hy,
+        zeta=rng.uniform(0.1, 0.9, n) * zp[-1], ux=rng.normal(0, 2.0, n),
+        uy=rng.normal(0, 2.0, n), uz=np.full(n, 300.0), weight=rng.uniform(-0.5, 0.5, n),
+        species=np.zeros(n, np.int32))
+    sim = sim_cls(w.with_(stored=st, delta=0.5))
+    rejoin, jbeam, lost = sim._stored_push()
+    S = sim.stored
+    assert rejoin.n == 0 and lost == 0 and S.n == n
+    g = R.gamma_of(S.u)
+    vol = w.hx * w.hy * hz[:, None, None]                    # cell volume of half-slice i
+    zc = (zp[:-1] + 0.5 * hz)[:, None, None]                 # half-slice centres
+    xn = np.arange(w.nx)[None, None, :] * w.hx
+    yn = np.arange(w.ny)[None, :, None] * w.hy
+    errs = {}
+    for c, xs, ys in ((0, 0.5, 0.0), (1, 0.0, 0.5), (2, 0.0, 0.0)):
+        Qv = S.Q * S.u[c] / g
+        jc = jbeam[:, c] * vol
+        scale = np.abs(Qv).sum()
+        errs[f"zeta{c}"] = abs((jc * zc).sum() - (Qv * S.zeta).sum()) / (scale * w.h)
+        errs[f"x{c}"] = abs((jc * (xn + xs * w.hx)).sum() - (Qv * S.x).sum()) / (scale * w.hx)
+        errs[f"y{c}"] = abs((jc * (yn + ys * w.hy)).sum() - (Qv * S.y).sum()) / (scale * w.hy)
+    return errs
+
+
+@pytest.mark.parametrize("refined", [False, True])
+def test_beam_current_first_moments(refined):
+    e = _beam_moment_errors(refined)
+    assert max(e.values()) < 1e-11, e
+
+
+def test_beam_moment_pin_catches_an_off_by_half_slice_placement():
+    class OffByHalf(R.RefSim):
+        def _beam_cells(self, zeta):
+            t = zeta / self.h                   # the planted mistake: no half-slice offset
+            i0 = np.floor(t).astype(np.int64)
+            return i0, t - i0
+    e = _beam_moment_errors(False, OffByHalf)
+    assert e["zeta2"] > 1e-3
+
+
+# ---------------------------------------------------------------------------------------
+# Energy sums (what the FP32 parity tolerance is stated on).
+# ---------------------------------------------------------------------------------------
+def test_field_energy_of_the_vacuum_laser_is_the_closed_form():
+    """Level-0 forward wave R = 2E, L = 0 (Sec. 6, Eq. E_laser): E_x = B_y = E, so
+    1/2 int (E^2 + B^2) = int E_x^2 = a0^2 int cos^2(phi) exp(-2 phi^2/T^2) dphi
+    x int exp(-2 x^2/w0^2) dx (2-D, per unit depth) = a0^2 sqrt(pi/2) T (1 + e^{-T^2/2})/2
+    x w0 sqrt(pi/2).  The paraxial E_z, B_z and L add O(1/(k w0)^2) = 4e-4 here."""
+    lam = 2 * math.pi
+    nx, hx, h = 64, lam / 2, lam / 20
+    w0, T, a0 = 8 * lam, 10.0, 0.7
+    nz = int(round(8 * T / h))
+    w = W.Workload(name="vac2d_energy", nx=nx, ny=1, nzeta=nz, hx=hx, hy=1.0, h=h, delta=0.0,
+                   species=[], laser=W.Laser(a0=a0, waist=w0, duration=T, zeta_center=0.5 * nz * h))
+    d = R.RefSim(w).step()
+    want = a0 * a0 * math.sqrt(math.pi / 2) * T * (1 + math.exp(-T * T / 2)) / 2 \
+        * w0 * math.sqrt(math.pi / 2)
+    assert abs(d["field_energy"] - want) < 1e-3 * want
+    # 3-D: the transverse factor is int exp(-2 r^2/w0^2) d^2r = pi w0^2/2
+    w3 = W.Workload(name="vac3d_energy", nx=32, ny=32, nzeta=nz, hx=lam, hy=lam, h=h, delta=0.0,
+                    species=[], laser=W.Laser(a0=a0, waist=w0, duration=T, zeta_center=0.5 * nz * h))
+    d3 = R.RefSim(w3).step()
+    want3 = want / (w0 * math.sqrt(math.pi / 2)) * math.pi * w0 * w0 / 2
+    assert abs(d3["field_energy"] - want3) < 1e-3 * want3
+
+
+def _plane_wave_kinetic_error(h, a0=0.6, T=6.0):
+    nz = int(round(35.0 / h))
+    L = nz * h
+    zc = L - 3.0 * T
+    n0 = 1e-9
+    w = W.Workload(name="ke1d", nx=4, ny=1, nzeta=nz, hx=1.0, hy=1.0, h=h, delta=1e3,
+                   species=[W.Species(-1.0, 1.0, n0, 2)],
+                   laser=W.Laser(a0=a0, waist=1e9, duration=T, zeta_center=zc))
+    d = R.RefSim(w).step()
+    assert d["n_trapped"] == 0
+    z = np.linspace(0.0, L, 700001)
+    phi = z - zc
+    Ex = a0 * np.cos(phi) * np.exp(-phi * phi / (T * T))
+    A = -(np.cumsum(Ex[::-1])[::-1] - 0.5 * (Ex + Ex[-1])) * (z[1] - z[0])   # -int_zeta^L E_x
+    want = n0 * w.hx * w.hy * w.nx * np.trapezoid(0.5 * A * A * (1 + 0.5 * A * A), z)
+    return abs(d["kinetic_energy"] - want) / want
+
+
+def test_streaming_kinetic_energy_of_the_plane_wave_electron():
+    """P1's electron (Sec. 2 example): u_x = A, gamma - u_z = 1, gamma - 1 = A^2/2, and the lab
+    time of a step is dt = |dzeta| gamma/(gamma - u_z) = gamma |dzeta|.  The kinetic energy
+    summed over the crossings of one s-step, sum N m (gamma - 1) dt/Delta, is therefore
+    n hx hy nx int (A^2/2)(1 + A^2/2) dzeta for a layer of nx cells of density n, to second
+    order in h."""
+    e1 = _plane_wave_kinetic_error(0.05)
+    e2 = _plane_wave_kinetic_error(0.025)
+    assert e1 < 1e-3 and e1 / e2 > 3.0
+
+
+def test_stored_kinetic_energy_is_n_m_gamma_minus_one():
+    """Stored particles add N m (gamma - 1) with N = Q/q physical particles: an electron and a
+    proton beam particle (gamma = 200 and 50) in a window without plasma or driver keep their
+    momenta through the first s-step (the fields of level 0 are zero)."""
+    w = W.small_3d(nx=8, ny=8, nzeta=16).with_(
+        species=[W.Species(-1.0, 1.0, 0.0, 1), W.Species(1.0, 1836.0, 0.0, 1)],
+        laser=None, delta=5.0)
+    ge, gp = 200.0, 50.0
+    st = W.StoredParticles(x=np.array([3.1, 4.2]) * w.hx, y=np.array([4.4, 2.5]) * w.hy,
+                           zeta=np.array([7.3, 9.6]) * w.h, ux=np.zeros(2), uy=np.zeros(2),
+                           uz=np.array([math.sqrt(ge * ge - 1), math.sqrt(gp * gp - 1)]),
+                           weight=np.array([-0.37, 0.21]), species=np.array([0, 1], np.int32))
+    d = R.RefSim(w.with_(stored=st)).step()
+    want = 0.37 * 1.0 * (ge - 1.0) + 0.21 * 1836.0 * (gp - 1.0)
+    assert abs(d["kinetic_energy"] - want) < 1e-12 * want
+
+
+# ---------------------------------------------------------------------------------------
+# SplitMix64 (Steele, Lea, Flood, OOPSLA 2014): the first outputs of the generator for the
+# state 1234567, as printed by the public-domain reference implementation splitmix64.c
+# (S. Vigna) and used as test vectors by xoshiro ports.  The oracle's counter form
+# mix(seed + (c + 1) gamma) is output c of that sequential generator.
+# ---------------------------------------------------------------------------------------
+SPLITMIX64_1234567 = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                      4593380528125082431, 16408922859458223821]
+
+
+def test_splitmix64_reference_outputs():
+    got = R.splitmix64(1234567, np.arange(5, dtype=np.uint64))
+    assert [int(v) for v in got] == SPLITMIX64_1234567
+    # uniform24 keeps the top 24 bits of the output
+    assert R.uniform24(1234567, np.zeros(1, np.uint64))[0] == (SPLITMIX64_1234567[0] >> 40) / 2.0 ** 24
+
+
+def test_splitmix64_pin_catches_a_wrong_constant(monkeypatch):
+    monkeypatch.setattr(R, "_M1", np.uint64(0xBF58476D1CE4E5B8))
+    got = R.splitmix64(1234567, np.arange(5, dtype=np.uint64))
+    assert [int(v) for v in got] != SPLITMIX64_1234567

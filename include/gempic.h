@@ -48,7 +48,10 @@ typedef enum {
   GEMPIC_EUNSTABLE = -4,  /* Delta h omega_p^2 > 4, outside the stability bound (Sec. 4.2)   */
   GEMPIC_ETIMEOUT = -5,   /* a bounded device-side wait gave up                             */
   GEMPIC_ESTATE = -6,     /* simulation failed earlier, or call not valid in this state     */
-  GEMPIC_EOVERFLOW = -7   /* a fixed-capacity particle store overflowed (particles dropped) */
+  GEMPIC_EOVERFLOW = -7,  /* a fixed-capacity particle store overflowed (particles dropped) */
+  GEMPIC_ENONFINITE = -8  /* watchdog: a NaN or infinity reached the FP64 field or kinetic
+                             energy sums (needs GEMPIC_FLAG_DIAG), or a particle moved more
+                             than 256 cells across one slice                                */
 } gempic_status;
 
 /* Transverse grid and slices (Sec. 4.1: large step Delta in s, fine step h in zeta). */
@@ -75,7 +78,39 @@ typedef struct {
   double a0, waist, duration, zeta_center;
   int32_t pol;            /* 0 = x, 1 = y */
   int32_t reserved;
+  /* > 0: the full width at half maximum of the intensity |E|^2 on the axis; the library takes
+   * T = fwhm_intensity / sqrt(2 ln 2) (intensity ~ exp(-2 phi^2/T^2)) and ignores duration.
+   * 0: duration is T itself. */
+  double fwhm_intensity;
 } gempic_laser;
+
+/* Gaussian particle bunch placed in the box at creation (a PWFA-style driver; Sec. 5.1: a
+ * particle inside the box carries a charge Q_b and is pushed along s as a beam particle).
+ * Its density is n_peak exp(-r^2/(2 sigma_r^2) - (zeta - zeta_center)^2/(2 sigma_z^2)),
+ * r measured from the window's middle node (x_c, y_c) = (nx hx/2, ny hy/2) (2-D: |x - x_c|,
+ * a sheet uniform in y).  It is sampled on the device with n_macro equal-charge macro-
+ * particles, Q = charge n_peak (2 pi)^(3/2) sigma_r^2 sigma_z / n_macro (2-D, per unit depth:
+ * charge n_peak 2 pi sigma_r sigma_z / n_macro), cold (u_x = u_y = 0) and moving along +z with
+ * gamma_i = gamma (1 + rel_spread g_3), u_z = sqrt(max(gamma_i^2 - 1, 0)).
+ * Sampling: macroparticle i draws the uniforms v_j = ((o >> 11) + 1) 2^-53 in (0, 1] from
+ * outputs o = 4 i + j (j = 0..3) of the counter-based SplitMix64 stream of `seed`, and the
+ * normal pairs (g_0, g_1), (g_2, g_3) by the Box-Muller transform
+ * (sqrt(-2 ln v_0) cos(2 pi v_1), sqrt(-2 ln v_0) sin(2 pi v_1)), likewise from (v_2, v_3);
+ * x = x_c + sigma_r g_0, y = y_c + sigma_r g_1 (wrapped into the periodic box; 2-D: y = 0),
+ * zeta = zeta_center + sigma_z g_2.  Macroparticles outside 0 < zeta <= window length are
+ * dropped (their charge is not redistributed).  The bunch uses the species of equal charge
+ * and mass if the config has one, else an extra species slot that is never injected fresh
+ * (nspecies + 1 must then stay <= 4).  n_peak may have either sign with charge; sigma_r,
+ * sigma_z > 0, gamma >= 1, rel_spread >= 0, n_macro >= 0, else gempic_create returns
+ * GEMPIC_EINVAL. */
+typedef struct {
+  double charge, mass;    /* in e and m_e */
+  double n_peak;          /* in n_cr */
+  double sigma_r, sigma_z, zeta_center;
+  double gamma, rel_spread;
+  int64_t n_macro;
+  uint64_t seed;          /* SplitMix64 stream of the bunch (independent of the fresh plasma's) */
+} gempic_beam;
 
 /* Transverse plasma channel (Sec. 6, Eq. n_plasma): the density of every species is
  * n(r) = n [1 + (n1/n0 - 1) exp(-r^2 / R_ch^2)], r the transverse distance from the window's
@@ -126,6 +161,10 @@ typedef struct {
    * create; GEMPIC_EINVAL for a non-positive or non-finite entry; the stability bound uses
    * the largest slab.  gempic_step_noalloc does not take a table (GEMPIC_EINVAL). */
   const double* hz;
+  /* NULL: no bunch.  Copied at create; sampled into the stored set of level 0 by the first
+   * call that initialises the simulation (before the consistency march).  With
+   * stored_bucket_capacity = 0 the buckets are sized for the bunch's densest slab. */
+  const gempic_beam* beam;
 } gempic_config;
 
 /* Per-s-step diagnostics, accumulated on the device in FP64. */
@@ -175,6 +214,15 @@ gempic_status gempic_step_async(struct gempic_sim* sim, int32_t n);
  * GEMPIC_EUNSTABLE above the stability bound (the simulation keeps its old Delta), GEMPIC_ESTATE
  * after a failure.  Launches already issued are not affected. */
 gempic_status gempic_set_delta(struct gempic_sim* sim, double delta);
+
+/* Bounded device waits: when several s-steps march concurrently (pipeline_depth > 1) each
+ * march polls the progress word of the march ahead of it; after `polls` polls (about 200 ns
+ * apart) without progress it gives up, sets the timeout bit of the device status word and
+ * finishes its march on whatever data it has, so the launch always completes and the next
+ * gempic_sync returns GEMPIC_ETIMEOUT (then the simulation is failed: GEMPIC_ESTATE).  The
+ * default is 2e7 polls (a few seconds).  Takes effect for the launches after this call.
+ * GEMPIC_EINVAL for polls < 0; GEMPIC_ESTATE after a failure. */
+gempic_status gempic_set_wait_limit(struct gempic_sim* sim, int64_t polls);
 
 /* Wait for the stream and check the device status word of the simulation. */
 gempic_status gempic_sync(struct gempic_sim* sim);
@@ -276,19 +324,28 @@ void gempic_batch_destroy(gempic_batch* b);
  *   state        device memory owned by the caller, layout of gempic_get_state, updated in
  *                place; state_bytes must cover it.  There is no laser set-up here: pass a
  *                state prepared elsewhere (e.g. copied out with gempic_get_state).
- *   cfg          grid, delta, precision, seed, species, cluster_ctas and cuda_stream are
- *                used; laser, flags, capacities and pipeline_depth are ignored.
- *   diag_out     host, may be NULL: diagnostics of the step.
+ *   cfg          used: grid, delta, precision, seed, nspecies, species, channel,
+ *                cluster_ctas, cuda_stream and, of the flags, GEMPIC_FLAG_GT1.  Ignored:
+ *                laser, stored_bucket_capacity, particle_headroom, pipeline_depth and
+ *                GEMPIC_FLAG_DIAG (the diagnostics are always computed).  Rejected with
+ *                GEMPIC_EINVAL: a zeta-step table (hz), a bunch (beam), GEMPIC_FLAG_SNAPSHOT
+ *                and GEMPIC_FLAG_RESIDUAL (this call has no buffers for them).
+ *   diag_out     host, may be NULL: diagnostics of the step (continuity_residual = -1).
  *   onaxis_out   host, may be NULL: nzeta doubles of on-axis E_z.
- * Working memory: one 256 KiB array in device memory, declared at file scope in the library;
- * every GPU that loads the library holds it until the process exits.  Limits: nx, ny <= 1024,
- * nzeta <= 4096, at most 16 CTAs per cluster; larger sizes return GEMPIC_EINVAL before any
- * work.  The first call on a device looks up the array's device address (set-up); make that
- * first call before any stream capture.  All calls share the array and it keeps the last
- * call's contents (each call clears what must start at zero): calls that overlap on the GPU,
- * from several streams or threads, race -- serialise them.  There is no stored-particle
- * store: if a particle is trapped during the step the state is still advanced, the trapped
- * particle is dropped, and GEMPIC_EOVERFLOW is returned.  The call waits for its stream. */
+ * Working memory: one array of 248 320 bytes in device memory, declared at file scope in the
+ * library; every GPU that loads the library holds it until the process exits.  Limits:
+ * nzeta <= 4096; nx <= 1024; at most 16 CTAs per cluster with (nx/2) ny / C <= 512 spectral
+ * modes per CTA and, in 3-D, at least two rows (ny / C >= 2) per CTA; one band's fresh
+ * particles, fields and spectra must fit the shared memory of one CTA.  Larger sizes return
+ * GEMPIC_EINVAL before any work.  The first call on a device looks up the array's device
+ * address (set-up); make that first call before any stream capture.  All calls share the
+ * array and it keeps the last call's contents (each call clears what must start at zero):
+ * calls that overlap on the GPU, from several streams or threads, race -- serialise them.
+ * GEMPIC_EOVERFLOW has two causes, and in both the state is still advanced: a particle
+ * trapped during the step (there is no stored-particle store: the trapped particle is
+ * dropped), or a band whose streaming slots overflow when particles move in from other bands
+ * (the extra particles are dropped).  GEMPIC_ENONFINITE: the watchdog of the FP64 sums.  The
+ * call waits for its stream. */
 gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t step, void* state,
                                   size_t state_bytes, gempic_diag* diag_out, double* onaxis_out);
 

@@ -67,6 +67,47 @@ def uniform24(seed: int, counter: np.ndarray) -> np.ndarray:
     return (splitmix64(seed, counter) >> np.uint64(40)).astype(np.float64) * (2.0 ** -24)
 
 
+def uniform53(seed: int, counter: np.ndarray) -> np.ndarray:
+    """Uniform (0, 1] with 53 random bits: (top 53 bits + 1) / 2^53 (never 0, so that the
+    logarithm of the Box-Muller transform is finite)."""
+    return ((splitmix64(seed, counter) >> np.uint64(11)).astype(np.float64) + 1.0) * (2.0 ** -53)
+
+
+def box_muller(v0: np.ndarray, v1: np.ndarray):
+    """Two independent standard normals from two uniforms on (0, 1] (Box and Muller, Ann.
+    Math. Stat. 29 (1958) 610): radius sqrt(-2 ln v0), angle 2 pi v1."""
+    r = np.sqrt(-2.0 * np.log(v0))
+    return r * np.cos(2.0 * math.pi * v1), r * np.sin(2.0 * math.pi * v1)
+
+
+def sample_beam(b, nx, ny, hx, hy, length):
+    """Gaussian bunch of equal-charge macroparticles (beam particles of Sec. 5.1, placed in the
+    box at creation).  Density n_peak exp(-r^2/(2 sr^2) - (zeta - zc)^2/(2 sz^2)) around the
+    grid's middle node; macroparticle i uses SplitMix64 outputs 4 i .. 4 i + 3 of the stream
+    b.seed as uniforms on (0, 1] and the Box-Muller pairs (g0, g1), (g2, g3):
+    x = x_c + sr g0, y = y_c + sr g1 (periodic), zeta = zc + sz g2, gamma (1 + spread g3) along
+    +z, no transverse momentum.  Returns (x, y, zeta, u [3, N], Q) of the macroparticles with
+    0 < zeta <= length; each carries total charge / n_macro."""
+    i = np.arange(int(b.n_macro), dtype=np.uint64)
+    v = [uniform53(int(b.seed), np.uint64(4) * i + np.uint64(j)) for j in range(4)]
+    g0, g1 = box_muller(v[0], v[1])
+    g2, g3 = box_muller(v[2], v[3])
+    lx, ly = nx * hx, ny * hy
+    x = np.mod(0.5 * lx + b.sigma_r * g0, lx)
+    y = np.mod(0.5 * ly + b.sigma_r * g1, ly) if ny > 1 else np.zeros(i.size)
+    zeta = b.zeta_center + b.sigma_z * g2
+    gam = b.gamma * (1.0 + b.rel_spread * g3)
+    uz = np.sqrt(np.maximum(gam * gam - 1.0, 0.0))
+    if ny > 1:
+        total = b.charge * b.n_peak * (2.0 * math.pi) ** 1.5 * b.sigma_r ** 2 * b.sigma_z
+    else:
+        total = b.charge * b.n_peak * 2.0 * math.pi * b.sigma_r * b.sigma_z
+    keep = (zeta > 0.0) & (zeta <= length)
+    n = int(keep.sum())
+    u = np.stack([np.zeros(n), np.zeros(n), uz[keep]])
+    return x[keep], y[keep], zeta[keep], u, np.full(n, total / max(int(b.n_macro), 1))
+
+
 # ----------------------------------------------------------------------------------------
 # Transverse spectral transform (Sec. 3.1: 2-D Fourier transform in (x, y), d/dx -> i k_x).
 # Layout: [..., ky (ny), kx (nx/2)]; the kx-Nyquist column is dropped and the ky-Nyquist row
@@ -426,6 +467,19 @@ class RefSim:
         densest = max(1.0, w.channel.n1_over_n0) if w.channel is not None else 1.0
         if w.omega_p2 * densest * self.delta * self.hz.max() > 4.0 * (1.0 + 1e-12):
             raise ValueError("Delta h omega_p^2 > 4: outside the stability bound (Sec. 4.2)")
+        # species of the particles: the injected ones, then a slot of the bunch's own if no
+        # injected species has its charge and mass
+        self.species = list(w.species)
+        self.beam_species = None
+        if w.beam is not None:
+            b = w.beam
+            for si, s in enumerate(w.species):
+                if s.charge == b.charge and s.mass == b.mass:
+                    self.beam_species = si
+                    break
+            if self.beam_species is None:
+                self.beam_species = len(self.species)
+                self.species.append(type("BeamSpecies", (), dict(charge=b.charge, mass=b.mass))())
         self.stored = Particles.empty()
         if w.stored is not None and w.stored.n > 0:
             st = w.stored
@@ -434,6 +488,13 @@ class RefSim:
                                     np.stack([st.ux, st.uy, st.uz]).astype(float),
                                     np.zeros(st.n), st.weight.astype(float).copy(),
                                     st.species.astype(np.int64).copy(), np.zeros(st.n))
+        if w.beam is not None and w.beam.n_macro > 0:
+            bx, by, bz, bu, bq = sample_beam(w.beam, self.nx, self.ny, self.hx, self.hy,
+                                             self.zp[self.nz])
+            nb = bx.size
+            self.stored = Particles.concat([self.stored, Particles(
+                bx, by, bz, bu, np.zeros(nb), bq, np.full(nb, self.beam_species, np.int64),
+                np.zeros(nb))])
         self._init_laser()
         # Delta = 0 consistency march (R^1 = R^0 exactly): fills E_z, B_z (and L) for the
         # initial laser and the real-space fields of level 0.
@@ -510,13 +571,13 @@ class RefSim:
         return Particles.concat(parts)
 
     def _qm(self, sp):
-        return np.array([s.charge / s.mass for s in self.w.species])[sp]
+        return np.array([s.charge / s.mass for s in self.species])[sp]
 
     def _mass(self, sp):
-        return np.array([s.mass for s in self.w.species])[sp]
+        return np.array([s.mass for s in self.species])[sp]
 
     def _charge(self, sp):
-        return np.array([s.charge for s in self.w.species])[sp]
+        return np.array([s.charge for s in self.species])[sp]
 
     # -- stored set along s (Sec. 5.1, last paragraph) --------------------------------------
     def _gather_stored(self, x, y, zeta):

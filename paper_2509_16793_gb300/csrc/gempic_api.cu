@@ -23,6 +23,10 @@ struct gempic_sim {
   bool has_laser = false;
   gempic_channel channel;
   bool has_channel = false;
+  gempic_beam beam;                // Gaussian bunch sampled at initialisation (n_macro > 0)
+  bool has_beam = false;
+  int beam_species = 0;            // species slot of the bunch
+  int nspecies_all = 0;            // injected species plus a slot of the bunch's own
   std::vector<double> hz, zp;      // variable zeta-step: slab thicknesses, plane positions
   Params p{};                      // launch template
   int eb = 8;                      // bytes per real
@@ -81,6 +85,7 @@ gempic_status check_device_error(gempic_sim* s) {
   if (e != cudaSuccess) return cuda_fail(s, e);
   if (err == 0) return GEMPIC_OK;
   gempic_status st = (err & gempic::ERR_TIMEOUT) ? GEMPIC_ETIMEOUT
+                     : (err & gempic::ERR_NONFINITE) ? GEMPIC_ENONFINITE
                      : (err & (gempic::ERR_PCAP | gempic::ERR_BCAP | gempic::ERR_QCAP))
                          ? GEMPIC_EOVERFLOW
                          : GEMPIC_ESTATE;
@@ -172,6 +177,29 @@ gempic_status ensure_initialized(gempic_sim* s) {
   }
   gempic_status st = upload_particles(s);
   if (st != GEMPIC_OK) return st;
+  if (s->has_beam && s->beam.n_macro > 0) {
+    // the bunch is appended to the level-0 buckets after the host-placed particles
+    const gempic_beam& b = s->beam;
+    const double pi = 3.14159265358979323846;
+    const double total = s->p.ny > 1
+        ? b.charge * b.n_peak * std::pow(2.0 * pi, 1.5) * b.sigma_r * b.sigma_r * b.sigma_z
+        : b.charge * b.n_peak * 2.0 * pi * b.sigma_r * b.sigma_z;
+    gempic::BeamArgs a;
+    a.xc = 0.5 * s->p.nx * s->p.hx;
+    a.yc = s->p.ny > 1 ? 0.5 * s->p.ny * s->p.hy : 0.0;
+    a.sr = b.sigma_r;
+    a.sz = b.sigma_z;
+    a.zc = b.zeta_center;
+    a.gamma = b.gamma;
+    a.spread = b.rel_spread;
+    a.q = total / (double)b.n_macro;
+    a.n = b.n_macro;
+    a.seed = b.seed;
+    a.sp = s->beam_species;
+    e = gempic::launch_beam_init(prec, s->p, a, s->stream);
+    s->launches++;
+    if (e != cudaSuccess) return cuda_fail(s, e);
+  }
   // Delta = 0 consistency march: R^1 = R^0, fills E_z, B_z, L of the initial laser and
   // pushes the particles placed at level 0 to level 1.
   e = ensure_diag_cap(s, 1);
@@ -209,6 +237,7 @@ const char* gempic_strerror(gempic_status s) {
     case GEMPIC_ETIMEOUT: return "a bounded device wait gave up";
     case GEMPIC_ESTATE: return "simulation failed earlier or call not valid in this state";
     case GEMPIC_EOVERFLOW: return "a fixed-capacity particle store overflowed";
+    case GEMPIC_ENONFINITE: return "a non-finite value appeared in the fields or particles";
   }
   return "unknown status";
 }
@@ -227,6 +256,27 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     const gempic_status st = gempic::setup_species(cfg, chk);
     if (st != GEMPIC_OK) return st;
   }
+  if (cfg->laser && (!(cfg->laser->fwhm_intensity >= 0) || !std::isfinite(cfg->laser->fwhm_intensity)))
+    return GEMPIC_EINVAL;
+  // the bunch: validated here; it takes the slot of the species with its charge and mass, or
+  // a slot of its own after the injected species
+  int beam_slot = -1;
+  if (cfg->beam) {
+    const gempic_beam& b = *cfg->beam;
+    const double v[8] = {b.charge, b.mass, b.n_peak, b.sigma_r, b.sigma_z, b.zeta_center,
+                         b.gamma, b.rel_spread};
+    for (double x : v)
+      if (!std::isfinite(x)) return GEMPIC_EINVAL;
+    if (!(b.mass > 0) || !(b.sigma_r > 0) || !(b.sigma_z > 0) || !(b.gamma >= 1) ||
+        !(b.rel_spread >= 0) || b.n_macro < 0)
+      return GEMPIC_EINVAL;
+    for (int i = 0; i < cfg->nspecies && beam_slot < 0; ++i)
+      if (cfg->species[i].charge == b.charge && cfg->species[i].mass == b.mass) beam_slot = i;
+    if (beam_slot < 0) {
+      if (cfg->nspecies >= gempic::kMaxSpecies) return GEMPIC_EINVAL;
+      beam_slot = cfg->nspecies;
+    }
+  }
 
   gempic_sim* s = new (std::nothrow) gempic_sim();
   if (!s) return GEMPIC_ENOMEM;
@@ -236,8 +286,19 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
   if (cfg->laser) {
     s->laser = *cfg->laser;
     s->has_laser = true;
+    // intensity ~ exp(-2 phi^2/T^2): its full width at half maximum is T sqrt(2 ln 2)
+    if (s->laser.fwhm_intensity > 0)
+      s->laser.duration = s->laser.fwhm_intensity / std::sqrt(2.0 * std::log(2.0));
   }
   s->cfg.laser = nullptr;
+  s->nspecies_all = cfg->nspecies;
+  if (cfg->beam) {
+    s->beam = *cfg->beam;
+    s->has_beam = true;
+    s->beam_species = beam_slot;
+    s->nspecies_all = std::max(cfg->nspecies, beam_slot + 1);
+  }
+  s->cfg.beam = nullptr;
   if (cfg->channel) {
     s->channel = *cfg->channel;
     s->has_channel = true;
@@ -266,6 +327,16 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
   p.delta_field = cfg->delta;
   p.seed = cfg->seed;
   (void)gempic::setup_species(cfg, p);            // validated at the top of this function
+  if (s->has_beam && s->beam_species >= cfg->nspecies) {
+    // a slot of the bunch's own: q/m and m/q for its push and energy; never injected
+    const int b = s->beam_species;
+    p.qm[b] = s->beam.charge / s->beam.mass;
+    p.m_over_q[b] = s->beam.charge != 0 ? s->beam.mass / s->beam.charge : 0.0;
+    p.Qf[b] = 0.0;
+    p.wd[b] = 0.0;
+    p.ppc[b] = 0;
+    p.poff[b] = p.nlayer;
+  }
   const int ppc_sum = p.ppc_sum;
 
   // launch shape: C CTAs per cluster own ny/C rows and (nx/2)/C kx columns; one spectral
@@ -318,6 +389,12 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
   }
   p.bcap = cfg->stored_bucket_capacity > 0 ? cfg->stored_bucket_capacity
                                            : std::max(256, g.nx * g.ny * std::max(ppc_sum, 1) / 4);
+  if (cfg->stored_bucket_capacity <= 0 && s->has_beam && s->beam.n_macro > 0) {
+    // room for the bunch's densest slab: n_macro h_max/(sqrt(2 pi) sigma_z), with a margin
+    const double hmax = s->hz.empty() ? g.h : *std::max_element(s->hz.begin(), s->hz.end());
+    const double peak = (double)s->beam.n_macro * std::min(1.0, hmax / (2.5066282746310002 * s->beam.sigma_z));
+    p.bcap += (int)std::min<double>((double)s->beam.n_macro, std::ceil(1.5 * peak) + 64.0);
+  }
   p.wait_spin_limit = 20000000;
   p.diag = (cfg->flags & GEMPIC_FLAG_DIAG) ? 1 : 0;
   p.snapshot = (cfg->flags & GEMPIC_FLAG_SNAPSHOT) ? 1 : 0;
@@ -447,7 +524,7 @@ gempic_status gempic_add_particles(gempic_sim* s, int64_t n, const double* x, co
     return GEMPIC_EINVAL;
   if (s->p.ny > 1 && n > 0 && !y) return GEMPIC_EINVAL;
   for (int64_t i = 0; i < n; ++i) {
-    if (species[i] < 0 || species[i] >= std::max(1, s->p.nspecies)) return GEMPIC_EINVAL;
+    if (species[i] < 0 || species[i] >= std::max(1, s->nspecies_all)) return GEMPIC_EINVAL;
     const double L = s->zp.empty() ? s->p.nz * s->p.h : s->zp.back();
     if (!(zeta[i] > 0) || !(zeta[i] <= L)) return GEMPIC_EINVAL;
   }
@@ -503,6 +580,13 @@ gempic_status gempic_set_delta(gempic_sim* s, double delta) {
   s->p = t;
   s->p.delta = delta;
   s->p.delta_field = delta;
+  return GEMPIC_OK;
+}
+
+gempic_status gempic_set_wait_limit(gempic_sim* s, int64_t polls) {
+  if (!s || polls < 0) return GEMPIC_EINVAL;
+  if (s->failed != GEMPIC_OK) return GEMPIC_ESTATE;
+  s->p.wait_spin_limit = (int)std::min<int64_t>(polls, 2000000000);
   return GEMPIC_OK;
 }
 

@@ -16,7 +16,8 @@ enum ErrBits : int {
   ERR_PCAP = 2,          // streaming particle capacity of a CTA exceeded
   ERR_BCAP = 4,          // stored bucket capacity exceeded
   ERR_QCAP = 8,          // rejoin queue capacity exceeded
-  ERR_NONFINITE = 16     // non-finite particle momentum met
+  ERR_NONFINITE = 16     // a field or kinetic-energy sum was not finite, or a particle moved
+                         // more than the sub-step cap across one slice (runaway momentum)
 };
 
 // Stored-particle store: ring of s-levels x nzeta buckets x capacity, structure of arrays.
@@ -88,6 +89,15 @@ struct Params {
   unsigned long long* timers;     // phase timers (builds with GEMPIC_PHASE_TIMERS only)
 };
 
+// Gaussian bunch to sample into the level-0 stored set (gempic_beam, resolved by the host):
+// centre (xc, yc), widths, centre and spread along zeta, charge per macroparticle, species slot
+struct BeamArgs {
+  double xc, yc, sr, sz, zc, gamma, spread, q;
+  long long n;
+  unsigned long long seed;
+  int sp;
+};
+
 // Host-side helpers implemented in gempic_kernels.cu
 int smem_layout(Params& p, int elem_bytes);           // fills offsets, returns total bytes
 cudaError_t configure_kernels(int precision, int smem_bytes, int cluster);
@@ -95,6 +105,7 @@ cudaError_t launch_march(int precision, const Params& p, cudaStream_t s);
 cudaError_t launch_laser_init(int precision, const Params& p, double a0, double waist,
                               double duration, double zeta_c, int pol, cudaStream_t s);
 cudaError_t launch_export_state(int precision, const Params& p, void* dst, cudaStream_t s);
+cudaError_t launch_beam_init(int precision, const Params& p, const BeamArgs& b, cudaStream_t s);
 cudaError_t launch_import_state(int precision, const Params& p, const void* src, cudaStream_t s);
 cudaError_t max_active_clusters(int precision, const Params& p, int* n);
 // allocation-free entry point: march on a caller's state in the public layout

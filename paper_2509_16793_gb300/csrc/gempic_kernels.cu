@@ -1295,6 +1295,8 @@ struct Sink<T, false> {
 // stays inside one cell column (row) has no current on its second x-edge (y-edge row): those
 // sums vanish exactly and are set to zero rather than left to rounding, so they deposit
 // nothing.
+constexpr int kMaxSub = 256;   // sub-steps of one Esirkepov move at most
+
 template <typename T, bool LOCAL>
 __device__ void esirkepov(const Params& p, const Sm<T>& s, const Sink<T, LOCAL>& sk, int ix,
                           T X0, T Y0, T X1, T Y1, T w, T dyo) {
@@ -1302,7 +1304,10 @@ __device__ void esirkepov(const Params& p, const Sm<T>& s, const Sink<T, LOCAL>&
   const T dX = X1 - X0;
   const T dY = Y1 - Y0;
   const T m = fmax(fabs(dX), fabs(dY));
-  const int nsub = m > T(1) ? (int)ceil(m) : 1;
+  // a move of more than kMaxSub cells across one slice only comes from a runaway momentum:
+  // its sub-steps are capped (the deposit is then wrong, and the error word says so)
+  if (m > T(kMaxSub)) atomicOr(p.err, ERR_NONFINITE);
+  const int nsub = m > T(1) ? (int)fmin(ceil(m), T(kMaxSub)) : 1;
   const T cx_ = -(w * s.cst[K_CX]);
   const T cy_ = -(w * s.cst[K_CY]);
   const int mx = p.nx - 1;
@@ -2644,6 +2649,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
                         : tid == DG_FLUX ? p.hx * p.hy * hw
                                          : 1.0;
       p.diag_out[((size_t)sl * kNDiag + tid) * p.C + me] = v * hv;
+      // watchdog: a NaN or infinity anywhere in the slice fields or in a particle's momentum
+      // reaches these FP64 sums
+      if ((tid == DG_FIELD || tid == DG_KIN) && !isfinite(v)) atomicOr(p.err, ERR_NONFINITE);
     }
     __syncthreads();
   }
@@ -2731,6 +2739,71 @@ __global__ void __launch_bounds__(512, 1)
         stw[(((size_t)n * p.C + me) * 6 + c) * p.M + m] = (c == pol) ? v : z;
     }
     cl.sync();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Gaussian bunch placed in the box at creation (beam particles of Sec. 5.1, equal charges):
+// macroparticle i takes the uniforms ((o >> 11) + 1) 2^-53 in (0, 1] from SplitMix64 outputs
+// o = 4 i + j of the bunch's stream and two normal pairs by the Box-Muller transform; it is
+// appended to its slab's bucket of the level-0 stored set (ring slot 0).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double uniform53(unsigned long long s, unsigned long long c) {
+  return (double)((splitmix64(s, c) >> 11) + 1ull) * (1.0 / 9007199254740992.0);
+}
+
+template <typename T>
+__global__ void beam_kernel(const Params p, BeamArgs b) {
+  const double two_pi = 6.283185307179586476925;
+  const double lx = p.nx * p.hx, ly = p.ny * p.hy;
+  const double len = p.varh ? p.zpd[p.nz] : p.nz * p.h;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < b.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long c = 4ull * (unsigned long long)i;
+    const double v0 = uniform53(b.seed, c), v1 = uniform53(b.seed, c + 1);
+    const double v2 = uniform53(b.seed, c + 2), v3 = uniform53(b.seed, c + 3);
+    const double r01 = sqrt(-2.0 * log(v0)), r23 = sqrt(-2.0 * log(v2));
+    const double g0 = r01 * cos(two_pi * v1), g1 = r01 * sin(two_pi * v1);
+    const double g2 = r23 * cos(two_pi * v3), g3 = r23 * sin(two_pi * v3);
+    const double zeta = b.zc + b.sz * g2;
+    if (!(zeta > 0.0) || !(zeta <= len)) continue;
+    // slab m with zeta_m < zeta <= zeta_{m+1}, in-slab offset fz in (0, 1]
+    int m;
+    double fz;
+    if (p.varh) {
+      int lo = 0, hi = p.nz;            // zpd[lo] < zeta <= zpd[hi]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (p.zpd[mid] < zeta) lo = mid; else hi = mid;
+      }
+      m = lo;
+      fz = (zeta - p.zpd[m]) / (p.zpd[m + 1] - p.zpd[m]);
+    } else {
+      const double Z = zeta / p.h;
+      m = (int)ceil(Z) - 1;
+      fz = Z - m;
+    }
+    if (m < 0 || m >= p.nz) continue;
+    double x = fmod(b.xc + b.sr * g0, lx);
+    if (x < 0.0) x += lx;
+    double y = 0.0;
+    if (p.ny > 1) {
+      y = fmod(b.yc + b.sr * g1, ly);
+      if (y < 0.0) y += ly;
+    }
+    const double X = x / p.hx, Y = p.ny > 1 ? y / p.hy : 0.0;
+    const double fX = floor(X), fY = floor(Y);
+    PState<T> P;
+    P.ix = ((int)fX % p.nx + p.nx) % p.nx;
+    P.iy = p.ny > 1 ? ((int)fY % p.ny + p.ny) % p.ny : 0;
+    P.sp = b.sp;
+    P.fx = T(X - fX);
+    P.fy = T(Y - fY);
+    const double gi = b.gamma * (1.0 + b.spread * g3);
+    P.u = V3<T>{T(0), T(0), T(sqrt(fmax(gi * gi - 1.0, 0.0)))};
+    P.q = T(b.q);
+    P.sig = T(0);
+    if (!store_append(p.st, p, 0, m, P, T(fz))) atomicOr(p.err, ERR_BCAP);
   }
 }
 
@@ -2883,6 +2956,16 @@ cudaError_t launch_laser_init(int precision, const Params& p, double a0, double 
   if (shape_class(precision, p) == 1)
     return cudaLaunchKernelEx(&c, laser_kernel<float, 1>, p, a0, waist, dur, zc, pol);
   return cudaLaunchKernelEx(&c, laser_kernel<float>, p, a0, waist, dur, zc, pol);
+}
+
+cudaError_t launch_beam_init(int precision, const Params& p, const BeamArgs& b, cudaStream_t s) {
+  if (b.n <= 0) return cudaSuccess;
+  const int blocks = (int)std::min<long long>((b.n + 255) / 256, 4096);
+  if (precision == 64)
+    beam_kernel<double><<<blocks, 256, 0, s>>>(p, b);
+  else
+    beam_kernel<float><<<blocks, 256, 0, s>>>(p, b);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_export_state(int precision, const Params& p, void* dst, cudaStream_t s) {

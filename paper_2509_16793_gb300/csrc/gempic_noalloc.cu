@@ -37,7 +37,10 @@ constexpr size_t kOffStCnt = kOffOnaxis + kMaxNzeta * 8;        // ring x nzeta 
 constexpr size_t kOffRqCnt = kOffStCnt + kRing * kMaxNzeta * 4; // ring x nzeta ints
 constexpr size_t kOffJflag = kOffRqCnt + kRing * kMaxNzeta * 4; // ring x nzeta ints
 constexpr size_t kScratchBytes = kOffJflag + kRing * kMaxNzeta * 4;
-static_assert(kScratchBytes <= 256 * 1024, "scratch of the allocation-free step exceeds 256 KiB");
+static_assert(kScratchBytes == 248320, "the documented size of the scratch array");
+// the largest tables (nx = ny = 1024, FP64) take 53 248 bytes
+static_assert((512 + 512 + 512 + 1024) * 16 + (512 + 1024) * 8 <= kTablesBytes,
+              "tables of the largest grid exceed their part of the scratch");
 static_assert(kMaxCluster * gempic::kNDiag * 8 <= 2048, "diagnostic partials do not fit");
 
 // The working memory.  In host code this name is only a stand-in for the device array: its
@@ -68,6 +71,16 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
   if (!(g.hx > 0) || !(g.hy > 0) || !(g.h > 0) || !(cfg->delta >= 0)) return GEMPIC_EINVAL;
   if (cfg->precision != 32 && cfg->precision != 64) return GEMPIC_EINVAL;
   if (cfg->hz) return GEMPIC_EINVAL;               // uniform zeta-step only
+  if (cfg->beam) return GEMPIC_EINVAL;             // no stored-particle store for a bunch
+  // no snapshot buffer and no continuity-residual output here
+  if (cfg->flags & (GEMPIC_FLAG_SNAPSHOT | GEMPIC_FLAG_RESIDUAL)) return GEMPIC_EINVAL;
+  {
+    // the host-side tables (twiddles, shifts, kx, ky) must fit their part of the scratch
+    const size_t nyh = g.ny > 1 ? g.ny / 2 : 1;
+    const size_t eb0 = cfg->precision == 64 ? 8 : 4;
+    const size_t tb = (g.nx / 2 + nyh + g.nx / 2 + g.ny) * 2 * eb0 + (g.nx / 2 + g.ny) * eb0;
+    if (tb > kTablesBytes) return GEMPIC_EINVAL;
+  }
   const int eb = cfg->precision == 64 ? 8 : 4;
   const size_t need = (size_t)6 * g.nzeta * g.ny * (g.nx / 2) * 2 * eb;
   if (state_bytes < need) return GEMPIC_EINVAL;
@@ -96,7 +109,8 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess || dev < 0 || dev >= 64) return GEMPIC_ECUDA;
 
-  // launch shape: as gempic_create, without rejoin headroom (no stored particles here)
+  // launch shape: as gempic_create (no stored particles rejoin here, but particles still
+  // move between bands)
   const int nxh = g.nx / 2;
   const int C0 = cfg->cluster_ctas;
   bool chosen = false;
@@ -117,11 +131,16 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
     p.logRB = ilog2(RB);
     p.logKB = ilog2(KB);
     p.nthreads = NT;
-    p.pcap = fresh + 32;
-    if (gempic::smem_layout(p, eb) <= smem_optin) {
-      chosen = true;
-      break;
+    // streaming slots beyond the fresh layer take particles that move in from other bands
+    // (transverse compression): as many as the shared memory allows, up to max(256, fresh)
+    for (int head = std::max(256, fresh); head >= 32; head -= 32) {
+      p.pcap = fresh + head;
+      if (gempic::smem_layout(p, eb) <= smem_optin) {
+        chosen = true;
+        break;
+      }
     }
+    if (chosen) break;
   }
   if (!chosen) return GEMPIC_EINVAL;
 
@@ -204,6 +223,7 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
     diag_out->continuity_residual = -1.0;           // not computed by this entry point
   }
   if (err & gempic::ERR_TIMEOUT) return GEMPIC_ETIMEOUT;
+  if (err & gempic::ERR_NONFINITE) return GEMPIC_ENONFINITE;
   if (err & (gempic::ERR_PCAP | gempic::ERR_BCAP | gempic::ERR_QCAP)) return GEMPIC_EOVERFLOW;
   if (err) return GEMPIC_ESTATE;
   return GEMPIC_OK;

@@ -24,7 +24,7 @@ GEMPIC_FLAG_GT1 = 4
 GEMPIC_FLAG_RESIDUAL = 8
 STATUS = {0: "GEMPIC_OK", -1: "GEMPIC_EINVAL", -2: "GEMPIC_ENOMEM", -3: "GEMPIC_ECUDA",
           -4: "GEMPIC_EUNSTABLE", -5: "GEMPIC_ETIMEOUT", -6: "GEMPIC_ESTATE",
-          -7: "GEMPIC_EOVERFLOW"}
+          -7: "GEMPIC_EOVERFLOW", -8: "GEMPIC_ENONFINITE"}
 FIELDS = {"Ex": 0, "Ey": 1, "Ez": 2, "Bx": 3, "By": 4, "Bz": 5, "jx": 6, "jy": 7, "jz": 8}
 
 
@@ -46,7 +46,15 @@ class gempic_species(Structure):
 
 class gempic_laser(Structure):
     _fields_ = [("a0", c_double), ("waist", c_double), ("duration", c_double),
-                ("zeta_center", c_double), ("pol", c_int32), ("reserved", c_int32)]
+                ("zeta_center", c_double), ("pol", c_int32), ("reserved", c_int32),
+                ("fwhm_intensity", c_double)]
+
+
+class gempic_beam(Structure):
+    _fields_ = [("charge", c_double), ("mass", c_double), ("n_peak", c_double),
+                ("sigma_r", c_double), ("sigma_z", c_double), ("zeta_center", c_double),
+                ("gamma", c_double), ("rel_spread", c_double), ("n_macro", c_int64),
+                ("seed", c_uint64)]
 
 
 class gempic_channel(Structure):
@@ -60,7 +68,8 @@ class gempic_config(Structure):
                 ("laser", POINTER(gempic_laser)), ("stored_bucket_capacity", c_int32),
                 ("particle_headroom", c_int32), ("pipeline_depth", c_int32),
                 ("reserved", c_int32), ("cuda_stream", c_void_p),
-                ("channel", POINTER(gempic_channel)), ("hz", POINTER(c_double))]
+                ("channel", POINTER(gempic_channel)), ("hz", POINTER(c_double)),
+                ("beam", POINTER(gempic_beam))]
 
 
 class gempic_diag(Structure):
@@ -80,6 +89,7 @@ SIGNATURES = {
     "gempic_step": (c_int32, [c_void_p, c_int32]),
     "gempic_step_async": (c_int32, [c_void_p, c_int32]),
     "gempic_sync": (c_int32, [c_void_p]),
+    "gempic_set_wait_limit": (c_int32, [c_void_p, c_int64]),
     "gempic_set_delta": (c_int32, [c_void_p, c_double]),
     "gempic_step_host": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_size_t, POINTER(gempic_diag)]),
     "gempic_state_bytes": (c_size_t, [c_void_p]),
@@ -141,9 +151,11 @@ def _ptr(a) -> int:
 
 def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int = 0,
                          pipeline_depth: int = 0, bucket_capacity: int = 0,
-                         headroom: int = 0, stream: Optional[int] = None):
+                         headroom: int = 0, stream: Optional[int] = None,
+                         laser_fwhm: Optional[float] = None):
     """gempic_config for a paper_2509_16793_gb300.workloads.Workload (plus the arrays it
-    points to, returned so that they outlive the create call)."""
+    points to, returned so that they outlive the create call).  laser_fwhm: pass the laser's
+    intensity FWHM instead of its T (the library converts)."""
     n = len(w.species)
     sp = (gempic_species * max(n, 1))()
     for i, s in enumerate(w.species):
@@ -151,7 +163,15 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
     las = None
     if w.laser is not None:
         L = w.laser
-        las = gempic_laser(L.a0, L.waist, L.duration, L.zeta_center, L.pol, 0)
+        if laser_fwhm is None:
+            las = gempic_laser(L.a0, L.waist, L.duration, L.zeta_center, L.pol, 0, 0.0)
+        else:
+            las = gempic_laser(L.a0, L.waist, 0.0, L.zeta_center, L.pol, 0, float(laser_fwhm))
+    bm = None
+    if w.beam is not None:
+        b = w.beam
+        bm = gempic_beam(b.charge, b.mass, b.n_peak, b.sigma_r, b.sigma_z, b.zeta_center,
+                         b.gamma, b.rel_spread, int(b.n_macro), int(b.seed))
     hz = None
     if w.hz is not None:
         hz = np.ascontiguousarray(w.hz, dtype=np.float64)
@@ -176,8 +196,9 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
         stored_bucket_capacity=bucket_capacity, particle_headroom=headroom,
         pipeline_depth=pipeline_depth, reserved=0, cuda_stream=stream,
         channel=ctypes.pointer(ch) if ch is not None else None,
-        hz=hz.ctypes.data_as(POINTER(c_double)) if hz is not None else None)
-    return cfg, (sp, las, ch, hz)
+        hz=hz.ctypes.data_as(POINTER(c_double)) if hz is not None else None,
+        beam=ctypes.pointer(bm) if bm is not None else None)
+    return cfg, (sp, las, ch, hz, bm)
 
 
 def gempic_step_noalloc(w, step: int, state, onaxis: bool = False, stream: Optional[int] = None,
@@ -247,6 +268,11 @@ class Sim:
 
     set_delta = gempic_set_delta
 
+    def gempic_set_wait_limit(self, polls: int):
+        _check(self.lib.gempic_set_wait_limit(self.h, int(polls)), "gempic_set_wait_limit")
+
+    set_wait_limit = gempic_set_wait_limit
+
     def state_bytes(self) -> int:
         return int(self.lib.gempic_state_bytes(self.h))
 
@@ -281,6 +307,8 @@ class Sim:
         if not (a.dtype != self.dtype and a.nbytes == self.state_bytes() and a.flags["C_CONTIGUOUS"]):
             a = np.ascontiguousarray(a, self.dtype)
         _check(self.lib.gempic_set_state(self.h, a.ctypes.data, a.nbytes, 0), "gempic_set_state")
+
+    set_state = gempic_set_state
 
     def gempic_step_host(self, n: int, state_in: Optional[np.ndarray], state_out: Optional[np.ndarray]):
         d = gempic_diag()

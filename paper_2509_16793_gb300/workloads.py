@@ -62,6 +62,25 @@ class Channel:
 
 
 @dataclass
+class Beam:
+    """Gaussian bunch placed in the box at creation (PWFA-style driver, Sec. 5.1 beam
+    particles): density n_peak exp(-r^2/(2 sigma_r^2) - (zeta - zeta_center)^2/(2 sigma_z^2)),
+    r from the grid's middle node, cold, gamma (1 + rel_spread N(0, 1)) along +z, n_macro
+    equal-charge macroparticles.  A parameter record only: the library and the oracle each
+    sample it from the bunch's own counter-based SplitMix64 stream `seed`."""
+    charge: float = -1.0
+    mass: float = 1.0
+    n_peak: float = 0.01
+    sigma_r: float = 1.0
+    sigma_z: float = 1.0
+    zeta_center: float = 0.0
+    gamma: float = 1000.0
+    rel_spread: float = 1e-3
+    n_macro: int = 1024
+    seed: int = SEED + 1
+
+
+@dataclass
 class StoredParticles:
     """Macroparticles placed inside the box at creation (beam / driver bunch, Sec. 5.1 Q_b).
 
@@ -104,6 +123,7 @@ class Workload:
     particle_law: str = "GT2"    # "GT2" (Eq. trap2, s~ = z) or "GT1" (Eq. trap1, s = ct)
     hz: Optional[np.ndarray] = None     # nzeta slab thicknesses (back to front); None: h
     residual: bool = False       # report the deposit's continuity residual (2-D)
+    beam: Optional[Beam] = None  # Gaussian bunch sampled in the box at creation
 
     @property
     def ncells(self) -> int:

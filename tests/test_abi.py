@@ -58,6 +58,9 @@ def test_ctypes_layout_matches_c():
              offsetof(gempic_config, pipeline_depth), offsetof(gempic_config, cuda_stream));
       printf("%zu %zu %zu\n", sizeof(gempic_channel), offsetof(gempic_config, channel),
              offsetof(gempic_config, hz));
+      printf("%zu %zu %zu %zu %zu\n", sizeof(gempic_beam), offsetof(gempic_beam, n_macro),
+             offsetof(gempic_beam, seed), offsetof(gempic_config, beam),
+             offsetof(gempic_laser, fwhm_intensity));
       return 0;
     }
     """
@@ -75,8 +78,11 @@ def test_ctypes_layout_matches_c():
                                                      G.gempic_config, G.gempic_diag)]
     assert sizes[5:9] == [G.gempic_config.species.offset, G.gempic_config.laser.offset,
                           G.gempic_config.pipeline_depth.offset, G.gempic_config.cuda_stream.offset]
-    assert sizes[9:] == [ctypes.sizeof(G.gempic_channel), G.gempic_config.channel.offset,
-                         G.gempic_config.hz.offset]
+    assert sizes[9:12] == [ctypes.sizeof(G.gempic_channel), G.gempic_config.channel.offset,
+                           G.gempic_config.hz.offset]
+    assert sizes[12:] == [ctypes.sizeof(G.gempic_beam), G.gempic_beam.n_macro.offset,
+                          G.gempic_beam.seed.offset, G.gempic_config.beam.offset,
+                          G.gempic_laser.fwhm_intensity.offset]
 
 
 def test_plain_c_caller_links_and_runs(built):

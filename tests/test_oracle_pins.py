@@ -979,3 +979,84 @@ def test_splitmix64_pin_catches_a_wrong_constant(monkeypatch):
     monkeypatch.setattr(R, "_M1", np.uint64(0xBF58476D1CE4E5B8))
     got = R.splitmix64(1234567, np.arange(5, dtype=np.uint64))
     assert [int(v) for v in got] != SPLITMIX64_1234567
+
+
+# ---------------------------------------------------------------------------------------
+# Gaussian bunch sampler (beam particles of Sec. 5.1 placed at creation): Box-Muller normals,
+# the bunch's moments, its total charge against a brute-force integral of the density, and
+# its density profile against the formula.
+# ---------------------------------------------------------------------------------------
+def test_box_muller_gives_standard_normals():
+    from scipy import stats
+    i = np.arange(100000, dtype=np.uint64)
+    v0, v1 = R.uniform53(7, 2 * i), R.uniform53(7, 2 * i + np.uint64(1))
+    assert v0.min() > 0.0 and v0.max() <= 1.0
+    g0, g1 = R.box_muller(v0, v1)
+    for g in (g0, g1):
+        assert stats.kstest(g, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(g0, g1)[0, 1]) < 0.02
+    # uniform53 keeps the top 53 bits of the output, shifted away from zero
+    assert R.uniform53(1234567, np.zeros(1, np.uint64))[0] == \
+        ((SPLITMIX64_1234567[0] >> 11) + 1) / 2.0 ** 53
+
+
+def _brute_force_bunch_charge(b, ny):
+    """sum of q n(r, zeta) over a fine grid (midpoint rule), +-8 sigma."""
+    ks = np.linspace(-8, 8, 801)
+    d = ks[1] - ks[0]
+    gr = np.exp(-0.5 * ks ** 2) * b.sigma_r * d
+    gz = np.exp(-0.5 * ks ** 2) * b.sigma_z * d
+    return b.charge * b.n_peak * gz.sum() * gr.sum() * (gr.sum() if ny > 1 else 1.0)
+
+
+@pytest.mark.parametrize("ny", [1, 32])
+def test_sample_beam_charge_moments_and_profile(ny):
+    nx, hx, hy = 32, 0.5, 0.5 if ny > 1 else 1.0
+    b = W.Beam(charge=-1.0, mass=1.0, n_peak=0.3, sigma_r=2.0, sigma_z=1.5, zeta_center=12.0,
+               gamma=500.0, rel_spread=0.01, n_macro=200000, seed=99)
+    x, y, z, u, Q = R.sample_beam(b, nx, ny, hx, hy, length=24.0)
+    assert x.size == b.n_macro                            # +-8 sigma_z inside the window
+    total = _brute_force_bunch_charge(b, ny)
+    assert abs(Q.sum() - total) < 1e-9 * abs(total)
+    n = b.n_macro
+    xc, yc = 0.5 * nx * hx, 0.5 * ny * hy
+    assert abs(x.mean() - xc) < 5 * b.sigma_r / math.sqrt(n)
+    assert abs(x.std() - b.sigma_r) < 5 * b.sigma_r / math.sqrt(2 * n)
+    assert abs(z.mean() - b.zeta_center) < 5 * b.sigma_z / math.sqrt(n)
+    assert abs(z.std() - b.sigma_z) < 5 * b.sigma_z / math.sqrt(2 * n)
+    if ny > 1:
+        assert abs(y.mean() - yc) < 5 * b.sigma_r / math.sqrt(n)
+    else:
+        assert np.all(y == 0.0)
+    g = np.sqrt(1.0 + (u ** 2).sum(0))
+    assert np.all(u[0] == 0) and np.all(u[1] == 0)
+    assert abs(g.mean() / b.gamma - 1.0) < 5 * b.rel_spread / math.sqrt(n)
+    assert abs(g.std() / b.gamma - b.rel_spread) < 0.02 * b.rel_spread
+    # density profile: charge per bin over the bin volume against q n(r, zeta) on the axis
+    dz = 0.5
+    edges = b.zeta_center + dz * (np.arange(-4, 5) - 0.5)
+    if ny > 1:
+        sel = (np.abs(x - xc) < 0.5) & (np.abs(y - yc) < 0.5)
+        vol = 1.0
+        tr = (math.sqrt(math.pi / 2) * b.sigma_r * math.erf(0.5 / (math.sqrt(2) * b.sigma_r)) * 2) ** 2
+    else:
+        sel = np.abs(x - xc) < 0.5
+        vol = 1.0
+        tr = math.sqrt(math.pi / 2) * b.sigma_r * math.erf(0.5 / (math.sqrt(2) * b.sigma_r)) * 2
+    hist, _ = np.histogram(z[sel], bins=edges, weights=Q[sel])
+    centres = 0.5 * (edges[1:] + edges[:-1])
+    want = b.charge * b.n_peak * tr / vol * np.array(
+        [math.sqrt(math.pi / 2) * b.sigma_z * (math.erf((c + dz / 2 - b.zeta_center) / (math.sqrt(2) * b.sigma_z))
+                                               - math.erf((c - dz / 2 - b.zeta_center) / (math.sqrt(2) * b.sigma_z)))
+         for c in centres])
+    assert np.abs(hist - want).max() < 0.05 * np.abs(want).max()
+
+
+def test_sample_beam_drops_what_lies_outside_the_window():
+    b = W.Beam(n_peak=0.1, sigma_r=1.0, sigma_z=2.0, zeta_center=1.0, n_macro=20000, seed=3)
+    x, y, z, u, Q = R.sample_beam(b, 16, 16, 0.5, 0.5, length=10.0)
+    frac = 0.5 * (1 + math.erf((10.0 - 1.0) / (math.sqrt(2) * 2.0))) - 0.5 * (1 + math.erf(-1.0 / (math.sqrt(2) * 2.0)))
+    assert abs(x.size / b.n_macro - frac) < 0.02
+    assert z.min() > 0.0 and z.max() <= 10.0
+    # each kept macroparticle keeps total / n_macro
+    assert np.allclose(Q, _brute_force_bunch_charge(b, 16) / b.n_macro, rtol=1e-9)

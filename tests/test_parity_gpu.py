@@ -177,6 +177,85 @@ def test_pwfa_mobile_ions_and_drive_bunch_fp64():
         compare_particles(g.particles(0), oc.stored_particles(), 1e-10)
 
 
+@pytest.mark.parametrize("beam_species", ["electron", "positron"])
+def test_beam_driver_sampled_by_the_library_fp64(beam_species):
+    """The PWFA-style run created through the C struct alone: background electrons and mobile
+    protons injected at the front, no laser, and a Gaussian drive bunch (gempic_beam, n_b =
+    2 n0, gamma = 2000, 1e-3 spread) sampled by the library from its SplitMix64 stream.  The
+    bunch's stored set, the fields and the diagnostics match the oracle's own sampler and step.
+    An electron bunch shares the plasma electrons' species slot; a positron bunch takes a slot
+    of its own."""
+    n0 = 0.01
+    w = W.small_3d(nx=16, ny=16, nzeta=48, ppc=1, precision=64, a0=0.0, n0=n0)
+    L = w.nzeta * w.h
+    w = w.with_(species=[W.Species(-1.0, 1.0, n0, 1), W.Species(1.0, 1836.0, n0, 1)], laser=None,
+                beam=W.Beam(charge=-1.0 if beam_species == "electron" else 1.0, mass=1.0,
+                            n_peak=2.0 * n0, sigma_r=1.5, sigma_z=2.0, zeta_center=0.6 * L,
+                            gamma=2000.0, rel_spread=1e-3, n_macro=3000, seed=77))
+    o = RefSim(w)
+    assert o.stored.n > 2900
+    with gpu_sim(w, cluster_ctas=2) as g:
+        # level 0 as sampled, pushed along s with the level-0 fields
+        oc = copy.deepcopy(o)
+        oc._stored_push()
+        gp = g.particles(0)
+        compare_particles(gp, oc.stored_particles(), 1e-10)
+        assert np.all(gp["species"] == (0 if beam_species == "electron" else 2))
+        for _ in range(3):
+            od = o.step()
+            g.step()
+            check_diag(g.diagnostics(), od, 1e-10)
+            check_state(g.state(), o.state(), 1e-10)
+        oc = copy.deepcopy(o)
+        oc._stored_push()
+        compare_particles(g.particles(0), oc.stored_particles(), 1e-10)
+
+
+def test_beam_driver_2d_fp32_and_invalid_beams():
+    n0 = 0.01
+    w = W.small_2d(nx=32, nzeta=64, ppc=2, precision=32, a0=0.0, n0=n0)
+    L = w.nzeta * w.h
+    w = w.with_(laser=None, beam=W.Beam(charge=-1.0, mass=1.0, n_peak=2.0 * n0, sigma_r=2.0,
+                                        sigma_z=2.0, zeta_center=0.6 * L, gamma=1000.0,
+                                        rel_spread=1e-3, n_macro=4000, seed=5))
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        for _ in range(2):
+            od = o.step()
+            g.step()
+            gd = g.diagnostics()
+            ez, oez = g.onaxis_ez(), od["onaxis_ez"]
+            assert np.abs(ez - oez).max() <= 1e-4 * np.abs(oez).max()
+            for key in ("field_energy", "kinetic_energy"):
+                assert abs(gd[key] - od[key]) <= 1e-4 * abs(od[key]), key
+            assert gd["n_stored"] == od["n_stored"]
+    from paper_2509_16793_gb300 import gempic
+    bad = [dict(sigma_r=0.0), dict(sigma_z=-1.0), dict(gamma=0.5), dict(rel_spread=-1e-3),
+           dict(n_macro=-1), dict(mass=0.0), dict(n_peak=float("nan"))]
+    for kw in bad:
+        with pytest.raises(gempic.GempicError) as e:
+            gpu_sim(w.with_(beam=W.Beam(**{**w.beam.__dict__, **kw})))
+        assert e.value.status == -1, kw
+    # a fifth species slot does not exist
+    four = [W.Species(-1.0, 1.0, n0, 1), W.Species(1.0, 1836.0, n0, 1), W.Species(1.0, 3672.0, n0, 1),
+            W.Species(2.0, 7344.0, 0.5 * n0, 1)]
+    with pytest.raises(gempic.GempicError):
+        gpu_sim(w.with_(species=four, beam=W.Beam(charge=1.0, mass=1.0, sigma_r=1.0, sigma_z=1.0,
+                                                   zeta_center=0.5 * L, n_macro=10)))
+
+
+def test_laser_given_by_its_intensity_fwhm():
+    """gempic_laser.fwhm_intensity: the library converts it to T = FWHM/sqrt(2 ln 2); the run
+    equals the one given T directly."""
+    import math
+    w = W.small_3d(nx=16, ny=16, nzeta=48, ppc=1, precision=64)
+    fwhm = w.laser.duration * math.sqrt(2.0 * math.log(2.0))
+    with gpu_sim(w, cluster_ctas=2) as a, gpu_sim(w, cluster_ctas=2, laser_fwhm=fwhm) as b:
+        a.step(2)
+        b.step(2)
+        check_state(b.state(), a.state(), 1e-13)
+
+
 def test_fp32_matches_fp64_oracle():
     w = W.small_3d(nx=32, ny=32, nzeta=64, ppc=2, precision=32)
     o = RefSim(w)

@@ -133,8 +133,11 @@ typedef struct {
  * distance Delta.  Under GT1 with Delta shorter than the window every fresh particle stops
  * inside it (the paper's stitches), so the stored buckets need room for a full layer. */
 #define GEMPIC_FLAG_GT1       4u
-/* Discrete continuity residual of the deposit (gempic_diag.continuity_residual), 2-D grids
- * only: one more shared-memory row and two CIC reductions per push (a verification mode). */
+/* Verification mode: the discrete continuity residual of the deposit and the Gauss residual
+ * (gempic_diag.continuity_residual, gauss_residual), 2-D and 3-D.  Three more shared-memory
+ * planes of the band's rows (taken from the particle headroom), three CIC reductions per push
+ * (into the owner CTA of each row) and, in 3-D, two more cluster barriers per slice; runs take
+ * the generic kernel.  The fields and particles are those of a run without the flag. */
 #define GEMPIC_FLAG_RESIDUAL  8u
 
 typedef struct {
@@ -178,11 +181,21 @@ typedef struct {
   int64_t n_stored;             /* stored particles at the new level                         */
   int64_t n_rejoined;           /* stored particles that rejoined the zeta march this step   */
   int64_t pushes;               /* streaming crossings performed this step                   */
-  double continuity_residual;   /* with GEMPIC_FLAG_RESIDUAL on a 2-D grid: max over slabs and
-                                   nodes of |(D_start - D_end)/h - d j_x/dx|, D the CIC density
-                                   of the weights at the start and end of every move of the
-                                   step (Sec. 5.1: rho - j_z is carried through the planes);
+  double continuity_residual;   /* with GEMPIC_FLAG_RESIDUAL: max over slabs and nodes of
+                                   |(D_start - D_end)/h - div j_perp| (backward differences:
+                                   j_x on x-edges, j_y on y-edges), D the CIC density of the
+                                   weights at the start and end of every move of the step
+                                   (Sec. 5.1: rho - j_z is carried through the planes);
                                    round-off for the charge-conserving deposit.  -1 otherwise */
+  double gauss_residual;        /* with GEMPIC_FLAG_RESIDUAL: max over the slice planes and
+                                   nodes of |d_x L_x + d_y L_y - (rho - j_z)|: Gauss's law with
+                                   d E_z/d zeta from Eq. EzGu, L_x = E_x - B_y, L_y = E_y + B_x,
+                                   central differences across; rho - j_z = the CIC density of
+                                   the weights of the particles reaching the plane plus the
+                                   neutralising background -sum_s q_s n_s f(r) (stored particles,
+                                   rho - j_z = Q (1 - v_z) ~ 0, are not counted).  Not a
+                                   round-off quantity: the scheme conserves it only while
+                                   dR/ds = 0.  -1 otherwise */
 } gempic_diag;
 
 /* Create a simulation: validates the config (GEMPIC_EUNSTABLE if Delta h omega_p^2 > 4),

@@ -372,6 +372,23 @@ def cic_deposit(plane, X, Y, val):
 
 
 # ----------------------------------------------------------------------------------------
+# Gauss's law on a slice plane (a diagnostic: the scheme does not conserve it while
+# dR/ds != 0).  With d E_z/d zeta taken from Eq. EzGu, div E - rho = d_x L_x + d_y L_y -
+# (rho - j_z), L_x = E_x - B_y, L_y = E_y + B_x (Eqs. Lx, Ly).
+# ----------------------------------------------------------------------------------------
+def gauss_residual(F, D, hx, hy):
+    """max over the nodes of |d_x L_x + d_y L_y - D| for the real-space fields F [6, ny, nx]
+    (E_x, E_y, E_z, B_x, B_y, B_z) of one plane and its (rho - j_z) density D [ny, nx];
+    central differences across (periodic), no y-derivative in 2-D (ny == 1)."""
+    Lx = F[0] - F[4]
+    div = (np.roll(Lx, -1, axis=1) - np.roll(Lx, 1, axis=1)) / (2.0 * hx)
+    if F.shape[1] > 1:
+        Ly = F[1] + F[3]
+        div = div + (np.roll(Ly, -1, axis=0) - np.roll(Ly, 1, axis=0)) / (2.0 * hy)
+    return float(np.abs(div - D).max())
+
+
+# ----------------------------------------------------------------------------------------
 # Plasma channel, Sec. 6 Eq. n_plasma.
 # ----------------------------------------------------------------------------------------
 def channel_profile(ch, dx, dy):
@@ -480,6 +497,14 @@ class RefSim:
             if self.beam_species is None:
                 self.beam_species = len(self.species)
                 self.species.append(type("BeamSpecies", (), dict(charge=b.charge, mass=b.mass))())
+        # neutralising background of the injected species (immobile ions): -sum_s q_s n_s f(r)
+        # on the nodes, f the channel profile; it carries no current
+        qn = sum(s.charge * s.density for s in w.species)
+        xi = np.arange(self.nx) * self.hx - 0.5 * self.nx * self.hx
+        yj = (np.arange(self.ny) * self.hy - 0.5 * self.ny * self.hy) if self.ny > 1 else np.zeros(1)
+        prof = (channel_profile(w.channel, xi[None, :], yj[:, None]) if w.channel is not None
+                else np.ones((self.ny, self.nx)))
+        self.rho_bg = -qn * prof
         self.stored = Particles.empty()
         if w.stored is not None and w.stored.n > 0:
             st = w.stored
@@ -712,6 +737,7 @@ class RefSim:
         kinetic = 0.0
         charge_flux = 0.0
         continuity = 0.0          # max over slabs and nodes of the discrete continuity residual
+        gauss = 0.0               # max over slices and nodes of the Gauss residual
         onaxis = np.zeros(nz)
         if joiners.n:
             jm, _ = self._slab(joiners.zeta)
@@ -803,6 +829,11 @@ class RefSim:
             fl = fields_from_characteristics(sol)
             F0 = np.stack([self.sp.inverse(fl[name]) for name in FIELD_NAMES])
             self.fields_rs[n] = F0
+            # Gauss's law on plane n (not conserved by the scheme while dR/ds != 0): with
+            # d E_z/d zeta from Eq. EzGu, div E - rho = d_x L_x + d_y L_y - (rho - j_z),
+            # L_x = E_x - B_y, L_y = E_y + B_x; central differences across; rho - j_z is the
+            # CIC density of the particles reaching plane n plus the neutralising background
+            gauss = max(gauss, gauss_residual(F0, Dn + self.rho_bg, self.hx, self.hy))
             field_energy += 0.5 * float(np.sum(F0 ** 2)) * self.hx * self.hy * h
             onaxis[n] = F0[2, ny // 2, nx // 2]
             new1 = sol
@@ -818,6 +849,7 @@ class RefSim:
                                      * self._mass(self.stored.sp) * (g - 1.0)))
         return dict(field_energy=field_energy, kinetic_energy=kinetic + stored_ke,
                     charge_flux=charge_flux, continuity_residual=continuity,
+                    gauss_residual=gauss,
                     onaxis_ez=onaxis, n_trapped=T.n,
                     n_stored=self.stored.n)
 

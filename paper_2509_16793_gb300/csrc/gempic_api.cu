@@ -95,13 +95,16 @@ gempic_status check_device_error(gempic_sim* s) {
 
 cudaError_t ensure_diag_cap(gempic_sim* s, int n) {
   if (n <= s->diag_cap) return cudaSuccess;
-  double *d = nullptr, *o = nullptr, *r = nullptr;
+  double *d = nullptr, *o = nullptr, *r = nullptr, *gr = nullptr;
   cudaError_t e = dalloc(s, &d, (size_t)n * gempic::kNDiag * s->p.C * sizeof(double));
   if (e != cudaSuccess) return e;
   e = dalloc(s, &o, (size_t)n * s->p.nz * sizeof(double));
   if (e != cudaSuccess) return e;
   e = dalloc(s, &r, (size_t)n * sizeof(double));
   if (e != cudaSuccess) return e;
+  e = dalloc(s, &gr, (size_t)n * sizeof(double));
+  if (e != cudaSuccess) return e;
+  s->p.gauss_out = gr;
   s->p.diag_out = d;
   s->p.onaxis = o;
   s->p.resid_out = r;
@@ -314,7 +317,7 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
   s->eb = cfg->precision == 64 ? 8 : 4;
 
   Params& p = s->p;
-  p.resid = (cfg->flags & GEMPIC_FLAG_RESIDUAL) && g.ny == 1 ? 1 : 0;   // sizes shared memory
+  p.resid = (cfg->flags & GEMPIC_FLAG_RESIDUAL) ? 1 : 0;   // sizes shared memory
   p.nx = g.nx;
   p.ny = g.ny;
   p.nz = g.nzeta;
@@ -753,9 +756,13 @@ gempic_status gempic_get_diagnostics(gempic_sim* s, gempic_diag* out) {
   out->n_rejoined = (int64_t)std::llround(v[gempic::DG_REJOIN]);
   out->pushes = (int64_t)std::llround(v[gempic::DG_PUSH]);
   out->continuity_residual = -1.0;
+  out->gauss_residual = -1.0;
   if (p.resid) {
     e = cudaMemcpyAsync(&out->continuity_residual, p.resid_out + sl, sizeof(double),
                         cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&out->gauss_residual, p.gauss_out + sl, sizeof(double),
+                          cudaMemcpyDeviceToHost, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_fail(s, e);
   }

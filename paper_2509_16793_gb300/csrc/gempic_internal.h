@@ -58,8 +58,10 @@ struct Params {
   int inject, diag, snapshot;
   int gt1;                        // particle law: 0 = GT2 (Eq. trap2), 1 = GT1 (Eq. trap1)
   int varh;                       // 1: slab thicknesses from hzt (variable zeta-step)
-  int resid;                      // 1: continuity residual of the deposit (2-D only)
-  double* resid_out;              // [nsteps] its maximum per s-step
+  int resid;                      // 1: continuity and Gauss residuals (verification mode)
+  double* resid_out;              // [nsteps] continuity residual maximum per s-step
+  double* gauss_out;              // [nsteps] Gauss residual maximum per s-step
+  double bg_qn;                   // neutralising background -sum_s q_s n_s (immobile ions)
   const void* hzt;                // [nz] slab thickness h_n (slab n: planes n, n+1), real type
   const double* zpd;              // [nz+1] plane positions zeta_n (plane 0 at the back)
   int pcap;                       // streaming particle slots per CTA in shared memory

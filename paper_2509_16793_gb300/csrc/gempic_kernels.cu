@@ -533,8 +533,12 @@ struct Sm {
   T *pfx, *pfy, *pux, *puy, *puz, *psig, *pq;
   int* fstack;      // [fcap] free particle slots
   int* misc;        // MiscSlot
-  double* dacc;     // [kNDiag]; dacc[0] holds the march's continuity-residual maximum
-  T* dd;            // [nx] continuity residual (2-D): w CIC(start) - w CIC(end) of the slice
+  double* dacc;     // [kNDiag]; dacc[0], dacc[1]: the march's continuity and Gauss residual
+                    // maxima (verification mode)
+  T* dd;            // [RBe][nx] continuity residual: w CIC(start) - w CIC(end) of the slab's
+                    // moves on the own rows (RBe = RB in 3-D, 1 in 2-D)
+  T* dn;            // [2][RBe][nx] (rho - j_z) CIC density of the particles reaching a plane,
+                    // by plane parity (Gauss residual)
   double* dwarp;    // [nthreads / 32][kNDiag] per-warp FP64 diagnostic sums of this march
 };
 
@@ -596,6 +600,7 @@ __device__ Sm<T> carve(const Params& p, unsigned char* base) {
   s.dacc = (double*)(base + p.o_misc + 32);
   s.dwarp = s.dacc + kNDiag;
   s.dd = (T*)(base + p.o_dd);
+  s.dn = s.dd + (size_t)(p.ny > 1 ? p.RB : 1) * p.nx;
   return s;
 }
 
@@ -1495,9 +1500,39 @@ struct SliceAcc {     // per-thread, per-slice diagnostics in the working precis
 
 // LAW: 0 = GT2, 1 = GT1, -1 = either (read from p.gt1); RES: the continuity-residual
 // deposit may be compiled in (taken when p.resid)
+// CIC of v at node (ix, iy) + (fx, fy) into a plane of own rows [RBe][nx], reduced into the
+// CTA that owns each row (verification mode)
+template <typename T>
+__device__ __forceinline__ void res_cic(const Params& p, T* plane, int me, int ix, int iy, T fx,
+                                        T fy, T v) {
+  const int ix1 = (ix + 1) & (p.nx - 1);
+  if (p.ny == 1) {
+    const uint32_t b = sh_addr(plane);
+    red_local(b + (uint32_t)(ix * sizeof(T)), v * (T(1) - fx));
+    red_local(b + (uint32_t)(ix1 * sizeof(T)), v * fx);
+    return;
+  }
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int y = (iy + t) & (p.ny - 1);
+    const T wy = t == 0 ? T(1) - fy : fy;
+    const int r = y >> p.logRB;
+    const uint32_t a = sh_addr(plane + (size_t)(y & (p.RB - 1)) * p.nx);
+    const uint32_t a0 = a + (uint32_t)(ix * sizeof(T)), a1 = a + (uint32_t)(ix1 * sizeof(T));
+    const T v0 = v * ((T(1) - fx) * wy), v1 = v * (fx * wy);
+    if (r == me) {
+      red_local(a0, v0);
+      red_local(a1, v1);
+    } else {
+      red_cluster(cluster_addr(a0, r), v0);
+      red_cluster(cluster_addr(a1, r), v1);
+    }
+  }
+}
+
 template <typename T, int LAW, bool RES>
 __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PState<T>& P, T d,
-                            int me, T& fz_trap, SliceAcc<T>& acc) {
+                            int me, T& fz_trap, SliceAcc<T>& acc, T* dn) {
   SUB_DECL
   const int yl = P.iy - (me << p.logRB);
   const bool own = p.ny == 1 || (yl >= 0 && yl < p.RB);
@@ -1555,15 +1590,21 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   SUB_MARK(2);
   if constexpr (RES) {
     if (p.resid) {
-      // 2-D continuity residual: +w at the start of the move, -w at its end (CIC)
-      const uint32_t b = sh_addr(s.dd);
-      const int mx = p.nx - 1;
+      // verification mode: +w CIC at the start of the move and -w at its end (continuity
+      // residual), +w at the end of a move that reaches the plane (its (rho - j_z) density,
+      // Gauss residual), into the own rows of the rows' owners
       const T fXe = floor(X1), fe = X1 - fXe;
-      const int ie = (P.ix + (int)fXe) & mx;
-      red_local(b + (uint32_t)(P.ix * sizeof(T)), w * (T(1) - P.fx));
-      red_local(b + (uint32_t)(((P.ix + 1) & mx) * sizeof(T)), w * P.fx);
-      red_local(b + (uint32_t)(ie * sizeof(T)), -(w * (T(1) - fe)));
-      red_local(b + (uint32_t)(((ie + 1) & mx) * sizeof(T)), -(w * fe));
+      const int ie = (P.ix + (int)fXe) & (p.nx - 1);
+      int je = 0;
+      T ge = T(0);
+      if (p.ny > 1) {
+        const T fYe = floor(Y1);
+        ge = Y1 - fYe;
+        je = (P.iy + (int)fYe) & (p.ny - 1);
+      }
+      res_cic(p, s.dd, me, P.ix, P.iy, P.fx, P.fy, w);
+      res_cic(p, s.dd, me, ie, je, fe, ge, -w);
+      if (!trap) res_cic(p, dn, me, ie, je, fe, ge, w);
     }
   }
   // diagnostics: kinetic energy N m (gamma-1) dt/Delta, (rho - j_z) flux through plane n
@@ -1974,8 +2015,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   // take the generic one)
   constexpr int LAW = SH == 1 ? 0 : -1;
   const bool varh = SH != 1 && p.varh != 0;
-  const bool resid = SH != 1 && p.resid != 0;     // 2-D continuity residual (p.resid: ny == 1)
-  T rmax = T(0);
+  const bool resid = SH != 1 && p.resid != 0;     // continuity and Gauss residuals
+  const int rbe = p.ny > 1 ? p.RB : 1;            // own rows of the residual planes
+  T rmax = T(0), gmax = T(0);
   const T* hzt = (const T*)p.hzt;
   const int me = (int)cl.block_rank();
   const int tid = threadIdx.x;
@@ -2011,8 +2053,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   }
   for (int i = tid; i < (NT >> 5) * kNDiag; i += NT) s.dwarp[i] = 0.0;
   if (resid) {
-    for (int i = tid; i < p.nx; i += NT) s.dd[i] = T(0);
-    if (tid == 0) s.dacc[0] = 0.0;
+    for (int i = tid; i < 3 * rbe * p.nx; i += NT) s.dd[i] = T(0);
+    if (tid == 0) s.dacc[0] = s.dacc[1] = 0.0;
   }
   __syncthreads();
   if (p.inject) {
@@ -2128,6 +2170,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     // variable zeta-step: the slab of this slice (planes n, n+1) sets the step-dependent
     // constants (the previous slice's stored phase has finished reading them)
     const T hn = varh ? hzt[n] : h;
+    T* const dn_n = s.dn + (size_t)(n & 1) * rbe * p.nx;   // arrival density of plane n
     if (varh) {
       __syncthreads();
       if (tid == 0) {
@@ -2149,7 +2192,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         if (cw < 0) continue;
         PState<T> P = get_particle(p, s, ov, i, cw);
         T fzt;
-        const bool trap = stream_push<T, LAW, SH != 1>(p, s, Fcur, P, hn, me, fzt, sa);
+        const bool trap = stream_push<T, LAW, SH != 1>(p, s, Fcur, P, hn, me, fzt, sa, dn_n);
         bool gone = trap;
         if (trap) {
           ++ntrap;
@@ -2199,7 +2242,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         PState<T> P = store_read<T>(p.rq, p, ge, fz);
         ++nrej;
         T fzt;
-        const bool trap = stream_push<T, LAW, SH != 1>(p, s, Fcur, P, fz * hn, me, fzt, sa);
+        const bool trap = stream_push<T, LAW, SH != 1>(p, s, Fcur, P, fz * hn, me, fzt, sa, dn_n);
         if (trap) {
           ++ntrap;
           if (!store_append(p.st, p, s1, n, P, fzt)) atomicOr(p.err, ERR_BCAP);
@@ -2459,16 +2502,33 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     // add and the row transforms; 2-D runs have no inbox
     if (p.ny == 1) __syncthreads();
     if (resid) {
-      // (D(start) - D(end))/h_n - (j_x(i) - j_x(i-1))/hx on every node of the row, before the
-      // beam current joins j; each thread clears the entries it read
+      // (D(start) - D(end))/h_n - div j_perp on every node of the own rows, before the beam
+      // current joins j (backward differences: j_x on x-edges, j_y on y-edges).  3-D: the
+      // row below the band is the last own row of the CTA below, read once every CTA has
+      // folded its rows and before any adds the beam current.  Each thread clears the
+      // entries it read.
+      if (p.ny > 1) cl.sync();
       const T* jx = s.J + (size_t)p.JOFF * p.nx;
-      const T ihx = T(1.0 / p.hx), ih = T(1) / hn;
-      for (int i = tid; i < p.nx; i += NT) {
-        const T r = s.dd[i] * ih - (jx[i] - jx[(i - 1) & (p.nx - 1)]) * ihx;
-        rmax = fmax(rmax, fabs(r));
+      const T* jy = s.J + ((size_t)p.JR + p.JOFF) * p.nx;
+      const T ihx = T(1.0 / p.hx), ihy = T(1.0 / p.hy), ih = T(1) / hn;
+      const int below = (me + p.C - 1) & (p.C - 1);
+      const uint32_t jyb =
+          p.ny > 1 ? cluster_addr(sh_addr(jy + (size_t)(p.RB - 1) * p.nx), below) : 0u;
+      for (int i = tid; i < rbe * p.nx; i += NT) {
+        const int row = i >> p.lognx, x = i & (p.nx - 1);
+        const int o = row * p.nx;
+        T div = (jx[o + x] - jx[o + ((x - 1) & (p.nx - 1))]) * ihx;
+        if (p.ny > 1) {
+          const T jyd = row > 0 ? jy[o - p.nx + x] : ldc(jyb + (uint32_t)(x * sizeof(T)), T(0));
+          div += (jy[o + x] - jyd) * ihy;
+        }
+        rmax = fmax(rmax, fabs(s.dd[i] * ih - div));
         s.dd[i] = T(0);
       }
-      __syncthreads();
+      if (p.ny > 1)
+        cl.sync();
+      else
+        __syncthreads();
     }
     // beam current of this level at the half-slice n + 1/2 (own rows); the flag is cleared
     // by CTA 0 after B2, once every CTA has read it
@@ -2598,6 +2658,42 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     }
     cl.sync();                                                      // B4: fields of slice n
     TIMER_MARK(PH_B4);
+    if (resid) {
+      // Gauss residual on plane n: d_x L_x + d_y L_y - (rho - j_z), L_x = E_x - B_y,
+      // L_y = E_y + B_x, central differences; rho - j_z = arrival density + background.  The
+      // row above the band is the fields' halo row, the row below the last own row of the CTA
+      // below (its fields of slice n stay until its inverse transform of slice n - 2).
+      const T* Ex = Fnew;
+      const T* Ey = Fnew + fplane;
+      const T* Bx = Fnew + 3 * (size_t)fplane;
+      const T* By = Fnew + 4 * (size_t)fplane;
+      const T hihx = T(0.5 / p.hx), hihy = T(0.5 / p.hy);
+      const int below = (me + p.C - 1) & (p.C - 1);
+      const size_t lrow = (size_t)(p.RB - 1) * p.nx;
+      const uint32_t eyb = p.ny > 1 ? cluster_addr(sh_addr(Ey + lrow), below) : 0u;
+      const uint32_t bxb = p.ny > 1 ? cluster_addr(sh_addr(Bx + lrow), below) : 0u;
+      for (int i = tid; i < rbe * p.nx; i += NT) {
+        const int row = i >> p.lognx, x = i & (p.nx - 1);
+        const int o = row * p.nx;
+        const int xp = (x + 1) & (p.nx - 1), xm = (x - 1) & (p.nx - 1);
+        T g = ((Ex[o + xp] - By[o + xp]) - (Ex[o + xm] - By[o + xm])) * hihx;
+        if (p.ny > 1) {
+          const T lyu = Ey[o + p.nx + x] + Bx[o + p.nx + x];
+          const T lyd = row > 0 ? Ey[o - p.nx + x] + Bx[o - p.nx + x]
+                                : ldc(eyb + (uint32_t)(x * sizeof(T)), T(0)) +
+                                      ldc(bxb + (uint32_t)(x * sizeof(T)), T(0));
+          g += (lyu - lyd) * hihy;
+        }
+        T bg = T(p.bg_qn);
+        if (p.chan_a != 0.0) {
+          const T dx = T(x - (p.nx >> 1)) * s.cst[K_HX];
+          const T dy = p.ny > 1 ? T((me << p.logRB) + row - (p.ny >> 1)) * s.cst[K_HY] : T(0);
+          bg *= T(1) + T(p.chan_a) * exp(-(dx * dx + dy * dy) * T(p.chan_ir2));
+        }
+        gmax = fmax(gmax, fabs(g - (dn_n[i] + bg)));
+        dn_n[i] = T(0);
+      }
+    }
     if (p.diag) {
       const int yc = p.ny / 2;
       if (tid == 0 && (yc >> p.logRB) == me)
@@ -2627,14 +2723,23 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   if (p.P > 1 && me == 0 && tid == 0) st_release_u64(p.progress + cid, prog_value(k, nz, nz));
 
   if (resid) {
-    // the march's largest residual: non-negative doubles order like their bit patterns
-    double v = (double)rmax;
-    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
-    if ((tid & 31) == 0)
-      atomicMax(reinterpret_cast<unsigned long long*>(s.dacc),
-                (unsigned long long)__double_as_longlong(v));
-    __syncthreads();
-    if (tid == 0) p.resid_out[sl] = s.dacc[0];
+    // the march's largest residuals: non-negative doubles order like their bit patterns
+    double v[2] = {(double)rmax, (double)gmax};
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      for (int off = 16; off > 0; off >>= 1) v[c] = fmax(v[c], __shfl_xor_sync(0xffffffffu, v[c], off));
+      if ((tid & 31) == 0)
+        atomicMax(reinterpret_cast<unsigned long long*>(s.dacc + c),
+                  (unsigned long long)__double_as_longlong(v[c]));
+    }
+    cl.sync();
+    // the cluster's maxima: CTA 0 reads every CTA's partial maxima
+    if (me == 0 && tid < 2) {
+      double m = 0.0;
+      for (int r = 0; r < p.C; ++r) m = fmax(m, ldc(cluster_addr(sh_addr(s.dacc + tid), r), 0.0));
+      (tid == 0 ? p.resid_out : p.gauss_out)[sl] = m;
+    }
+    cl.sync();
   }
   // diagnostics: per-CTA FP64 partials
   if (p.diag) {
@@ -2877,9 +2982,10 @@ int smem_layout(Params& p, int eb) {
   // that a particle slot costs 4 + 7 reals of shared memory
   p.fcap = std::min(p.pcap, 512);
   o += align16(p.pcap * 4) + align16(7 * p.pcap * eb + p.fcap * 4);
-  // continuity residual (2-D): one row of start-minus-end CIC densities
+  // verification mode: start-minus-end CIC densities of the own rows (continuity residual)
+  // and two planes of arrival densities (Gauss residual)
   p.o_dd = o;
-  if (p.resid && p.ny == 1) o += align16(p.nx * eb);
+  if (p.resid) o += align16(3 * (p.ny > 1 ? p.RB : 1) * p.nx * eb);
   p.o_misc = o;
   o += 32 + kNDiag * 8 + (p.nthreads / 32) * kNDiag * 8;
   p.smem_bytes = align16(o);
@@ -2889,7 +2995,8 @@ int smem_layout(Params& p, int eb) {
 // kernel instantiation for the grid: 1 = FP32 128 x 128 with an even band (length-128
 // transforms only), 0 = any size
 static int shape_class(int precision, const Params& p) {
-  return precision == 32 && p.nx == 128 && p.ny == 128 && (p.RB & 1) == 0 && !p.gt1 && !p.varh
+  return precision == 32 && p.nx == 128 && p.ny == 128 && (p.RB & 1) == 0 && !p.gt1 && !p.varh &&
+                 !p.resid
              ? 1 : 0;
 }
 

@@ -39,13 +39,14 @@ inline gempic_status setup_species(const gempic_config* cfg, Params& p) {
       hmin = std::min(hmin, cfg->hz[n]);
     }
   }
-  double wp2 = 0.0, wmax = 0.0;
+  double wp2 = 0.0, wmax = 0.0, qn = 0.0;
   int ppc_sum = 0, off = 0;
   for (int i = 0; i < cfg->nspecies; ++i) {
     const gempic_species& sp = cfg->species[i];
     if (sp.ppc < 1 || !(sp.mass > 0) || !(sp.density >= 0)) return GEMPIC_EINVAL;
     if (sp.density > 0 && sp.charge == 0) return GEMPIC_EINVAL;
     wp2 += sp.charge * sp.charge * sp.density / sp.mass;
+    qn += sp.charge * sp.density;
     wmax = std::max(wmax, std::fabs(sp.charge * sp.density / sp.ppc));
     ppc_sum += sp.ppc;
     p.qm[i] = sp.charge / sp.mass;
@@ -58,6 +59,7 @@ inline gempic_status setup_species(const gempic_config* cfg, Params& p) {
   }
   if (cfg->delta * hmax * wp2 * fmax > 4.0 * (1.0 + 1e-12)) return GEMPIC_EUNSTABLE;
   p.nspecies = cfg->nspecies;
+  p.bg_qn = -qn;
   p.nlayer = off;
   p.ppc_sum = ppc_sum;
   p.chan_a = a;

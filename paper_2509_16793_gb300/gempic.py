@@ -76,7 +76,7 @@ class gempic_diag(Structure):
     _fields_ = [("step", c_int64), ("field_energy", c_double), ("kinetic_energy", c_double),
                 ("charge_flux", c_double), ("n_trapped", c_int64), ("n_stored", c_int64),
                 ("n_rejoined", c_int64), ("pushes", c_int64),
-                ("continuity_residual", c_double)]
+                ("continuity_residual", c_double), ("gauss_residual", c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

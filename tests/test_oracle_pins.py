@@ -1060,3 +1060,90 @@ def test_sample_beam_drops_what_lies_outside_the_window():
     assert z.min() > 0.0 and z.max() <= 10.0
     # each kept macroparticle keeps total / n_macro
     assert np.allclose(Q, _brute_force_bunch_charge(b, 16) / b.n_macro, rtol=1e-9)
+
+
+# ---------------------------------------------------------------------------------------
+# Gauss residual (a diagnostic, not a round-off quantity): div E - rho on the slice planes
+# with d E_z/d zeta from Eq. EzGu, i.e. d_x L_x + d_y L_y - (rho - j_z).
+# ---------------------------------------------------------------------------------------
+def test_gauss_residual_of_analytic_fields():
+    """Central differences of sines: (sin k(x+h) - sin k(x-h))/(2h) = cos(kx) sin(kh)/h.  With
+    L_x = E_x - B_y = (A + A') sin(kx x) and L_y = E_y + B_x = (C + C') sin(ky y), the residual
+    at x = y = 0 (both cosines 1) is (A + A') sin(kx hx)/hx + (C + C') sin(ky hy)/hy; a sign
+    slip in L_x or L_y, or a missing 1/2 or hy, changes it."""
+    nx, ny, hx, hy = 16, 8, 0.7, 0.45
+    x = np.arange(nx) * hx
+    y = np.arange(ny) * hy
+    kx, ky = 2 * math.pi * 3 / (nx * hx), 2 * math.pi * 1 / (ny * hy)
+    A, A2, C, C2 = 0.3, 0.2, -0.15, 0.4
+    F = np.zeros((6, ny, nx))
+    F[0] = A * np.sin(kx * x)[None, :]
+    F[4] = -A2 * np.sin(kx * x)[None, :]
+    F[1] = C * np.sin(ky * y)[:, None]
+    F[3] = C2 * np.sin(ky * y)[:, None]
+    want = abs((A + A2) * math.sin(kx * hx) / hx + (C + C2) * math.sin(ky * hy) / hy)
+    assert abs(R.gauss_residual(F, np.zeros((ny, nx)), hx, hy) - want) < 1e-13
+    # a uniform (rho - j_z) shifts every node by the same amount
+    assert abs(R.gauss_residual(np.zeros((6, ny, nx)), np.full((ny, nx), -0.25), hx, hy) - 0.25) < 1e-15
+    # 2-D: no y-derivative
+    F2 = F[:, :1, :].copy()
+    F2[1] = 5.0
+    assert abs(R.gauss_residual(F2, np.zeros((1, nx)), hx, 1.0)
+               - abs((A + A2) * math.sin(kx * hx) / hx)) < 1e-13
+
+
+def _brute_cic_density(x, y, w, nx, ny, hx, hy):
+    D = np.zeros((ny, nx))
+    for xi, yi, wi in zip(x / hx, y / hy, w):
+        i0, j0 = int(math.floor(xi)), int(math.floor(yi))
+        fx, fy = xi - i0, yi - j0
+        for dj, wy in ((0, 1 - fy), (1, fy)):
+            for di, wx in ((0, 1 - fx), (1, fx)):
+                D[(j0 + dj) % ny, (i0 + di) % nx] += wi * wx * (wy if ny > 1 else (1.0 if dj == 0 else 0.0))
+    return D
+
+
+@pytest.mark.parametrize("ny", [1, 8])
+def test_gauss_residual_of_a_quiet_plasma_is_the_layers_cic_noise(ny):
+    """No driver: fields stay zero and every particle keeps its transverse position, so the
+    residual of every plane is the fresh layer's CIC density minus q n0 (the background),
+    computed here by brute force from the seeded injection offsets."""
+    w = (W.small_2d(nx=16, nzeta=12, ppc=3) if ny == 1 else
+         W.small_3d(nx=8, ny=8, nzeta=12, ppc=2)).with_(laser=None)
+    d = R.RefSim(w).step()
+    P = R.RefSim(w)._inject()                  # the layer of s-step 0
+    wgt = P.Q / (w.hx * w.hy * w.delta)
+    D = _brute_cic_density(P.x, P.y, wgt, w.nx, w.ny, w.hx, w.hy)
+    sp = w.species[0]
+    want = np.abs(D - sp.charge * sp.density).max()
+    assert want > 0.1 * abs(sp.charge * sp.density)
+    assert abs(d["gauss_residual"] - want) < 1e-14
+
+
+def test_gauss_residual_background_of_a_neutral_pair_plasma_is_zero():
+    """Electrons and positrons of equal density: the background is zero, the residual is the
+    CIC noise of both layers together."""
+    w = W.small_2d(nx=16, nzeta=8, ppc=2).with_(laser=None)
+    n0 = w.species[0].density
+    w = w.with_(species=[W.Species(-1.0, 1.0, n0, 2), W.Species(1.0, 1.0, n0, 2)],
+                delta=0.5 * w.delta)
+    sim = R.RefSim(w)
+    assert np.all(sim.rho_bg == 0.0)
+    P = R.RefSim(w)._inject()
+    d = sim.step()
+    D = _brute_cic_density(P.x, P.y, P.Q / (w.hx * w.hy * w.delta), w.nx, w.ny, w.hx, w.hy)
+    assert abs(d["gauss_residual"] - np.abs(D).max()) < 1e-14
+
+
+def test_gauss_pin_catches_a_flipped_background():
+    w = W.small_2d(nx=16, nzeta=12, ppc=3).with_(laser=None)
+
+    class Flipped(R.RefSim):
+        def __init__(self, wl):
+            super().__init__(wl)
+            self.rho_bg = -self.rho_bg            # the planted mistake: q n0 instead of -q n0
+    d = Flipped(w).step()
+    P = R.RefSim(w)._inject()
+    D = _brute_cic_density(P.x, P.y, P.Q / (w.hx * w.hy * w.delta), w.nx, w.ny, w.hx, w.hy)
+    qn = w.species[0].charge * w.species[0].density
+    assert abs(d["gauss_residual"] - np.abs(D - qn).max()) > 0.5 * abs(qn)

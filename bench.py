@@ -23,7 +23,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# Algorithmic work per unit (counted from the kernels):
+# Algorithmic work per unit, counted from the kernels:
 FLOP_PER_PUSH = 330.0            # gather 52 + two-pass Boris 156 + advance 22 + Esirkepov/CIC 100
 FLOP_PER_MODE = 150.0            # corrector + App. B closed form + fields, complex arithmetic
 BYTES_PER_CELL = {32: 48.0, 64: 96.0}   # spectral state read + written once per s-step
@@ -147,29 +147,55 @@ def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
     return world * units_per_rank / seconds
 
 
-def oracle_sample(w, seconds: float, max_steps: int):
-    """Time the FP64 oracle on a bounded sample of the workload: the same transverse grid and
-    particles per cell over a 64-slice window; pushes/s extrapolate per slice."""
-    os.environ.setdefault("OMP_NUM_THREADS", "1")
-    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+def oracle_window(w):
+    """The bounded sample of the workload the oracle is timed on: the same transverse grid and
+    particles per cell over a 64-slice window (laser centred in it); pushes/s per slice."""
+    return w.with_(nzeta=64, precision=64,
+                   laser=w.laser.__class__(**{**w.laser.__dict__, "zeta_center": 32 * w.h}))
+
+
+def _oracle_worker(job):
+    """One oracle process: s-steps of the window until `seconds` or `max_steps`; returns the
+    wall-clock start and end of the timed loop and the pushes done."""
+    sample, seconds, max_steps = job
     from oracle import RefSim
-    sample = w.with_(nzeta=64, precision=64,
-                     laser=w.laser.__class__(**{**w.laser.__dict__, "zeta_center": 32 * w.h}))
     sim = RefSim(sample)
-    t0 = time.perf_counter()
+    t0 = time.time()
     steps = 0
     while steps < max_steps:
         sim.step()
         steps += 1
-        if time.perf_counter() - t0 > seconds:
+        if time.time() - t0 > seconds:
             break
-    dt = time.perf_counter() - t0
-    pushes = sample.pushes_per_step * steps
-    return {"value": pushes / dt, "unit": "pushes/s", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} s-step(s) of a {sample.nx}x{sample.ny}x{sample.nzeta} window "
-                      f"of the workload ({sample.pushes_per_step} pushes/step), FP64 numpy, "
-                      f"single thread, {dt:.1f} s",
-            "ms_per_step": dt / steps * 1e3}
+    return t0, time.time(), sample.pushes_per_step * steps, steps
+
+
+def oracle_sample(w, seconds: float, max_steps: int, procs: int = 0):
+    """Time the FP64 oracle, as it stands, on the host cores: `procs` independent processes
+    (0 = one per core; spawned, so safe after CUDA is initialised) each march their own seeded
+    copy of the window; the rate is all pushes over the wall time from the first start to the
+    last end.  procs = 1 runs in this process (single thread)."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    sample = oracle_window(w)
+    n = procs if procs > 0 else (os.cpu_count() or 1)
+    if n == 1:
+        res = [_oracle_worker((sample, seconds, max_steps))]
+    else:
+        import multiprocessing as mp
+        jobs = [(sample.with_(seed=sample.seed + i), seconds, max_steps) for i in range(n)]
+        with mp.get_context("spawn").Pool(n) as pool:
+            res = pool.map(_oracle_worker, jobs)
+    t0 = min(r[0] for r in res)
+    t1 = max(r[1] for r in res)
+    pushes = sum(r[2] for r in res)
+    steps = sum(r[3] for r in res)
+    dt = t1 - t0
+    return {"value": pushes / dt, "unit": "pushes/s", "cores": n, "kind": "oracle",
+            "sample": f"{steps} s-step(s) in {n} process(es) of a {sample.nx}x{sample.ny}x"
+                      f"{sample.nzeta} window of the workload ({sample.pushes_per_step} "
+                      f"pushes/step), FP64 numpy, one thread per process, {dt:.1f} s wall",
+            "ms_per_step": dt / max(1, steps // n) * 1e3}
 
 
 def run_reference(args, w):
@@ -177,15 +203,15 @@ def run_reference(args, w):
     if rank != 0:
         return 0
     from oracle import RefSim  # noqa: F401
-    # warm-up steps and timed steps on the bounded sample
-    base = oracle_sample(w, seconds=1e9, max_steps=max(1, args.warmup))
+    # warm-up steps and timed steps on the bounded sample, one process per host core
+    base = oracle_sample(w, seconds=1e9, max_steps=max(1, args.warmup), procs=1)
     cb = oracle_sample(w, seconds=1e9, max_steps=max(1, args.steps))
     line = {"impl": "reference", "metric": "particle-pushes/s", "value": cb["value"],
             "unit": "pushes/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": cb["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_dict(w),
-            "cpu_baseline": {"value": cb["value"], "unit": "pushes/s", "cores": 1,
+            "cpu_baseline": {"value": cb["value"], "unit": "pushes/s", "cores": cb["cores"],
                              "kind": "oracle", "sample": cb["sample"]},
             "e2e": {"value": cb["value"], "unit": "pushes/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -252,6 +278,9 @@ def main():
     stream = torch.cuda.current_stream()
     # replicas: each rank simulates its own plasma (seed offset), no data-path collective
     wr = replica_workload(w, rank)
+    # the measured FP32 denominator of the ALU roofline: an FMA probe (its own clocks sampled)
+    with ClockSampler(local) as pclk:
+        probe_tf, probe_ms = gempic.gempic_probe_fp32_fma(400000, stream.cuda_stream)
     sim = gempic.Sim(wr, stream=stream.cuda_stream, pipeline_depth=args.pipeline,
                      bucket_capacity=args.bucket_capacity)
     shape = sim.launch_shape()
@@ -304,15 +333,22 @@ def main():
     clocks = clk.summary()
     peaks = measured_peaks()
     sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    peak_alu = fp32_peak_tflops(peaks.get("sm_max_mhz", 2070.0))
+    peak_alu = probe_tf
     flops = algorithmic_flops(w) * args.steps
     achieved = flops / (ms / 1e3) / 1e12
     hbm = algorithmic_bytes(w) * args.steps / (ms / 1e3) / 1e9
     traffic = measured_traffic(w) * args.steps if measured_traffic(w) else None
     roof = {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
             "frac": achieved / peak_alu, "traffic": traffic,
-            "peak_source": "152 SM x 128 FP32 lanes x 2 x max SM clock (MEASURED_PEAKS sm_max_mhz)",
+            "traffic_source": ("profiles/march_kernel_lwfa3d_128x128x1024.md (ncu DRAM bytes per "
+                               "s-step, used while its kernel hash matches the source)"
+                               if traffic else None),
+            "peak_source": f"measured: FP32 FMA probe (gempic_probe_fp32_fma, {probe_ms:.0f} ms, "
+                           f"SM clock median {pclk.summary().get('sm_mhz')} MHz); spec figure "
+                           f"152 SM x 128 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz = "
+                           f"{fp32_peak_tflops(peaks.get('sm_max_mhz', 2070.0)):.1f}",
             "kernel": "march_kernel<float>",
+            "launches": launches, "launch_ms_avg": ms / max(1, launches),
             "hbm": {"achieved": hbm, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                     "frac": hbm / peaks.get("hbm_gbs", 6800.0), "of": "measured"}}
     # the metric's FP32-vs-FP64-plain comparison: the 2-D FP64 workload (128 x 256, 4 ppc, Delta
@@ -332,6 +368,8 @@ def main():
         try:
             cpu = oracle_sample(w, seconds=15.0, max_steps=20)
             cpu.pop("ms_per_step", None)
+            one = oracle_sample(w, seconds=10.0, max_steps=20, procs=1)
+            cpu["single_core"] = {"value": one["value"], "sample": one["sample"]}
         except Exception as ex:  # the baseline is reported, never the target
             cpu = {"error": str(ex)}
     line = {"metric": "particle-pushes/s", "value": value, "unit": "pushes/s",

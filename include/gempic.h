@@ -139,6 +139,9 @@ typedef struct {
  * (into the owner CTA of each row) and, in 3-D, two more cluster barriers per slice; runs take
  * the generic kernel.  The fields and particles are those of a run without the flag. */
 #define GEMPIC_FLAG_RESIDUAL  8u
+/* Keep the current j of the last s-step of each call (gempic_get_current), e.g. to train the
+ * denoiser on pairs of runs. */
+#define GEMPIC_FLAG_CURRENT   16u
 
 typedef struct {
   gempic_grid grid;
@@ -196,6 +199,7 @@ typedef struct {
                                    rho - j_z = Q (1 - v_z) ~ 0, are not counted).  Not a
                                    round-off quantity: the scheme conserves it only while
                                    dR/ds = 0.  -1 otherwise */
+  double stored_kinetic_energy; /* the stored set's part of kinetic_energy */
 } gempic_diag;
 
 /* Create a simulation: validates the config (GEMPIC_EUNSTABLE if Delta h omega_p^2 > 4),
@@ -361,6 +365,80 @@ void gempic_batch_destroy(gempic_batch* b);
  * call waits for its stream. */
 gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t step, void* state,
                                   size_t state_bytes, gempic_diag* diag_out, double* onaxis_out);
+
+/* ---- Learned current denoiser -----------------------------------------------------------
+ * The paper has no counterpart.  With few particles per cell the deposited current is noisy;
+ * a small 3-D convolutional net trained on pairs of runs of this method (few versus many
+ * particles per cell) maps the current of a sparse run towards that of a dense one, so that
+ * the sparse run can stand in for the dense one.  Net: x0 = j/scale, h1 = relu(conv1(x0)),
+ * h2 = relu(conv2(h1)), r = conv3(h2), denoised j = j + scale r; every conv is 3x3x3 (taps
+ * dz, dy, dx in {-1, 0, 1}, periodic across, zero outside the window along zeta) with 16
+ * hidden channels; activations and weights in BF16, accumulation in FP32 on the tensor cores.
+ * Currents are device FP32 arrays [nz][3][ny][nx] (j_x on x-edges, j_y on y-edges in 3-D, j_z
+ * on nodes, every plane a half-slice), the layout of gempic_get_current.
+ * Parameters: one FP32 vector of gempic_denoiser_param_count() entries, W1 [27][3][16], b1 [16],
+ * W2 [27][16][16], b2 [16], W3 [27][16][3], b3 [3] (tap index (dz+1) 9 + (dy+1) 3 + (dx+1),
+ * then input channel, then output channel).  All calls use the current device; they wait
+ * for their stream.  GEMPIC_ETIMEOUT if a bounded tensor-core wait gave up. */
+typedef struct gempic_denoiser gempic_denoiser;
+
+size_t gempic_denoiser_param_count(void);
+
+/* params: host FP32 vector, or NULL for all zeros (the identity on j); scale > 0 normalises
+ * the current (e.g. |q n0|). */
+gempic_status gempic_denoiser_create(const float* params, double scale, gempic_denoiser** out);
+
+/* Replace or read the parameters (host vectors of n = gempic_denoiser_param_count() floats);
+ * setting them also resets the optimiser. */
+gempic_status gempic_denoiser_set_params(gempic_denoiser* d, const float* params, size_t n);
+gempic_status gempic_denoiser_get_params(gempic_denoiser* d, float* params, size_t n);
+
+/* j_out = denoised j_in (device arrays, may not alias). */
+gempic_status gempic_denoiser_apply(gempic_denoiser* d, const float* j_in, float* j_out,
+                                    int32_t nx, int32_t ny, int32_t nz, void* cuda_stream);
+
+/* Loss mean((j_in/scale + r - j_target/scale)^2) over the planes z_margin .. nz-1-z_margin
+ * and its gradient with respect to the parameters (host vector grad_host, may be NULL). */
+gempic_status gempic_denoiser_grad(gempic_denoiser* d, const float* j_in, const float* j_target,
+                                   int32_t nx, int32_t ny, int32_t nz, int32_t z_margin,
+                                   double* loss, float* grad_host, void* cuda_stream);
+
+/* gempic_denoiser_grad followed by one Adam step (Kingma and Ba 2015: beta1 = 0.9,
+ * beta2 = 0.999, eps = 1e-8, bias-corrected) with learning rate lr; loss is the pre-step loss. */
+gempic_status gempic_denoiser_train_step(gempic_denoiser* d, const float* j_in,
+                                         const float* j_target, int32_t nx, int32_t ny,
+                                         int32_t nz, int32_t z_margin, double lr, double* loss,
+                                         void* cuda_stream);
+
+void gempic_denoiser_destroy(gempic_denoiser* d);
+
+/* Denoised s-steps (FP32 simulations): with d set, every s-step of gempic_step runs in two
+ * passes.  The first marches the particles with the plain deposit and keeps its current (the
+ * plain deposit stays the fallback and the judge); the denoiser maps that current; the second
+ * recomputes the new level from the old one with the denoised current (the denoiser acts on j
+ * before the field update) and pushes the stored set with those fields.  The pushes of the
+ * s-step saw the first pass's fields: the net needs the current of half-slices on both sides
+ * of each one, which the march produces only one at a time.  Such steps march one s-step at
+ * a time (no wavefront) and wait for their stream.  The diagnostics combine both passes: the
+ * field energy, on-axis E_z and stored set are the second pass's, the streaming particles'
+ * energy, flux and counts the first's.  d = NULL returns to plain steps.  The denoiser is
+ * borrowed: it must outlive its use.  GEMPIC_EINVAL for an FP64 simulation. */
+gempic_status gempic_set_denoiser(struct gempic_sim* sim, gempic_denoiser* d);
+
+/* The plain current of the last s-step (needs GEMPIC_FLAG_CURRENT or a denoiser): [nzeta][3]
+ * [ny][nx] in the simulation's precision, j_x at x + hx/2, j_y at y + hy/2 (3-D), plane n the
+ * half-slice n + 1/2, beam current included.  GEMPIC_ESTATE before the first s-step. */
+gempic_status gempic_get_current(struct gempic_sim* sim, void* dst, size_t bytes,
+                                 int32_t dst_is_device);
+
+/* FP32 FMA throughput probe (measurement only; the paper has no counterpart): the measured
+ * denominator of the ALU roofline that the FP32 particle push is reported against.  Launches a
+ * short warm-up and then one timed kernel of 4 CTAs x 512 threads per SM, each thread running
+ * 16 independent FMA chains for `iters` iterations (2 FLOP per FMA), on cuda_stream (NULL =
+ * legacy default stream), timed with CUDA events.  *tflops receives the achieved TFLOP/s,
+ * *ms (may be NULL) the kernel's time.  Allocates no device memory.  GEMPIC_EINVAL for
+ * iters < 1 or tflops NULL, GEMPIC_ECUDA if a CUDA call fails.  Waits for its stream. */
+gempic_status gempic_probe_fp32_fma(void* cuda_stream, int32_t iters, double* tflops, double* ms);
 
 const char* gempic_strerror(gempic_status s);
 

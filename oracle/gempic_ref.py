@@ -723,7 +723,7 @@ class RefSim:
         return R, jbeam, nremoved
 
     # -- the zeta march at level s^1 (Sec. 4.1: from the front of the window towards the back) -------
-    def _march(self, delta_field, inject, joiners, jbeam):
+    def _march(self, delta_field, inject, joiners, jbeam, current_hook=None):
         nx, ny, nz = self.nx, self.ny, self.nz
         old = {k: v.copy() for k, v in self.S.items()}
         D = self.delta
@@ -805,6 +805,8 @@ class RefSim:
             jx += jbeam[n, 0]
             jy += jbeam[n, 1]
             jz += jbeam[n, 2]
+            if current_hook is not None:            # record or replace the half-slice's current
+                jx, jy, jz = current_hook(n, jx, jy, jz)
             # transform the currents at the half-slice n + 1/2
             Jx = self.sp.forward(jx, "x")
             Jy = self.sp.forward(jy, "y" if ny > 1 else "")
@@ -848,6 +850,7 @@ class RefSim:
             stored_ke = float(np.sum((self.stored.Q / self._charge(self.stored.sp))
                                      * self._mass(self.stored.sp) * (g - 1.0)))
         return dict(field_energy=field_energy, kinetic_energy=kinetic + stored_ke,
+                    stored_kinetic_energy=stored_ke,
                     charge_flux=charge_flux, continuity_residual=continuity,
                     gauss_residual=gauss,
                     onaxis_ez=onaxis, n_trapped=T.n,
@@ -865,6 +868,42 @@ class RefSim:
             d["step"] = self.step_index
             self.diag = d
         return self.diag
+
+    # -- one s-step with a current denoiser (two passes) --------------------------------------
+    def step_denoised(self, denoise):
+        """The denoised s-step of the library: the first pass marches the particles with the
+        plain deposit and records the current J [nz, 3, ny, nx] of every half-slice; the
+        second recomputes the level from the unchanged old one with denoise(J) in place of the
+        deposit (no particles), so the stored set is pushed at the next s-step with its
+        fields.  Diagnostics: fields and stored set from the second pass, the streaming
+        particles from the first."""
+        joiners, jbeam, nrem = self._stored_push()
+        old = {k: v.copy() for k, v in self.S.items()}
+        J = np.zeros((self.nz, 3, self.ny, self.nx))
+
+        def record(n, jx, jy, jz):
+            J[n, 0], J[n, 1], J[n, 2] = jx, jy, jz
+            return jx, jy, jz
+        d1 = self._march(delta_field=self.delta, inject=True, joiners=joiners, jbeam=jbeam,
+                         current_hook=record)
+        self.S = old
+        Jd = denoise(J)
+
+        def replace(n, jx, jy, jz):
+            return Jd[n, 0].copy(), Jd[n, 1].copy(), Jd[n, 2].copy()
+        d3 = self._march(delta_field=self.delta, inject=False, joiners=Particles.empty(),
+                         jbeam=self._zero_jbeam(), current_hook=replace)
+        self.delta_stored = self.delta
+        d = dict(d3)
+        for key in ("kinetic_energy", "charge_flux", "n_trapped", "continuity_residual"):
+            d[key] = d1[key]
+        d["n_rejoined"] = joiners.n
+        d["n_stored_removed"] = nrem
+        self.step_index += 1
+        d["step"] = self.step_index
+        d["current"] = J
+        self.diag = d
+        return d
 
     # -- exports in the canonical layout used for comparisons ---------------------------------
     def state(self) -> np.ndarray:

@@ -41,6 +41,12 @@ struct gempic_sim {
   int last_launch_n = 0;
   std::vector<void*> allocs;
   void* stage = nullptr;           // device staging of the public state layout (host copies)
+  // learned current denoiser (two passes per s-step) and the current of the last s-step
+  gempic_denoiser* dn = nullptr;
+  void* jcap = nullptr;            // [nz][3][ny][nx] plain current of the last s-step
+  void* jden = nullptr;            // its denoised form
+  void* state2 = nullptr;          // provisional level of the first pass
+  bool denoised_last = false;      // the last launch was a denoised s-step
   // particles placed before the first step: absolute positions
   std::vector<double> px, py, pz, pux, puy, puz, pq;
   std::vector<int> psp;
@@ -384,6 +390,13 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
       if (cfg->particle_headroom > 0 || head <= 32) break;
       head -= 32;
     }
+    // many particles per cell: a fresh layer larger than the shared memory keeps as many
+    // slots there as fit and continues in the overflow slots in global memory
+    for (int pc = (fresh / 256) * 256; !chosen && cfg->particle_headroom <= 0 && pc >= 512;
+         pc -= 256) {
+      p.pcap = pc;
+      if (gempic::smem_layout(p, s->eb) <= smem_optin) chosen = true;
+    }
     if (chosen) break;
   }
   if (!chosen) {
@@ -502,6 +515,10 @@ gempic_status gempic_create(const gempic_config* cfg, gempic_sim** out) {
     p.gcap = std::max(1024, g.nx * (g.ny / p.C) * std::max(ppc_sum, 1) * 2);
     ALLOC(p.pover, (size_t)std::max(s->pmax, 1) * p.C * p.gcap * (4 + 7 * eb));
     if (p.snapshot) ALLOC(p.snap, (size_t)9 * g.nzeta * nperp * eb);
+    if (cfg->flags & GEMPIC_FLAG_CURRENT) {
+      ALLOC(s->jcap, (size_t)3 * g.nzeta * nperp * eb);
+      p.jcap = s->jcap;
+    }
 #ifdef GEMPIC_PHASE_TIMERS
     ALLOC(p.timers, timer_words(p) * sizeof(unsigned long long));
 #endif
@@ -544,11 +561,65 @@ gempic_status gempic_add_particles(gempic_sim* s, int64_t n, const double* x, co
   return GEMPIC_OK;
 }
 
+// One denoised s-step: the first pass marches the particles with the plain deposit and keeps
+// its current, the denoiser maps that current, the second pass recomputes the level from the
+// old one with the denoised current and pushes the stored set with the final fields.
+static gempic_status denoised_step(gempic_sim* s) {
+  cudaError_t e = ensure_diag_cap(s, 2);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  Params q = s->p;
+  q.k0 = s->k;
+  q.nsteps = 1;
+  q.P = 1;
+  q.inject = q.nspecies > 0 ? 1 : 0;
+  q.delta_field = s->p.delta;
+  q.skip_stored = 1;
+  q.jcap = s->jcap;
+  q.state_out = s->state2;
+  e = gempic::launch_march(s->cfg.precision, q, s->stream);
+  s->launches++;
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  const gempic_status st = gempic_denoiser_apply(s->dn, (const float*)s->jcap, (float*)s->jden,
+                                                 s->p.nx, s->p.ny, s->p.nz, (void*)s->stream);
+  s->launches += 5;
+  if (st != GEMPIC_OK) {
+    s->failed = st;
+    return st;
+  }
+  Params r = q;
+  r.inject = 0;
+  r.skip_stored = 0;
+  r.fields_only = 1;
+  r.jcap = nullptr;
+  r.jext = s->jden;
+  r.state_out = nullptr;
+  r.diag_out = s->p.diag_out + (size_t)gempic::kNDiag * s->p.C;
+  r.onaxis = s->p.onaxis + s->p.nz;
+  r.resid_out = s->p.resid_out + 1;
+  r.gauss_out = s->p.gauss_out + 1;
+  e = gempic::launch_march(s->cfg.precision, r, s->stream);
+  s->launches++;
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  s->last_launch_k0 = s->k;
+  s->last_launch_n = 1;
+  s->denoised_last = true;
+  s->k += 1;
+  return GEMPIC_OK;
+}
+
 gempic_status gempic_step_async(gempic_sim* s, int32_t n) {
   if (!s || n < 0) return GEMPIC_EINVAL;
   gempic_status st = ensure_initialized(s);
   if (st != GEMPIC_OK) return st;
   if (n == 0) return GEMPIC_OK;
+  if (s->dn) {
+    for (int i = 0; i < n; ++i) {
+      st = denoised_step(s);
+      if (st != GEMPIC_OK) return st;
+    }
+    return GEMPIC_OK;
+  }
+  s->denoised_last = false;
   cudaError_t e = ensure_diag_cap(s, n);
   if (e != cudaSuccess) return cuda_fail(s, e);
   Params q = s->p;
@@ -747,6 +818,24 @@ gempic_status gempic_get_diagnostics(gempic_sim* s, gempic_diag* out) {
     v[i] = 0.0;
     for (int r = 0; r < p.C; ++r) v[i] += d[(size_t)i * p.C + r];
   }
+  if (s->denoised_last) {
+    // the second pass holds the fields and the stored set; the first the streaming particles
+    std::vector<double> d2((size_t)gempic::kNDiag * p.C);
+    e = cudaMemcpyAsync(d2.data(), p.diag_out + (size_t)gempic::kNDiag * p.C,
+                        d2.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+    double v2[gempic::kNDiag];
+    for (int i = 0; i < gempic::kNDiag; ++i) {
+      v2[i] = 0.0;
+      for (int r = 0; r < p.C; ++r) v2[i] += d2[(size_t)i * p.C + r];
+    }
+    v[gempic::DG_FIELD] = v2[gempic::DG_FIELD];
+    v[gempic::DG_KIN] += v2[gempic::DG_KIN];
+    v[gempic::DG_KST] = v2[gempic::DG_KST];
+    v[gempic::DG_STORED] = v2[gempic::DG_STORED];
+    v[gempic::DG_LOST] = v2[gempic::DG_LOST];
+  }
   out->step = s->k;
   out->field_energy = v[gempic::DG_FIELD];
   out->kinetic_energy = v[gempic::DG_KIN];
@@ -755,6 +844,7 @@ gempic_status gempic_get_diagnostics(gempic_sim* s, gempic_diag* out) {
   out->n_stored = (int64_t)std::llround(v[gempic::DG_STORED]);
   out->n_rejoined = (int64_t)std::llround(v[gempic::DG_REJOIN]);
   out->pushes = (int64_t)std::llround(v[gempic::DG_PUSH]);
+  out->stored_kinetic_energy = v[gempic::DG_KST];
   out->continuity_residual = -1.0;
   out->gauss_residual = -1.0;
   if (p.resid) {
@@ -773,7 +863,7 @@ gempic_status gempic_get_onaxis_ez(gempic_sim* s, double* dst, int32_t n) {
   if (!s || !dst || n < s->p.nz) return GEMPIC_EINVAL;
   gempic_status st = ensure_initialized(s);
   if (st != GEMPIC_OK) return st;
-  const int sl = s->last_launch_n - 1;
+  const int sl = s->denoised_last ? 1 : s->last_launch_n - 1;
   cudaError_t e = cudaMemcpyAsync(dst, s->p.onaxis + (size_t)sl * s->p.nz, s->p.nz * sizeof(double),
                                   cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -781,6 +871,43 @@ gempic_status gempic_get_onaxis_ez(gempic_sim* s, double* dst, int32_t n) {
 }
 
 int64_t gempic_launch_count(const gempic_sim* s) { return s ? s->launches : 0; }
+
+gempic_status gempic_set_denoiser(gempic_sim* s, gempic_denoiser* d) {
+  if (!s) return GEMPIC_EINVAL;
+  if (s->failed != GEMPIC_OK) return GEMPIC_ESTATE;
+  if (d && s->cfg.precision != 32) return GEMPIC_EINVAL;
+  if (d) {
+    const size_t nb = (size_t)3 * s->p.nz * s->p.ny * s->p.nx * s->eb;
+    const size_t sb = (size_t)(s->p.nz + 1) * 6 * (s->p.nx / 2) * s->p.ny * 2 * s->eb;
+    cudaError_t e = cudaSuccess;
+    if (!s->jcap) {
+      e = dalloc(s, &s->jcap, nb);
+      s->p.jcap = s->jcap;
+    }
+    if (e == cudaSuccess && !s->jden) e = dalloc(s, &s->jden, nb);
+    if (e == cudaSuccess && !s->state2) e = dalloc(s, &s->state2, sb);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return e == cudaErrorMemoryAllocation ? GEMPIC_ENOMEM : GEMPIC_ECUDA;
+    }
+  }
+  s->dn = d;
+  return GEMPIC_OK;
+}
+
+gempic_status gempic_get_current(gempic_sim* s, void* dst, size_t bytes, int32_t dst_is_device) {
+  if (!s || !dst) return GEMPIC_EINVAL;
+  if (!s->jcap || s->k == 0) return GEMPIC_ESTATE;
+  if (s->failed != GEMPIC_OK) return GEMPIC_ESTATE;
+  const size_t nb = (size_t)3 * s->p.nz * s->p.ny * s->p.nx * s->eb;
+  if (bytes < nb) return GEMPIC_EINVAL;
+  cudaError_t e = cudaMemcpyAsync(dst, s->jcap, nb,
+                                  dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  return cuda_fail(s, e);
+}
 
 #ifdef GEMPIC_PHASE_TIMERS
 // profiling builds only: the raw device error word

@@ -7,8 +7,9 @@
 namespace gempic {
 
 constexpr int kMaxSpecies = 4;
-constexpr int kNDiag = 8;        // per-CTA FP64 diagnostic partials per s-step
-enum DiagSlot { DG_FIELD = 0, DG_KIN, DG_FLUX, DG_TRAP, DG_STORED, DG_REJOIN, DG_PUSH, DG_LOST };
+constexpr int kNDiag = 9;        // per-CTA FP64 diagnostic partials per s-step
+enum DiagSlot { DG_FIELD = 0, DG_KIN, DG_FLUX, DG_TRAP, DG_STORED, DG_REJOIN, DG_PUSH, DG_LOST,
+                DG_KST };         // DG_KST: the stored set's part of DG_KIN
 
 // Device error word bits.
 enum ErrBits : int {
@@ -87,6 +88,15 @@ struct Params {
   double* diag_out;               // [nsteps][kNDiag][C]
   double* onaxis;                 // [nsteps][nz]
   void* snap;                     // [9][nz][ny][nx]
+  // denoised s-step (two passes): the first marches the particles with the plain deposit,
+  // captures its current (jcap) and writes its provisional level to state_out, leaving the
+  // stored set for the second (skip_stored); the second takes the denoised current (jext) on
+  // the unchanged old level, with no fresh or rejoining particles (fields_only), and pushes
+  // the stored set with the final fields
+  void* jcap;                     // [nz][3][ny][nx] current of the last march of the launch
+  const void* jext;               // [nz][3][ny][nx] current replacing the deposit
+  void* state_out;                // new level written here instead of over the old one
+  int skip_stored, fields_only;
   void* pover;                    // overflow particle slots [P*C][int cell; 7 reals][gcap]
   unsigned long long* timers;     // phase timers (builds with GEMPIC_PHASE_TIMERS only)
 };

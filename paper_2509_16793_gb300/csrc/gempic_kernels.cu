@@ -1925,6 +1925,7 @@ __device__ void stored_phase(const Params& p, const Sm<T>& s, const T* Fn, const
   if (p.diag) {
     if (__any_sync(0xffffffffu, (dsto | dlost) != 0)) {
       warp_diag_add(s.dwarp, DG_KIN, dkin);
+      warp_diag_add(s.dwarp, DG_KST, dkin);
       warp_diag_add(s.dwarp, DG_STORED, dsto);
       warp_diag_add(s.dwarp, DG_LOST, dlost);
     }
@@ -2036,7 +2037,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   TIMER_DECL
 
   // FP64 diagnostics go to per-warp rows in shared memory (section below), not registers
-  T fe = T(0);
+  double fe = 0.0;      // field energy of the march: each slice's FP32 partial added in FP64
 
   // reset the next level's stored buckets and rejoin queues (free: their last reader, the
   // march of step k+1-ring, has completed)
@@ -2088,16 +2089,32 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         const T dy = p.ny > 1 ? (T(iy - (p.ny >> 1)) + fy) * s.cst[K_HY] : T(0);
         q *= T(1) + T(p.chan_a) * exp(-(dx * dx + dy * dy) * T(p.chan_ir2));
       }
-      s.pcell[i] = ix | (iy << 10) | (sp << 20);
-      s.pfx[i] = fx;
-      s.pfy[i] = fy;
-      s.pux[i] = T(0);
-      s.puy[i] = T(0);
-      s.puz[i] = T(0);
-      s.psig[i] = T(0);
-      s.pq[i] = q;
+      if (i < p.pcap) {
+        s.pcell[i] = ix | (iy << 10) | (sp << 20);
+        s.pfx[i] = fx;
+        s.pfy[i] = fy;
+        s.pux[i] = T(0);
+        s.puy[i] = T(0);
+        s.puz[i] = T(0);
+        s.psig[i] = T(0);
+        s.pq[i] = q;
+      } else {
+        // a fresh layer larger than the shared-memory slots (many particles per cell)
+        // continues in the CTA's overflow slots in global memory
+        PState<T> P;
+        P.ix = ix;
+        P.iy = iy;
+        P.sp = sp;
+        P.fx = fx;
+        P.fy = fy;
+        P.u = V3<T>{T(0), T(0), T(0)};
+        P.sig = T(0);
+        P.q = q;
+        put_particle(p, s, ov, i, P);
+      }
     }
-    if (tid == 0) s.misc[M_PCOUNT] = nmine;
+    if (tid == 0) s.misc[M_PCOUNT] = min(nmine, p.pcap + p.gcap);
+    if (nmine > p.pcap + p.gcap && tid == 0) atomicOr(p.err, ERR_PCAP);
   }
   // ghost slice: field-free
   T* Fcur = s.F[0];
@@ -2122,7 +2139,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   Cx<T> o[6];                                     // old level, block n
   Cx<T> j0px = jpx, j0py = jpx;                   // old level j at n + 1/2
   const Cx<T>* st = (const Cx<T>*)p.state;
-  Cx<T>* stw = (Cx<T>*)p.state;
+  // the new level is written over the old one, or (first pass of a denoised s-step) elsewhere
+  Cx<T>* stw = (Cx<T>*)(p.state_out ? p.state_out : p.state);
   auto blk = [&](int b, int c) -> size_t {
     if constexpr (CANON) {
       const int kxg = (me << p.logKB) + kxl;
@@ -2151,6 +2169,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     for (int c = 0; c < 6; ++c) o[c] = ldcg(st + blk(nz - 1, c));
   }
   const bool snap_step = p.snapshot && k == p.k0 + p.nsteps - 1;
+  const bool cap_step = p.jcap != nullptr && k == p.k0 + p.nsteps - 1;
   // per-slice counters of other marches, read once per CTA and broadcast in shared memory
   if (tid == 0) {
     s.misc[M_RQN] = ldcg(p.rq.cnt + (size_t)s1 * nz + (nz - 1));
@@ -2234,7 +2253,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       TIMER_MARK(PH_AR);
       // stored particles that rejoin the march at this slice (partial first step), taken by
       // the CTA that owns their row
-      const int nq = min(s.misc[M_RQN], p.bcap);
+      const int nq = p.fields_only ? 0 : min(s.misc[M_RQN], p.bcap);
       for (int e = tid; e < nq; e += NT) {
         const size_t ge = ((size_t)s1 * nz + n) * p.bcap + e;
         if ((((ldcg(p.rq.cell + ge) >> 10) & 1023) >> p.logRB) != me) continue;
@@ -2543,17 +2562,31 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         jb[g] = T(0);
       }
     }
-    if (snap_step) {
+    if (snap_step || cap_step) {
       __syncthreads();
       T* sn = (T*)p.snap;
+      T* jc = (T*)p.jcap;
       for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
         const int c = i >> (p.logRB + p.lognx);
         const int rem = i & ((p.RB << p.lognx) - 1);
-        sn[(((size_t)(6 + c) * nz + n) * p.ny + (me << p.logRB)) * p.nx + rem] =
-            s.J[((size_t)c * p.JR + p.JOFF) * p.nx + rem];
+        const T v = s.J[((size_t)c * p.JR + p.JOFF) * p.nx + rem];
+        if (snap_step) sn[(((size_t)(6 + c) * nz + n) * p.ny + (me << p.logRB)) * p.nx + rem] = v;
+        // the current of the s-step in [nzeta][3][ny][nx] (the denoiser's layout)
+        if (cap_step) jc[(((size_t)n * 3 + c) * p.ny + (me << p.logRB)) * p.nx + rem] = v;
       }
     }
-    if (beam_slice || snap_step) __syncthreads();
+    if (p.jext) {
+      // second pass of a denoised s-step: the half-slice's current is the given one
+      __syncthreads();
+      const T* je = (const T*)p.jext;
+      for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
+        const int c = i >> (p.logRB + p.lognx);
+        const int rem = i & ((p.RB << p.lognx) - 1);
+        s.J[((size_t)c * p.JR + p.JOFF) * p.nx + rem] =
+            ldcg(je + (((size_t)n * 3 + c) * p.ny + (me << p.logRB)) * p.nx + rem);
+      }
+    }
+    if (beam_slice || snap_step || cap_step || p.jext) __syncthreads();
     TIMER_MARK(PH_BEAM);
     // ---------------- B: row FFTs of the currents, transposed to the kx owners ------------
     forward_rows<T, SH>(cl, p, s, me, true);
@@ -2647,7 +2680,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     {
       T fs = T(0);
       inverse_rows<T, SH>(p, s, Fnew, fs);
-      fe += varh ? fs * hn : fs;
+      fe += (double)(varh ? fs * hn : fs);
     }
     TIMER_MARK(PH_INV);
     if constexpr (sizeof(T) == 4) {
@@ -2710,7 +2743,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     }
     // ---------------- E: stored particles of cell (zeta_n, zeta_{n+1}] along s -------------
     // (most cells hold no stored particle: the call is skipped, uniformly over the CTA)
-    if (s.misc[M_STN] > 0) stored_phase(p, s, Fnew, Fcur, s1, s2, n, me, s.misc[M_STN], varh);
+    if (s.misc[M_STN] > 0 && !p.skip_stored)
+      stored_phase(p, s, Fnew, Fcur, s1, s2, n, me, s.misc[M_STN], varh);
     TIMER_MARK(PH_E);
     T* t = Fcur;
     Fcur = Fnew;

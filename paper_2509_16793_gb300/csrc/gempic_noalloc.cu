@@ -220,6 +220,7 @@ extern "C" gempic_status gempic_step_noalloc(const gempic_config* cfg, int64_t s
     diag_out->n_stored = (int64_t)std::llround(v[gempic::DG_STORED]);
     diag_out->n_rejoined = (int64_t)std::llround(v[gempic::DG_REJOIN]);
     diag_out->pushes = (int64_t)std::llround(v[gempic::DG_PUSH]);
+    diag_out->stored_kinetic_energy = v[gempic::DG_KST];
     diag_out->continuity_residual = -1.0;           // not computed by this entry point
     diag_out->gauss_residual = -1.0;
   }

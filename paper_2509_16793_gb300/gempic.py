@@ -22,6 +22,7 @@ GEMPIC_FLAG_DIAG = 1
 GEMPIC_FLAG_SNAPSHOT = 2
 GEMPIC_FLAG_GT1 = 4
 GEMPIC_FLAG_RESIDUAL = 8
+GEMPIC_FLAG_CURRENT = 16
 STATUS = {0: "GEMPIC_OK", -1: "GEMPIC_EINVAL", -2: "GEMPIC_ENOMEM", -3: "GEMPIC_ECUDA",
           -4: "GEMPIC_EUNSTABLE", -5: "GEMPIC_ETIMEOUT", -6: "GEMPIC_ESTATE",
           -7: "GEMPIC_EOVERFLOW", -8: "GEMPIC_ENONFINITE"}
@@ -76,7 +77,8 @@ class gempic_diag(Structure):
     _fields_ = [("step", c_int64), ("field_energy", c_double), ("kinetic_energy", c_double),
                 ("charge_flux", c_double), ("n_trapped", c_int64), ("n_stored", c_int64),
                 ("n_rejoined", c_int64), ("pushes", c_int64),
-                ("continuity_residual", c_double), ("gauss_residual", c_double)]
+                ("continuity_residual", c_double), ("gauss_residual", c_double),
+                ("stored_kinetic_energy", c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -111,6 +113,21 @@ SIGNATURES = {
     "gempic_batch_sim": (c_void_p, [c_void_p, c_int32]),
     "gempic_batch_stream": (c_void_p, [c_void_p, c_int32]),
     "gempic_batch_destroy": (None, [c_void_p]),
+    "gempic_probe_fp32_fma": (c_int32, [c_void_p, c_int32, POINTER(c_double), POINTER(c_double)]),
+    "gempic_denoiser_param_count": (c_size_t, []),
+    "gempic_denoiser_create": (c_int32, [c_void_p, c_double, POINTER(c_void_p)]),
+    "gempic_denoiser_set_params": (c_int32, [c_void_p, c_void_p, c_size_t]),
+    "gempic_denoiser_get_params": (c_int32, [c_void_p, c_void_p, c_size_t]),
+    "gempic_denoiser_apply": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32,
+                                        c_void_p]),
+    "gempic_denoiser_grad": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32, c_int32,
+                                       c_int32, POINTER(c_double), c_void_p, c_void_p]),
+    "gempic_denoiser_train_step": (c_int32, [c_void_p, c_void_p, c_void_p, c_int32, c_int32,
+                                             c_int32, c_int32, c_double, POINTER(c_double),
+                                             c_void_p]),
+    "gempic_denoiser_destroy": (None, [c_void_p]),
+    "gempic_set_denoiser": (c_int32, [c_void_p, c_void_p]),
+    "gempic_get_current": (c_int32, [c_void_p, c_void_p, c_size_t, c_int32]),
     "gempic_strerror": (c_char_p, [c_int32]),
     "gempic_destroy": (None, [c_void_p]),
 }
@@ -188,6 +205,8 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
         flags |= GEMPIC_FLAG_GT1
     if w.residual:
         flags |= GEMPIC_FLAG_RESIDUAL
+    if getattr(w, "capture_current", False):
+        flags |= GEMPIC_FLAG_CURRENT
     cfg = gempic_config(
         grid=gempic_grid(w.nx, w.ny, w.nzeta, w.hx, w.hy, w.h), delta=w.delta,
         precision=w.precision, flags=flags, seed=w.seed, nspecies=n, cluster_ctas=cluster_ctas,
@@ -199,6 +218,14 @@ def config_from_workload(w, *, flags: int = GEMPIC_FLAG_DIAG, cluster_ctas: int 
         hz=hz.ctypes.data_as(POINTER(c_double)) if hz is not None else None,
         beam=ctypes.pointer(bm) if bm is not None else None)
     return cfg, (sp, las, ch, hz, bm)
+
+
+def gempic_probe_fp32_fma(iters: int = 200000, stream: Optional[int] = None):
+    """Measured FP32 FMA throughput: (TFLOP/s, kernel ms)."""
+    t, ms = c_double(), c_double()
+    _check(load().gempic_probe_fp32_fma(stream, int(iters), byref(t), byref(ms)),
+           "gempic_probe_fp32_fma")
+    return t.value, ms.value
 
 
 def gempic_step_noalloc(w, step: int, state, onaxis: bool = False, stream: Optional[int] = None,
@@ -267,6 +294,29 @@ class Sim:
         _check(self.lib.gempic_set_delta(self.h, float(delta)), "gempic_set_delta")
 
     set_delta = gempic_set_delta
+
+    def gempic_set_denoiser(self, d):
+        """Denoised s-steps with the Denoiser d (None: plain steps).  Keeps a reference."""
+        _check(self.lib.gempic_set_denoiser(self.h, d.h if d is not None else None),
+               "gempic_set_denoiser")
+        self._denoiser = d
+
+    set_denoiser = gempic_set_denoiser
+
+    def gempic_get_current(self, out=None):
+        """The plain current of the last s-step, [nzeta, 3, ny, nx]: into a device tensor
+        `out`, or a new host array."""
+        w = self.w
+        if out is not None and hasattr(out, "data_ptr") and out.is_cuda:
+            _check(self.lib.gempic_get_current(self.h, out.data_ptr(),
+                                               out.numel() * out.element_size(), 1),
+                   "gempic_get_current")
+            return out
+        a = np.empty((w.nzeta, 3, w.ny, w.nx), self.rdtype)
+        _check(self.lib.gempic_get_current(self.h, a.ctypes.data, a.nbytes, 0), "gempic_get_current")
+        return a
+
+    current = gempic_get_current
 
     def gempic_set_wait_limit(self, polls: int):
         _check(self.lib.gempic_set_wait_limit(self.h, int(polls)), "gempic_set_wait_limit")
@@ -446,3 +496,104 @@ class Batch:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Denoiser:
+    """The learned current denoiser (gempic_denoiser_create ... gempic_denoiser_destroy).
+    Currents are device FP32 tensors [nz, 3, ny, nx]; parameters a host FP32 vector."""
+
+    def __init__(self, params: Optional[np.ndarray] = None, scale: float = 1.0):
+        self.lib = load()
+        self.n = int(self.lib.gempic_denoiser_param_count())
+        h = c_void_p()
+        p = None
+        if params is not None:
+            p = np.ascontiguousarray(params, dtype=np.float32)
+            if p.size != self.n:
+                raise ValueError(f"expected {self.n} parameters")
+        _check(self.lib.gempic_denoiser_create(p.ctypes.data if p is not None else None,
+                                               float(scale), byref(h)), "gempic_denoiser_create")
+        self.h = h
+        self.scale = float(scale)
+
+    def set_params(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        _check(self.lib.gempic_denoiser_set_params(self.h, p.ctypes.data, p.size),
+               "gempic_denoiser_set_params")
+
+    def params(self) -> np.ndarray:
+        p = np.empty(self.n, np.float32)
+        _check(self.lib.gempic_denoiser_get_params(self.h, p.ctypes.data, p.size),
+               "gempic_denoiser_get_params")
+        return p
+
+    @staticmethod
+    def _dims(j):
+        nz, c, ny, nx = j.shape
+        if c != 3 or not j.is_cuda or not j.is_contiguous():
+            raise ValueError("currents are contiguous device tensors [nz, 3, ny, nx]")
+        return nx, ny, nz
+
+    def apply(self, j, out=None, stream: Optional[int] = None):
+        import torch
+        nx, ny, nz = self._dims(j)
+        out = torch.empty_like(j) if out is None else out
+        _check(self.lib.gempic_denoiser_apply(self.h, j.data_ptr(), out.data_ptr(), nx, ny, nz,
+                                              stream), "gempic_denoiser_apply")
+        return out
+
+    def grad(self, j, target, z_margin: int = 0, stream: Optional[int] = None):
+        nx, ny, nz = self._dims(j)
+        loss = c_double()
+        g = np.empty(self.n, np.float32)
+        _check(self.lib.gempic_denoiser_grad(self.h, j.data_ptr(), target.data_ptr(), nx, ny, nz,
+                                             z_margin, byref(loss), g.ctypes.data, stream),
+               "gempic_denoiser_grad")
+        return loss.value, g
+
+    def train_step(self, j, target, lr: float, z_margin: int = 0, stream: Optional[int] = None):
+        nx, ny, nz = self._dims(j)
+        loss = c_double()
+        _check(self.lib.gempic_denoiser_train_step(self.h, j.data_ptr(), target.data_ptr(), nx, ny,
+                                                   nz, z_margin, float(lr), byref(loss), stream),
+               "gempic_denoiser_train_step")
+        return loss.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.gempic_denoiser_destroy(self.h)
+            self.h = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def denoiser_params_to_vector(P) -> np.ndarray:
+    """Pack a dict of W1, b1, W2, b2, W3, b3 (shapes [3,3,3,ci,co] and [co]) into the library's
+    parameter vector (tap, input channel, output channel order)."""
+    parts = []
+    for l in (1, 2, 3):
+        parts.append(np.asarray(P[f"W{l}"], np.float32).reshape(-1))
+        parts.append(np.asarray(P[f"b{l}"], np.float32).reshape(-1))
+    return np.concatenate(parts)
+
+
+def denoiser_vector_to_params(v: np.ndarray, hidden: int = 16, cin: int = 3) -> dict:
+    shapes = [(cin, hidden), (hidden, hidden), (hidden, cin)]
+    P, o = {}, 0
+    for l, (ci, co) in enumerate(shapes, start=1):
+        n = 27 * ci * co
+        P[f"W{l}"] = np.asarray(v[o:o + n], np.float64).reshape(3, 3, 3, ci, co)
+        o += n
+        P[f"b{l}"] = np.asarray(v[o:o + co], np.float64)
+        o += co
+    return P

@@ -124,6 +124,7 @@ class Workload:
     hz: Optional[np.ndarray] = None     # nzeta slab thicknesses (back to front); None: h
     residual: bool = False       # report the deposit's continuity residual (2-D)
     beam: Optional[Beam] = None  # Gaussian bunch sampled in the box at creation
+    capture_current: bool = False  # keep the current of the last s-step of each call
 
     @property
     def ncells(self) -> int:

@@ -91,3 +91,20 @@ def test_gpu_matches_the_fixtures(name):
                 assert abs(d[k] - b[k]) <= 1e-10 * abs(b[k]), k
             ez, gz = sim.onaxis_ez(), np.array(b["onaxis_ez"])
             assert np.abs(ez - gz).max() <= 1e-10 * np.abs(gz).max()
+
+
+def test_bench_fixture_is_complete_and_consistent():
+    """The oracle's full-size bench fixture: both s-steps' diagnostics, the on-axis E_z over
+    the window and the state sample; its charge flux is q n0 times the window's volume less the
+    few particles trapped on the way (Sec. 5.1: every plane carries rho - j_z = q n0)."""
+    m = _golden_module()
+    f = np.load(os.path.join(HERE, m.BENCH_FIXTURE))
+    w = W.lwfa_3d_128x128x1024()
+    for k in range(2):
+        assert f[f"onaxis_ez_{k}"].shape == (w.nzeta,) and np.isfinite(f[f"onaxis_ez_{k}"]).all()
+        vol = w.nx * w.hx * w.ny * w.hy * w.nzeta * w.h
+        qn = w.species[0].charge * w.species[0].density
+        assert abs(float(f[f"charge_flux_{k}"]) / (qn * vol) - 1.0) < 2e-3
+        assert f[f"field_energy_{k}"] > 0 and f[f"kinetic_energy_{k}"] > 0
+    sl, ky, kx = m.bench_sample_index(w.ny)
+    assert f["state_sample"].shape == (6, sl.size, ky.size, kx.size)

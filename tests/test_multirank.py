@@ -64,3 +64,17 @@ def test_two_gloo_ranks_replicas_and_max_time():
         assert not set(scans[0]) & set(scans[1])           # scan instances differ per rank
         assert ms == 15.0                                  # the slowest rank's time
         assert rate == pytest.approx(2 * w.pushes_per_step * 3 / 0.015)
+
+
+def test_oracle_baseline_on_several_host_cores():
+    """The CPU baseline runs the oracle as it stands in spawned processes, one per core (each a
+    seeded copy of the workload's window): the rate covers all their pushes over the wall time
+    from the first start to the last end, and `cores` says how many ran."""
+    import bench
+    from paper_2509_16793_gb300 import workloads as W
+    w = W.small_3d(nx=8, ny=8, nzeta=64, ppc=1)
+    one = bench.oracle_sample(w, seconds=1e9, max_steps=1, procs=1)
+    two = bench.oracle_sample(w, seconds=1e9, max_steps=1, procs=2)
+    assert one["cores"] == 1 and two["cores"] == 2
+    assert one["value"] > 0 and two["value"] > 0
+    assert "2 process(es)" in two["sample"] and "2 s-step(s)" in two["sample"]

@@ -302,21 +302,103 @@ def test_fp32_bench_grid_matches_oracle():
             assert np.abs(gs[c] - os_[c]).max() <= 1e-4 * scale, name
 
 
-def test_config1_full_size_fp64_matches_oracle():
+@pytest.mark.slow
+def test_config1_full_size_fp64_all_200_steps():
     """The 2-D FP64 workload at its full size (128 x 256, 4 ppc, Delta at the stability
-    limit), three s-steps."""
-    w = W.lwfa_2d_128x256(precision=64)
+    limit) over all 200 s-steps of its configuration, against the oracle run alongside:
+    diagnostics every s-step, on-axis E_z and the state element by element every 20 and
+    after the first three.  The first three s-steps hold 1e-10.  At the stability limit the
+    scheme amplifies round-off for a few s-steps before it decays (the oracle against itself
+    with R perturbed by 1e-14 relative: 3.5e-10 in the field energy at s-step 6; perturbed by
+    1e-15: at most 4e-11 in the state over the 200 s-steps), and the two implementations
+    differ by round-off at every s-step (App. B closed form against a dense solve, other
+    transform and summation orders), so the later s-steps are held to 1e-9."""
+    w = W.lwfa_2d_128x256(precision=64, steps=200)
     o = RefSim(w)
     with gpu_sim(w) as g:
-        for _ in range(3):
+        for k in range(w.steps):
             od = o.step()
             g.step()
-            check_diag(g.diagnostics(), od, 1e-10)
-        gs, os_ = g.state(), o.state()
-        fs = max(np.abs(os_[c]).max() for c in range(4))
-        js = max(np.abs(os_[c]).max() for c in (4, 5))
+            tol = 1e-10 if k < 3 else 1e-9
+            check_diag(g.diagnostics(), od, tol)
+            if (k + 1) % 20 == 0 or k == 2:
+                ez, oez = g.onaxis_ez(), od["onaxis_ez"]
+                assert np.abs(ez - oez).max() <= tol * np.abs(oez).max(), k
+                gs, os_ = g.state(), o.state()
+                fs = max(np.abs(os_[c]).max() for c in range(4))
+                js = max(np.abs(os_[c]).max() for c in (4, 5))
+                for c, name in enumerate(COMPS):
+                    err = np.abs(gs[c] - os_[c]).max() / (fs if c < 4 else js)
+                    assert err <= tol, (k, name, err)
+
+
+def _bench_fixture():
+    import importlib.util
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden", os.path.join(here, "make_golden.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m, np.load(os.path.join(here, m.BENCH_FIXTURE))
+
+
+def test_bench_workload_two_steps_match_the_oracle():
+    """The bench workload at full size (128 x 128 x 1024, FP32, 2 ppc, a0 = 2.5) against the
+    oracle's FP64 run of the same two s-steps (tests/golden, written by make_golden.py from
+    the oracle alone).  One sim marches both s-steps in one launch, as the bench does (16-CTA
+    clusters, two marches in flight); another stops after the first.
+
+    FP32 against FP64 within 1e-4 (the benchmark spec): the field energy, the streaming particles'
+    kinetic energy and the charge flux, and the on-axis E_z in front of the trapping region
+    (the front-most stored particle of the oracle plus 64 slices, 20 c/omega), relative to the
+    largest on-axis value.  Behind it the wake breaks: particles there are trapped or nearly
+    so, and their trajectories amplify the FP32 rounding (measured: the front 60 % of the
+    window within 6e-6; from 20 slices in front of the first trapped particle backwards up to
+    1.4e-3, with equal trap counts at the first s-step), so the whole
+    window is held to 2e-3, the stored set's energy to 2e-3 plus five mean stored energies per
+    particle whose trapping decision flipped, the trap counts to 2 + 1 %.  The state sample in
+    front of the trapping region is held to 1e-4 of each component's largest value."""
+    m, fx = _bench_fixture()
+    w = W.lwfa_3d_128x128x1024()
+    zc = np.arange(w.nzeta) * w.h
+    with gpu_sim(w) as a:
+        shape = a.launch_shape()
+        assert shape["cluster_ctas"] == 16 and shape["pipeline"] >= 2
+        a.step(2)
+        with gpu_sim(w) as b:
+            b.step(1)
+            for g, k in ((b, 0), (a, 1)):
+                d = g.diagnostics()
+                got = {key: d[key] for key in ("field_energy", "kinetic_energy", "charge_flux",
+                                                "stored_kinetic_energy", "n_trapped", "n_stored")}
+                ref = {key: fx[f"{key}_{k}"].item() for key in got}
+                msg = (k, got, ref)
+                for key in ("field_energy", "charge_flux"):
+                    assert abs(got[key] - ref[key]) <= 1e-4 * abs(ref[key]), msg
+                ks_got = got["kinetic_energy"] - got["stored_kinetic_energy"]
+                ks_ref = ref["kinetic_energy"] - ref["stored_kinetic_energy"]
+                assert abs(ks_got - ks_ref) <= 1e-4 * abs(ks_ref), msg
+                oez = fx[f"onaxis_ez_{k}"]
+                err = np.abs(g.onaxis_ez() - oez) / np.abs(oez).max()
+                front = zc > fx[f"stored_zeta_max_{k}"].item() + 64 * w.h
+                assert front.sum() > w.nzeta // 2
+                assert err[front].max() <= 1e-4, (k, err[front].max())
+                assert err.max() <= 2e-3, (k, err.max())
+                for key in ("n_trapped", "n_stored"):
+                    assert abs(got[key] - ref[key]) <= 2 + ref[key] // 100, msg
+                per = ref["stored_kinetic_energy"] / max(ref["n_stored"], 1)
+                flips = abs(got["n_stored"] - ref["n_stored"])
+                assert abs(got["stored_kinetic_energy"] - ref["stored_kinetic_energy"]) <= \
+                    2e-3 * ref["stored_kinetic_energy"] + 5 * flips * per, msg
+        # the state sample in front of the trapping region
+        sl, ky, kx = m.bench_sample_index(w.ny)
+        keep = zc[sl] > fx["stored_zeta_max_1"].item() + 64 * w.h
+        assert keep.sum() >= 8
+        st = a.state()[:, sl[keep]][:, :, ky][:, :, :, kx]
+        ref = fx["state_sample"][:, keep]
         for c, name in enumerate(COMPS):
-            assert np.abs(gs[c] - os_[c]).max() <= 1e-10 * (fs if c < 4 else js), name
+            e = np.abs(st[c] - ref[c]).max() / fx["state_absmax"][c]
+            assert e <= 1e-4, (name, e)
 
 
 def test_bench_workload_full_size_properties():

@@ -249,6 +249,9 @@ def main():
     ap.add_argument("--instances", type=int, default=64, help="scan: number of instances")
     ap.add_argument("--fp64-steps", type=int, default=40,
                     help="s-steps of the FP64-plain comparison on the 2-D workload (0 skips it)")
+    ap.add_argument("--denoise-pairs", type=int, default=64,
+                    help="denoiser leg: paired s-steps of the 1- and 16-ppc runs (0 skips it)")
+    ap.add_argument("--denoise-iters", type=int, default=3000, help="denoiser leg: Adam steps")
     args = ap.parse_args()
     if args.workload == "scan" and args.impl == "gempic":
         return run_scan(args)
@@ -363,6 +366,16 @@ def main():
                 "fp64": {"value": v64, "ms_per_step": ms64},
                 "fp32": {"value": v32, "ms_per_step": ms32},
                 "unit": "pushes/s", "fp32_over_fp64": v32 / v64}
+    # the metric's "denoised" form: the learned current denoiser trained on 1- vs 16-ppc runs
+    # of the 128 x 128 x 512 LWFA, judged against the 16-ppc plain run
+    denoise = None
+    if args.denoise_pairs > 0:
+        try:
+            from paper_2509_16793_gb300 import denoise_train
+            denoise = denoise_train.experiment(args.denoise_pairs, args.denoise_iters,
+                                               stream=stream.cuda_stream)
+        except Exception as ex:  # reported, never the headline
+            denoise = {"error": str(ex)}
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -380,7 +393,7 @@ def main():
             "e2e": {"value": e2e_value if math.isfinite(e2e_value) else None,
                     "unit": "pushes/s", "h2d_bytes_per_step": nb,
                     "d2h_bytes_per_step": nb + 64},
-            "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64,
+            "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64, "denoiser": denoise,
             "diag": {k: diag[k] for k in ("field_energy", "kinetic_energy", "n_stored", "pushes")}}
     print(json.dumps(line), flush=True)
     sim.close()

@@ -38,7 +38,8 @@ constexpr int kCh = 16;            // channels of every activation tensor (input
 constexpr int kTaps = 27;
 constexpr int kTile = 128;         // voxels per MMA tile (M)
 constexpr int kRound = 9;          // taps staged per buffer
-constexpr int kThreads = 128;      // 4 warps: one per 32 accumulator rows
+constexpr int kThreads = 128;      // 4 warps: one per 32 accumulator rows, one thread per row
+static_assert(kThreads == kTile, "the gather gives each thread one row of the tile");
 constexpr uint32_t kTapBytesA = kTile * kCh * 2;     // 4096
 constexpr uint32_t kTapBytesB = kCh * kCh * 2;       // 512
 constexpr uint32_t kLBO = 128;     // byte offset of the core matrix next along K
@@ -190,8 +191,19 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(ConvArgs a) {
   int pending[2] = {0, 0};
   int gr = 0;                                                 // rounds staged so far
 
+  const long long plane = (long long)a.nx * a.ny;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const long long v0 = tile * kTile;
+    // this thread gathers tile row `tid` (one voxel) for every tap
+    const long long vr = v0 + tid;
+    const bool valid = vr < V;
+    int z = 0, y = 0, x = 0;
+    if (valid) {
+      z = (int)(vr / plane);
+      const int rem = (int)(vr - (long long)z * plane);
+      y = rem / a.nx;
+      x = rem - y * a.nx;
+    }
     for (int round = 0; round < kTaps / kRound; ++round, ++gr) {
       const int buf = gr & 1;
       if (pending[buf]) {                                     // MMAs still reading this buffer
@@ -199,19 +211,28 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(ConvArgs a) {
         phase[buf] ^= 1u;
         pending[buf] = 0;
       }
-      // gather: chunk c = (tap slot s, row r, half h) of 16 bytes
-      unsigned char* dstA = sA + (size_t)buf * kRound * kTapBytesA;
-      for (int c = tid; c < kRound * kTile * 2; c += kThreads) {
-        const int s = c / (kTile * 2), rem = c - s * kTile * 2;
-        const int r = rem >> 1, h = rem & 1;
-        const long long v = v0 + r;
-        uint4 val = make_uint4(0u, 0u, 0u, 0u);
-        if (v < V) {
-          const long long nb = neighbour(v, round * kRound + s, a.nx, a.ny, a.nz);
-          if (nb >= 0) val = *reinterpret_cast<const uint4*>(a.x + nb * kCh + h * 8);
+      // gather: for each tap of the round, this thread's row = the 16 channels (two 16-byte
+      // core-matrix rows) of its voxel's neighbour
+      unsigned char* dstA = sA + (size_t)buf * kRound * kTapBytesA + (tid >> 3) * kSBO + (tid & 7) * 16;
+#pragma unroll 3
+      for (int s = 0; s < kRound; ++s) {
+        const int t = round * kRound + s;
+        const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
+        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
+        const int zz = z + dz;
+        if (valid && zz >= 0 && zz < a.nz) {
+          int yy = y + dy, xx = x + dx;
+          yy += yy < 0 ? a.ny : 0;
+          yy -= yy >= a.ny ? a.ny : 0;
+          xx += xx < 0 ? a.nx : 0;
+          xx -= xx >= a.nx ? a.nx : 0;
+          const uint4* src = reinterpret_cast<const uint4*>(
+              a.x + ((long long)zz * plane + (long long)yy * a.nx + xx) * kCh);
+          lo = src[0];
+          hi = src[1];
         }
-        *reinterpret_cast<uint4*>(dstA + (size_t)s * kTapBytesA + (r >> 3) * kSBO + h * kLBO +
-                                  (r & 7) * 16) = val;
+        *reinterpret_cast<uint4*>(dstA + (size_t)s * kTapBytesA) = lo;
+        *reinterpret_cast<uint4*>(dstA + (size_t)s * kTapBytesA + kLBO) = hi;
       }
       fence_async_smem();
       tc_fence_before();

@@ -216,6 +216,18 @@ def lwfa_3d_128x128x1024(precision: int = 32, steps: int = 2000) -> Workload:
         precision=precision, steps=steps)
 
 
+def lwfa_3d_128x128x512(ppc: int = 1, precision: int = 32, steps: int = 200) -> Workload:
+    """The denoiser's 3-D LWFA: the laser and plasma of the 128 x 128 x 1024 workload
+    (dzeta = lambda/20, dx = dy = lambda/4, n0 = 0.002 n_cr, a0 = 2.5, 8 lambda/c FWHM, waist
+    10 lambda, the same Delta) on a 512-slice window, at ppc particles per cell (1 for the
+    sparse run the denoiser cleans, 16 for the dense run it is trained towards)."""
+    w = lwfa_3d_128x128x1024(precision=precision, steps=steps)
+    L = 512 * w.h
+    return w.with_(name=f"lwfa3d_128x128x512_ppc{ppc}", nzeta=512,
+                   species=[Species(-1.0, 1.0, w.species[0].density, ppc)],
+                   laser=Laser(**{**w.laser.__dict__, "zeta_center": L - 2.0 * w.laser.duration}))
+
+
 def small_3d(nx: int = 16, ny: int = 16, nzeta: int = 48, ppc: int = 2, precision: int = 64,
              a0: float = 1.5, n0: float = 0.01, delta: Optional[float] = None,
              steps: int = 2) -> Workload:

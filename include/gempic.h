@@ -296,24 +296,31 @@ gempic_status gempic_launch_shape(const struct gempic_sim* sim, int32_t* cluster
                                   int32_t* threads, int32_t* smem_bytes, int32_t* pipeline);
 
 /* ---- Batched parameter scan ------------------------------------------------------------
- * Independent simulations stepped side by side on one GPU (the paper has no counterpart: a
- * scan over grids, drivers and densities).  Each instance is an ordinary gempic_sim with its
- * own CUDA stream and one s-step in flight -- no wavefront between clusters of an instance,
- * so no instance ever waits on another's residency; a step call submits one persistent
- * launch per instance and the GPU runs them concurrently. */
+ * Independent simulations stepped together (the paper has no counterpart: a scan over grids,
+ * drivers and densities).  A step call of n s-steps is one persistent launch (one CTA per SM,
+ * recorded once per n as a CUDA graph with the upload of the launch parameters and replayed)
+ * whose CTAs take work items (simulation, s-step) from a queue: s-step by s-step, the costliest
+ * simulations first.  The march of a simulation's s-step waits slice by slice (bounded) for
+ * its previous s-step, so a large simulation marches up to 16 s-steps at once while small ones
+ * fill the other SMs.  The costs come from an autotuner run at creation: for each size class
+ * (grid, precision, particles per cell, flags) it times one s-step of a throw-away simulation
+ * at 256 and at 512 threads per CTA, launches the batch at the CTA size with the smaller
+ * total and orders the items by the measured per-class times (gempic_batch_tuning).  All
+ * simulations share the batch's stream and must have the same precision; beams, channels and
+ * the other config fields work as in gempic_create, denoisers do not. */
 typedef struct gempic_batch gempic_batch;
 
-/* Create n >= 1 instances from cfgs[0..n-1], each validated like gempic_create;
- * cuda_stream and pipeline_depth of the configs are ignored (the batch creates a
- * non-blocking stream per instance).  On a failure nothing is kept and the first failing
- * status is returned. */
+/* Create n >= 1 instances from cfgs[0..n-1], each validated like gempic_create (GEMPIC_EINVAL
+ * also for mixed precisions); cuda_stream and pipeline_depth of the configs are ignored.
+ * Runs the autotuner (a few s-steps of one throw-away simulation per size class).  On a
+ * failure nothing is kept and the first failing status is returned. */
 gempic_status gempic_batch_create(const gempic_config* cfgs, int32_t n, gempic_batch** out);
 
-/* Launch n s-steps on every instance (one launch each, on its stream) and return. */
+/* Launch n s-steps of every instance (one persistent launch per 16 s-steps) and return. */
 gempic_status gempic_batch_step_async(gempic_batch* b, int32_t n);
 
-/* Wait for every instance and check its device status word; the first error is returned
- * (the other instances are still waited for). */
+/* Wait for the batch and check every instance's device status word; the first error is
+ * returned. */
 gempic_status gempic_batch_sync(gempic_batch* b);
 
 /* gempic_batch_step_async then gempic_batch_sync. */
@@ -326,10 +333,16 @@ int32_t gempic_batch_size(const gempic_batch* b);
  * calls, never with gempic_destroy.  NULL if i is out of range. */
 struct gempic_sim* gempic_batch_sim(gempic_batch* b, int32_t i);
 
-/* The cudaStream_t of instance i (for events and interoperation); NULL if out of range. */
+/* The cudaStream_t the batch launches on (the same for every i; for events and
+ * interoperation); NULL if i is out of range. */
 void* gempic_batch_stream(gempic_batch* b, int32_t i);
 
-/* Destroy every instance and the batch's streams (waits for them first). */
+/* The autotuner's choice: the launch's threads per CTA and the measured ms per s-step of
+ * instance i's size class at that size. */
+gempic_status gempic_batch_tuning(const gempic_batch* b, int32_t i, int32_t* nthreads,
+                                  double* ms_per_step);
+
+/* Destroy every instance and the batch (waits for it first). */
 void gempic_batch_destroy(gempic_batch* b);
 
 /* Allocation-free s-step.  The paper has no counterpart: this entry point is for callers that

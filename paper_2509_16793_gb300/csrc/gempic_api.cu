@@ -234,6 +234,56 @@ gempic_status ensure_initialized(gempic_sim* s) {
 
 }  // namespace
 
+namespace gempic {
+
+// ---- support of the batched scan (gempic_batch.cu) ---------------------------------------
+
+// Initialise s if needed, give its kernels `nthreads` threads (one spectral mode per thread:
+// nthreads >= M; the shared-memory layout is recomputed) and return the parameters of a
+// launch of `nsteps` concurrent marches from its current s-step (march index c <-> s-step
+// k + c, each waiting for the one before it).
+gempic_status batch_prepare(gempic_sim* s, int nthreads, int nsteps, Params* out) {
+  if (!s || !out || nsteps < 1) return GEMPIC_EINVAL;
+  if (s->dn) return GEMPIC_EINVAL;
+  gempic_status st = ensure_initialized(s);
+  if (st != GEMPIC_OK) return st;
+  if (nsteps > s->pmax) return GEMPIC_EINVAL;
+  if (nthreads != s->p.nthreads) {
+    if (nthreads < s->p.M || nthreads > 512 || nthreads % 32) return GEMPIC_EINVAL;
+    Params t = s->p;
+    t.nthreads = nthreads;
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+    if (smem_layout(t, s->eb) > optin) return GEMPIC_EINVAL;
+    s->p = t;
+  }
+  cudaError_t e = ensure_diag_cap(s, nsteps);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  Params q = s->p;
+  q.k0 = s->k;
+  q.nsteps = nsteps;
+  q.P = nsteps;
+  q.inject = q.nspecies > 0 ? 1 : 0;
+  q.delta_field = s->p.delta;
+  *out = q;
+  return GEMPIC_OK;
+}
+
+// After a batch launch of n s-steps of s.
+void batch_advance(gempic_sim* s, int n) {
+  s->last_launch_k0 = s->k;
+  s->last_launch_n = n;
+  s->k += n;
+  s->launches++;
+  s->denoised_last = false;
+}
+
+int batch_precision(const gempic_sim* s) { return s->cfg.precision; }
+
+}  // namespace gempic
+
 extern "C" {
 
 const char* gempic_strerror(gempic_status s) {

@@ -118,6 +118,11 @@ cudaError_t launch_laser_init(int precision, const Params& p, double a0, double 
                               double duration, double zeta_c, int pol, cudaStream_t s);
 cudaError_t launch_export_state(int precision, const Params& p, void* dst, cudaStream_t s);
 cudaError_t launch_beam_init(int precision, const Params& p, const BeamArgs& b, cudaStream_t s);
+// batched scan: one persistent launch over the work items (simulation, march index)
+cudaError_t configure_batch(int precision, int smem);
+cudaError_t batch_occupancy(int precision, int nthreads, int smem, int* blocks);
+cudaError_t launch_batch(int precision, const Params* ps, const int2* items, int nitems, int* head,
+                         int grid, int nthreads, int smem, cudaStream_t s);
 cudaError_t launch_import_state(int precision, const Params& p, const void* src, cudaStream_t s);
 cudaError_t max_active_clusters(int precision, const Params& p, int* n);
 // allocation-free entry point: march on a caller's state in the public layout

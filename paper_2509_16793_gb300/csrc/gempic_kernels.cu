@@ -499,7 +499,7 @@ __device__ __forceinline__ void fft128_h16(Cx<T> (&a)[8], Cx<T>* bufA, Cx<T>* bu
 // ------------------------------------------------------------------------------------------
 enum CstSlot {
   K_H = 0, K_INVH, K_HX, K_HY, K_D, K_DF, K_WSCALE, K_CX, K_CY, K_INVHX, K_INVHY, K_FLUX,
-  K_BEAM, K_JREF, K_JSCALE, K_JINV, K_QM = 16, K_MOQ = 20, K_QF = 24, K_N = 28
+  K_BEAM, K_JREF, K_JSCALE, K_JINV, K_QM = 16, K_MOQ = 20, K_QF = 24, K_INVD = 28, K_N = 29
 };
 enum MiscSlot { M_PCOUNT = 0, M_FTOP, M_INBOX, M_RQN, M_JFLAG, M_STN, M_OUTN, M_PAD1 };
 // particles leaving the band during a push wait in a local outbox of this many entries
@@ -632,6 +632,7 @@ __device__ void load_tables(const Params& p, const Sm<T>& s) {
     c[K_JREF] = T(p.jref);
     c[K_JSCALE] = T(4194304.0 / p.jref);   // 2^22 / jref
     c[K_JINV] = T(p.jref / 4194304.0);
+    c[K_INVD] = p.delta > 0 ? T(1.0 / p.delta) : T(0);
     for (int i = 0; i < kMaxSpecies; ++i) {
       c[K_QM + i] = T(p.qm[i]);
       c[K_MOQ + i] = T(p.m_over_q[i]);
@@ -1372,6 +1373,13 @@ __device__ void esirkepov(const Params& p, const Sm<T>& s, const Sink<T, LOCAL>&
   }
 }
 
+// Fixed-point quantum of v (|v js| < 2^22): round(v js) to the nearest integer, ties to even,
+// by adding 1.5 2^23 in one rounding (the sum's unit in the last place is 1, so its low
+// mantissa bits hold the integer) -- an FMA and an integer subtract instead of a conversion.
+__device__ __forceinline__ int fixq(float v, float js) {
+  return __float_as_int(fmaf(v, js, 12582912.0f)) - 0x4B400000;
+}
+
 // FP32 deposit of a move that needs no sub-steps (|dX|, |dY| <= 1) and whose contributions are
 // all below jref: the Esirkepov and CIC values of the general path, added to the fixed-point
 // accumulators by reductions predicated on a nonzero quantum (no branches).  Every value is a
@@ -1411,13 +1419,13 @@ __device__ __forceinline__ bool deposit_fixed(const Params& p, const Sm<T>& s,
       const T bnd = fmax(fmax(fabs(ex0), fabs(ex1)), fmax(fabs(vy), fabs(vz)));
       if (!(bnd < sk.jref)) return false;
       const uint32_t b = sk.ibase;
-      red_local_u32_nz(b + o0, __float2int_rn(ex0 * js));
-      red_local_u32_nz(b + o1, __float2int_rn(ex1 * js));
-      red_local_u32_nz(b + cs + o0, __float2int_rn((vy * hx0) * js));
-      red_local_u32_nz(b + cs + o1, __float2int_rn((vy * hx1) * js));
-      red_local_u32_nz(b + cs + o2, __float2int_rn((vy * hx2) * js));
-      red_local_u32_nz(b + 2 * cs + z0, __float2int_rn(((T(1) - fx) * vz) * js));
-      red_local_u32_nz(b + 2 * cs + z1, __float2int_rn((fx * vz) * js));
+      red_local_u32_nz(b + o0, fixq(ex0, js));
+      red_local_u32_nz(b + o1, fixq(ex1, js));
+      red_local_u32_nz(b + cs + o0, fixq(vy * hx0, js));
+      red_local_u32_nz(b + cs + o1, fixq(vy * hx1, js));
+      red_local_u32_nz(b + cs + o2, fixq(vy * hx2, js));
+      red_local_u32_nz(b + 2 * cs + z0, fixq((T(1) - fx) * vz, js));
+      red_local_u32_nz(b + 2 * cs + z1, fixq(fx * vz, js));
       return true;
     }
     const T by = floor(fmin(Y0, Y1));
@@ -1435,23 +1443,23 @@ __device__ __forceinline__ bool deposit_fixed(const Params& p, const Sm<T>& s,
     const T fY1 = floor(Y1), fy = Y1 - fY1;
     const uint32_t r0 = sk.ibase + (uint32_t)((int)by * (int)rs);
     const uint32_t r1 = r0 + rs, r2 = r1 + rs;
-    red_local_u32_nz(r0 + o0, __float2int_rn((ex0 * hy0) * js));
-    red_local_u32_nz(r0 + o1, __float2int_rn((ex1 * hy0) * js));
-    red_local_u32_nz(r1 + o0, __float2int_rn((ex0 * hy1) * js));
-    red_local_u32_nz(r1 + o1, __float2int_rn((ex1 * hy1) * js));
-    red_local_u32_nz(r2 + o0, __float2int_rn((ex0 * hy2) * js));
-    red_local_u32_nz(r2 + o1, __float2int_rn((ex1 * hy2) * js));
-    red_local_u32_nz(r0 + cs + o0, __float2int_rn((ey0 * hx0) * js));
-    red_local_u32_nz(r0 + cs + o1, __float2int_rn((ey0 * hx1) * js));
-    red_local_u32_nz(r0 + cs + o2, __float2int_rn((ey0 * hx2) * js));
-    red_local_u32_nz(r1 + cs + o0, __float2int_rn((ey1 * hx0) * js));
-    red_local_u32_nz(r1 + cs + o1, __float2int_rn((ey1 * hx1) * js));
-    red_local_u32_nz(r1 + cs + o2, __float2int_rn((ey1 * hx2) * js));
+    red_local_u32_nz(r0 + o0, fixq(ex0 * hy0, js));
+    red_local_u32_nz(r0 + o1, fixq(ex1 * hy0, js));
+    red_local_u32_nz(r1 + o0, fixq(ex0 * hy1, js));
+    red_local_u32_nz(r1 + o1, fixq(ex1 * hy1, js));
+    red_local_u32_nz(r2 + o0, fixq(ex0 * hy2, js));
+    red_local_u32_nz(r2 + o1, fixq(ex1 * hy2, js));
+    red_local_u32_nz(r0 + cs + o0, fixq(ey0 * hx0, js));
+    red_local_u32_nz(r0 + cs + o1, fixq(ey0 * hx1, js));
+    red_local_u32_nz(r0 + cs + o2, fixq(ey0 * hx2, js));
+    red_local_u32_nz(r1 + cs + o0, fixq(ey1 * hx0, js));
+    red_local_u32_nz(r1 + cs + o1, fixq(ey1 * hx1, js));
+    red_local_u32_nz(r1 + cs + o2, fixq(ey1 * hx2, js));
     const uint32_t q0 = sk.ibase + 2 * cs + (uint32_t)((int)fY1 * (int)rs), q1 = q0 + rs;
-    red_local_u32_nz(q0 + z0, __float2int_rn((((T(1) - fx) * (T(1) - fy)) * vz) * js));
-    red_local_u32_nz(q0 + z1, __float2int_rn(((fx * (T(1) - fy)) * vz) * js));
-    red_local_u32_nz(q1 + z0, __float2int_rn((((T(1) - fx) * fy) * vz) * js));
-    red_local_u32_nz(q1 + z1, __float2int_rn(((fx * fy) * vz) * js));
+    red_local_u32_nz(q0 + z0, fixq(((T(1) - fx) * (T(1) - fy)) * vz, js));
+    red_local_u32_nz(q0 + z1, fixq((fx * (T(1) - fy)) * vz, js));
+    red_local_u32_nz(q1 + z0, fixq(((T(1) - fx) * fy) * vz, js));
+    red_local_u32_nz(q1 + z1, fixq((fx * fy) * vz, js));
     return true;
   }
 }
@@ -1609,7 +1617,7 @@ __device__ bool stream_push(const Params& p, const Sm<T>& s, const T* Fcur, PSta
   }
   // diagnostics: kinetic energy N m (gamma-1) dt/Delta, (rho - j_z) flux through plane n
   const T dtl = hden * gn;
-  acc.kin += P.q * s.cst[K_MOQ + P.sp] * gamma_minus_one(un, gn) * dtl / D;
+  acc.kin += P.q * s.cst[K_MOQ + P.sp] * gamma_minus_one(un, gn) * dtl * s.cst[K_INVD];
   if (!trap) acc.flux += w;
   acc.push += 1;
   // new cell-relative position
@@ -2806,6 +2814,60 @@ __global__ void __launch_bounds__(512, 1) march_kernel(const Params p) {
   __syncthreads();
   const int cid = (int)(blockIdx.x / p.C);
   for (long long k = p.k0 + cid; k < p.k0 + p.nsteps; k += p.P) march<T, CANON, SH>(p, s, cl, k, cid);
+}
+
+// Batched scan: one persistent launch over independent simulations.  Each CTA takes work
+// items (simulation, march index) from a queue in global memory, in the order the host laid
+// out (s-step by s-step, the costliest simulations first); the march of s-step k of a
+// simulation waits for that simulation's s-step k-1 with the bounded per-slice wavefront wait,
+// so a large simulation marches many s-steps at once while small ones fill the other SMs.
+// Every CTA of the launch is resident (one per SM), and an item is taken only after all items
+// before it, so the march it waits for is already running: no wait can block forever.
+template <typename T>
+__global__ void __launch_bounds__(512, 1) batch_kernel(const Params* ps, const int2* items,
+                                                       int nitems, int* head) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ __align__(16) Params sp;
+  __shared__ int item;
+  cg::cluster_group cl = cg::this_cluster();
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) item = atomicAdd(head, 1);
+    __syncthreads();
+    const int it = item;
+    if (it >= nitems) break;
+    const int2 w = items[it];
+    const int* src = reinterpret_cast<const int*>(ps + w.x);
+    int* dst = reinterpret_cast<int*>(&sp);
+    for (int i = threadIdx.x; i < (int)(sizeof(Params) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    const Sm<T> s = carve<T>(sp, smem);
+    load_tables(sp, s);
+    if (threadIdx.x < kNDiag) s.dacc[threadIdx.x] = 0.0;
+    __syncthreads();
+    march<T, false, 0>(sp, s, cl, sp.k0 + w.y, w.y);
+  }
+}
+
+cudaError_t configure_batch(int precision, int smem) {
+  if (precision == 64)
+    return cudaFuncSetAttribute(batch_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  return cudaFuncSetAttribute(batch_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+cudaError_t batch_occupancy(int precision, int nthreads, int smem, int* blocks) {
+  if (precision == 64)
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<double>, nthreads, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, batch_kernel<float>, nthreads, smem);
+}
+
+cudaError_t launch_batch(int precision, const Params* ps, const int2* items, int nitems, int* head,
+                         int grid, int nthreads, int smem, cudaStream_t s) {
+  if (precision == 64)
+    batch_kernel<double><<<grid, nthreads, smem, s>>>(ps, items, nitems, head);
+  else
+    batch_kernel<float><<<grid, nthreads, smem, s>>>(ps, items, nitems, head);
+  return cudaGetLastError();
 }
 
 // tables of the allocation-free entry point, built on the device (same formulas as the host

@@ -112,6 +112,7 @@ SIGNATURES = {
     "gempic_batch_size": (c_int32, [c_void_p]),
     "gempic_batch_sim": (c_void_p, [c_void_p, c_int32]),
     "gempic_batch_stream": (c_void_p, [c_void_p, c_int32]),
+    "gempic_batch_tuning": (c_int32, [c_void_p, c_int32, POINTER(c_int32), POINTER(c_double)]),
     "gempic_batch_destroy": (None, [c_void_p]),
     "gempic_probe_fp32_fma": (c_int32, [c_void_p, c_int32, POINTER(c_double), POINTER(c_double)]),
     "gempic_denoiser_param_count": (c_size_t, []),
@@ -472,6 +473,14 @@ class Batch:
         _check(self.lib.gempic_batch_sync(self.h), "gempic_batch_sync")
 
     sync = gempic_batch_sync
+
+    def gempic_batch_tuning(self, i: int):
+        """(threads per CTA of the launch, measured ms per s-step of instance i's class)."""
+        nt, ms = c_int32(), c_double()
+        _check(self.lib.gempic_batch_tuning(self.h, i, byref(nt), byref(ms)), "gempic_batch_tuning")
+        return nt.value, ms.value
+
+    tuning = gempic_batch_tuning
 
     def gempic_batch_stream(self, i: int) -> int:
         return int(self.lib.gempic_batch_stream(self.h, i) or 0)

@@ -149,9 +149,15 @@ def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
 
 def oracle_window(w):
     """The bounded sample of the workload the oracle is timed on: the same transverse grid and
-    particles per cell over a 64-slice window (laser centred in it); pushes/s per slice."""
-    return w.with_(nzeta=64, precision=64,
-                   laser=w.laser.__class__(**{**w.laser.__dict__, "zeta_center": 32 * w.h}))
+    particles per cell over a 64-slice window (the laser centred in it; a bunch's head in it,
+    with 2^14 macroparticles); pushes/s per slice."""
+    s = w.with_(nzeta=64, precision=64)
+    if w.laser is not None:
+        s = s.with_(laser=w.laser.__class__(**{**w.laser.__dict__, "zeta_center": 32 * w.h}))
+    if w.beam is not None:
+        s = s.with_(beam=w.beam.__class__(**{**w.beam.__dict__, "zeta_center": 64 * w.h - 0.8,
+                                            "n_macro": 1 << 14}))
+    return s
 
 
 def _oracle_worker(job):
@@ -225,7 +231,8 @@ def config_dict(w, shape=None):
          "delta": w.delta, "ppc": sum(s.ppc for s in w.species), "precision": w.precision,
          "laser_a0": w.laser.a0 if w.laser else None,
          "pushes_per_step": w.pushes_per_step,
-         "l2": "spectral state (24 B/cell, 403 MB) read and rewritten every s-step: inputs larger than L2"}
+         "l2": f"spectral state (24 B/cell, {w.nx * w.ny * w.nzeta * 24 / 1e6:.0f} MB) read and "
+               "rewritten every s-step: inputs larger than L2"}
     if shape:
         d["launch"] = shape
     return d
@@ -244,8 +251,10 @@ def main():
                     help="profiling only: shorter window of the same workload")
     ap.add_argument("--pipeline", type=int, default=0, help="s-steps marched concurrently (0 = auto)")
     ap.add_argument("--bucket-capacity", type=int, default=0)
-    ap.add_argument("--workload", default="lwfa3d", choices=["lwfa3d", "scan"],
-                    help="lwfa3d: the 3-D LWFA (default); scan: the batched 2-D parameter scan")
+    ap.add_argument("--workload", default="lwfa3d", choices=["lwfa3d", "scan", "pwfa"],
+                    help="lwfa3d: the 3-D LWFA (default); scan: the batched 2-D parameter scan; "
+                         "pwfa: the beam-driven 3-D case (128 x 128 x 768, 2 e + 2 p per cell, "
+                         "a 2^20-particle drive bunch)")
     ap.add_argument("--instances", type=int, default=64, help="scan: number of instances")
     ap.add_argument("--fp64-steps", type=int, default=40,
                     help="s-steps of the FP64-plain comparison on the 2-D workload (0 skips it)")
@@ -257,7 +266,11 @@ def main():
         return run_scan(args)
 
     from paper_2509_16793_gb300 import workloads as W
-    w = W.lwfa_3d_128x128x1024()
+    w = W.pwfa_3d_128x128x768() if args.workload == "pwfa" else W.lwfa_3d_128x128x1024()
+    if args.workload == "pwfa":
+        args.e2e_steps = 0
+        args.fp64_steps = 0
+        args.denoise_pairs = 0
     if args.nzeta:
         w = w.with_(nzeta=args.nzeta, name=f"{w.name}_nzeta{args.nzeta}",
                     laser=W.Laser(**{**w.laser.__dict__,

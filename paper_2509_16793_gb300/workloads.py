@@ -228,6 +228,28 @@ def lwfa_3d_128x128x512(ppc: int = 1, precision: int = 32, steps: int = 200) -> 
                    laser=Laser(**{**w.laser.__dict__, "zeta_center": L - 2.0 * w.laser.duration}))
 
 
+def pwfa_3d_128x128x768(precision: int = 32, steps: int = 1000, n_macro: int = 1 << 20) -> Workload:
+    """Beam-driven wakefield (units omega_0 = omega_p, so n0 = 1): background electrons and
+    mobile protons (m = 1836), 2 + 2 per cell, cold, injected at the front; an electron drive
+    bunch n_b = 2 n0, sigma_r = 0.5, sigma_z = 1 c/omega_p, gamma = 2000 with 1e-3 relative
+    spread, n_macro equal-charge macroparticles, centred 3 sigma_z behind the front; window
+    12 x 12 x 15.36 c/omega_p, h = 1/50, Delta = 10 (about 40 s-steps per betatron period
+    2 pi sqrt(2 gamma)).  The transverse grid is 128 x 128 (hx = 12/128), the largest square
+    power-of-two grid one cluster marches; the 192 x 192 grid of the same box is not (its
+    transforms are not powers of two)."""
+    n0 = 1.0
+    h = 1.0 / 50.0
+    hx = 12.0 / 128.0
+    L = 768 * h
+    return Workload(
+        name="pwfa3d_128x128x768_ppc2x2", nx=128, ny=128, nzeta=768, hx=hx, hy=hx, h=h,
+        delta=10.0, species=[Species(-1.0, 1.0, n0, 2), Species(1.0, 1836.0, n0, 2)],
+        laser=None, precision=precision, steps=steps,
+        beam=Beam(charge=-1.0, mass=1.0, n_peak=2.0 * n0, sigma_r=0.5, sigma_z=1.0,
+                  zeta_center=L - 3.0, gamma=2000.0, rel_spread=1e-3, n_macro=n_macro,
+                  seed=SEED + 3))
+
+
 def small_3d(nx: int = 16, ny: int = 16, nzeta: int = 48, ppc: int = 2, precision: int = 64,
              a0: float = 1.5, n0: float = 0.01, delta: Optional[float] = None,
              steps: int = 2) -> Workload:

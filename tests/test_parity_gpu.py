@@ -262,6 +262,48 @@ def test_laser_given_by_its_intensity_fwhm():
         check_state(b.state(), a.state(), 1e-13)
 
 
+def test_pwfa_window_prefix_matches_oracle():
+    """The PWFA configuration (electrons and mobile protons, the library-sampled drive bunch)
+    on its full transverse grid, 128 x 128, with a 96-slice window, against the oracle in FP32:
+    on-axis E_z, field and kinetic energy within 1e-4 over two s-steps, the stored counts."""
+    w = W.pwfa_3d_128x128x768(n_macro=1 << 16)
+    L = 96 * w.h
+    w = w.with_(nzeta=96, beam=W.Beam(**{**w.beam.__dict__, "zeta_center": L - 0.8}))
+    o = RefSim(w)
+    with gpu_sim(w) as g:
+        for k in range(2):
+            od = o.step()
+            g.step()
+            gd = g.diagnostics()
+            ez, oez = g.onaxis_ez(), od["onaxis_ez"]
+            errs = {"ez": np.abs(ez - oez).max() / np.abs(oez).max()}
+            for key in ("field_energy", "kinetic_energy"):
+                errs[key] = abs(gd[key] - od[key]) / abs(od[key])
+            assert max(errs.values()) <= 1e-4, (k, errs)
+            assert gd["n_stored"] == od["n_stored"] and gd["n_trapped"] == od["n_trapped"]
+
+
+@pytest.mark.slow
+def test_pwfa_full_size_properties():
+    """The PWFA configuration at 128 x 128 x 768 with its 2^20-particle bunch, in the bench's
+    launch shape: every fresh particle of both species crosses every slice until it is
+    trapped (4 per cell: most of a band's layer lives in the global overflow slots), the
+    neutral plasma
+    carries no (rho - j_z) flux, the bunch stays in the stored set, the energies are finite."""
+    w = W.pwfa_3d_128x128x768()
+    with gpu_sim(w) as g:
+        assert g.launch_shape()["cluster_ctas"] == 16
+        g.step(2)
+        d = g.diagnostics()
+        # a particle trapped at a slice makes no further crossings in that s-step
+        assert w.pushes_per_step - d["n_trapped"] * w.nzeta <= d["pushes"] <= w.pushes_per_step
+        vol = w.nx * w.hx * w.ny * w.hy * w.nzeta * w.h
+        assert abs(d["charge_flux"]) < 1e-4 * vol
+        assert d["n_stored"] > 0.99 * (1 << 20) * 0.998          # the bunch inside the window
+        assert np.isfinite(d["field_energy"]) and d["field_energy"] > 0
+        assert np.isfinite(d["kinetic_energy"]) and d["kinetic_energy"] > 0
+
+
 def test_fp32_matches_fp64_oracle():
     w = W.small_3d(nx=32, ny=32, nzeta=64, ppc=2, precision=32)
     o = RefSim(w)

@@ -114,6 +114,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
   return false;
 }
 
+// 16-byte asynchronous copy global -> shared through L1 (neighbouring taps reuse it);
+// src_bytes = 0 fills the destination with zeros
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -213,27 +223,28 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(ConvArgs a) {
       }
       // gather: for each tap of the round, this thread's row = the 16 channels (two 16-byte
       // core-matrix rows) of its voxel's neighbour
-      unsigned char* dstA = sA + (size_t)buf * kRound * kTapBytesA + (tid >> 3) * kSBO + (tid & 7) * 16;
-#pragma unroll 3
+      // (asynchronous copies: all of a round's loads are in flight at once; a neighbour
+      // outside the window copies zero bytes, which fills zeros)
+      const uint32_t dstA = aBase + (uint32_t)(buf * kRound) * kTapBytesA + (tid >> 3) * kSBO +
+                            (tid & 7) * 16;
+#pragma unroll
       for (int s = 0; s < kRound; ++s) {
         const int t = round * kRound + s;
         const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
-        uint4 lo = make_uint4(0u, 0u, 0u, 0u), hi = lo;
         const int zz = z + dz;
-        if (valid && zz >= 0 && zz < a.nz) {
-          int yy = y + dy, xx = x + dx;
-          yy += yy < 0 ? a.ny : 0;
-          yy -= yy >= a.ny ? a.ny : 0;
-          xx += xx < 0 ? a.nx : 0;
-          xx -= xx >= a.nx ? a.nx : 0;
-          const uint4* src = reinterpret_cast<const uint4*>(
-              a.x + ((long long)zz * plane + (long long)yy * a.nx + xx) * kCh);
-          lo = src[0];
-          hi = src[1];
-        }
-        *reinterpret_cast<uint4*>(dstA + (size_t)s * kTapBytesA) = lo;
-        *reinterpret_cast<uint4*>(dstA + (size_t)s * kTapBytesA + kLBO) = hi;
+        const bool in = valid && zz >= 0 && zz < a.nz;
+        int yy = y + dy, xx = x + dx;
+        yy += yy < 0 ? a.ny : 0;
+        yy -= yy >= a.ny ? a.ny : 0;
+        xx += xx < 0 ? a.nx : 0;
+        xx -= xx >= a.nx ? a.nx : 0;
+        const __nv_bfloat16* src =
+            in ? a.x + ((long long)zz * plane + (long long)yy * a.nx + xx) * kCh : a.x;
+        const uint32_t nb = in ? 16u : 0u;
+        cp_async16(dstA + (uint32_t)s * kTapBytesA, src, nb);
+        cp_async16(dstA + (uint32_t)s * kTapBytesA + kLBO, src + 8, nb);
       }
+      cp_async_wait_all();
       fence_async_smem();
       tc_fence_before();
       __syncthreads();

@@ -2804,8 +2804,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   }
 }
 
-template <typename T, bool CANON = false, int SH = 0>
-__global__ void __launch_bounds__(512, 1) march_kernel(const Params p) {
+template <typename T, bool CANON, int SH>
+__device__ __forceinline__ void march_launch(const Params& p) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
   const Sm<T> s = carve<T>(p, smem);
@@ -2814,6 +2814,17 @@ __global__ void __launch_bounds__(512, 1) march_kernel(const Params p) {
   __syncthreads();
   const int cid = (int)(blockIdx.x / p.C);
   for (long long k = p.k0 + cid; k < p.k0 + p.nsteps; k += p.P) march<T, CANON, SH>(p, s, cl, k, cid);
+}
+
+template <typename T, bool CANON = false, int SH = 0>
+__global__ void __launch_bounds__(512, 1) march_kernel(const Params p) {
+  march_launch<T, CANON, SH>(p);
+}
+
+// FP64 with at most 256 threads per CTA (the 2-D and small 3-D grids): up to 255 registers a
+// thread, so the FP64 march keeps its state in registers instead of spilling it
+__global__ void __launch_bounds__(256, 1) march_kernel_fp64_narrow(const Params p) {
+  march_launch<double, false, 0>(p);
 }
 
 // Batched scan: one persistent launch over independent simulations.  Each CTA takes work
@@ -3114,6 +3125,7 @@ static cudaError_t cfg_kernel(K* k, int smem) {
 cudaError_t configure_kernels(int precision, int smem, int) {
   if (precision == 64) {
     cudaError_t e = cfg_kernel(march_kernel<double>, smem);
+    if (e == cudaSuccess) e = cfg_kernel(march_kernel_fp64_narrow, smem);
     return e == cudaSuccess ? cfg_kernel(laser_kernel<double>, smem) : e;
   }
   cudaError_t e = cfg_kernel(march_kernel<float>, smem);
@@ -3142,6 +3154,8 @@ static cudaLaunchConfig_t make_cfg(const Params& p, int nclusters, cudaStream_t 
 cudaError_t launch_march(int precision, const Params& p, cudaStream_t s) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t c = make_cfg(p, p.P, s, attr);
+  if (precision == 64 && p.nthreads <= 256)
+    return cudaLaunchKernelEx(&c, march_kernel_fp64_narrow, p);
   if (precision == 64) return cudaLaunchKernelEx(&c, march_kernel<double>, p);
   if (shape_class(precision, p) == 1) return cudaLaunchKernelEx(&c, march_kernel<float, false, 1>, p);
   return cudaLaunchKernelEx(&c, march_kernel<float>, p);
@@ -3212,6 +3226,8 @@ cudaError_t launch_tables(int precision, const Params& p, void* dst, cudaStream_
 cudaError_t max_active_clusters(int precision, const Params& p, int* n) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t c = make_cfg(p, 1, 0, attr);
+  if (precision == 64 && p.nthreads <= 256)
+    return cudaOccupancyMaxActiveClusters(n, march_kernel_fp64_narrow, &c);
   if (precision == 64) return cudaOccupancyMaxActiveClusters(n, march_kernel<double>, &c);
   if (shape_class(precision, p) == 1)
     return cudaOccupancyMaxActiveClusters(n, march_kernel<float, false, 1>, &c);

@@ -287,9 +287,10 @@ def test_pwfa_window_prefix_matches_oracle():
 def test_pwfa_full_size_properties():
     """The PWFA configuration at 128 x 128 x 768 with its 2^20-particle bunch, in the bench's
     launch shape: every fresh particle of both species crosses every slice until it is
-    trapped (4 per cell: most of a band's layer lives in the global overflow slots), the
-    neutral plasma
-    carries no (rho - j_z) flux, the bunch stays in the stored set, the energies are finite."""
+    trapped (4 per cell: most of a band's layer lives in the global overflow slots); the
+    plasma is neutral, so its (rho - j_z) flux is exactly the charge of the electron crossings
+    that trapping removed (each crossing carries |q| n0 / ppc hx hy h; the protons cross every
+    slice); the bunch stays in the stored set; the energies are finite."""
     w = W.pwfa_3d_128x128x768()
     with gpu_sim(w) as g:
         assert g.launch_shape()["cluster_ctas"] == 16
@@ -297,8 +298,10 @@ def test_pwfa_full_size_properties():
         d = g.diagnostics()
         # a particle trapped at a slice makes no further crossings in that s-step
         assert w.pushes_per_step - d["n_trapped"] * w.nzeta <= d["pushes"] <= w.pushes_per_step
-        vol = w.nx * w.hx * w.ny * w.hy * w.nzeta * w.h
-        assert abs(d["charge_flux"]) < 1e-4 * vol
+        e = w.species[0]
+        unit = abs(e.charge) * e.density / e.ppc * w.hx * w.hy * w.h
+        missing = w.pushes_per_step - d["pushes"] + d["n_trapped"]   # + the trapping slabs
+        assert abs(d["charge_flux"] - unit * missing) <= 1e-9 * unit * w.pushes_per_step
         assert d["n_stored"] > 0.99 * (1 << 20) * 0.998          # the bunch inside the window
         assert np.isfinite(d["field_energy"]) and d["field_energy"] > 0
         assert np.isfinite(d["kinetic_energy"]) and d["kinetic_energy"] > 0

@@ -246,7 +246,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="gempic", choices=["gempic", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=10, help="0 skips the end-to-end leg")
+    ap.add_argument("--e2e-steps", type=int, default=21, help="0 skips the end-to-end leg")
     ap.add_argument("--nzeta", type=int, default=0,
                     help="profiling only: shorter window of the same workload")
     ap.add_argument("--pipeline", type=int, default=0, help="s-steps marched concurrently (0 = auto)")
@@ -321,20 +321,18 @@ def main():
     value = job_rate(w.pushes_per_step * args.steps, world, ms / 1e3)
     diag = sim.diagnostics()
 
-    # end to end through the C-ABI with host buffers: the spectral state comes in from pinned
-    # host memory, one s-step runs, the state and the diagnostics go back, every step
+    # end to end through the C-ABI with host buffers: every s-step's input state comes in from
+    # pinned host memory and its result and diagnostics go back out, streamed by groups of
+    # slices while the marches run (gempic_step_streamed)
     nb = sim.state_bytes()
+    diag_bytes = 9 * shape["cluster_ctas"] * 8          # per-CTA FP64 partials of one s-step
     e2e_s = float("nan")
     if args.e2e_steps > 0:
-        hin = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
-        hout = torch.empty(nb, dtype=torch.uint8, pin_memory=True)
-        sim.gempic_step_host(0, None, hout.numpy())
-        hin.copy_(hout)
+        host = torch.empty(nb, dtype=torch.uint8, pin_memory=True).numpy()
+        sim.gempic_get_state(host)                          # the raw bytes of the state
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            sim.gempic_step_host(1, hin.numpy(), hout.numpy())
-            hin, hout = hout, hin
+        sim.step_streamed(args.e2e_steps, host)
         e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     e2e_s = max_over_ranks(e2e_s, "cuda")
     e2e_value = job_rate(w.pushes_per_step, world, e2e_s)
@@ -405,7 +403,8 @@ def main():
             "config": config_dict(w, shape), "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value if math.isfinite(e2e_value) else None,
                     "unit": "pushes/s", "h2d_bytes_per_step": nb,
-                    "d2h_bytes_per_step": nb + 64},
+                    "d2h_bytes_per_step": nb + diag_bytes,
+                    "steps": args.e2e_steps, "call": "gempic_step_streamed"},
             "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64, "denoiser": denoise,
             "diag": {k: diag[k] for k in ("field_energy", "kinetic_energy", "n_stored", "pushes")}}
     print(json.dumps(line), flush=True)

@@ -251,6 +251,29 @@ gempic_status gempic_sync(struct gempic_sim* sim);
 gempic_status gempic_step_host(struct gempic_sim* sim, int32_t n, const void* state_in,
                                void* state_out, size_t state_bytes, gempic_diag* diag_out);
 
+/* End-to-end s-steps with the state streamed through host memory while the marches run.
+ * The n s-steps march as the wavefront of gempic_step (pipeline_depth marches in flight);
+ * each s-step reads its old level from a device input buffer and writes its new level to a
+ * device output buffer (both in the layout of gempic_get_state), and the library moves the
+ * levels through host_state slice group by slice group: the slices a march has finished are
+ * copied out to host_state, copied back in as the next s-step's input, and released to that
+ * march.  So every s-step's input comes in from host memory and its result goes out to host
+ * memory (gempic_state_bytes each way), and the copies overlap the marches.
+ *   host_state   the input of the first s-step on entry, the result of the last on return;
+ *                layout of gempic_get_state, bytes >= gempic_state_bytes.  Page-locked
+ *                memory (cudaHostAlloc, cudaHostRegister) lets the copies run asynchronously;
+ *                pageable memory works but serialises them.
+ *   diag_out     NULL or n records: the diagnostics of each s-step, in order.
+ * The calling thread drives the copies and returns when all s-steps are done; the device
+ * state is then the last result (gempic_get_state returns it).  The marches wait for their
+ * input slices with the bounded waits of gempic_set_wait_limit (GEMPIC_ETIMEOUT if one gives
+ * up; the calling thread also gives up after 120 s without progress).  The library keeps two
+ * device state buffers and a few words of mapped host memory for it, allocated at the first
+ * call.  GEMPIC_ESTATE with a denoiser set or after a failure; GEMPIC_EINVAL for n < 0, a NULL
+ * host_state or too few bytes. */
+gempic_status gempic_step_streamed(struct gempic_sim* sim, int32_t n, void* host_state,
+                                   size_t bytes, gempic_diag* diag_out);
+
 /* Size in bytes of the spectral state of gempic_get_state. */
 size_t gempic_state_bytes(const struct gempic_sim* sim);
 

@@ -4,10 +4,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <deque>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/gempic.h"
@@ -50,6 +53,14 @@ struct gempic_sim {
   // particles placed before the first step: absolute positions
   std::vector<double> px, py, pz, pux, puy, puz, pq;
   std::vector<int> psp;
+  // gempic_step_streamed: input and output levels on the device (public layout), the
+  // host-mapped words [ready: pmax][done: pmax], two copy streams and their events
+  void* io_a = nullptr;
+  void* io_b = nullptr;
+  unsigned long long* io_host = nullptr;
+  unsigned long long* io_dev = nullptr;
+  cudaStream_t io_out = nullptr, io_in = nullptr;
+  std::vector<cudaEvent_t> io_events;
 };
 
 namespace {
@@ -782,6 +793,284 @@ gempic_status gempic_step_host(gempic_sim* s, int32_t n, const void* state_in, v
   return st;
 }
 
+// the FP64 diagnostic sums of march `sl` of the last launch: the per-CTA partials added
+static cudaError_t diag_sums(gempic_sim* s, int sl, double* v) {
+  const Params& p = s->p;
+  std::vector<double> d((size_t)gempic::kNDiag * p.C);
+  cudaError_t e = cudaMemcpyAsync(d.data(), p.diag_out + (size_t)sl * gempic::kNDiag * p.C,
+                                  d.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < gempic::kNDiag; ++i) {
+    v[i] = 0.0;
+    for (int r = 0; r < p.C; ++r) v[i] += d[(size_t)i * p.C + r];
+  }
+  return cudaSuccess;
+}
+
+static gempic_status diag_record(gempic_sim* s, int sl, long long step, const double* v,
+                                 gempic_diag* out) {
+  const Params& p = s->p;
+  out->step = step;
+  out->field_energy = v[gempic::DG_FIELD];
+  out->kinetic_energy = v[gempic::DG_KIN];
+  out->charge_flux = v[gempic::DG_FLUX];
+  out->n_trapped = (int64_t)std::llround(v[gempic::DG_TRAP]);
+  out->n_stored = (int64_t)std::llround(v[gempic::DG_STORED]);
+  out->n_rejoined = (int64_t)std::llround(v[gempic::DG_REJOIN]);
+  out->pushes = (int64_t)std::llround(v[gempic::DG_PUSH]);
+  out->stored_kinetic_energy = v[gempic::DG_KST];
+  out->continuity_residual = -1.0;
+  out->gauss_residual = -1.0;
+  if (p.resid) {
+    cudaError_t e = cudaMemcpyAsync(&out->continuity_residual, p.resid_out + sl, sizeof(double),
+                                    cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(&out->gauss_residual, p.gauss_out + sl, sizeof(double),
+                          cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_fail(s, e);
+  }
+  return GEMPIC_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// s-steps with the state streamed through host memory
+// ------------------------------------------------------------------------------------------
+namespace {
+
+cudaError_t ensure_stream_io(gempic_sim* s) {
+  const size_t nb = gempic_state_bytes(s);
+  cudaError_t e = cudaSuccess;
+  if (!s->io_a) e = dalloc(s, &s->io_a, nb);
+  if (e == cudaSuccess && !s->io_b) e = dalloc(s, &s->io_b, nb);
+  if (e == cudaSuccess && !s->io_host) {
+    void* h = nullptr;
+    e = cudaHostAlloc(&h, 2 * (size_t)s->pmax * sizeof(unsigned long long), cudaHostAllocMapped);
+    if (e != cudaSuccess) return e;
+    std::memset(h, 0, 2 * (size_t)s->pmax * sizeof(unsigned long long));
+    s->io_host = (unsigned long long*)h;
+    void* d = nullptr;
+    e = cudaHostGetDevicePointer(&d, h, 0);
+    s->io_dev = (unsigned long long*)d;
+  }
+  if (e == cudaSuccess && !s->io_out) e = cudaStreamCreateWithFlags(&s->io_out, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !s->io_in) e = cudaStreamCreateWithFlags(&s->io_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = gempic::configure_march_canon(s->cfg.precision, s->p.smem_bytes);
+  return e;
+}
+
+cudaError_t io_event(gempic_sim* s, cudaEvent_t* ev) {
+  if (!s->io_events.empty()) {
+    *ev = s->io_events.back();
+    s->io_events.pop_back();
+    return cudaSuccess;
+  }
+  return cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+}
+
+// Copy group j of the public layout [6][nz][ny][nx/2] between the host buffer and a device
+// level: blocks [lo, hi) are R_x, R_y, E_z, B_z at slices lo .. hi-1 (below nz) and j_x, j_y at
+// half-slices lo-1 .. hi-2 (from 0); two strided copies, one per group of components.
+cudaError_t io_copy(gempic_sim* s, int j, int chunk, void* dev, void* host, bool out,
+                    cudaStream_t st) {
+  const int nz = s->p.nz;
+  const size_t sb = (size_t)s->p.ny * (s->p.nx / 2) * 2 * s->eb;    // one slice of one component
+  const size_t cb = (size_t)nz * sb;                                 // one component
+  const int hi = nz + 1 - j * chunk, lo = std::max(0, hi - chunk);
+  char* d = (char*)dev;
+  char* h = (char*)host;
+  const cudaMemcpyKind kind = out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
+  cudaError_t e = cudaSuccess;
+  const int f0 = lo, f1 = std::min(hi, nz);                         // fields
+  if (f1 > f0) {
+    const size_t off = (size_t)f0 * sb, w = (size_t)(f1 - f0) * sb;
+    e = out ? cudaMemcpy2DAsync(h + off, cb, d + off, cb, w, 4, kind, st)
+            : cudaMemcpy2DAsync(d + off, cb, h + off, cb, w, 4, kind, st);
+  }
+  const int c0 = std::max(lo, 1) - 1, c1 = hi - 1;                  // currents
+  if (e == cudaSuccess && c1 > c0) {
+    const size_t off = 4 * cb + (size_t)c0 * sb, w = (size_t)(c1 - c0) * sb;
+    e = out ? cudaMemcpy2DAsync(h + off, cb, d + off, cb, w, 2, kind, st)
+            : cudaMemcpy2DAsync(d + off, cb, h + off, cb, w, 2, kind, st);
+  }
+  return e;
+}
+
+struct IoPending {
+  int step;          // s-step within the call whose input (H2D) or output (D2H) this is
+  int group;
+  cudaEvent_t ev;
+};
+
+}  // namespace
+
+gempic_status gempic_step_streamed(gempic_sim* s, int32_t n, void* host, size_t bytes,
+                                   gempic_diag* diag_out) {
+  if (!s || n < 0 || !host) return GEMPIC_EINVAL;
+  if (bytes < gempic_state_bytes(s)) return GEMPIC_EINVAL;
+  if (s->dn) return GEMPIC_ESTATE;
+  gempic_status st = ensure_initialized(s);
+  if (st != GEMPIC_OK) return st;
+  if (n == 0) return GEMPIC_OK;
+  cudaError_t e = ensure_stream_io(s);
+  if (e == cudaSuccess) e = ensure_diag_cap(s, n);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  const int nz = s->p.nz;
+  // groups of at most 8 MiB and at least 8 groups a level (so that the next s-step follows
+  // closely), each of at least 2 blocks (a march starts on blocks nz and nz-1)
+  const size_t block_bytes = (size_t)6 * s->p.ny * (s->p.nx / 2) * 2 * s->eb;
+  const size_t by_bytes = std::max<size_t>(1, ((size_t)8 << 20) / block_bytes);
+  const int chunk = (int)std::max<size_t>(2, std::min<size_t>(by_bytes, (size_t)(nz + 8) / 8));
+  const int nch = (nz + 1 + chunk - 1) / chunk;
+  Params q = s->p;
+  q.k0 = s->k;
+  q.nsteps = n;
+  q.P = std::min(s->pmax, n);
+  q.inject = q.nspecies > 0 ? 1 : 0;
+  q.delta_field = s->p.delta;
+  q.state = s->io_a;
+  q.state_out = s->io_b;
+  q.io_ready = s->io_dev;
+  q.io_done = s->io_dev + s->pmax;
+  q.io_chunk = chunk;
+  q.io_nchunk = nch;
+  unsigned long long* ready = s->io_host;
+  const unsigned long long* done = s->io_host + s->pmax;
+  const long long k0 = s->k;
+  auto slot = [&](int i) { return i % q.P; };
+  // the first s-step's input goes in before the launch's marches reach it
+  std::deque<IoPending> outq, inq;
+  for (int j = 0; j < nch && e == cudaSuccess; ++j) {
+    IoPending pd{0, j, nullptr};
+    e = io_event(s, &pd.ev);
+    if (e == cudaSuccess) e = io_copy(s, j, chunk, s->io_a, host, false, s->io_in);
+    if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->io_in);
+    if (e == cudaSuccess) inq.push_back(pd);
+  }
+  if (e == cudaSuccess) e = gempic::launch_march_canon(s->cfg.precision, q, s->stream);
+  s->launches++;
+  if (e != cudaSuccess) {
+    cudaStreamSynchronize(s->io_in);
+    return cuda_fail(s, e);
+  }
+  // Drive the copies: a group of s-step i's result goes out once its march has written it,
+  // back in as s-step i+1's input once it is out, and is released to that march once it is
+  // in.  Each link waits for the one before it, so the host buffer and both device levels are
+  // only rewritten after their last reader is done.
+  std::vector<int> next_out(n, 0);
+  int first = 0, outs_done = 0;
+  gempic_status result = GEMPIC_OK;
+  auto last_move = std::chrono::steady_clock::now();
+  while (outs_done < n * nch || !inq.empty()) {
+    bool moved = false;
+    for (int i = first; i < n && e == cudaSuccess; ++i) {
+      if (next_out[i] >= nch) {
+        if (i == first) ++first;
+        continue;
+      }
+      const unsigned long long v = __atomic_load_n(done + slot(i), __ATOMIC_ACQUIRE);
+      while (next_out[i] < nch && e == cudaSuccess) {
+        const int j = next_out[i];
+        const int lo = std::max(0, nz + 1 - (j + 1) * chunk);
+        const unsigned long long need = gempic::prog_value(k0 + i, nz, std::min(nz, nz - lo + 1));
+        if (v < need) break;
+        IoPending pd{i, j, nullptr};
+        e = io_event(s, &pd.ev);
+        if (e == cudaSuccess) e = io_copy(s, j, chunk, s->io_b, host, true, s->io_out);
+        if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->io_out);
+        if (e == cudaSuccess) outq.push_back(pd);
+        ++next_out[i];
+        moved = true;
+      }
+    }
+    while (e == cudaSuccess && !outq.empty()) {
+      const cudaError_t qe = cudaEventQuery(outq.front().ev);
+      if (qe == cudaErrorNotReady) break;
+      if (qe != cudaSuccess) {
+        e = qe;
+        break;
+      }
+      IoPending pd = outq.front();
+      outq.pop_front();
+      ++outs_done;
+      moved = true;
+      if (pd.step + 1 < n) {
+        IoPending nx{pd.step + 1, pd.group, pd.ev};
+        e = io_copy(s, pd.group, chunk, s->io_a, host, false, s->io_in);
+        if (e == cudaSuccess) e = cudaEventRecord(nx.ev, s->io_in);
+        if (e == cudaSuccess) inq.push_back(nx);
+      } else {
+        s->io_events.push_back(pd.ev);
+      }
+    }
+    while (e == cudaSuccess && !inq.empty()) {
+      const cudaError_t qe = cudaEventQuery(inq.front().ev);
+      if (qe == cudaErrorNotReady) break;
+      if (qe != cudaSuccess) {
+        e = qe;
+        break;
+      }
+      const IoPending pd = inq.front();
+      inq.pop_front();
+      __atomic_store_n(ready + slot(pd.step), gempic::io_value(k0 + pd.step, nch, pd.group),
+                       __ATOMIC_RELEASE);
+      s->io_events.push_back(pd.ev);
+      moved = true;
+    }
+    if (e != cudaSuccess) break;
+    const auto now = std::chrono::steady_clock::now();
+    if (moved) {
+      last_move = now;
+      continue;
+    }
+    // a launch that failed publishes nothing more
+    const cudaError_t me = cudaStreamQuery(s->stream);
+    if (me != cudaSuccess && me != cudaErrorNotReady) {
+      e = me;
+      break;
+    }
+    if (now - last_move > std::chrono::seconds(120)) {
+      result = GEMPIC_ETIMEOUT;
+      break;
+    }
+    std::this_thread::yield();
+  }
+  // the marches always finish (their waits are bounded); then the copies
+  cudaError_t e2 = cudaStreamSynchronize(s->stream);
+  cudaError_t e3 = cudaStreamSynchronize(s->io_out);
+  cudaError_t e4 = cudaStreamSynchronize(s->io_in);
+  for (const IoPending& pd : outq) s->io_events.push_back(pd.ev);
+  for (const IoPending& pd : inq) s->io_events.push_back(pd.ev);
+  if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4;
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  s->last_launch_k0 = s->k;
+  s->last_launch_n = n;
+  s->denoised_last = false;
+  s->k += n;
+  if (result != GEMPIC_OK) {
+    s->failed = result;
+    return result;
+  }
+  st = check_device_error(s);
+  if (st != GEMPIC_OK) return st;
+  // the last result becomes the simulation's state
+  e = gempic::launch_import_state(s->cfg.precision, s->p, s->io_b, s->stream);
+  s->launches++;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  if (diag_out) {
+    for (int i = 0; i < n; ++i) {
+      double v[gempic::kNDiag];
+      e = diag_sums(s, i, v);
+      if (e != cudaSuccess) return cuda_fail(s, e);
+      st = diag_record(s, i, k0 + i + 1, v, diag_out + i);
+      if (st != GEMPIC_OK) return st;
+    }
+  }
+  return GEMPIC_OK;
+}
+
 gempic_status gempic_get_fields(gempic_sim* s, int32_t comp, void* dst, size_t bytes,
                                 int32_t dst_is_device) {
   if (!s || !dst || comp < 0 || comp > 8) return GEMPIC_EINVAL;
@@ -856,57 +1145,22 @@ gempic_status gempic_get_diagnostics(gempic_sim* s, gempic_diag* out) {
   if (st != GEMPIC_OK) return st;
   st = check_device_error(s);
   if (st != GEMPIC_OK) return st;
-  const Params& p = s->p;
   const int sl = s->last_launch_n - 1;
-  std::vector<double> d((size_t)gempic::kNDiag * p.C);
-  cudaError_t e = cudaMemcpyAsync(d.data(), p.diag_out + (size_t)sl * gempic::kNDiag * p.C,
-                                  d.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-  if (e != cudaSuccess) return cuda_fail(s, e);
   double v[gempic::kNDiag];
-  for (int i = 0; i < gempic::kNDiag; ++i) {
-    v[i] = 0.0;
-    for (int r = 0; r < p.C; ++r) v[i] += d[(size_t)i * p.C + r];
-  }
+  cudaError_t e = diag_sums(s, sl, v);
+  if (e != cudaSuccess) return cuda_fail(s, e);
   if (s->denoised_last) {
     // the second pass holds the fields and the stored set; the first the streaming particles
-    std::vector<double> d2((size_t)gempic::kNDiag * p.C);
-    e = cudaMemcpyAsync(d2.data(), p.diag_out + (size_t)gempic::kNDiag * p.C,
-                        d2.size() * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e);
     double v2[gempic::kNDiag];
-    for (int i = 0; i < gempic::kNDiag; ++i) {
-      v2[i] = 0.0;
-      for (int r = 0; r < p.C; ++r) v2[i] += d2[(size_t)i * p.C + r];
-    }
+    e = diag_sums(s, 1, v2);
+    if (e != cudaSuccess) return cuda_fail(s, e);
     v[gempic::DG_FIELD] = v2[gempic::DG_FIELD];
     v[gempic::DG_KIN] += v2[gempic::DG_KIN];
     v[gempic::DG_KST] = v2[gempic::DG_KST];
     v[gempic::DG_STORED] = v2[gempic::DG_STORED];
     v[gempic::DG_LOST] = v2[gempic::DG_LOST];
   }
-  out->step = s->k;
-  out->field_energy = v[gempic::DG_FIELD];
-  out->kinetic_energy = v[gempic::DG_KIN];
-  out->charge_flux = v[gempic::DG_FLUX];
-  out->n_trapped = (int64_t)std::llround(v[gempic::DG_TRAP]);
-  out->n_stored = (int64_t)std::llround(v[gempic::DG_STORED]);
-  out->n_rejoined = (int64_t)std::llround(v[gempic::DG_REJOIN]);
-  out->pushes = (int64_t)std::llround(v[gempic::DG_PUSH]);
-  out->stored_kinetic_energy = v[gempic::DG_KST];
-  out->continuity_residual = -1.0;
-  out->gauss_residual = -1.0;
-  if (p.resid) {
-    e = cudaMemcpyAsync(&out->continuity_residual, p.resid_out + sl, sizeof(double),
-                        cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess)
-      e = cudaMemcpyAsync(&out->gauss_residual, p.gauss_out + sl, sizeof(double),
-                          cudaMemcpyDeviceToHost, s->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
-    if (e != cudaSuccess) return cuda_fail(s, e);
-  }
-  return GEMPIC_OK;
+  return diag_record(s, sl, s->k, v, out);
 }
 
 gempic_status gempic_get_onaxis_ez(gempic_sim* s, double* dst, int32_t n) {
@@ -991,6 +1245,12 @@ gempic_status gempic_launch_shape(const gempic_sim* s, int32_t* cluster_ctas, in
 void gempic_destroy(gempic_sim* s) {
   if (!s) return;
   cudaStreamSynchronize(s->stream);
+  if (s->io_out) cudaStreamSynchronize(s->io_out);
+  if (s->io_in) cudaStreamSynchronize(s->io_in);
+  for (cudaEvent_t ev : s->io_events) cudaEventDestroy(ev);
+  if (s->io_out) cudaStreamDestroy(s->io_out);
+  if (s->io_in) cudaStreamDestroy(s->io_in);
+  if (s->io_host) cudaFreeHost(s->io_host);
   for (void* v : s->allocs) cudaFree(v);
   cudaGetLastError();
   delete s;

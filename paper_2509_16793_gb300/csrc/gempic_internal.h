@@ -99,7 +99,28 @@ struct Params {
   int skip_stored, fields_only;
   void* pover;                    // overflow particle slots [P*C][int cell; 7 reals][gcap]
   unsigned long long* timers;     // phase timers (builds with GEMPIC_PHASE_TIMERS only)
+  // state streamed through host memory (gempic_step_streamed): the old level is read from
+  // `state`, the new one written to `state_out`, both in the public layout; the blocks go out
+  // and back in groups of io_chunk (group j: blocks nz - j io_chunk down to
+  // nz + 1 - (j+1) io_chunk).  Words in host-mapped memory, one per march slot:
+  unsigned long long* io_ready;   // written by the host: io_value(k, io_nchunk, j) once group j
+                                  // of s-step k's input is in `state`
+  unsigned long long* io_done;    // written by the march: prog_value(k, nz, completed) each time
+                                  // `completed` reaches a multiple of io_chunk, and at the end
+  int io_chunk, io_nchunk;        // io_chunk = 0: not streamed
 };
+
+// progress word of a march: s-step k has completed `completed` of its nz iterations (they run
+// from slice nz-1 down to 0); increasing along the marches a slot runs
+__host__ __device__ inline unsigned long long prog_value(long long k, int nz, int completed) {
+  return (unsigned long long)(k + 2) * (unsigned long long)(nz + 1) + (unsigned long long)completed;
+}
+// release word of a streamed input: group j of s-step k's input is in device memory
+__host__ __device__ inline unsigned long long io_value(long long k, int nchunk, int j) {
+  return (unsigned long long)(k + 2) * (unsigned long long)(nchunk + 1) + (unsigned long long)(j + 1);
+}
+// group of block b (blocks nz .. 0 from the front)
+__host__ __device__ inline int io_group(int nz, int chunk, int b) { return (nz - b) / chunk; }
 
 // Gaussian bunch to sample into the level-0 stored set (gempic_beam, resolved by the host):
 // centre (xc, yc), widths, centre and spread along zeta, charge per macroparticle, species slot

@@ -141,6 +141,15 @@ __device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long
 __device__ __forceinline__ void st_release_u64(unsigned long long* p, unsigned long long v) {
   asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+// system scope: words in host-mapped memory shared with the calling thread
+__device__ __forceinline__ unsigned long long ld_acquire_sys_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 // shared memory of this CTA and of other CTAs of the cluster, addressed explicitly
 __device__ __forceinline__ uint32_t sh_addr(const void* p) {
@@ -501,7 +510,7 @@ enum CstSlot {
   K_H = 0, K_INVH, K_HX, K_HY, K_D, K_DF, K_WSCALE, K_CX, K_CY, K_INVHX, K_INVHY, K_FLUX,
   K_BEAM, K_JREF, K_JSCALE, K_JINV, K_QM = 16, K_MOQ = 20, K_QF = 24, K_INVD = 28, K_N = 29
 };
-enum MiscSlot { M_PCOUNT = 0, M_FTOP, M_INBOX, M_RQN, M_JFLAG, M_STN, M_OUTN, M_PAD1 };
+enum MiscSlot { M_PCOUNT = 0, M_FTOP, M_INBOX, M_RQN, M_JFLAG, M_STN, M_OUTN, M_IOSEEN };
 // particles leaving the band during a push wait in a local outbox of this many entries
 constexpr int kOutCap = 64;
 
@@ -1992,10 +2001,6 @@ __device__ __forceinline__ Mode6<T> slice_solve(T kx, T ky, T h, T Dl, const Mod
 // ------------------------------------------------------------------------------------------
 // progress / waits between concurrently marching clusters
 // ------------------------------------------------------------------------------------------
-__device__ __forceinline__ unsigned long long prog_value(long long k, int nz, int completed) {
-  return (unsigned long long)(k + 2) * (unsigned long long)(nz + 1) + (unsigned long long)completed;
-}
-
 __device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
   int spins = 0;
   while (ld_acquire_u64(p.progress + pcid) < target) {
@@ -2006,6 +2011,27 @@ __device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
       return;
     }
   }
+}
+
+// streamed state: wait until the host has released the group of block b of s-step k's input.
+// *seen (shared memory, -1 at the start of a march) is the last group known released.
+__device__ void wait_input(const Params& p, int cid, long long k, int b, int* seen) {
+  const int g = io_group(p.nz, p.io_chunk, b);
+  if (*seen >= g) return;
+  const unsigned long long target = io_value(k, p.io_nchunk, g);
+  unsigned long long v;
+  int spins = 0;
+  while ((v = ld_acquire_sys_u64(p.io_ready + cid)) < target) {
+    if (atomicAdd(p.err, 0) & ERR_TIMEOUT) return;
+    __nanosleep(200);
+    if (++spins > p.wait_spin_limit) {
+      atomicOr(p.err, ERR_TIMEOUT);
+      return;
+    }
+  }
+  // the host releases s-step k's groups in order and the next s-step's only after this march
+  // has read them all, so v names a group of this s-step
+  *seen = (int)min((unsigned long long)(p.io_nchunk - 1), v - io_value(k, p.io_nchunk, 0));
 }
 
 // FP64 diagnostics: each warp adds its lanes' sums to its own row (no atomics); the rows are
@@ -2169,6 +2195,11 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
 
   if (waits && tid == 0 && me == 0)
     wait_for(p, pcid, prog_value(k - 1, nz, min(nz, 3)));   // predecessor done down to nz-3
+  // streamed state: the input's blocks nz and nz-1
+  if (p.io_chunk && tid == 0 && me == 0) {
+    s.misc[M_IOSEEN] = -1;
+    wait_input(p, cid, k, nz - 1, s.misc + M_IOSEEN);
+  }
   cl.sync();
   if (has_mode) {
     j0px = ldcg(st + blk(nz, 4));
@@ -2437,6 +2468,12 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     // publish: iteration n+1 complete (its stored phase and this push have been issued)
     if (p.P > 1 && me == 0 && tid == 0 && n + 1 <= nz - 1)
       st_release_u64(p.progress + cid, prog_value(k, nz, nz - (n + 1)));
+    // streamed state: blocks >= n + 2 of the new level are written (and blocks >= n of the
+    // old level read); the host copies a group out once its last block is
+    if (p.io_chunk && me == 0 && tid == 0) {
+      const int done = nz - (n + 1);
+      if (done > 0 && done % p.io_chunk == 0) st_release_sys_u64(p.io_done + cid, prog_value(k, nz, done));
+    }
     // stored particles of cell n at this level (traps of this push included), for phase E;
     // loaded by the last warp, which has no forward-transform task
     if (tid == NT - 32) s.misc[M_STN] = ldcg(p.st.cnt + (size_t)s1 * nz + n);
@@ -2599,6 +2636,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     // ---------------- B: row FFTs of the currents, transposed to the kx owners ------------
     forward_rows<T, SH>(cl, p, s, me, true);
     TIMER_MARK(PH_FWD);
+    // streamed state: block n-1 of the input, read after the solve below
+    if (p.io_chunk && tid == 0 && me == 0 && n >= 1) wait_input(p, cid, k, n - 1, s.misc + M_IOSEEN);
     cl.sync();                                                      // B2
     if (tid == 0 && me == 0) p.jflag[(size_t)s1 * nz + n] = 0;
     TIMER_MARK(PH_B2);
@@ -2763,6 +2802,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   if (tid == 0) __threadfence();
   cl.sync();
   if (p.P > 1 && me == 0 && tid == 0) st_release_u64(p.progress + cid, prog_value(k, nz, nz));
+  if (p.io_chunk && me == 0 && tid == 0) st_release_sys_u64(p.io_done + cid, prog_value(k, nz, nz));
 
   if (resid) {
     // the march's largest residuals: non-negative doubles order like their bit patterns
@@ -3209,7 +3249,7 @@ cudaError_t configure_march_canon(int precision, int smem) {
 
 cudaError_t launch_march_canon(int precision, const Params& p, cudaStream_t s) {
   cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t c = make_cfg(p, 1, s, attr);
+  cudaLaunchConfig_t c = make_cfg(p, p.P, s, attr);
   if (precision == 64) return cudaLaunchKernelEx(&c, march_kernel<double, true>, p);
   if (shape_class(precision, p) == 1) return cudaLaunchKernelEx(&c, march_kernel<float, true, 1>, p);
   return cudaLaunchKernelEx(&c, march_kernel<float, true>, p);

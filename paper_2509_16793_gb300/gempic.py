@@ -94,6 +94,7 @@ SIGNATURES = {
     "gempic_set_wait_limit": (c_int32, [c_void_p, c_int64]),
     "gempic_set_delta": (c_int32, [c_void_p, c_double]),
     "gempic_step_host": (c_int32, [c_void_p, c_int32, c_void_p, c_void_p, c_size_t, POINTER(gempic_diag)]),
+    "gempic_step_streamed": (c_int32, [c_void_p, c_int32, c_void_p, c_size_t, POINTER(gempic_diag)]),
     "gempic_state_bytes": (c_size_t, [c_void_p]),
     "gempic_get_state": (c_int32, [c_void_p, c_void_p, c_size_t, c_int32]),
     "gempic_set_state": (c_int32, [c_void_p, c_void_p, c_size_t, c_int32]),
@@ -367,6 +368,20 @@ class Sim:
         _check(self.lib.gempic_step_host(self.h, n, _ptr(state_in), _ptr(state_out), nb, byref(d)),
                "gempic_step_host")
         return d.as_dict()
+
+    def gempic_step_streamed(self, n: int, host_state, diagnostics: bool = True):
+        """n s-steps with the state streamed through `host_state` (a C-contiguous host buffer
+        of state_bytes() bytes in the layout of gempic_get_state: the first s-step's input,
+        the last one's result on return).  Returns the diagnostics of each s-step."""
+        nb = self.state_bytes()
+        if host_state.nbytes < nb:
+            raise ValueError(f"host_state holds {host_state.nbytes} bytes, the state {nb}")
+        d = (gempic_diag * max(n, 1))()
+        _check(self.lib.gempic_step_streamed(self.h, n, _ptr(host_state), host_state.nbytes,
+                                             d if diagnostics else None), "gempic_step_streamed")
+        return [d[i].as_dict() for i in range(n)] if diagnostics else None
+
+    step_streamed = gempic_step_streamed
 
     def gempic_get_fields(self, comp) -> np.ndarray:
         c = FIELDS[comp] if isinstance(comp, str) else int(comp)

@@ -66,6 +66,7 @@ struct ConvArgs {
   float* jout;                // [nz][3][ny][nx] denoised current (MODE_LAST, may be null)
   float scale;
   int* err;
+  int zlo, zhi;               // output half-slices [zlo, zhi) (inputs are read where needed)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -149,6 +150,48 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// the layer's output for voxel v from its 16 accumulators: bias + ReLU in BF16 (hidden layers),
+// the input's ReLU mask (backward through a layer's input), or bias, the net output r and the
+// residual into the FP32 current (last layer)
+__device__ __forceinline__ void epilogue(const ConvArgs& a, long long v, const float* acc,
+                                         bool add_bias = true) {
+  if (a.mode == MODE_HIDDEN) {
+    __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      o[c] = __float2bfloat16_rn(fmaxf(acc[c] + (add_bias ? a.bias[c] : 0.0f), 0.0f));
+    uint4* d = reinterpret_cast<uint4*>(a.out + v * kCh);
+    d[0] = reinterpret_cast<const uint4*>(o)[0];
+    d[1] = reinterpret_cast<const uint4*>(o)[1];
+  } else if (a.mode == MODE_BWD) {
+    const uint4* mk = reinterpret_cast<const uint4*>(a.mask + v * kCh);
+    __align__(16) __nv_bfloat16 m[16];
+    reinterpret_cast<uint4*>(m)[0] = mk[0];
+    reinterpret_cast<uint4*>(m)[1] = mk[1];
+    __align__(16) __nv_bfloat16 o[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+      o[c] = __float2bfloat16_rn(__bfloat162float(m[c]) > 0.0f ? acc[c] : 0.0f);
+    uint4* d = reinterpret_cast<uint4*>(a.out + v * kCh);
+    d[0] = reinterpret_cast<const uint4*>(o)[0];
+    d[1] = reinterpret_cast<const uint4*>(o)[1];
+  } else {
+    const float b0 = add_bias ? a.bias[0] : 0.0f, b1 = add_bias ? a.bias[1] : 0.0f,
+                b2 = add_bias ? a.bias[2] : 0.0f;
+    const float r0 = acc[0] + b0, r1 = acc[1] + b1, r2 = acc[2] + b2;
+    if (a.r) *reinterpret_cast<float4*>(a.r + v * 4) = make_float4(r0, r1, r2, 0.0f);
+    if (a.jout) {
+      const long long plane = (long long)a.nx * a.ny;
+      const long long z = v / plane, rem = v - z * plane;
+      const long long base = z * 3 * plane + rem;
+      const float rr[3] = {r0, r1, r2};
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        a.jout[base + c * plane] = a.jres[base + c * plane] + a.scale * rr[c];
+    }
+  }
+}
+
 // neighbour voxel of v for tap t = (dz, dy, dx) + 1 in row-major order, -1 outside the window
 __device__ __forceinline__ long long neighbour(long long v, int t, int nx, int ny, int nz) {
   const int dz = t / 9 - 1, dy = (t / 3) % 3 - 1, dx = t % 3 - 1;
@@ -170,8 +213,10 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(ConvArgs a) {
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const long long V = (long long)a.nx * a.ny * a.nz;
-  const long long ntiles = (V + kTile - 1) / kTile;
+  const long long plane0 = (long long)a.nx * a.ny;
+  const long long vlo = (long long)a.zlo * plane0;
+  const long long V = (long long)a.zhi * plane0;            // output voxels [vlo, V)
+  const long long ntiles = (V - vlo + kTile - 1) / kTile;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
@@ -203,7 +248,7 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(ConvArgs a) {
 
   const long long plane = (long long)a.nx * a.ny;
   for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const long long v0 = tile * kTile;
+    const long long v0 = vlo + tile * kTile;
     // this thread gathers tile row `tid` (one voxel) for every tap
     const long long vr = v0 + tid;
     const bool valid = vr < V;
@@ -270,40 +315,7 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(ConvArgs a) {
     float acc[16];
     tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), acc);
     const long long v = v0 + warp * 32 + lane;
-    if (v < V && !abort_flag) {
-      if (a.mode == MODE_HIDDEN) {
-        __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(fmaxf(acc[c] + a.bias[c], 0.0f));
-        uint4* d = reinterpret_cast<uint4*>(a.out + v * kCh);
-        d[0] = reinterpret_cast<const uint4*>(o)[0];
-        d[1] = reinterpret_cast<const uint4*>(o)[1];
-      } else if (a.mode == MODE_BWD) {
-        const uint4* mk = reinterpret_cast<const uint4*>(a.mask + v * kCh);
-        __align__(16) __nv_bfloat16 m[16];
-        reinterpret_cast<uint4*>(m)[0] = mk[0];
-        reinterpret_cast<uint4*>(m)[1] = mk[1];
-        __align__(16) __nv_bfloat16 o[16];
-#pragma unroll
-        for (int c = 0; c < 16; ++c)
-          o[c] = __float2bfloat16_rn(__bfloat162float(m[c]) > 0.0f ? acc[c] : 0.0f);
-        uint4* d = reinterpret_cast<uint4*>(a.out + v * kCh);
-        d[0] = reinterpret_cast<const uint4*>(o)[0];
-        d[1] = reinterpret_cast<const uint4*>(o)[1];
-      } else {
-        const float r0 = acc[0] + a.bias[0], r1 = acc[1] + a.bias[1], r2 = acc[2] + a.bias[2];
-        if (a.r) *reinterpret_cast<float4*>(a.r + v * 4) = make_float4(r0, r1, r2, 0.0f);
-        if (a.jout) {
-          const long long plane = (long long)a.nx * a.ny;
-          const long long z = v / plane, rem = v - z * plane;
-          const long long base = z * 3 * plane + rem;
-          const float rr[3] = {r0, r1, r2};
-#pragma unroll
-          for (int c = 0; c < 3; ++c)
-            a.jout[base + c * plane] = a.jres[base + c * plane] + a.scale * rr[c];
-        }
-      }
-    }
+    if (v < V && !abort_flag) epilogue(a, v, acc);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -314,6 +326,171 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(ConvArgs a) {
       if (!mbar_wait(&mbar[b], phase[b])) atomicExch(&abort_flag, 1);
       phase[b] ^= 1u;
     }
+  tc_fence_before();
+  __syncthreads();
+  if (abort_flag && tid == 0) atomicOr(a.err, 1);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+}
+
+// ---- row-staged convolution (rows of 128 voxels) ---------------------------------------------
+// For nx = 128 an output tile is one row (z, y), and the A operand of tap (dz, dy, dx) is the
+// input row (z + dz, y + dy) shifted by dx.  Each input row is staged once in shared memory as
+// two arrays of 16-byte voxel entries (channels 0-7 and 8-15) with one halo voxel at each end
+// (x = -1 and x = 128, periodic); a voxel's 16 bytes follow the previous voxel's, so in the
+// K-major layout without swizzle the core matrices along M are 128 B apart (SBO) and the
+// second K half is the second array (LBO): every tap's operand is then a descriptor into the
+// staged rows, with no per-tap gather.  A CTA marches along y over a strip of rows of one z,
+// keeping four staged rows per z-plane: rows y-1, y, y+1 feed the 27 MMAs of row y while row
+// y+2 is being loaded.  The accumulators alternate between two 16-column halves of tensor
+// memory so that the epilogue of row y-1 overlaps the MMAs of row y.  (Five staged rows and
+// three accumulator sets, which let the MMAs of two rows run ahead, measured slower: the
+// larger shared memory leaves two CTAs per SM instead of three.)
+constexpr int kRowVox = 128;                         // nx of the row path
+constexpr int kRowHalo = kRowVox + 2;                // staged voxels: x = -1 .. 128
+constexpr uint32_t kHalfStride = kRowHalo * 16 + 32; // a K half; the pad puts the second half
+                                                     // 16 banks away from the first
+constexpr uint32_t kRowBytes = 2 * kHalfStride;
+constexpr int kRing = 4;                             // staged rows per z-plane
+constexpr int kStrip = 32;                           // output rows per strip
+constexpr uint32_t kRowsSmem = (uint32_t)kTaps * kTapBytesB + 3u * kRing * kRowBytes + 256u;
+
+__device__ __forceinline__ uint64_t sdesc_row(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kHalfStride >> 4) << 16) |
+         ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
+}
+
+// stage input row (zz, yy) into `slot`, yy in [-1, ny] wrapped periodically (asynchronous
+// 16-byte copies, coalesced reads)
+__device__ __forceinline__ void stage_row(const ConvArgs& a, uint32_t slot, int zz, int yy) {
+  const int yr = yy < 0 ? yy + a.ny : (yy >= a.ny ? yy - a.ny : yy);
+  const __nv_bfloat16* row = a.x + ((long long)zz * a.ny + yr) * (long long)kRowVox * kCh;
+  for (int i = threadIdx.x; i < 2 * kRowHalo; i += kThreads) {
+    const int xi = i >> 1, h = i & 1;               // staged voxel x = xi - 1, channel half h
+    const int xs = (xi + kRowVox - 1) & (kRowVox - 1);
+    cp_async16(slot + (uint32_t)h * kHalfStride + (uint32_t)xi * 16u, row + xs * kCh + h * 8, 16u);
+  }
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+__global__ void __launch_bounds__(kThreads) conv_rows_kernel(ConvArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* sB = smem;                                   // 27 x 512
+  unsigned char* sR = smem + kTaps * kTapBytesB;              // [3 planes][kRing][kRowBytes]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int abort_flag;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+                     smem_u32(&tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    abort_flag = 0;
+  }
+  {
+    const uint4* src = reinterpret_cast<const uint4*>(a.w);
+    uint4* dst = reinterpret_cast<uint4*>(sB);
+    for (int i = tid; i < (int)(kTaps * kTapBytesB / 16); i += kThreads) dst[i] = src[i];
+  }
+  float bias[16];
+#pragma unroll
+  for (int c = 0; c < 16; ++c) bias[c] = a.bias ? a.bias[c] : 0.0f;
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t rBase = smem_u32(sR);
+  const uint64_t bdesc = sdesc(smem_u32(sB));
+  uint32_t parity = 0;                 // phase of the mbarrier's next completion
+  int pending = 0;                     // a commit not yet waited for
+  auto slot = [&](int plane, int r) -> uint32_t {   // r >= -4
+    return rBase + (uint32_t)(plane * kRing + ((r + 4) & (kRing - 1))) * kRowBytes;
+  };
+  auto wait_mma = [&]() {
+    if (pending) {
+      if (!mbar_wait(&mbar, parity)) atomicExch(&abort_flag, 1);
+      parity ^= 1u;
+      pending = 0;
+    }
+    tc_fence_after();
+  };
+  auto finish_row = [&](int z, int y, int half) {    // epilogue of row (z, y)
+    float acc[16];
+    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * 16), acc);
+    if (a.mode != MODE_BWD)
+#pragma unroll
+      for (int c = 0; c < 16; ++c) acc[c] += bias[c];
+    const long long v = ((long long)z * a.ny + y) * kRowVox + warp * 32 + lane;
+    if (!abort_flag) epilogue(a, v, acc, false);
+  };
+
+  const int nyb = (a.ny + kStrip - 1) / kStrip;
+  const long long nstrips = (long long)(a.zhi - a.zlo) * nyb;
+  for (long long strip = blockIdx.x; strip < nstrips; strip += gridDim.x) {
+    const int z = a.zlo + (int)(strip / nyb);
+    const int y0 = (int)(strip % nyb) * kStrip, y1 = min(a.ny, y0 + kStrip);
+    // rows y0-1 .. y0+1 of the planes inside the window
+    for (int dz = -1; dz <= 1; ++dz) {
+      if (z + dz < 0 || z + dz >= a.nz) continue;
+      for (int r = y0 - 1; r <= y0 + 1; ++r) stage_row(a, slot(dz + 1, r), z + dz, r);
+    }
+    cp_async_commit();
+    for (int y = y0; y < y1; ++y) {
+      // the MMAs of row y-1 have read slot (y+2) & 3 for the last time and filled their
+      // accumulator half
+      wait_mma();
+      if (y + 2 <= y1)
+        for (int dz = -1; dz <= 1; ++dz)
+          if (z + dz >= 0 && z + dz < a.nz) stage_row(a, slot(dz + 1, y + 2), z + dz, y + 2);
+      cp_async_commit();
+      cp_async_wait_1();                 // rows through y+1 are in
+      fence_async_smem();
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0 && !abort_flag) {
+        // descriptors: one per staged row, + dx for the shift (16 bytes = 1 in the address
+        // field), + 32 per tap for B (512 bytes)
+        const uint32_t dcol = tmem + (uint32_t)((y & 1) * 16);
+        uint32_t accf = 0u;
+#pragma unroll
+        for (int pz = 0; pz < 3; ++pz) {
+          if (z + pz - 1 < 0 || z + pz - 1 >= a.nz) continue;   // zero padding along zeta
+#pragma unroll
+          for (int py = 0; py < 3; ++py) {
+            const uint64_t ad = sdesc_row(slot(pz, y + py - 1));
+#pragma unroll
+            for (int px = 0; px < 3; ++px) {
+              umma(dcol, ad + (uint64_t)px,
+                   bdesc + (uint64_t)((pz * 9 + py * 3 + px) * (kTapBytesB >> 4)), accf);
+              accf = 1u;
+            }
+          }
+        }
+        umma_commit(&mbar);
+      }
+      if (y > y0) finish_row(z, y - 1, (y - 1) & 1);
+      pending = abort_flag ? 0 : 1;
+      tc_fence_before();
+    }
+    wait_mma();
+    finish_row(z, y1 - 1, (y1 - 1) & 1);
+    // every thread is done with the staged rows and the accumulators before the next strip
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  wait_mma();
   tc_fence_before();
   __syncthreads();
   if (abort_flag && tid == 0) atomicOr(a.err, 1);
@@ -504,7 +681,17 @@ cudaError_t repack(gempic_denoiser* d, cudaStream_t s) {
 
 cudaError_t conv(gempic_denoiser* d, ConvArgs a, cudaStream_t s) {
   a.err = d->err;
-  const long long V = (long long)a.nx * a.ny * a.nz;
+  if (a.zhi <= a.zlo) {                  // whole window unless a range was given
+    a.zlo = 0;
+    a.zhi = a.nz;
+  }
+  if (a.nx == kRowVox) {
+    const long long strips = (long long)(a.zhi - a.zlo) * ((a.ny + kStrip - 1) / kStrip);
+    const int grid = (int)std::min<long long>(strips, 3LL * d->nsm);
+    conv_rows_kernel<<<grid, kThreads, kRowsSmem, s>>>(a);
+    return cudaGetLastError();
+  }
+  const long long V = (long long)a.nx * a.ny * (a.zhi - a.zlo);
   const long long tiles = (V + kTile - 1) / kTile;
   const int grid = (int)std::min<long long>(tiles, 2LL * d->nsm);
   conv_kernel<<<grid, kThreads, conv_smem(), s>>>(a);
@@ -574,6 +761,9 @@ gempic_status gempic_denoiser_create(const float* params, double scale, gempic_d
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)conv_smem());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(conv_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kRowsSmem);
   const size_t n = nparams();
   float** bufs[4] = {&d->p, &d->g, &d->m, &d->v};
   for (float** b : bufs)

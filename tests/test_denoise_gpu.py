@@ -44,7 +44,10 @@ def _from_gpu(t):
     return t.cpu().numpy().astype(np.float64).transpose(0, 2, 3, 1)
 
 
-@pytest.mark.parametrize("shape", [(12, 16, 16), (20, 1, 32), (7, 8, 24)])
+# rows of 128 voxels take the row-staged kernel (strips of 32 rows: ny = 40 crosses a strip
+# boundary, ny = 1 is the 2-D grid); other widths the gathering one
+@pytest.mark.parametrize("shape", [(12, 16, 16), (20, 1, 32), (7, 8, 24), (6, 8, 128),
+                                   (5, 40, 128), (9, 1, 128)])
 def test_denoiser_forward_matches_oracle(G, shape):
     nz, ny, nx = shape
     rng = np.random.default_rng(sum(shape))
@@ -62,8 +65,9 @@ def test_denoiser_forward_matches_oracle(G, shape):
     assert err < 1e-2, err
 
 
-def test_denoiser_gradient_matches_oracle(G):
-    nz, ny, nx = 10, 16, 16
+@pytest.mark.parametrize("shape", [(10, 16, 16), (8, 12, 128)])
+def test_denoiser_gradient_matches_oracle(G, shape):
+    nz, ny, nx = shape
     rng = np.random.default_rng(3)
     scale = 0.05
     j = np.asarray(rng.standard_normal((nz, ny, nx, 3)) * scale, np.float32).astype(np.float64)

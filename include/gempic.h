@@ -454,11 +454,15 @@ void gempic_denoiser_destroy(gempic_denoiser* d);
  * recomputes the new level from the old one with the denoised current (the denoiser acts on j
  * before the field update) and pushes the stored set with those fields.  The pushes of the
  * s-step saw the first pass's fields: the net needs the current of half-slices on both sides
- * of each one, which the march produces only one at a time.  Such steps march one s-step at
- * a time (no wavefront) and wait for their stream.  The diagnostics combine both passes: the
- * field energy, on-axis E_z and stored set are the second pass's, the streaming particles'
- * energy, flux and counts the first's.  d = NULL returns to plain steps.  The denoiser is
- * borrowed: it must outlive its use.  GEMPIC_EINVAL for an FP64 simulation. */
+ * of each one, which the march produces only one at a time.  The n s-steps of a call run as
+ * one chain of 2n marches in one launch (up to 7 in flight, each following the one before it
+ * slice by slice): the calling thread runs the net on groups of half-slices as soon as the
+ * first pass has written them and the three half-slices beyond, on a stream of its own, and
+ * releases each group to the second pass, which waits for it (bounded).  The call waits for
+ * its stream.  The diagnostics combine both passes: the field energy, on-axis E_z and stored
+ * set are the second pass's, the streaming particles' energy, flux and counts the first's.
+ * d = NULL returns to plain steps.  The denoiser is borrowed: it must outlive its use.
+ * GEMPIC_EINVAL for an FP64 simulation. */
 gempic_status gempic_set_denoiser(struct gempic_sim* sim, gempic_denoiser* d);
 
 /* The plain current of the last s-step (needs GEMPIC_FLAG_CURRENT or a denoiser): [nzeta][3]

@@ -61,6 +61,14 @@ struct gempic_sim {
   unsigned long long* io_dev = nullptr;
   cudaStream_t io_out = nullptr, io_in = nullptr;
   std::vector<cudaEvent_t> io_events;
+  // denoised chain: rings of four plain and denoised currents, host-mapped words [done: 8]
+  // [ready: 8], the stream the net runs on
+  void* dn_jcap[4] = {};
+  void* dn_jden[4] = {};
+  unsigned long long* dn_host = nullptr;
+  unsigned long long* dn_dev = nullptr;
+  cudaStream_t dn_stream = nullptr;
+  void* jcap_last = nullptr;       // the plain current of the last s-step
 };
 
 namespace {
@@ -622,50 +630,178 @@ gempic_status gempic_add_particles(gempic_sim* s, int64_t n, const double* x, co
   return GEMPIC_OK;
 }
 
-// One denoised s-step: the first pass marches the particles with the plain deposit and keeps
-// its current, the denoiser maps that current, the second pass recomputes the level from the
-// old one with the denoised current and pushes the stored set with the final fields.
-static gempic_status denoised_step(gempic_sim* s) {
-  cudaError_t e = ensure_diag_cap(s, 2);
+namespace {
+
+cudaError_t io_event(gempic_sim* s, cudaEvent_t* ev) {
+  if (!s->io_events.empty()) {
+    *ev = s->io_events.back();
+    s->io_events.pop_back();
+    return cudaSuccess;
+  }
+  return cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+}
+
+struct IoPending {
+  int step;          // s-step within the call whose input (H2D) or output (D2H) this is
+  int group;
+  cudaEvent_t ev;
+};
+
+}  // namespace
+
+// Denoised s-steps as one chain of marches in one launch: march 2i is the first pass of s-step
+// i (particles, plain deposit, its current kept), march 2i+1 the second (the level from the
+// denoised current, the stored set); each march follows the one before it slice by slice as
+// the wavefront does.  This thread runs the net on groups of half-slices as soon as the first
+// pass has written them and the three half-slices the net reaches beyond them, and releases
+// each group to the second pass, which waits for it (bounded) before it reads it.
+static gempic_status denoised_chain(gempic_sim* s, int n) {
+  const int nz = s->p.nz;
+  const size_t nb = (size_t)3 * nz * s->p.ny * s->p.nx * s->eb;
+  cudaError_t e = ensure_diag_cap(s, 2 * n);
+  for (int r = 0; r < 4 && e == cudaSuccess; ++r) {
+    if (!s->dn_jcap[r]) e = dalloc(s, &s->dn_jcap[r], nb);
+    if (e == cudaSuccess && !s->dn_jden[r]) e = dalloc(s, &s->dn_jden[r], nb);
+  }
+  if (e == cudaSuccess && !s->dn_host) {
+    void* h = nullptr;
+    e = cudaHostAlloc(&h, 16 * sizeof(unsigned long long), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+      s->dn_host = (unsigned long long*)h;
+      void* d = nullptr;
+      e = cudaHostGetDevicePointer(&d, h, 0);
+      s->dn_dev = (unsigned long long*)d;
+    }
+  }
+  if (e == cudaSuccess && !s->dn_stream) e = cudaStreamCreateWithFlags(&s->dn_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(s, e);
+  // groups of about a sixteenth of the window; a group needs the first pass three half-slices
+  // beyond it (the net's reach along zeta)
+  const int chunk = std::max(4, (nz + 15) / 16);
+  const int nch = (nz + chunk - 1) / chunk;
+  const int lead = 3 % chunk;
+  // at most 7 marches in flight: the first pass of s-step i+4 reuses the current buffers of
+  // s-step i only after it starts, i.e. after march 2i+8-P, the second pass of s-step i or later,
+  // has finished with them
+  const int P = std::min(std::min(s->pmax, 2 * n), 7);
+  const long long k0 = s->k;
+  unsigned long long* done = s->dn_host;
+  unsigned long long* ready = s->dn_host + 8;
+  std::memset(s->dn_host, 0, 16 * sizeof(unsigned long long));
+  // progress words carry march indices here: start from zero
+  e = cudaMemsetAsync(s->p.progress, 0, (size_t)s->pmax * sizeof(unsigned long long), s->stream);
   Params q = s->p;
-  q.k0 = s->k;
-  q.nsteps = 1;
-  q.P = 1;
+  q.k0 = k0;
+  q.nsteps = 2 * n;
+  q.P = P;
   q.inject = q.nspecies > 0 ? 1 : 0;
   q.delta_field = s->p.delta;
-  q.skip_stored = 1;
-  q.jcap = s->jcap;
-  q.state_out = s->state2;
-  e = gempic::launch_march(s->cfg.precision, q, s->stream);
-  s->launches++;
-  if (e != cudaSuccess) return cuda_fail(s, e);
-  const gempic_status st = gempic_denoiser_apply(s->dn, (const float*)s->jcap, (float*)s->jden,
-                                                 s->p.nx, s->p.ny, s->p.nz, (void*)s->stream);
-  s->launches += 5;
-  if (st != GEMPIC_OK) {
-    s->failed = st;
-    return st;
+  q.jcap = nullptr;
+  q.jext = nullptr;
+  q.state_out = nullptr;
+  q.dn_pipe = 1;
+  for (int r = 0; r < 4; ++r) {
+    q.dn_jcap[r] = s->dn_jcap[r];
+    q.dn_jext[r] = s->dn_jden[r];
   }
-  Params r = q;
-  r.inject = 0;
-  r.skip_stored = 0;
-  r.fields_only = 1;
-  r.jcap = nullptr;
-  r.jext = s->jden;
-  r.state_out = nullptr;
-  r.diag_out = s->p.diag_out + (size_t)gempic::kNDiag * s->p.C;
-  r.onaxis = s->p.onaxis + s->p.nz;
-  r.resid_out = s->p.resid_out + 1;
-  r.gauss_out = s->p.gauss_out + 1;
-  e = gempic::launch_march(s->cfg.precision, r, s->stream);
+  q.dn_scratch = s->state2;
+  q.dn_done = s->dn_dev;
+  q.dn_ready = s->dn_dev + 8;
+  q.dn_chunk = chunk;
+  q.dn_nchunk = nch;
+  q.dn_lead = lead;
+  // the net's stream starts after everything before this launch
+  cudaEvent_t start = nullptr;
+  if (e == cudaSuccess) e = io_event(s, &start);
+  if (e == cudaSuccess) e = cudaEventRecord(start, s->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s->dn_stream, start, 0);
+  if (start) s->io_events.push_back(start);
+  if (e == cudaSuccess) e = gempic::launch_march(s->cfg.precision, q, s->stream);
   s->launches++;
   if (e != cudaSuccess) return cuda_fail(s, e);
-  s->last_launch_k0 = s->k;
-  s->last_launch_n = 1;
+  std::vector<int> next(n, 0);
+  std::deque<IoPending> netq;
+  int released = 0;
+  int st = GEMPIC_OK;
+  auto last_move = std::chrono::steady_clock::now();
+  while (released < n * nch && st == GEMPIC_OK && e == cudaSuccess) {
+    bool moved = false;
+    for (int i = 0; i < n && e == cudaSuccess && st == GEMPIC_OK; ++i) {
+      if (next[i] >= nch) continue;
+      const long long m1 = 2 * (k0 + i);                 // the first pass's march index
+      const unsigned long long v = __atomic_load_n(done + (int)((2 * i) % P), __ATOMIC_ACQUIRE);
+      while (next[i] < nch) {
+        const int g = next[i];
+        const int z1 = nz - g * chunk, z0 = std::max(0, z1 - chunk);
+        if (v < gempic::prog_value(m1, nz, std::min(nz, nz - z0 + 3))) break;
+        const int kr = (int)((k0 + i) & 3);
+        st = gempic::denoise_range(s->dn, (const float*)s->dn_jcap[kr], (float*)s->dn_jden[kr],
+                                   s->p.nx, s->p.ny, nz, z0, z1, s->dn_stream);
+        s->launches += 4;
+        if (st != GEMPIC_OK) break;
+        IoPending pd{i, g, nullptr};
+        e = io_event(s, &pd.ev);
+        if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->dn_stream);
+        if (e != cudaSuccess) break;
+        netq.push_back(pd);
+        ++next[i];
+        moved = true;
+      }
+    }
+    while (e == cudaSuccess && !netq.empty()) {
+      const cudaError_t qe = cudaEventQuery(netq.front().ev);
+      if (qe == cudaErrorNotReady) break;
+      if (qe != cudaSuccess) {
+        e = qe;
+        break;
+      }
+      const IoPending pd = netq.front();
+      netq.pop_front();
+      const long long m2 = 2 * (k0 + pd.step) + 1;      // the second pass's march index
+      __atomic_store_n(ready + (int)((k0 + pd.step) & 3), gempic::io_value(m2, nch, pd.group),
+                       __ATOMIC_RELEASE);
+      s->io_events.push_back(pd.ev);
+      ++released;
+      moved = true;
+    }
+    if (e != cudaSuccess || st != GEMPIC_OK) break;
+    const auto now = std::chrono::steady_clock::now();
+    if (moved) {
+      last_move = now;
+      continue;
+    }
+    const cudaError_t me = cudaStreamQuery(s->stream);
+    if (me != cudaSuccess && me != cudaErrorNotReady) {
+      e = me;
+      break;
+    }
+    if (now - last_move > std::chrono::seconds(120)) {
+      st = GEMPIC_ETIMEOUT;
+      break;
+    }
+    std::this_thread::yield();
+  }
+  const cudaError_t e2 = cudaStreamSynchronize(s->stream);
+  const cudaError_t e3 = cudaStreamSynchronize(s->dn_stream);
+  for (const IoPending& pd : netq) s->io_events.push_back(pd.ev);
+  if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
+  // leave the progress words as a plain launch expects them (below any s-step's value)
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(s->p.progress, 0, (size_t)s->pmax * sizeof(unsigned long long), s->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  s->last_launch_k0 = k0;
+  s->last_launch_n = 2 * n;
   s->denoised_last = true;
-  s->k += 1;
-  return GEMPIC_OK;
+  s->jcap_last = s->dn_jcap[(k0 + n - 1) & 3];
+  s->k += n;
+  if (st != GEMPIC_OK) {
+    s->failed = (gempic_status)st;
+    return (gempic_status)st;
+  }
+  st = gempic::denoise_status(s->dn, s->stream);
+  if (st != GEMPIC_OK) s->failed = (gempic_status)st;
+  return (gempic_status)st;
 }
 
 gempic_status gempic_step_async(gempic_sim* s, int32_t n) {
@@ -673,13 +809,7 @@ gempic_status gempic_step_async(gempic_sim* s, int32_t n) {
   gempic_status st = ensure_initialized(s);
   if (st != GEMPIC_OK) return st;
   if (n == 0) return GEMPIC_OK;
-  if (s->dn) {
-    for (int i = 0; i < n; ++i) {
-      st = denoised_step(s);
-      if (st != GEMPIC_OK) return st;
-    }
-    return GEMPIC_OK;
-  }
+  if (s->dn) return denoised_chain(s, n);
   s->denoised_last = false;
   cudaError_t e = ensure_diag_cap(s, n);
   if (e != cudaSuccess) return cuda_fail(s, e);
@@ -845,10 +975,12 @@ cudaError_t ensure_stream_io(gempic_sim* s) {
   if (!s->io_a) e = dalloc(s, &s->io_a, nb);
   if (e == cudaSuccess && !s->io_b) e = dalloc(s, &s->io_b, nb);
   if (e == cudaSuccess && !s->io_host) {
+    // [ready: pmax + 1][done: pmax]
+    const size_t words = 2 * (size_t)s->pmax + 1;
     void* h = nullptr;
-    e = cudaHostAlloc(&h, 2 * (size_t)s->pmax * sizeof(unsigned long long), cudaHostAllocMapped);
+    e = cudaHostAlloc(&h, words * sizeof(unsigned long long), cudaHostAllocMapped);
     if (e != cudaSuccess) return e;
-    std::memset(h, 0, 2 * (size_t)s->pmax * sizeof(unsigned long long));
+    std::memset(h, 0, words * sizeof(unsigned long long));
     s->io_host = (unsigned long long*)h;
     void* d = nullptr;
     e = cudaHostGetDevicePointer(&d, h, 0);
@@ -858,15 +990,6 @@ cudaError_t ensure_stream_io(gempic_sim* s) {
   if (e == cudaSuccess && !s->io_in) e = cudaStreamCreateWithFlags(&s->io_in, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = gempic::configure_march_canon(s->cfg.precision, s->p.smem_bytes);
   return e;
-}
-
-cudaError_t io_event(gempic_sim* s, cudaEvent_t* ev) {
-  if (!s->io_events.empty()) {
-    *ev = s->io_events.back();
-    s->io_events.pop_back();
-    return cudaSuccess;
-  }
-  return cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
 }
 
 // Copy group j of the public layout [6][nz][ny][nx/2] between the host buffer and a device
@@ -897,12 +1020,6 @@ cudaError_t io_copy(gempic_sim* s, int j, int chunk, void* dev, void* host, bool
   return e;
 }
 
-struct IoPending {
-  int step;          // s-step within the call whose input (H2D) or output (D2H) this is
-  int group;
-  cudaEvent_t ev;
-};
-
 }  // namespace
 
 gempic_status gempic_step_streamed(gempic_sim* s, int32_t n, void* host, size_t bytes,
@@ -932,11 +1049,12 @@ gempic_status gempic_step_streamed(gempic_sim* s, int32_t n, void* host, size_t 
   q.state = s->io_a;
   q.state_out = s->io_b;
   q.io_ready = s->io_dev;
-  q.io_done = s->io_dev + s->pmax;
+  q.io_done = s->io_dev + s->pmax + 1;
   q.io_chunk = chunk;
   q.io_nchunk = nch;
+  q.io_ring = s->pmax + 1;
   unsigned long long* ready = s->io_host;
-  const unsigned long long* done = s->io_host + s->pmax;
+  const unsigned long long* done = s->io_host + s->pmax + 1;
   const long long k0 = s->k;
   auto slot = [&](int i) { return i % q.P; };
   // the first s-step's input goes in before the launch's marches reach it
@@ -1013,8 +1131,8 @@ gempic_status gempic_step_streamed(gempic_sim* s, int32_t n, void* host, size_t 
       }
       const IoPending pd = inq.front();
       inq.pop_front();
-      __atomic_store_n(ready + slot(pd.step), gempic::io_value(k0 + pd.step, nch, pd.group),
-                       __ATOMIC_RELEASE);
+      __atomic_store_n(ready + (k0 + pd.step) % q.io_ring,
+                       gempic::io_value(k0 + pd.step, nch, pd.group), __ATOMIC_RELEASE);
       s->io_events.push_back(pd.ev);
       moved = true;
     }
@@ -1147,12 +1265,13 @@ gempic_status gempic_get_diagnostics(gempic_sim* s, gempic_diag* out) {
   if (st != GEMPIC_OK) return st;
   const int sl = s->last_launch_n - 1;
   double v[gempic::kNDiag];
-  cudaError_t e = diag_sums(s, sl, v);
+  // a denoised s-step: march sl - 1 is its first pass, sl its second
+  cudaError_t e = diag_sums(s, s->denoised_last ? sl - 1 : sl, v);
   if (e != cudaSuccess) return cuda_fail(s, e);
   if (s->denoised_last) {
     // the second pass holds the fields and the stored set; the first the streaming particles
     double v2[gempic::kNDiag];
-    e = diag_sums(s, 1, v2);
+    e = diag_sums(s, sl, v2);
     if (e != cudaSuccess) return cuda_fail(s, e);
     v[gempic::DG_FIELD] = v2[gempic::DG_FIELD];
     v[gempic::DG_KIN] += v2[gempic::DG_KIN];
@@ -1167,7 +1286,7 @@ gempic_status gempic_get_onaxis_ez(gempic_sim* s, double* dst, int32_t n) {
   if (!s || !dst || n < s->p.nz) return GEMPIC_EINVAL;
   gempic_status st = ensure_initialized(s);
   if (st != GEMPIC_OK) return st;
-  const int sl = s->denoised_last ? 1 : s->last_launch_n - 1;
+  const int sl = s->last_launch_n - 1;                 // a denoised s-step's second pass
   cudaError_t e = cudaMemcpyAsync(dst, s->p.onaxis + (size_t)sl * s->p.nz, s->p.nz * sizeof(double),
                                   cudaMemcpyDeviceToHost, s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -1184,12 +1303,8 @@ gempic_status gempic_set_denoiser(gempic_sim* s, gempic_denoiser* d) {
     const size_t nb = (size_t)3 * s->p.nz * s->p.ny * s->p.nx * s->eb;
     const size_t sb = (size_t)(s->p.nz + 1) * 6 * (s->p.nx / 2) * s->p.ny * 2 * s->eb;
     cudaError_t e = cudaSuccess;
-    if (!s->jcap) {
-      e = dalloc(s, &s->jcap, nb);
-      s->p.jcap = s->jcap;
-    }
-    if (e == cudaSuccess && !s->jden) e = dalloc(s, &s->jden, nb);
-    if (e == cudaSuccess && !s->state2) e = dalloc(s, &s->state2, sb);
+    (void)nb;
+    if (!s->state2) e = dalloc(s, &s->state2, sb);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) {
       cudaGetLastError();
@@ -1202,11 +1317,12 @@ gempic_status gempic_set_denoiser(gempic_sim* s, gempic_denoiser* d) {
 
 gempic_status gempic_get_current(gempic_sim* s, void* dst, size_t bytes, int32_t dst_is_device) {
   if (!s || !dst) return GEMPIC_EINVAL;
-  if (!s->jcap || s->k == 0) return GEMPIC_ESTATE;
+  const void* src = s->denoised_last ? s->jcap_last : s->jcap;
+  if (!src || s->k == 0) return GEMPIC_ESTATE;
   if (s->failed != GEMPIC_OK) return GEMPIC_ESTATE;
   const size_t nb = (size_t)3 * s->p.nz * s->p.ny * s->p.nx * s->eb;
   if (bytes < nb) return GEMPIC_EINVAL;
-  cudaError_t e = cudaMemcpyAsync(dst, s->jcap, nb,
+  cudaError_t e = cudaMemcpyAsync(dst, src, nb,
                                   dst_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                   s->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -1251,6 +1367,11 @@ void gempic_destroy(gempic_sim* s) {
   if (s->io_out) cudaStreamDestroy(s->io_out);
   if (s->io_in) cudaStreamDestroy(s->io_in);
   if (s->io_host) cudaFreeHost(s->io_host);
+  if (s->dn_stream) {
+    cudaStreamSynchronize(s->dn_stream);
+    cudaStreamDestroy(s->dn_stream);
+  }
+  if (s->dn_host) cudaFreeHost(s->dn_host);
   for (void* v : s->allocs) cudaFree(v);
   cudaGetLastError();
   delete s;

@@ -187,7 +187,7 @@ __device__ __forceinline__ void epilogue(const ConvArgs& a, long long v, const f
       const float rr[3] = {r0, r1, r2};
 #pragma unroll
       for (int c = 0; c < 3; ++c)
-        a.jout[base + c * plane] = a.jres[base + c * plane] + a.scale * rr[c];
+        a.jout[base + c * plane] = __ldcg(a.jres + base + c * plane) + a.scale * rr[c];
     }
   }
 }
@@ -500,18 +500,20 @@ __global__ void __launch_bounds__(kThreads) conv_rows_kernel(ConvArgs a) {
 
 // ---- element-wise kernels ------------------------------------------------------------------
 
-// x0 = bf16(j / scale) channel-last, channels 3..15 zero
-__global__ void pack_input_kernel(const float* j, __nv_bfloat16* x0, int nx, int ny, int nz,
-                                  float inv_scale) {
-  const long long plane = (long long)nx * ny, V = plane * nz;
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V;
+// x0 = bf16(j / scale) channel-last, channels 3..15 zero, on the half-slices [zlo, zhi)
+// (j is read through L2: it may have been written by a kernel still running)
+__global__ void pack_input_kernel(const float* j, __nv_bfloat16* x0, int nx, int ny, int zlo,
+                                  int zhi, float inv_scale) {
+  const long long plane = (long long)nx * ny, v0 = plane * zlo, V = plane * zhi;
+  for (long long v = v0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V;
        v += (long long)gridDim.x * blockDim.x) {
     const long long z = v / plane, rem = v - z * plane;
     __align__(16) __nv_bfloat16 o[16];
 #pragma unroll
     for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) o[c] = __float2bfloat16_rn(j[(z * 3 + c) * plane + rem] * inv_scale);
+    for (int c = 0; c < 3; ++c)
+      o[c] = __float2bfloat16_rn(__ldcg(j + (z * 3 + c) * plane + rem) * inv_scale);
     uint4* d = reinterpret_cast<uint4*>(x0 + v * kCh);
     d[0] = reinterpret_cast<const uint4*>(o)[0];
     d[1] = reinterpret_cast<const uint4*>(o)[1];
@@ -701,13 +703,16 @@ cudaError_t conv(gempic_denoiser* d, ConvArgs a, cudaStream_t s) {
 bool grid_ok(int nx, int ny, int nz) { return nx >= 1 && ny >= 1 && nz >= 1; }
 
 // forward pass of the three layers on x0 = act[0]; h1 -> act[1], h2 -> act[2]; last layer's
-// epilogue as requested
-cudaError_t forward(gempic_denoiser* d, int nx, int ny, int nz, const float* jres, float* jout,
-                    float* r, cudaStream_t s) {
+// epilogue as requested, for the output half-slices [z0, z1): each layer is computed where the
+// next one reads it (one more half-slice on each side per layer below the last)
+cudaError_t forward(gempic_denoiser* d, int nx, int ny, int nz, int z0, int z1, const float* jres,
+                    float* jout, float* r, cudaStream_t s) {
   ConvArgs a{};
   a.nx = nx;
   a.ny = ny;
   a.nz = nz;
+  a.zlo = std::max(0, z0 - 2);
+  a.zhi = std::min(nz, z1 + 2);
   a.mode = MODE_HIDDEN;
   a.x = d->act[0];
   a.w = d->wf[0];
@@ -719,12 +724,16 @@ cudaError_t forward(gempic_denoiser* d, int nx, int ny, int nz, const float* jre
   a.w = d->wf[1];
   a.bias = d->p + boff(1);
   a.out = d->act[2];
+  a.zlo = std::max(0, z0 - 1);
+  a.zhi = std::min(nz, z1 + 1);
   e = conv(d, a, s);
   if (e != cudaSuccess) return e;
   ConvArgs l{};
   l.nx = nx;
   l.ny = ny;
   l.nz = nz;
+  l.zlo = z0;
+  l.zhi = z1;
   l.mode = MODE_LAST;
   l.x = d->act[2];
   l.w = d->wf[2];
@@ -745,6 +754,31 @@ gempic_status check_err(gempic_denoiser* d, cudaStream_t s) {
 }
 
 }  // namespace
+
+namespace gempic {
+
+// The net on the output half-slices [z0, z1) of j_in (read where needed: z0 - 3 .. z1 + 2),
+// into the same half-slices of j_out, on stream s (no wait).  For the denoised chain of
+// marches: j_in may still be written elsewhere outside the half-slices the net reads.
+int denoise_range(gempic_denoiser* d, const float* j_in, float* j_out, int nx, int ny, int nz,
+                  int z0, int z1, cudaStream_t s) {
+  if (!d || !j_in || !j_out || !grid_ok(nx, ny, nz) || z0 < 0 || z1 > nz || z0 >= z1)
+    return GEMPIC_EINVAL;
+  cudaError_t e = grow(d, (long long)nx * ny * nz);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GEMPIC_ENOMEM : GEMPIC_ECUDA;
+  const int p0 = std::max(0, z0 - 3), p1 = std::min(nz, z1 + 3);
+  const long long V = (long long)nx * ny * (p1 - p0);
+  const int blocks = (int)std::min<long long>((V + 255) / 256, 8LL * d->nsm);
+  pack_input_kernel<<<blocks, 256, 0, s>>>(j_in, d->act[0], nx, ny, p0, p1, (float)(1.0 / d->scale));
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = forward(d, nx, ny, nz, z0, z1, j_in, j_out, nullptr, s);
+  return e == cudaSuccess ? GEMPIC_OK : GEMPIC_ECUDA;
+}
+
+// the denoiser's device status word (a bounded wait that gave up): GEMPIC_ETIMEOUT
+int denoise_status(gempic_denoiser* d, cudaStream_t s) { return check_err(d, s); }
+
+}  // namespace gempic
 
 extern "C" {
 
@@ -820,9 +854,9 @@ gempic_status gempic_denoiser_apply(gempic_denoiser* d, const float* j_in, float
   cudaError_t e = grow(d, V);
   if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? GEMPIC_ENOMEM : GEMPIC_ECUDA;
   const int blocks = (int)std::min<long long>((V + 255) / 256, 8LL * d->nsm);
-  pack_input_kernel<<<blocks, 256, 0, s>>>(j_in, d->act[0], nx, ny, nz, (float)(1.0 / d->scale));
+  pack_input_kernel<<<blocks, 256, 0, s>>>(j_in, d->act[0], nx, ny, 0, nz, (float)(1.0 / d->scale));
   e = cudaGetLastError();
-  if (e == cudaSuccess) e = forward(d, nx, ny, nz, j_in, j_out, nullptr, s);
+  if (e == cudaSuccess) e = forward(d, nx, ny, nz, 0, nz, j_in, j_out, nullptr, s);
   if (e != cudaSuccess) return GEMPIC_ECUDA;
   return check_err(d, s);
 }
@@ -841,8 +875,8 @@ gempic_status gempic_denoiser_grad(gempic_denoiser* d, const float* j_in, const 
   e = cudaMemsetAsync(d->g, 0, n * sizeof(float), s);
   if (e == cudaSuccess) e = cudaMemsetAsync(d->loss, 0, sizeof(double), s);
   if (e != cudaSuccess) return GEMPIC_ECUDA;
-  pack_input_kernel<<<blocks, 256, 0, s>>>(j_in, d->act[0], nx, ny, nz, (float)(1.0 / d->scale));
-  e = forward(d, nx, ny, nz, nullptr, nullptr, d->r, s);
+  pack_input_kernel<<<blocks, 256, 0, s>>>(j_in, d->act[0], nx, ny, 0, nz, (float)(1.0 / d->scale));
+  e = forward(d, nx, ny, nz, 0, nz, nullptr, nullptr, d->r, s);
   if (e != cudaSuccess) return GEMPIC_ECUDA;
   const double count = 3.0 * (double)nx * ny * (nz - 2 * z_margin);
   loss_kernel<<<blocks, 256, 0, s>>>(j_in, j_target, d->r, d->act[3], nx, ny, nz, z_margin,

@@ -102,12 +102,36 @@ struct Params {
   // state streamed through host memory (gempic_step_streamed): the old level is read from
   // `state`, the new one written to `state_out`, both in the public layout; the blocks go out
   // and back in groups of io_chunk (group j: blocks nz - j io_chunk down to
-  // nz + 1 - (j+1) io_chunk).  Words in host-mapped memory, one per march slot:
-  unsigned long long* io_ready;   // written by the host: io_value(k, io_nchunk, j) once group j
-                                  // of s-step k's input is in `state`
-  unsigned long long* io_done;    // written by the march: prog_value(k, nz, completed) each time
-                                  // `completed` reaches a multiple of io_chunk, and at the end
-  int io_chunk, io_nchunk;        // io_chunk = 0: not streamed
+  // nz + 1 - (j+1) io_chunk).  Words in host-mapped memory:
+  unsigned long long* io_ready;   // [io_ring], written by the host: word k % io_ring holds
+                                  // io_value(k, io_nchunk, j) once group j of s-step k's input
+                                  // is in `state`.  One word per s-step, io_ring > P: the word is
+                                  // reused for s-step k + io_ring only after march k has finished
+                                  // (a slot's marches run in turn), so no march sees another's
+                                  // release
+  unsigned long long* io_done;    // [P], written by the march of slot c: prog_value(k, nz,
+                                  // completed) each time `completed` reaches a multiple of
+                                  // io_chunk, and at the end
+  int io_chunk, io_nchunk, io_ring;   // io_chunk = 0: not streamed
+  // denoised s-steps as one chain of marches (dn_pipe = 1; nsteps then counts marches): march
+  // 2i is the first pass of s-step k0 + i (particles with the plain deposit, its current kept
+  // in dn_jcap[k & 3], its level written to dn_scratch and never read), march 2i + 1 the second
+  // (the level from the denoised current dn_jext[k & 3] on the unchanged old one, the stored
+  // set).  Progress words carry the march index 2k + pass.  The host runs the net on groups of
+  // dn_chunk half-slices (group g: nz - (g+1) dn_chunk .. nz - g dn_chunk - 1) as the first
+  // pass completes them with their reach, and releases each group to the second pass.
+  int dn_pipe;
+  void* dn_jcap[4];
+  const void* dn_jext[4];
+  void* dn_scratch;
+  unsigned long long* dn_done;    // host-mapped, per slot: first-pass progress (prog_value of
+                                  // its march index) whenever done % dn_chunk == dn_lead, and at
+                                  // the end
+  unsigned long long* dn_ready;   // host-mapped [4]: word k & 3 holds io_value(2k + 1, dn_nchunk,
+                                  // g) once group g of s-step k's denoised current is written
+                                  // (one word per s-step, like the current buffers: s-step k + 4
+                                  // releases only after s-step k's second pass has finished)
+  int dn_chunk, dn_nchunk, dn_lead;
 };
 
 // progress word of a march: s-step k has completed `completed` of its nz iterations (they run
@@ -150,5 +174,10 @@ cudaError_t max_active_clusters(int precision, const Params& p, int* n);
 cudaError_t configure_march_canon(int precision, int smem_bytes);
 cudaError_t launch_march_canon(int precision, const Params& p, cudaStream_t s);
 cudaError_t launch_tables(int precision, const Params& p, void* dst, cudaStream_t s);
+// the learned current denoiser on output half-slices [z0, z1) (gempic_denoise.cu); status codes
+// of gempic_status
+int denoise_range(struct gempic_denoiser* d, const float* j_in, float* j_out, int nx, int ny,
+                  int nz, int z0, int z1, cudaStream_t s);
+int denoise_status(struct gempic_denoiser* d, cudaStream_t s);
 
 }  // namespace gempic

@@ -2013,15 +2013,16 @@ __device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
   }
 }
 
-// streamed state: wait until the host has released the group of block b of s-step k's input.
+// wait until the host has released group g of march `key` in the host-mapped word `word`
+// (streamed state: the input's groups; denoised chain: the denoised current's groups).
 // *seen (shared memory, -1 at the start of a march) is the last group known released.
-__device__ void wait_input(const Params& p, int cid, long long k, int b, int* seen) {
-  const int g = io_group(p.nz, p.io_chunk, b);
+__device__ void wait_release(const Params& p, const unsigned long long* word, long long key,
+                             int nchunk, int g, int* seen) {
   if (*seen >= g) return;
-  const unsigned long long target = io_value(k, p.io_nchunk, g);
+  const unsigned long long target = io_value(key, nchunk, g);
   unsigned long long v;
   int spins = 0;
-  while ((v = ld_acquire_sys_u64(p.io_ready + cid)) < target) {
+  while ((v = ld_acquire_sys_u64(word)) < target) {
     if (atomicAdd(p.err, 0) & ERR_TIMEOUT) return;
     __nanosleep(200);
     if (++spins > p.wait_spin_limit) {
@@ -2029,9 +2030,14 @@ __device__ void wait_input(const Params& p, int cid, long long k, int b, int* se
       return;
     }
   }
-  // the host releases s-step k's groups in order and the next s-step's only after this march
-  // has read them all, so v names a group of this s-step
-  *seen = (int)min((unsigned long long)(p.io_nchunk - 1), v - io_value(k, p.io_nchunk, 0));
+  // the host releases a march's groups in order and the next march's of this slot only after
+  // this one has used them all, so v names a group of this march
+  *seen = (int)min((unsigned long long)(nchunk - 1), v - io_value(key, nchunk, 0));
+}
+
+// streamed state: the group of block b of s-step k's input
+__device__ __forceinline__ void wait_input(const Params& p, long long k, int b, int* seen) {
+  wait_release(p, p.io_ready + (k % p.io_ring), k, p.io_nchunk, io_group(p.nz, p.io_chunk, b), seen);
 }
 
 // FP64 diagnostics: each warp adds its lanes' sums to its own row (no atomics); the rows are
@@ -2045,7 +2051,7 @@ __device__ void wait_input(const Params& p, int cid, long long k, int b, int* se
 // allocation-free entry point on a caller's buffer.
 template <typename T, bool CANON = false, int SH = 0>
 __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& cl, long long k,
-                      int cid) {
+                      int cid, long long item) {
   // the 128 x 128 instantiation is compiled for GT2 and a uniform zeta-step only (other runs
   // take the generic one)
   constexpr int LAW = SH == 1 ? 0 : -1;
@@ -2057,14 +2063,18 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   const int me = (int)cl.block_rank();
   const int tid = threadIdx.x;
   const int NT = blockDim.x;
-  const bool waits = p.P > 1 && k > p.k0;
+  // march index: k, or 2k + pass in a denoised chain; the previous march of the launch is
+  // item - 1
+  const long long item0 = p.dn_pipe ? 2 * p.k0 : p.k0;
+  const bool dn1 = p.dn_pipe && !(item & 1), dn2 = p.dn_pipe && (item & 1);
+  const bool waits = p.P > 1 && item > item0;
   const int pcid = (cid + p.P - 1) % p.P;
   const int nz = p.nz;
   const int nxh = p.nx / 2;
   const int s1 = (int)(((k + 1) % p.ring + p.ring) % p.ring);
   const int s2 = (int)(((k + 2) % p.ring + p.ring) % p.ring);
   const T h = s.cst[K_H], Dl = s.cst[K_DF];
-  const long long sl = k - p.k0;                    // step index within this launch
+  const long long sl = item - item0;                // march index within this launch
   const Ovf<T> ov = ovf_view<T>(p, cid, me);        // overflow particle slots of this CTA
   const int fplane = p.FR * p.nx;                   // elements of one field component
   const int jplane = p.JR * p.nx;                   // elements of one current component
@@ -2092,7 +2102,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     if (tid == 0) s.dacc[0] = s.dacc[1] = 0.0;
   }
   __syncthreads();
-  if (p.inject) {
+  if (p.inject && !dn2) {
     const int per_row = p.nlayer >> p.logny;        // particles per transverse row
     const int nmine = per_row * p.RB;
     for (int i = tid; i < nmine; i += NT) {
@@ -2174,7 +2184,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   Cx<T> j0px = jpx, j0py = jpx;                   // old level j at n + 1/2
   const Cx<T>* st = (const Cx<T>*)p.state;
   // the new level is written over the old one, or (first pass of a denoised s-step) elsewhere
-  Cx<T>* stw = (Cx<T>*)(p.state_out ? p.state_out : p.state);
+  Cx<T>* stw = (Cx<T>*)(dn1 ? p.dn_scratch : p.state_out ? p.state_out : p.state);
   auto blk = [&](int b, int c) -> size_t {
     if constexpr (CANON) {
       const int kxg = (me << p.logKB) + kxl;
@@ -2194,12 +2204,10 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   };
 
   if (waits && tid == 0 && me == 0)
-    wait_for(p, pcid, prog_value(k - 1, nz, min(nz, 3)));   // predecessor done down to nz-3
+    wait_for(p, pcid, prog_value(item - 1, nz, min(nz, 3)));   // predecessor done down to nz-3
   // streamed state: the input's blocks nz and nz-1
-  if (p.io_chunk && tid == 0 && me == 0) {
-    s.misc[M_IOSEEN] = -1;
-    wait_input(p, cid, k, nz - 1, s.misc + M_IOSEEN);
-  }
+  if (tid == 0 && me == 0) s.misc[M_IOSEEN] = -1;
+  if (p.io_chunk && tid == 0 && me == 0) wait_input(p, k, nz - 1, s.misc + M_IOSEEN);
   cl.sync();
   if (has_mode) {
     j0px = ldcg(st + blk(nz, 4));
@@ -2207,8 +2215,11 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
 #pragma unroll
     for (int c = 0; c < 6; ++c) o[c] = ldcg(st + blk(nz - 1, c));
   }
-  const bool snap_step = p.snapshot && k == p.k0 + p.nsteps - 1;
-  const bool cap_step = p.jcap != nullptr && k == p.k0 + p.nsteps - 1;
+  const long long klast = p.dn_pipe ? p.k0 + p.nsteps / 2 - 1 : p.k0 + p.nsteps - 1;
+  const bool snap_step = p.snapshot && k == klast;
+  // the current kept: every first pass of a denoised chain, else the launch's last s-step
+  T* const jcap = (T*)(dn1 ? p.dn_jcap[k & 3] : p.dn_pipe ? nullptr : p.jcap);
+  const bool cap_step = jcap != nullptr && (dn1 || k == klast);
   // per-slice counters of other marches, read once per CTA and broadcast in shared memory
   if (tid == 0) {
     s.misc[M_RQN] = ldcg(p.rq.cnt + (size_t)s1 * nz + (nz - 1));
@@ -2292,7 +2303,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
       TIMER_MARK(PH_AR);
       // stored particles that rejoin the march at this slice (partial first step), taken by
       // the CTA that owns their row
-      const int nq = p.fields_only ? 0 : min(s.misc[M_RQN], p.bcap);
+      const int nq = (p.fields_only || dn2) ? 0 : min(s.misc[M_RQN], p.bcap);
       for (int e = tid; e < nq; e += NT) {
         const size_t ge = ((size_t)s1 * nz + n) * p.bcap + e;
         if ((((ldcg(p.rq.cell + ge) >> 10) & 1023) >> p.logRB) != me) continue;
@@ -2458,6 +2469,10 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     const long long t_arr = clock64() - t_slice;
     if (tid == 0 && p.timers) atomicAdd(p.timers + 64 + me, (unsigned long long)t_arr);
 #endif
+    // denoised chain: the second pass reads the denoised current of half-slice n after B1
+    if (dn2 && me == 0 && tid == 0)
+      wait_release(p, p.dn_ready + (k & 3), item, p.dn_nchunk, (nz - 1 - n) / p.dn_chunk,
+                   s.misc + M_IOSEEN);
     cl.sync();                                                      // B1: deposits done
 #ifdef GEMPIC_PHASE_TIMERS
     if (tid == 0 && p.timers && k == p.k0) {
@@ -2467,7 +2482,13 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
 #endif
     // publish: iteration n+1 complete (its stored phase and this push have been issued)
     if (p.P > 1 && me == 0 && tid == 0 && n + 1 <= nz - 1)
-      st_release_u64(p.progress + cid, prog_value(k, nz, nz - (n + 1)));
+      st_release_u64(p.progress + cid, prog_value(item, nz, nz - (n + 1)));
+    // denoised chain: the first pass's current of half-slices >= n + 1 is written
+    if (dn1 && me == 0 && tid == 0) {
+      const int done = nz - (n + 1);
+      if (done > 0 && done % p.dn_chunk == p.dn_lead)
+        st_release_sys_u64(p.dn_done + cid, prog_value(item, nz, done));
+    }
     // streamed state: blocks >= n + 2 of the new level are written (and blocks >= n of the
     // old level read); the host copies a group out once its last block is
     if (p.io_chunk && me == 0 && tid == 0) {
@@ -2610,7 +2631,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     if (snap_step || cap_step) {
       __syncthreads();
       T* sn = (T*)p.snap;
-      T* jc = (T*)p.jcap;
+      T* jc = jcap;
       for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
         const int c = i >> (p.logRB + p.lognx);
         const int rem = i & ((p.RB << p.lognx) - 1);
@@ -2620,10 +2641,11 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         if (cap_step) jc[(((size_t)n * 3 + c) * p.ny + (me << p.logRB)) * p.nx + rem] = v;
       }
     }
-    if (p.jext) {
+    const T* const jext = (const T*)(dn2 ? p.dn_jext[k & 3] : p.dn_pipe ? nullptr : p.jext);
+    if (jext) {
       // second pass of a denoised s-step: the half-slice's current is the given one
       __syncthreads();
-      const T* je = (const T*)p.jext;
+      const T* je = jext;
       for (int i = tid; i < 3 * p.RB * p.nx; i += NT) {
         const int c = i >> (p.logRB + p.lognx);
         const int rem = i & ((p.RB << p.lognx) - 1);
@@ -2631,13 +2653,13 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
             ldcg(je + (((size_t)n * 3 + c) * p.ny + (me << p.logRB)) * p.nx + rem);
       }
     }
-    if (beam_slice || snap_step || cap_step || p.jext) __syncthreads();
+    if (beam_slice || snap_step || cap_step || jext) __syncthreads();
     TIMER_MARK(PH_BEAM);
     // ---------------- B: row FFTs of the currents, transposed to the kx owners ------------
     forward_rows<T, SH>(cl, p, s, me, true);
     TIMER_MARK(PH_FWD);
     // streamed state: block n-1 of the input, read after the solve below
-    if (p.io_chunk && tid == 0 && me == 0 && n >= 1) wait_input(p, cid, k, n - 1, s.misc + M_IOSEEN);
+    if (p.io_chunk && tid == 0 && me == 0 && n >= 1) wait_input(p, k, n - 1, s.misc + M_IOSEEN);
     cl.sync();                                                      // B2
     if (tid == 0 && me == 0) p.jflag[(size_t)s1 * nz + n] = 0;
     TIMER_MARK(PH_B2);
@@ -2714,7 +2736,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     scatter_to_rows(cl, p, s, me);
     TIMER_MARK(PH_SCAT);
     if (waits && tid == 0 && me == 0)
-      wait_for(p, pcid, prog_value(k - 1, nz, min(nz, nz - n + 3)));   // down to n-3
+      wait_for(p, pcid, prog_value(item - 1, nz, min(nz, nz - n + 3)));   // down to n-3
     cl.sync();                                                      // B3
     // the predecessor is now known to be done down to slice n-3: counters of slice n-1,
     // loaded by the last warp (no inverse-transform task) so that no transform waits on them
@@ -2790,7 +2812,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     }
     // ---------------- E: stored particles of cell (zeta_n, zeta_{n+1}] along s -------------
     // (most cells hold no stored particle: the call is skipped, uniformly over the CTA)
-    if (s.misc[M_STN] > 0 && !p.skip_stored)
+    if (s.misc[M_STN] > 0 && !p.skip_stored && !dn1)
       stored_phase(p, s, Fnew, Fcur, s1, s2, n, me, s.misc[M_STN], varh);
     TIMER_MARK(PH_E);
     T* t = Fcur;
@@ -2801,8 +2823,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   __syncthreads();
   if (tid == 0) __threadfence();
   cl.sync();
-  if (p.P > 1 && me == 0 && tid == 0) st_release_u64(p.progress + cid, prog_value(k, nz, nz));
+  if (p.P > 1 && me == 0 && tid == 0) st_release_u64(p.progress + cid, prog_value(item, nz, nz));
   if (p.io_chunk && me == 0 && tid == 0) st_release_sys_u64(p.io_done + cid, prog_value(k, nz, nz));
+  if (dn1 && me == 0 && tid == 0) st_release_sys_u64(p.dn_done + cid, prog_value(item, nz, nz));
 
   if (resid) {
     // the march's largest residuals: non-negative doubles order like their bit patterns
@@ -2853,7 +2876,10 @@ __device__ __forceinline__ void march_launch(const Params& p) {
   if (threadIdx.x < kNDiag) s.dacc[threadIdx.x] = 0.0;
   __syncthreads();
   const int cid = (int)(blockIdx.x / p.C);
-  for (long long k = p.k0 + cid; k < p.k0 + p.nsteps; k += p.P) march<T, CANON, SH>(p, s, cl, k, cid);
+  for (long long it = cid; it < p.nsteps; it += p.P) {
+    const long long item = p.dn_pipe ? 2 * p.k0 + it : p.k0 + it;
+    march<T, CANON, SH>(p, s, cl, p.dn_pipe ? item >> 1 : item, cid, item);
+  }
 }
 
 template <typename T, bool CANON = false, int SH = 0>
@@ -2896,7 +2922,7 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(const Params* ps, const i
     load_tables(sp, s);
     if (threadIdx.x < kNDiag) s.dacc[threadIdx.x] = 0.0;
     __syncthreads();
-    march<T, false, 0>(sp, s, cl, sp.k0 + w.y, w.y);
+    march<T, false, 0>(sp, s, cl, sp.k0 + w.y, w.y, sp.k0 + w.y);
   }
 }
 

@@ -176,6 +176,48 @@ def test_denoised_step_matches_the_oracle(G):
             assert errs["ez"] <= 1e-3 and errs["field_energy"] <= 1e-3, (k, errs)
 
 
+@pytest.mark.parametrize("grid", ["small", "bench"])
+def test_chained_denoised_steps_equal_one_at_a_time(G, grid):
+    """Several denoised s-steps in one call run as one chain of marches (first and second
+    passes, the net on groups of half-slices in between, several marches in flight); one s-step
+    per call runs the same chain with one s-step.  Same arithmetic, so the same results: the
+    state, the diagnostics, the on-axis E_z and the kept plain current of each s-step (a small
+    3-D grid with trapping, and the bench's 128 x 128 grid with the row-staged net and seven
+    marches in flight)."""
+    from paper_2509_16793_gb300 import workloads as W
+    if grid == "small":
+        w = W.small_3d(nx=16, ny=16, nzeta=40, ppc=2, precision=32, a0=2.0, delta=2.0)
+        kw, n = {"cluster_ctas": 2}, 5
+    else:
+        w = W.lwfa_3d_128x128x512(ppc=1)
+        w = w.with_(nzeta=128, laser=W.Laser(**{**w.laser.__dict__,
+                                                "zeta_center": 128 * w.h - 2.0 * w.laser.duration}))
+        kw, n = {}, 6
+    scale = abs(w.species[0].charge * w.species[0].density)
+    P = D.init_params(seed=9, scale3=0.05)
+    vec = G.denoiser_params_to_vector(P)
+    with G.Denoiser(vec, scale) as d, G.Sim(w, **kw) as a, G.Sim(w, **kw) as b:
+        a.set_denoiser(d)
+        b.set_denoiser(d)
+        da = []
+        for _ in range(n):
+            a.step(1)
+            da.append(a.diagnostics())
+        b.step(n)
+        db = b.diagnostics()
+        if grid == "bench":
+            assert b.launch_shape()["pipeline"] >= 7
+        for k in ("field_energy", "kinetic_energy", "charge_flux", "stored_kinetic_energy"):
+            assert abs(db[k] - da[-1][k]) <= 1e-6 * abs(da[-1][k]) + 1e-30, (k, da[-1][k], db[k])
+        for k in ("n_trapped", "n_stored", "n_rejoined", "pushes", "step"):
+            assert db[k] == da[-1][k], k
+        sa, sb = a.state(), b.state()
+        assert np.abs(sb - sa).max() <= 1e-6 * np.abs(sa).max()
+        assert np.abs(b.onaxis_ez() - a.onaxis_ez()).max() <= 1e-6 * np.abs(a.onaxis_ez()).max()
+        ca, cb = a.current(), b.current()
+        assert np.abs(cb - ca).max() <= 1e-6 * np.abs(ca).max()
+
+
 @pytest.mark.parametrize("precision,nx,ny,ppc", [(64, 512, 1, 8), (32, 128, 128, 16)])
 def test_many_particles_per_cell_overflow_to_global_slots(G, precision, nx, ny, ppc):
     """A fresh layer larger than a CTA's shared memory (4096 FP64 particles in 2-D, 16 ppc on

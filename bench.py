@@ -327,13 +327,19 @@ def main():
     nb = sim.state_bytes()
     diag_bytes = 9 * shape["cluster_ctas"] * 8          # per-CTA FP64 partials of one s-step
     e2e_s = float("nan")
+    e2e_error = None
     if args.e2e_steps > 0:
         host = torch.empty(nb, dtype=torch.uint8, pin_memory=True).numpy()
         sim.gempic_get_state(host)                          # the raw bytes of the state
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sim.step_streamed(args.e2e_steps, host)
-        e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        try:
+            sim.step_streamed(args.e2e_steps, host)
+            e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+        except gempic.GempicError as ex:
+            # the streamed call needs its copies to run beside the marches (a profiler that
+            # serialises the device makes its bounded waits give up)
+            e2e_error = str(ex)
     e2e_s = max_over_ranks(e2e_s, "cuda")
     e2e_value = job_rate(w.pushes_per_step, world, e2e_s)
 
@@ -404,7 +410,8 @@ def main():
             "e2e": {"value": e2e_value if math.isfinite(e2e_value) else None,
                     "unit": "pushes/s", "h2d_bytes_per_step": nb,
                     "d2h_bytes_per_step": nb + diag_bytes,
-                    "steps": args.e2e_steps, "call": "gempic_step_streamed"},
+                    "steps": args.e2e_steps, "call": "gempic_step_streamed",
+                    **({"error": e2e_error} if e2e_error else {})},
             "gpu_launches": launches, "clocks": clocks, "fp64_plain": fp64, "denoiser": denoise,
             "diag": {k: diag[k] for k in ("field_energy", "kinetic_energy", "n_stored", "pushes")}}
     print(json.dumps(line), flush=True)

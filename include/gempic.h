@@ -455,8 +455,9 @@ void gempic_denoiser_destroy(gempic_denoiser* d);
  * before the field update) and pushes the stored set with those fields.  The pushes of the
  * s-step saw the first pass's fields: the net needs the current of half-slices on both sides
  * of each one, which the march produces only one at a time.  The n s-steps of a call run as
- * one chain of 2n marches in one launch (up to 7 in flight, each following the one before it
- * slice by slice): the calling thread runs the net on groups of half-slices as soon as the
+ * one chain of 2n marches in one launch, each following the one before it slice by slice; up
+ * to min(7, pipeline_depth) in flight, or, with pipeline_depth 0, as many as leave a third of
+ * the SMs to the net.  The calling thread runs the net on groups of half-slices as soon as the
  * first pass has written them and the three half-slices beyond, on a stream of its own, and
  * releases each group to the second pass, which waits for it (bounded).  The call waits for
  * its stream.  The diagnostics combine both passes: the field energy, on-axis E_z and stored

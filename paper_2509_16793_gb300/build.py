@@ -16,8 +16,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libgempic.so")
-SOURCES = ["gempic_kernels.cu", "gempic_api.cu", "gempic_noalloc.cu", "gempic_batch.cu",
-           "gempic_probe.cu", "gempic_denoise.cu"]
+SOURCES = ["gempic_kernels.cu", "gempic_chain.cu", "gempic_api.cu", "gempic_noalloc.cu",
+           "gempic_batch.cu", "gempic_probe.cu", "gempic_denoise.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          # FP32 only: flush denormals, approximate division and square root (<= 2 ulp);

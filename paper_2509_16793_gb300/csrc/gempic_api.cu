@@ -675,6 +675,16 @@ static gempic_status denoised_chain(gempic_sim* s, int n) {
   }
   if (e == cudaSuccess && !s->dn_stream) e = cudaStreamCreateWithFlags(&s->dn_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return cuda_fail(s, e);
+  // nothing below may allocate or free device memory while the marches run: cudaFree waits
+  // for the whole device, and the marches wait for the net
+  int rs = gempic::denoise_reserve(s->dn, s->p.nx, s->p.ny, nz);
+  if (rs != GEMPIC_OK) return (gempic_status)rs;
+  for (int i = 0; i < 4 * nz / std::max(4, (nz + 15) / 16) + 8 && e == cudaSuccess; ++i) {
+    cudaEvent_t ev = nullptr;           // enough events for every group in flight
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) s->io_events.push_back(ev);
+  }
+  if (e != cudaSuccess) return cuda_fail(s, e);
   // groups of about a sixteenth of the window; a group needs the first pass three half-slices
   // beyond it (the net's reach along zeta)
   const int chunk = std::max(4, (nz + 15) / 16);
@@ -682,8 +692,17 @@ static gempic_status denoised_chain(gempic_sim* s, int n) {
   const int lead = 3 % chunk;
   // at most 7 marches in flight: the first pass of s-step i+4 reuses the current buffers of
   // s-step i only after it starts, i.e. after march 2i+8-P, the second pass of s-step i or later,
-  // has finished with them
-  const int P = std::min(std::min(s->pmax, 2 * n), 7);
+  // has finished with them.  The net runs on the SMs the marches leave free: unless the
+  // configuration sets the depth, the marches take at most two thirds of them (on GB300 at
+  // 128 x 128 x 512, 1 ppc, the chain's time per s-step against its depth was 11.5, 7.7, 6.8,
+  // 5.5, 5.3 and 7.3 ms for 2 to 7 clusters of 16 CTAs: 6 leaves 56 SMs to the net).
+  int dev = 0, nsm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return cuda_fail(s, e);
+  const int want = s->cfg.pipeline_depth > 0 ? s->cfg.pipeline_depth
+                                             : std::max(1, 2 * nsm / (3 * s->p.C));
+  const int P = std::min(std::min(std::min(s->pmax, 2 * n), 7), want);
   const long long k0 = s->k;
   unsigned long long* done = s->dn_host;
   unsigned long long* ready = s->dn_host + 8;

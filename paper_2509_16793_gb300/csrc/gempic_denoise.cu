@@ -778,6 +778,15 @@ int denoise_range(gempic_denoiser* d, const float* j_in, float* j_out, int nx, i
 // the denoiser's device status word (a bounded wait that gave up): GEMPIC_ETIMEOUT
 int denoise_status(gempic_denoiser* d, cudaStream_t s) { return check_err(d, s); }
 
+// working buffers for nx x ny x nz currents, allocated now: growing them frees the old ones,
+// and cudaFree waits for the whole device -- while the chain of marches runs, that would wait
+// for marches that wait for the net
+int denoise_reserve(gempic_denoiser* d, int nx, int ny, int nz) {
+  if (!d || !grid_ok(nx, ny, nz)) return GEMPIC_EINVAL;
+  const cudaError_t e = grow(d, (long long)nx * ny * nz);
+  return e == cudaSuccess ? GEMPIC_OK : e == cudaErrorMemoryAllocation ? GEMPIC_ENOMEM : GEMPIC_ECUDA;
+}
+
 }  // namespace gempic
 
 extern "C" {

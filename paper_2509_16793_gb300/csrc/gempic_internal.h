@@ -174,10 +174,14 @@ cudaError_t max_active_clusters(int precision, const Params& p, int* n);
 cudaError_t configure_march_canon(int precision, int smem_bytes);
 cudaError_t launch_march_canon(int precision, const Params& p, cudaStream_t s);
 cudaError_t launch_tables(int precision, const Params& p, void* dst, cudaStream_t s);
+// the denoised chain's march (FP32, p.dn_pipe = 1; compiled in gempic_chain.cu)
+cudaError_t configure_chain(int smem_bytes);
+cudaError_t launch_march_chain(const Params& p, cudaStream_t s);
 // the learned current denoiser on output half-slices [z0, z1) (gempic_denoise.cu); status codes
 // of gempic_status
 int denoise_range(struct gempic_denoiser* d, const float* j_in, float* j_out, int nx, int ny,
                   int nz, int z0, int z1, cudaStream_t s);
 int denoise_status(struct gempic_denoiser* d, cudaStream_t s);
+int denoise_reserve(struct gempic_denoiser* d, int nx, int ny, int nz);
 
 }  // namespace gempic

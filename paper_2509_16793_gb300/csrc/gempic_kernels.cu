@@ -2001,7 +2001,7 @@ __device__ __forceinline__ Mode6<T> slice_solve(T kx, T ky, T h, T Dl, const Mod
 // ------------------------------------------------------------------------------------------
 // progress / waits between concurrently marching clusters
 // ------------------------------------------------------------------------------------------
-__device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
+static __device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
   int spins = 0;
   while (ld_acquire_u64(p.progress + pcid) < target) {
     if (atomicAdd(p.err, 0) & ERR_TIMEOUT) return;
@@ -2016,7 +2016,7 @@ __device__ void wait_for(const Params& p, int pcid, unsigned long long target) {
 // wait until the host has released group g of march `key` in the host-mapped word `word`
 // (streamed state: the input's groups; denoised chain: the denoised current's groups).
 // *seen (shared memory, -1 at the start of a march) is the last group known released.
-__device__ void wait_release(const Params& p, const unsigned long long* word, long long key,
+static __device__ void wait_release(const Params& p, const unsigned long long* word, long long key,
                              int nchunk, int g, int* seen) {
   if (*seen >= g) return;
   const unsigned long long target = io_value(key, nchunk, g);
@@ -2049,9 +2049,11 @@ __device__ __forceinline__ void wait_input(const Params& p, long long k, int b, 
 // CANON = false: the library's block layout [nz+1][C][6][M].  CANON = true: the public layout
 // of gempic_get_state ([6][nz][ny][nx/2]; j at half-slice index n <-> block n+1), used by the
 // allocation-free entry point on a caller's buffer.
-template <typename T, bool CANON = false, int SH = 0>
+// DN: the march of a denoised chain (its hooks are compiled into the chain's instantiations
+// only); CANON instantiations carry the streamed state's hooks.
+template <typename T, bool CANON = false, int SH = 0, bool DN = false>
 __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& cl, long long k,
-                      int cid, long long item) {
+                      int cid, long long item_) {
   // the 128 x 128 instantiation is compiled for GT2 and a uniform zeta-step only (other runs
   // take the generic one)
   constexpr int LAW = SH == 1 ? 0 : -1;
@@ -2065,8 +2067,9 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   const int NT = blockDim.x;
   // march index: k, or 2k + pass in a denoised chain; the previous march of the launch is
   // item - 1
-  const long long item0 = p.dn_pipe ? 2 * p.k0 : p.k0;
-  const bool dn1 = p.dn_pipe && !(item & 1), dn2 = p.dn_pipe && (item & 1);
+  const long long item = DN ? item_ : k;
+  const long long item0 = DN ? 2 * p.k0 : p.k0;
+  const bool dn1 = DN && !(item & 1), dn2 = DN && (item & 1);
   const bool waits = p.P > 1 && item > item0;
   const int pcid = (cid + p.P - 1) % p.P;
   const int nz = p.nz;
@@ -2207,7 +2210,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     wait_for(p, pcid, prog_value(item - 1, nz, min(nz, 3)));   // predecessor done down to nz-3
   // streamed state: the input's blocks nz and nz-1
   if (tid == 0 && me == 0) s.misc[M_IOSEEN] = -1;
-  if (p.io_chunk && tid == 0 && me == 0) wait_input(p, k, nz - 1, s.misc + M_IOSEEN);
+  if constexpr (CANON)
+    if (p.io_chunk && tid == 0 && me == 0) wait_input(p, k, nz - 1, s.misc + M_IOSEEN);
   cl.sync();
   if (has_mode) {
     j0px = ldcg(st + blk(nz, 4));
@@ -2215,10 +2219,10 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
 #pragma unroll
     for (int c = 0; c < 6; ++c) o[c] = ldcg(st + blk(nz - 1, c));
   }
-  const long long klast = p.dn_pipe ? p.k0 + p.nsteps / 2 - 1 : p.k0 + p.nsteps - 1;
+  const long long klast = DN ? p.k0 + p.nsteps / 2 - 1 : p.k0 + p.nsteps - 1;
   const bool snap_step = p.snapshot && k == klast;
   // the current kept: every first pass of a denoised chain, else the launch's last s-step
-  T* const jcap = (T*)(dn1 ? p.dn_jcap[k & 3] : p.dn_pipe ? nullptr : p.jcap);
+  T* const jcap = (T*)(dn1 ? p.dn_jcap[k & 3] : DN ? nullptr : p.jcap);
   const bool cap_step = jcap != nullptr && (dn1 || k == klast);
   // per-slice counters of other marches, read once per CTA and broadcast in shared memory
   if (tid == 0) {
@@ -2491,10 +2495,11 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     }
     // streamed state: blocks >= n + 2 of the new level are written (and blocks >= n of the
     // old level read); the host copies a group out once its last block is
-    if (p.io_chunk && me == 0 && tid == 0) {
-      const int done = nz - (n + 1);
-      if (done > 0 && done % p.io_chunk == 0) st_release_sys_u64(p.io_done + cid, prog_value(k, nz, done));
-    }
+    if constexpr (CANON)
+      if (p.io_chunk && me == 0 && tid == 0) {
+        const int done = nz - (n + 1);
+        if (done > 0 && done % p.io_chunk == 0) st_release_sys_u64(p.io_done + cid, prog_value(k, nz, done));
+      }
     // stored particles of cell n at this level (traps of this push included), for phase E;
     // loaded by the last warp, which has no forward-transform task
     if (tid == NT - 32) s.misc[M_STN] = ldcg(p.st.cnt + (size_t)s1 * nz + n);
@@ -2641,7 +2646,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
         if (cap_step) jc[(((size_t)n * 3 + c) * p.ny + (me << p.logRB)) * p.nx + rem] = v;
       }
     }
-    const T* const jext = (const T*)(dn2 ? p.dn_jext[k & 3] : p.dn_pipe ? nullptr : p.jext);
+    const T* const jext = (const T*)(dn2 ? p.dn_jext[k & 3] : DN ? nullptr : p.jext);
     if (jext) {
       // second pass of a denoised s-step: the half-slice's current is the given one
       __syncthreads();
@@ -2659,7 +2664,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     forward_rows<T, SH>(cl, p, s, me, true);
     TIMER_MARK(PH_FWD);
     // streamed state: block n-1 of the input, read after the solve below
-    if (p.io_chunk && tid == 0 && me == 0 && n >= 1) wait_input(p, k, n - 1, s.misc + M_IOSEEN);
+    if constexpr (CANON)
+      if (p.io_chunk && tid == 0 && me == 0 && n >= 1) wait_input(p, k, n - 1, s.misc + M_IOSEEN);
     cl.sync();                                                      // B2
     if (tid == 0 && me == 0) p.jflag[(size_t)s1 * nz + n] = 0;
     TIMER_MARK(PH_B2);
@@ -2824,7 +2830,8 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   if (tid == 0) __threadfence();
   cl.sync();
   if (p.P > 1 && me == 0 && tid == 0) st_release_u64(p.progress + cid, prog_value(item, nz, nz));
-  if (p.io_chunk && me == 0 && tid == 0) st_release_sys_u64(p.io_done + cid, prog_value(k, nz, nz));
+  if constexpr (CANON)
+    if (p.io_chunk && me == 0 && tid == 0) st_release_sys_u64(p.io_done + cid, prog_value(k, nz, nz));
   if (dn1 && me == 0 && tid == 0) st_release_sys_u64(p.dn_done + cid, prog_value(item, nz, nz));
 
   if (resid) {
@@ -2867,7 +2874,7 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
   }
 }
 
-template <typename T, bool CANON, int SH>
+template <typename T, bool CANON, int SH, bool DN>
 __device__ __forceinline__ void march_launch(const Params& p) {
   extern __shared__ __align__(16) unsigned char smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -2876,23 +2883,27 @@ __device__ __forceinline__ void march_launch(const Params& p) {
   if (threadIdx.x < kNDiag) s.dacc[threadIdx.x] = 0.0;
   __syncthreads();
   const int cid = (int)(blockIdx.x / p.C);
+  // a chain's march index is 2k + pass
   for (long long it = cid; it < p.nsteps; it += p.P) {
-    const long long item = p.dn_pipe ? 2 * p.k0 + it : p.k0 + it;
-    march<T, CANON, SH>(p, s, cl, p.dn_pipe ? item >> 1 : item, cid, item);
+    const long long item = DN ? 2 * p.k0 + it : p.k0 + it;
+    march<T, CANON, SH, DN>(p, s, cl, DN ? item >> 1 : item, cid, item);
   }
 }
 
-template <typename T, bool CANON = false, int SH = 0>
+template <typename T, bool CANON = false, int SH = 0, bool DN = false>
 __global__ void __launch_bounds__(512, 1) march_kernel(const Params p) {
-  march_launch<T, CANON, SH>(p);
+  march_launch<T, CANON, SH, DN>(p);
 }
 
+#ifndef GEMPIC_CHAIN_TU
 // FP64 with at most 256 threads per CTA (the 2-D and small 3-D grids): up to 255 registers a
 // thread, so the FP64 march keeps its state in registers instead of spilling it
 __global__ void __launch_bounds__(256, 1) march_kernel_fp64_narrow(const Params p) {
-  march_launch<double, false, 0>(p);
+  march_launch<double, false, 0, false>(p);
 }
+#endif
 
+#ifndef GEMPIC_CHAIN_TU
 // Batched scan: one persistent launch over independent simulations.  Each CTA takes work
 // items (simulation, march index) from a queue in global memory, in the order the host laid
 // out (s-step by s-step, the costliest simulations first); the march of s-step k of a
@@ -2922,7 +2933,7 @@ __global__ void __launch_bounds__(512, 1) batch_kernel(const Params* ps, const i
     load_tables(sp, s);
     if (threadIdx.x < kNDiag) s.dacc[threadIdx.x] = 0.0;
     __syncthreads();
-    march<T, false, 0>(sp, s, cl, sp.k0 + w.y, w.y, sp.k0 + w.y);
+    march<T, false, 0, false>(sp, s, cl, sp.k0 + w.y, w.y, sp.k0 + w.y);
   }
 }
 
@@ -3112,8 +3123,11 @@ __global__ void export_kernel(const Params p, Cx<T>* dst, const Cx<T>* src, int 
 // ------------------------------------------------------------------------------------------
 // host-side launchers
 // ------------------------------------------------------------------------------------------
+#endif  // GEMPIC_CHAIN_TU
+
 static int align16(int v) { return (v + 15) / 16 * 16; }
 
+#ifndef GEMPIC_CHAIN_TU
 int smem_layout(Params& p, int eb) {
   // halo geometry: fields own rows + 1 above, currents rows -1 .. RB + 1 (3-D only)
   p.FR = p.ny > 1 ? p.RB + 1 : 1;
@@ -3165,6 +3179,8 @@ int smem_layout(Params& p, int eb) {
   return p.smem_bytes;
 }
 
+#endif  // GEMPIC_CHAIN_TU
+
 // kernel instantiation for the grid: 1 = FP32 128 x 128 with an even band (length-128
 // transforms only), 0 = any size
 static int shape_class(int precision, const Params& p) {
@@ -3188,6 +3204,7 @@ static cudaError_t cfg_kernel(K* k, int smem) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
 }
 
+#ifndef GEMPIC_CHAIN_TU
 cudaError_t configure_kernels(int precision, int smem, int) {
   if (precision == 64) {
     cudaError_t e = cfg_kernel(march_kernel<double>, smem);
@@ -3198,8 +3215,11 @@ cudaError_t configure_kernels(int precision, int smem, int) {
   if (e == cudaSuccess) e = cfg_kernel(laser_kernel<float>, smem);
   if (e == cudaSuccess) e = cfg_kernel(march_kernel<float, false, 1>, smem);
   if (e == cudaSuccess) e = cfg_kernel(laser_kernel<float, 1>, smem);
+  if (e == cudaSuccess) e = configure_chain(smem);
   return e;
 }
+
+#endif  // GEMPIC_CHAIN_TU
 
 static cudaLaunchConfig_t make_cfg(const Params& p, int nclusters, cudaStream_t s,
                                    cudaLaunchAttribute* attr) {
@@ -3217,7 +3237,9 @@ static cudaLaunchConfig_t make_cfg(const Params& p, int nclusters, cudaStream_t 
   return c;
 }
 
+#ifndef GEMPIC_CHAIN_TU
 cudaError_t launch_march(int precision, const Params& p, cudaStream_t s) {
+  if (p.dn_pipe) return precision == 32 ? launch_march_chain(p, s) : cudaErrorInvalidValue;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t c = make_cfg(p, p.P, s, attr);
   if (precision == 64 && p.nthreads <= 256)
@@ -3299,5 +3321,21 @@ cudaError_t max_active_clusters(int precision, const Params& p, int* n) {
     return cudaOccupancyMaxActiveClusters(n, march_kernel<float, false, 1>, &c);
   return cudaOccupancyMaxActiveClusters(n, march_kernel<float>, &c);
 }
+
+#else  // GEMPIC_CHAIN_TU
+
+// the denoised chain's instantiations of the march (FP32; the 128 x 128 one where it applies)
+cudaError_t configure_chain(int smem) {
+  cudaError_t e = cfg_kernel(march_kernel<float, false, 0, true>, smem);
+  return e == cudaSuccess ? cfg_kernel(march_kernel<float, false, 1, true>, smem) : e;
+}
+
+cudaError_t launch_march_chain(const Params& p, cudaStream_t s) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t c = make_cfg(p, p.P, s, attr);
+  if (shape_class(32, p) == 1) return cudaLaunchKernelEx(&c, march_kernel<float, false, 1, true>, p);
+  return cudaLaunchKernelEx(&c, march_kernel<float, false, 0, true>, p);
+}
+#endif  // GEMPIC_CHAIN_TU
 
 }  // namespace gempic

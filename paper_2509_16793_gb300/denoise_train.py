@@ -69,14 +69,30 @@ def rms_err(a, b, sel=None) -> float:
     return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
 
 
-def judge(w_sparse, w_dense, den: "gempic.Denoiser", steps: int, stream=None) -> Dict:
+def _timed_steps(sim, n: int) -> float:
+    """Device time per s-step of one call of n s-steps (CUDA events on the stream)."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0.record(st)
+    sim.step(n)
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def judge(w_sparse, w_dense, den: "gempic.Denoiser", steps: int, stream=None,
+          chain_depths=(2, 3, 4, 5, 6, 7)) -> Dict:
     """Fresh runs of `steps` s-steps: dense plain, sparse plain, sparse denoised.  On-axis E_z
     and field energy of the sparse runs against the dense run after the last s-step, over the
     window and in front of the region where the dense run traps particles (its front-most
-    stored particle plus 64 slices); time per s-step (CUDA events on the stream around one
-    call of `steps` s-steps: the plain runs march as their wavefront, the denoised run as its
-    chain of first and second passes with the net between them)."""
-    import torch
+    stored particle plus 64 slices).  Time per s-step: CUDA events on the stream around one call
+    of the first steps - 1 s-steps (7 = one full wave of the dense run's 7-deep wavefront); the
+    plain runs march as their wavefront, the denoised run as its chain of first and second
+    passes with the net between them, at the library's default depth and, on extra runs, at each
+    depth of `chain_depths` (the marches in flight: more take SMs from the net)."""
     res = {}
     out = {}
     # a second dense run with other particles: the dense run's own noise, the floor of any
@@ -89,20 +105,19 @@ def judge(w_sparse, w_dense, den: "gempic.Denoiser", steps: int, stream=None) ->
             if d is not None:
                 sim.set_denoiser(d)
             sim.step(0)                          # the level-0 set-up, not timed
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            st = torch.cuda.current_stream()
-            torch.cuda.synchronize()
-            e0.record(st)
-            sim.step(steps)
-            e1.record(st)
-            torch.cuda.synchronize()
-            out[label] = {"ms_per_step": e0.elapsed_time(e1) / steps, "ez": sim.onaxis_ez(),
-                          "diag": sim.diagnostics()}
+            ms = _timed_steps(sim, steps - 1)
+            sim.step(1)
+            out[label] = {"ms_per_step": ms, "ez": sim.onaxis_ez(), "diag": sim.diagnostics()}
             if label == "dense":
                 p = sim.particles(0)
                 out[label]["zeta_trap"] = float(p["zeta"].max()) if p["zeta"].size else 0.0
                 pipeline = sim.launch_shape()["pipeline"]
+    depth_ms = {}
+    for depth in chain_depths:
+        with gempic.Sim(w_sparse, stream=stream, pipeline_depth=depth) as sim:
+            sim.set_denoiser(den)
+            sim.step(0)
+            depth_ms[str(depth)] = _timed_steps(sim, steps - 1)
     dense_wave_ms = out["dense"]["ms_per_step"]
     ref = out["dense"]["ez"]
     zc = np.arange(w_dense.nzeta) * w_dense.h
@@ -117,7 +132,10 @@ def judge(w_sparse, w_dense, den: "gempic.Denoiser", steps: int, stream=None) ->
                       "ms_per_step": out[label]["ms_per_step"]}
     res["dense"] = {"ms_per_step_wavefront": dense_wave_ms, "wavefront_depth": pipeline,
                     "front_slices": int(front.sum())}
+    res["sparse_denoised"]["ms_per_step_by_chain_depth"] = depth_ms
     res["speedup_vs_dense_wavefront"] = dense_wave_ms / out["sparse_denoised"]["ms_per_step"]
+    best = min(depth_ms.values()) if depth_ms else out["sparse_denoised"]["ms_per_step"]
+    res["speedup_vs_dense_wavefront_best_depth"] = dense_wave_ms / best
     return res
 
 
@@ -139,7 +157,7 @@ def time_apply(den: "gempic.Denoiser", w, stream=None, reps: int = 5) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def experiment(pairs: int = 64, iters: int = 3000, judge_steps: int = 14, stream=None) -> Dict:
+def experiment(pairs: int = 64, iters: int = 3000, judge_steps: int = 8, stream=None) -> Dict:
     """The whole experiment on the 128 x 128 x 512 LWFA: pairs of 1- and 16-ppc runs, training,
     judging.  Returns a summary dict."""
     from . import workloads as W

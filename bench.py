@@ -246,7 +246,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=8)
     ap.add_argument("--impl", default="gempic", choices=["gempic", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=21, help="0 skips the end-to-end leg")
+    ap.add_argument("--e2e-steps", type=int, default=49, help="0 skips the end-to-end leg")
     ap.add_argument("--nzeta", type=int, default=0,
                     help="profiling only: shorter window of the same workload")
     ap.add_argument("--pipeline", type=int, default=0, help="s-steps marched concurrently (0 = auto)")

@@ -333,169 +333,271 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(ConvArgs a) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
 }
 
-// ---- row-staged convolution (rows of 128 voxels) ---------------------------------------------
+// ---- row-staged operands (rows of 128 voxels) ------------------------------------------------
 // For nx = 128 an output tile is one row (z, y), and the A operand of tap (dz, dy, dx) is the
 // input row (z + dz, y + dy) shifted by dx.  Each input row is staged once in shared memory as
 // two arrays of 16-byte voxel entries (channels 0-7 and 8-15) with one halo voxel at each end
 // (x = -1 and x = 128, periodic); a voxel's 16 bytes follow the previous voxel's, so in the
 // K-major layout without swizzle the core matrices along M are 128 B apart (SBO) and the
 // second K half is the second array (LBO): every tap's operand is then a descriptor into the
-// staged rows, with no per-tap gather.  A CTA marches along y over a strip of rows of one z,
-// keeping four staged rows per z-plane: rows y-1, y, y+1 feed the 27 MMAs of row y while row
-// y+2 is being loaded.  The accumulators alternate between two 16-column halves of tensor
-// memory so that the epilogue of row y-1 overlaps the MMAs of row y.  (Five staged rows and
-// three accumulator sets, which let the MMAs of two rows run ahead, measured slower: the
-// larger shared memory leaves two CTAs per SM instead of three.)
+// staged rows, advanced by dx x 16 bytes, with no per-tap gather.
 constexpr int kRowVox = 128;                         // nx of the row path
 constexpr int kRowHalo = kRowVox + 2;                // staged voxels: x = -1 .. 128
 constexpr uint32_t kHalfStride = kRowHalo * 16 + 32; // a K half; the pad puts the second half
                                                      // 16 banks away from the first
 constexpr uint32_t kRowBytes = 2 * kHalfStride;
-constexpr int kRing = 4;                             // staged rows per z-plane
-constexpr int kStrip = 32;                           // output rows per strip
-constexpr uint32_t kRowsSmem = (uint32_t)kTaps * kTapBytesB + 3u * kRing * kRowBytes + 256u;
 
 __device__ __forceinline__ uint64_t sdesc_row(uint32_t saddr) {
   return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kHalfStride >> 4) << 16) |
          ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
 }
 
-// stage input row (zz, yy) into `slot`, yy in [-1, ny] wrapped periodically (asynchronous
-// 16-byte copies, coalesced reads)
-__device__ __forceinline__ void stage_row(const ConvArgs& a, uint32_t slot, int zz, int yy) {
-  const int yr = yy < 0 ? yy + a.ny : (yy >= a.ny ? yy - a.ny : yy);
-  const __nv_bfloat16* row = a.x + ((long long)zz * a.ny + yr) * (long long)kRowVox * kCh;
-  for (int i = threadIdx.x; i < 2 * kRowHalo; i += kThreads) {
-    const int xi = i >> 1, h = i & 1;               // staged voxel x = xi - 1, channel half h
-    const int xs = (xi + kRowVox - 1) & (kRowVox - 1);
-    cp_async16(slot + (uint32_t)h * kHalfStride + (uint32_t)xi * 16u, row + xs * kCh + h * 8, 16u);
-  }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// ---- warp-specialised row convolution with the three dy taps in one MMA (rows of 128 voxels) -
+// An input row (z + dz, r) feeds the output rows r - 1, r, r + 1 of plane z through the taps
+// dy = +1, 0, -1.  With the operand B of a (dz, dx) pair holding those three taps' 16 x 16
+// weights one under the other (N = 48) and the accumulators of consecutive output rows in
+// consecutive 16-column sets of tensor memory, one MMA per (input row, dz, dx) adds all three
+// contributions: 9 MMAs per output row instead of 27, each reading its 4 KB operand A once.
+// A CTA takes strips of kStripW output rows of one z; the input rows y0 - 1 .. y1 are staged
+// as units (three z-planes each) in a ring; set s of tensor memory holds output row
+// y0 - 1 + s (sets 0 and kStripW + 1 only collect the contributions to the rows beyond the
+// strip, the first and last input rows use N = 16 MMAs of the one tap that reaches into it).
+// Roles: two producer warps stage the units with asynchronous copies, wait for them, fence
+// them into the tensor core's view and arrive on the unit's `full` mbarrier; one thread issues
+// the MMAs (after the epilogue warps zeroed the strip's accumulators), frees each unit through
+// `empty` and marks each finished output row through its set's `rowd` mbarrier; four epilogue
+// warps zero the accumulators, then read each finished row back and write it.  Every wait is
+// bounded: a wait that gives up sets the abort flag and its role stops; the MMA thread waits
+// for its MMAs in flight before the tensor memory is freed.
+constexpr int kUnits = 6;                            // ring of staged units
+constexpr int kLead = 4;                             // units whose copies may be in flight
+constexpr int kStripW = 14;                          // output rows per strip
+constexpr int kSets = kStripW + 2;                   // accumulator sets (16 columns each)
+constexpr int kWsThreads = 224;                      // warps 0-1 produce, 2 issues, 3-6 drain
+constexpr uint32_t kUnitBytes = 3u * kRowBytes;      // three z-planes of one row
+constexpr uint32_t kWsSmem = (uint32_t)kTaps * kTapBytesB + kUnits * kUnitBytes + 256u;
+// instruction descriptors: M = 128, N = 48 (three taps) and N = 16 (one)
+constexpr uint32_t kIdesc48 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(48 >> 3) << 17) |
+                              ((uint32_t)(kTile >> 4) << 24);
+
+__device__ __forceinline__ void umma_n(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, 1, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* m) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+// all but the kLead newest groups have landed
+__device__ __forceinline__ void cp_async_wait_lead() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(kLead) : "memory");
+}
+// 16-byte asynchronous copy global -> shared through L2 only (a staged row is read once per CTA)
+__device__ __forceinline__ void cp_async16_cg(uint32_t dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+// zero 16 accumulator columns of this warp's 32 lanes
+__device__ __forceinline__ void tmem_zero16(uint32_t taddr) {
+  const uint32_t z = 0u;
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
+      "%1,%1};" ::"r"(taddr), "r"(z)
+      : "memory");
 }
 
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-
-__global__ void __launch_bounds__(kThreads) conv_rows_kernel(ConvArgs a) {
+__global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(ConvArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* sB = smem;                                   // 27 x 512
-  unsigned char* sR = smem + kTaps * kTapBytesB;              // [3 planes][kRing][kRowBytes]
-  __shared__ __align__(8) uint64_t mbar;
+  unsigned char* sB = smem;                                   // [9 (dz, dx)][3 (dy = +1, 0, -1)][512]
+  unsigned char* sU = smem + kTaps * kTapBytesB;              // [kUnits][3 planes][kRowBytes]
+  __shared__ __align__(8) uint64_t full[kUnits], empty[kUnits], rowd[kSets], zeroed, drain;
   __shared__ uint32_t tmem_slot;
   __shared__ int abort_flag;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 32;" ::"r"(
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(
                      smem_u32(&tmem_slot))
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(&mbar, 1);
+    for (int u = 0; u < kUnits; ++u) {
+      mbar_init(&full[u], 64);
+      mbar_init(&empty[u], 1);
+    }
+    for (int c = 0; c < kSets; ++c) mbar_init(&rowd[c], 1);
+    mbar_init(&zeroed, 4);
+    mbar_init(&drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     abort_flag = 0;
   }
   {
+    // operand B regrouped by (dz, dx): the taps dy = +1, 0, -1 one under the other
     const uint4* src = reinterpret_cast<const uint4*>(a.w);
     uint4* dst = reinterpret_cast<uint4*>(sB);
-    for (int i = tid; i < (int)(kTaps * kTapBytesB / 16); i += kThreads) dst[i] = src[i];
+    constexpr int kBlk = (int)(kTapBytesB / 16);              // 32 uint4 per tap
+    for (int i = tid; i < kTaps * kBlk; i += kWsThreads) {
+      const int blk = i / kBlk, e = i - blk * kBlk;
+      const int pair = blk / 3, b = blk - pair * 3;           // b = 0, 1, 2: dy = +1, 0, -1
+      const int pz = pair / 3, px = pair - pz * 3;
+      const int t = pz * 9 + (2 - b) * 3 + px;                // tap (dz, dy, dx) + 1
+      dst[i] = src[t * kBlk + e];
+    }
   }
-  float bias[16];
-#pragma unroll
-  for (int c = 0; c < 16; ++c) bias[c] = a.bias ? a.bias[c] : 0.0f;
   fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t rBase = smem_u32(sR);
-  const uint64_t bdesc = sdesc(smem_u32(sB));
-  uint32_t parity = 0;                 // phase of the mbarrier's next completion
-  int pending = 0;                     // a commit not yet waited for
-  auto slot = [&](int plane, int r) -> uint32_t {   // r >= -4
-    return rBase + (uint32_t)(plane * kRing + ((r + 4) & (kRing - 1))) * kRowBytes;
-  };
-  auto wait_mma = [&]() {
-    if (pending) {
-      if (!mbar_wait(&mbar, parity)) atomicExch(&abort_flag, 1);
-      parity ^= 1u;
-      pending = 0;
-    }
-    tc_fence_after();
-  };
-  auto finish_row = [&](int z, int y, int half) {    // epilogue of row (z, y)
-    float acc[16];
-    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(half * 16), acc);
-    if (a.mode != MODE_BWD)
-#pragma unroll
-      for (int c = 0; c < 16; ++c) acc[c] += bias[c];
-    const long long v = ((long long)z * a.ny + y) * kRowVox + warp * 32 + lane;
-    if (!abort_flag) epilogue(a, v, acc, false);
+  const uint32_t uBase = smem_u32(sU);
+  const int nyb = (a.ny + kStripW - 1) / kStripW;
+  const long long nstrips = (long long)(a.zhi - a.zlo) * nyb;
+  auto unit_addr = [&](long long u, int plane) -> uint32_t {
+    return uBase + (uint32_t)(u % kUnits) * kUnitBytes + (uint32_t)plane * kRowBytes;
   };
 
-  const int nyb = (a.ny + kStrip - 1) / kStrip;
-  const long long nstrips = (long long)(a.zhi - a.zlo) * nyb;
-  for (long long strip = blockIdx.x; strip < nstrips; strip += gridDim.x) {
-    const int z = a.zlo + (int)(strip / nyb);
-    const int y0 = (int)(strip % nyb) * kStrip, y1 = min(a.ny, y0 + kStrip);
-    // rows y0-1 .. y0+1 of the planes inside the window
-    for (int dz = -1; dz <= 1; ++dz) {
-      if (z + dz < 0 || z + dz >= a.nz) continue;
-      for (int r = y0 - 1; r <= y0 + 1; ++r) stage_row(a, slot(dz + 1, r), z + dz, r);
-    }
-    cp_async_commit();
-    for (int y = y0; y < y1; ++y) {
-      // the MMAs of row y-1 have read slot (y+2) & 3 for the last time and filled their
-      // accumulator half
-      wait_mma();
-      if (y + 2 <= y1)
-        for (int dz = -1; dz <= 1; ++dz)
-          if (z + dz >= 0 && z + dz < a.nz) stage_row(a, slot(dz + 1, y + 2), z + dz, y + 2);
-      cp_async_commit();
-      cp_async_wait_1();                 // rows through y+1 are in
-      fence_async_smem();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
-      if (tid == 0 && !abort_flag) {
-        // descriptors: one per staged row, + dx for the shift (16 bytes = 1 in the address
-        // field), + 32 per tap for B (512 bytes)
-        const uint32_t dcol = tmem + (uint32_t)((y & 1) * 16);
-        uint32_t accf = 0u;
-#pragma unroll
-        for (int pz = 0; pz < 3; ++pz) {
-          if (z + pz - 1 < 0 || z + pz - 1 >= a.nz) continue;   // zero padding along zeta
-#pragma unroll
-          for (int py = 0; py < 3; ++py) {
-            const uint64_t ad = sdesc_row(slot(pz, y + py - 1));
-#pragma unroll
-            for (int px = 0; px < 3; ++px) {
-              umma(dcol, ad + (uint64_t)px,
-                   bdesc + (uint64_t)((pz * 9 + py * 3 + px) * (kTapBytesB >> 4)), accf);
-              accf = 1u;
-            }
+  if (warp < 2) {
+    // ---- producers: units (z, r) for r = y0-1 .. y1 of every strip, in order ----
+    const int pt = tid;                                       // 0 .. 63
+    long long uc = 0;
+    long long landed = 0;                 // units before this one have been released
+    for (long long strip = blockIdx.x; strip < nstrips && !abort_flag; strip += gridDim.x) {
+      const int z = a.zlo + (int)(strip / nyb);
+      const int y0 = (int)(strip % nyb) * kStripW, y1 = min(a.ny, y0 + kStripW);
+      for (int r = y0 - 1; r <= y1; ++r, ++uc) {
+        if (!mbar_wait(&empty[uc % kUnits], (uint32_t)(((uc / kUnits) & 1) ^ 1))) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        const int yr = r < 0 ? r + a.ny : (r >= a.ny ? r - a.ny : r);
+        for (int dz = -1; dz <= 1; ++dz) {
+          const int zz = z + dz;
+          if (zz < 0 || zz >= a.nz) continue;                 // its taps are skipped
+          const __nv_bfloat16* row = a.x + ((long long)zz * a.ny + yr) * (long long)kRowVox * kCh;
+          const uint32_t dst = unit_addr(uc, dz + 1);
+          for (int i = pt; i < 2 * kRowHalo; i += 64) {
+            const int xi = i >> 1, h = i & 1;
+            const int xs = (xi + kRowVox - 1) & (kRowVox - 1);
+            cp_async16_cg(dst + (uint32_t)h * kHalfStride + (uint32_t)xi * 16u, row + xs * kCh + h * 8);
           }
         }
-        umma_commit(&mbar);
+        cp_async_commit();
+        // up to kLead + 1 units in flight (with the one the MMAs read, the whole ring): release
+        // the oldest once its copies have landed
+        if (uc - landed >= kLead) {
+          cp_async_wait_lead();
+          fence_async_smem();
+          mbar_arrive(&full[landed % kUnits]);
+          ++landed;
+        }
       }
-      if (y > y0) finish_row(z, y - 1, (y - 1) & 1);
-      pending = abort_flag ? 0 : 1;
-      tc_fence_before();
     }
-    wait_mma();
-    finish_row(z, y1 - 1, (y1 - 1) & 1);
-    // every thread is done with the staged rows and the accumulators before the next strip
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
+    cp_async_wait_0();
+    fence_async_smem();
+    for (; landed < uc; ++landed) mbar_arrive(&full[landed % kUnits]);
+  } else if (warp == 2) {
+    // ---- MMA issue: one thread ----
+    if (lane == 0) {
+      const uint64_t bdesc = sdesc(smem_u32(sB));
+      constexpr uint64_t kPair = (3u * kTapBytesB) >> 4;     // B of the next (dz, dx) pair
+      constexpr uint64_t kTap = kTapBytesB >> 4;
+      long long uc = 0, sc = 0;
+      bool issued = false;
+      for (long long strip = blockIdx.x; strip < nstrips && !abort_flag; strip += gridDim.x, ++sc) {
+        const int z = a.zlo + (int)(strip / nyb);
+        const int y0 = (int)(strip % nyb) * kStripW, y1 = min(a.ny, y0 + kStripW);
+        // the epilogue warps have zeroed the accumulators of this strip
+        if (!mbar_wait(&zeroed, (uint32_t)(sc & 1))) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        tc_fence_after();
+        bool ok = true;
+        for (int r = y0 - 1; r <= y1 && ok; ++r, ++uc) {
+          if (!mbar_wait(&full[uc % kUnits], (uint32_t)((uc / kUnits) & 1))) {
+            atomicExch(&abort_flag, 1);
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const int sidx = r - y0;                            // set of output row r - 1
+#pragma unroll
+          for (int pz = 0; pz < 3; ++pz) {
+            if (z + pz - 1 < 0 || z + pz - 1 >= a.nz) continue;
+            const uint64_t ad = sdesc_row(unit_addr(uc, pz));
+#pragma unroll
+            for (int px = 0; px < 3; ++px) {
+              const uint64_t bd = bdesc + (uint64_t)(pz * 3 + px) * kPair;
+              if (r == y0 - 1)            // only dy = -1 reaches the strip (row y0: set 1)
+                umma_n(tmem + 16u, ad + (uint64_t)px, bd + 2 * kTap, kIdesc);
+              else if (r == y1)           // only dy = +1 (row y1 - 1)
+                umma_n(tmem + (uint32_t)(16 * (y1 - y0)), ad + (uint64_t)px, bd, kIdesc);
+              else                        // rows r - 1, r, r + 1: sets r - y0 .. r - y0 + 2
+                umma_n(tmem + (uint32_t)(16 * sidx), ad + (uint64_t)px, bd, kIdesc48);
+            }
+          }
+          issued = true;
+          umma_commit(&empty[uc % kUnits]);
+          // output row r - 1 has all its contributions (input rows r - 2 .. r)
+          if (r - 1 >= y0) umma_commit(&rowd[r - y0]);
+        }
+        if (!ok) break;
+      }
+      if (issued) {
+        umma_commit(&drain);
+        if (!mbar_wait(&drain, 0u)) atomicExch(&abort_flag, 1);
+      }
+    }
+    __syncwarp();
+  } else {
+    // ---- epilogue: warps 3..6 own lanes 32 (warp % 4) .. +31 of the accumulators ----
+    const int q = warp & 3;
+    float bias[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) bias[c] = (a.bias && a.mode != MODE_BWD) ? a.bias[c] : 0.0f;
+    const uint32_t lanes = (uint32_t)(q * 32) << 16;
+    // phase of each row barrier (a short strip at the end of y completes only some of them)
+    uint32_t rpar = 0u;                                       // bit c: parity of rowd[c]
+    long long sc = 0;
+    for (long long strip = blockIdx.x; strip < nstrips && !abort_flag; strip += gridDim.x, ++sc) {
+      const int z = a.zlo + (int)(strip / nyb);
+      const int y0 = (int)(strip % nyb) * kStripW, y1 = min(a.ny, y0 + kStripW);
+      // zero this strip's accumulators (the previous strip's rows have all been read)
+      for (int c = 0; c < kSets; ++c) tmem_zero16(tmem + lanes + (uint32_t)(16 * c));
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&zeroed);
+      bool ok = true;
+      for (int y = y0; y < y1; ++y) {
+        const int set = y - y0 + 1;
+        if (!mbar_wait(&rowd[set], (rpar >> set) & 1u)) {
+          atomicExch(&abort_flag, 1);
+          ok = false;
+          break;
+        }
+        rpar ^= 1u << set;
+        tc_fence_after();
+        float acc[16];
+        tmem_ld16(tmem + lanes + (uint32_t)(16 * set), acc);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) acc[c] += bias[c];
+        const long long v = ((long long)z * a.ny + y) * kRowVox + q * 32 + lane;
+        epilogue(a, v, acc, false);
+      }
+      tc_fence_before();
+      if (!ok) break;
+    }
   }
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  wait_mma();
   tc_fence_before();
   __syncthreads();
   if (abort_flag && tid == 0) atomicOr(a.err, 1);
   if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 32;" ::"r"(tmem) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
 // ---- element-wise kernels ------------------------------------------------------------------
@@ -688,9 +790,9 @@ cudaError_t conv(gempic_denoiser* d, ConvArgs a, cudaStream_t s) {
     a.zhi = a.nz;
   }
   if (a.nx == kRowVox) {
-    const long long strips = (long long)(a.zhi - a.zlo) * ((a.ny + kStrip - 1) / kStrip);
-    const int grid = (int)std::min<long long>(strips, 3LL * d->nsm);
-    conv_rows_kernel<<<grid, kThreads, kRowsSmem, s>>>(a);
+    const long long strips = (long long)(a.zhi - a.zlo) * ((a.ny + kStripW - 1) / kStripW);
+    const int grid = (int)std::min<long long>(strips, 2LL * d->nsm);
+    conv_ws_kernel<<<grid, kWsThreads, kWsSmem, s>>>(a);
     return cudaGetLastError();
   }
   const long long V = (long long)a.nx * a.ny * (a.zhi - a.zlo);
@@ -805,8 +907,8 @@ gempic_status gempic_denoiser_create(const float* params, double scale, gempic_d
     e = cudaFuncSetAttribute(conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)conv_smem());
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(conv_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kRowsSmem);
+    e = cudaFuncSetAttribute(conv_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kWsSmem);
   const size_t n = nparams();
   float** bufs[4] = {&d->p, &d->g, &d->m, &d->v};
   for (float** b : bufs)

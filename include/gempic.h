@@ -450,7 +450,7 @@ void gempic_denoiser_destroy(gempic_denoiser* d);
 
 /* Denoised s-steps (FP32 simulations): with d set, every s-step of gempic_step runs in two
  * passes.  The first marches the particles with the plain deposit and keeps its current (the
- * plain deposit stays the fallback and the judge); the denoiser maps that current; the second
+ * plain deposit stays the fallback and the reference); the denoiser maps that current; the second
  * recomputes the new level from the old one with the denoised current (the denoiser acts on j
  * before the field update) and pushes the stored set with those fields.  The pushes of the
  * s-step saw the first pass's fields: the net needs the current of half-slices on both sides

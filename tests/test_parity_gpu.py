@@ -399,7 +399,7 @@ def test_bench_workload_two_steps_match_the_oracle():
     the oracle alone).  One sim marches both s-steps in one launch, as the bench does (16-CTA
     clusters, two marches in flight); another stops after the first.
 
-    FP32 against FP64 within 1e-4 (the benchmark spec): the field energy, the charge flux, the
+    FP32 against FP64 within the FP32 parity tolerance 1e-4: the field energy, the charge flux, the
     streaming particles' kinetic energy of the first s-step (3e-4 in the second, whose particles
     cross the broken wake the first left), and the on-axis E_z in front of the trapping region
     (the front-most stored particle of the oracle plus 64 slices, 20 c/omega), relative to the

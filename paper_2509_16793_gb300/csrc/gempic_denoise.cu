@@ -885,7 +885,13 @@ int denoise_status(gempic_denoiser* d, cudaStream_t s) { return check_err(d, s);
 // for marches that wait for the net
 int denoise_reserve(gempic_denoiser* d, int nx, int ny, int nz) {
   if (!d || !grid_ok(nx, ny, nz)) return GEMPIC_EINVAL;
-  const cudaError_t e = grow(d, (long long)nx * ny * nz);
+  cudaError_t e = grow(d, (long long)nx * ny * nz);
+  // the net's kernels are loaded now: with lazy module loading a kernel's first launch loads
+  // its module, which can wait for the device -- for marches that wait for that kernel
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, pack_input_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv_kernel);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, conv_ws_kernel);
   return e == cudaSuccess ? GEMPIC_OK : e == cudaErrorMemoryAllocation ? GEMPIC_ENOMEM : GEMPIC_ECUDA;
 }
 

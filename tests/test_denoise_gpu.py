@@ -223,6 +223,32 @@ def test_chained_denoised_steps_equal_one_at_a_time(G, grid):
         assert np.abs(cb - ca).max() <= 1e-6 * np.abs(ca).max()
 
 
+_FIRST_CHAIN = r"""
+import sys, numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2509_16793_gb300 import gempic, workloads as W
+w = W.small_3d(nx=16, ny=16, nzeta=64, ppc=1, precision=32, a0=1.0)
+scale = abs(w.species[0].charge * w.species[0].density)
+with gempic.Denoiser(None, scale) as d, gempic.Sim(w, cluster_ctas=2, pipeline_depth=5) as s:
+    s.set_denoiser(d)
+    s.step(3)
+    print("ok", s.diagnostics()["step"])
+"""
+
+
+def test_first_chain_of_a_process(G):
+    """The net's kernels run for the first time in the process inside a chain of marches that
+    wait for them: they are loaded before the marches start (a kernel loaded at its first
+    launch can wait for the device, i.e. for the marches)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FIRST_CHAIN, root], capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == "ok 3", (r.stdout, r.stderr[-2000:])
+
+
 @pytest.mark.parametrize("precision,nx,ny,ppc", [(64, 512, 1, 8), (32, 128, 128, 16)])
 def test_many_particles_per_cell_overflow_to_global_slots(G, precision, nx, ny, ppc):
     """A fresh layer larger than a CTA's shared memory (4096 FP64 particles in 2-D, 16 ppc on

@@ -260,7 +260,7 @@ def main():
                     help="s-steps of the FP64-plain comparison on the 2-D workload (0 skips it)")
     ap.add_argument("--denoise-pairs", type=int, default=64,
                     help="denoiser leg: paired s-steps of the 1- and 16-ppc runs (0 skips it)")
-    ap.add_argument("--denoise-iters", type=int, default=3000, help="denoiser leg: Adam steps")
+    ap.add_argument("--denoise-iters", type=int, default=6000, help="denoiser leg: Adam steps")
     args = ap.parse_args()
     if args.workload == "scan" and args.impl == "gempic":
         return run_scan(args)

@@ -1013,7 +1013,8 @@ cudaError_t ensure_stream_io(gempic_sim* s) {
 
 // Copy group j of the public layout [6][nz][ny][nx/2] between the host buffer and a device
 // level: blocks [lo, hi) are R_x, R_y, E_z, B_z at slices lo .. hi-1 (below nz) and j_x, j_y at
-// half-slices lo-1 .. hi-2 (from 0); two strided copies, one per group of components.
+// half-slices lo-1 .. hi-2 (from 0); one contiguous copy per component (measured faster than
+// strided two-dimensional copies of the same bytes).
 cudaError_t io_copy(gempic_sim* s, int j, int chunk, void* dev, void* host, bool out,
                     cudaStream_t st) {
   const int nz = s->p.nz;
@@ -1024,17 +1025,12 @@ cudaError_t io_copy(gempic_sim* s, int j, int chunk, void* dev, void* host, bool
   char* h = (char*)host;
   const cudaMemcpyKind kind = out ? cudaMemcpyDeviceToHost : cudaMemcpyHostToDevice;
   cudaError_t e = cudaSuccess;
-  const int f0 = lo, f1 = std::min(hi, nz);                         // fields
-  if (f1 > f0) {
-    const size_t off = (size_t)f0 * sb, w = (size_t)(f1 - f0) * sb;
-    e = out ? cudaMemcpy2DAsync(h + off, cb, d + off, cb, w, 4, kind, st)
-            : cudaMemcpy2DAsync(d + off, cb, h + off, cb, w, 4, kind, st);
-  }
-  const int c0 = std::max(lo, 1) - 1, c1 = hi - 1;                  // currents
-  if (e == cudaSuccess && c1 > c0) {
-    const size_t off = 4 * cb + (size_t)c0 * sb, w = (size_t)(c1 - c0) * sb;
-    e = out ? cudaMemcpy2DAsync(h + off, cb, d + off, cb, w, 2, kind, st)
-            : cudaMemcpy2DAsync(d + off, cb, h + off, cb, w, 2, kind, st);
+  for (int c = 0; c < 6 && e == cudaSuccess; ++c) {
+    const int s0 = c < 4 ? lo : std::max(lo, 1) - 1;                // fields / currents
+    const int s1 = c < 4 ? std::min(hi, nz) : hi - 1;
+    if (s1 <= s0) continue;
+    const size_t off = (size_t)c * cb + (size_t)s0 * sb, w = (size_t)(s1 - s0) * sb;
+    e = out ? cudaMemcpyAsync(h + off, d + off, w, kind, st) : cudaMemcpyAsync(d + off, h + off, w, kind, st);
   }
   return e;
 }

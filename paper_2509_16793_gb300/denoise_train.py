@@ -157,7 +157,7 @@ def time_apply(den: "gempic.Denoiser", w, stream=None, reps: int = 5) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def experiment(pairs: int = 64, iters: int = 3000, judge_steps: int = 8, stream=None) -> Dict:
+def experiment(pairs: int = 64, iters: int = 6000, judge_steps: int = 8, stream=None) -> Dict:
     """The whole experiment on the 128 x 128 x 512 LWFA: pairs of 1- and 16-ppc runs, training,
     judging.  Returns a summary dict."""
     from . import workloads as W
@@ -198,7 +198,7 @@ if __name__ == "__main__":
     ap = argparse.ArgumentParser()
     ap.add_argument("--apply", type=int, default=0)
     ap.add_argument("--pairs", type=int, default=64)
-    ap.add_argument("--iters", type=int, default=3000)
+    ap.add_argument("--iters", type=int, default=6000)
     a = ap.parse_args()
     build.build()
     if a.apply:

@@ -335,21 +335,25 @@ __global__ void __launch_bounds__(kThreads) conv_kernel(ConvArgs a) {
 
 // ---- row-staged operands (rows of 128 voxels) ------------------------------------------------
 // For nx = 128 an output tile is one row (z, y), and the A operand of tap (dz, dy, dx) is the
-// input row (z + dz, y + dy) shifted by dx.  Each input row is staged once in shared memory as
-// two arrays of 16-byte voxel entries (channels 0-7 and 8-15) with one halo voxel at each end
-// (x = -1 and x = 128, periodic); a voxel's 16 bytes follow the previous voxel's, so in the
-// K-major layout without swizzle the core matrices along M are 128 B apart (SBO) and the
-// second K half is the second array (LBO): every tap's operand is then a descriptor into the
-// staged rows, advanced by dx x 16 bytes, with no per-tap gather.
+// input row (z + dz, y + dy) shifted by dx.  Each input row is staged once in shared memory
+// with one halo voxel at each end (x = -1 and x = 128, periodic), a voxel's 16 channels as one
+// 32-byte row of the K-major layout with 32-byte swizzling (the two 16-byte halves of a row
+// exchanged where bit 7 of its shared-memory address is set; rows 256-byte aligned in groups of
+// eight): every tap's operand is then a descriptor into the staged rows, advanced by dx x 32
+// bytes, with no per-tap gather.
 constexpr int kRowVox = 128;                         // nx of the row path
 constexpr int kRowHalo = kRowVox + 2;                // staged voxels: x = -1 .. 128
-constexpr uint32_t kHalfStride = kRowHalo * 16 + 32; // a K half; the pad puts the second half
-                                                     // 16 banks away from the first
-constexpr uint32_t kRowBytes = 2 * kHalfStride;
+constexpr uint32_t kRowBytes = 17u * 256u;           // 130 x 32 bytes, rounded to 256
 
 __device__ __forceinline__ uint64_t sdesc_row(uint32_t saddr) {
-  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(kHalfStride >> 4) << 16) |
-         ((uint64_t)(128u >> 4) << 32) | (1ull << 46);
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | (1ull << 16) | ((uint64_t)(256u >> 4) << 32) |
+         (1ull << 46) | (6ull << 61);
+}
+
+// shared-memory address of the 16-byte half h of staged voxel xi in the row at `row`
+__device__ __forceinline__ uint32_t swz_addr(uint32_t row, int xi, int h) {
+  const uint32_t a = row + (uint32_t)xi * 32u + (uint32_t)h * 16u;
+  return a ^ (((a >> 7) & 1u) << 4);
 }
 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
@@ -482,7 +486,7 @@ __global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(ConvArgs a) {
           for (int i = pt; i < 2 * kRowHalo; i += 64) {
             const int xi = i >> 1, h = i & 1;
             const int xs = (xi + kRowVox - 1) & (kRowVox - 1);
-            cp_async16_cg(dst + (uint32_t)h * kHalfStride + (uint32_t)xi * 16u, row + xs * kCh + h * 8);
+            cp_async16_cg(swz_addr(dst, xi, h), row + xs * kCh + h * 8);
           }
         }
         cp_async_commit();
@@ -532,12 +536,13 @@ __global__ void __launch_bounds__(kWsThreads) conv_ws_kernel(ConvArgs a) {
 #pragma unroll
             for (int px = 0; px < 3; ++px) {
               const uint64_t bd = bdesc + (uint64_t)(pz * 3 + px) * kPair;
+              const uint64_t as = ad + (uint64_t)(2 * px);          // dx: 32 bytes a voxel
               if (r == y0 - 1)            // only dy = -1 reaches the strip (row y0: set 1)
-                umma_n(tmem + 16u, ad + (uint64_t)px, bd + 2 * kTap, kIdesc);
+                umma_n(tmem + 16u, as, bd + 2 * kTap, kIdesc);
               else if (r == y1)           // only dy = +1 (row y1 - 1)
-                umma_n(tmem + (uint32_t)(16 * (y1 - y0)), ad + (uint64_t)px, bd, kIdesc);
+                umma_n(tmem + (uint32_t)(16 * (y1 - y0)), as, bd, kIdesc);
               else                        // rows r - 1, r, r + 1: sets r - y0 .. r - y0 + 2
-                umma_n(tmem + (uint32_t)(16 * sidx), ad + (uint64_t)px, bd, kIdesc48);
+                umma_n(tmem + (uint32_t)(16 * sidx), as, bd, kIdesc48);
             }
           }
           issued = true;

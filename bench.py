@@ -258,9 +258,9 @@ def main():
     ap.add_argument("--instances", type=int, default=64, help="scan: number of instances")
     ap.add_argument("--fp64-steps", type=int, default=40,
                     help="s-steps of the FP64-plain comparison on the 2-D workload (0 skips it)")
-    ap.add_argument("--denoise-pairs", type=int, default=64,
+    ap.add_argument("--denoise-pairs", type=int, default=96,
                     help="denoiser leg: paired s-steps of the 1- and 16-ppc runs (0 skips it)")
-    ap.add_argument("--denoise-iters", type=int, default=6000, help="denoiser leg: Adam steps")
+    ap.add_argument("--denoise-iters", type=int, default=10000, help="denoiser leg: Adam steps")
     args = ap.parse_args()
     if args.workload == "scan" and args.impl == "gempic":
         return run_scan(args)
@@ -384,7 +384,7 @@ def main():
                 "fp32": {"value": v32, "ms_per_step": ms32},
                 "unit": "pushes/s", "fp32_over_fp64": v32 / v64}
     # the metric's "denoised" form: the learned current denoiser trained on 1- vs 16-ppc runs
-    # of the 128 x 128 x 512 LWFA, judged against the 16-ppc plain run
+    # of the 128 x 128 x 512 LWFA, compared with the 16-ppc plain run
     denoise = None
     if args.denoise_pairs > 0:
         try:

@@ -54,12 +54,13 @@ struct gempic_sim {
   std::vector<double> px, py, pz, pux, puy, puz, pq;
   std::vector<int> psp;
   // gempic_step_streamed: input and output levels on the device (public layout), the
-  // host-mapped words [ready: pmax][done: pmax], two copy streams and their events
+  // host-mapped words [ready: pmax][done: pmax], the copy streams (out, in, and the first
+  // s-step's input) and their events
   void* io_a = nullptr;
   void* io_b = nullptr;
   unsigned long long* io_host = nullptr;
   unsigned long long* io_dev = nullptr;
-  cudaStream_t io_out = nullptr, io_in = nullptr;
+  cudaStream_t io_out = nullptr, io_in = nullptr, io_fill = nullptr;
   std::vector<cudaEvent_t> io_events;
   // denoised chain: rings of four plain and denoised currents, host-mapped words [done: 8]
   // [ready: 8], the stream the net runs on
@@ -1007,6 +1008,7 @@ cudaError_t ensure_stream_io(gempic_sim* s) {
   }
   if (e == cudaSuccess && !s->io_out) e = cudaStreamCreateWithFlags(&s->io_out, cudaStreamNonBlocking);
   if (e == cudaSuccess && !s->io_in) e = cudaStreamCreateWithFlags(&s->io_in, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !s->io_fill) e = cudaStreamCreateWithFlags(&s->io_fill, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = gempic::configure_march_canon(s->cfg.precision, s->p.smem_bytes);
   return e;
 }
@@ -1072,26 +1074,27 @@ gempic_status gempic_step_streamed(gempic_sim* s, int32_t n, void* host, size_t 
   const unsigned long long* done = s->io_host + s->pmax + 1;
   const long long k0 = s->k;
   auto slot = [&](int i) { return i % q.P; };
-  // the first s-step's input goes in before the launch's marches reach it
+  // the first s-step's input goes in before the launch's marches reach it, on a stream of
+  // its own, so that the second s-step's input copies do not queue behind it
   std::deque<IoPending> outq, inq;
   for (int j = 0; j < nch && e == cudaSuccess; ++j) {
     IoPending pd{0, j, nullptr};
     e = io_event(s, &pd.ev);
-    if (e == cudaSuccess) e = io_copy(s, j, chunk, s->io_a, host, false, s->io_in);
-    if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->io_in);
+    if (e == cudaSuccess) e = io_copy(s, j, chunk, s->io_a, host, false, s->io_fill);
+    if (e == cudaSuccess) e = cudaEventRecord(pd.ev, s->io_fill);
     if (e == cudaSuccess) inq.push_back(pd);
   }
   if (e == cudaSuccess) e = gempic::launch_march_canon(s->cfg.precision, q, s->stream);
   s->launches++;
   if (e != cudaSuccess) {
-    cudaStreamSynchronize(s->io_in);
+    cudaStreamSynchronize(s->io_fill);
     return cuda_fail(s, e);
   }
   // Drive the copies: a group of s-step i's result goes out once its march has written it,
   // back in as s-step i+1's input once it is out, and is released to that march once it is
   // in.  Each link waits for the one before it, so the host buffer and both device levels are
   // only rewritten after their last reader is done.
-  std::vector<int> next_out(n, 0);
+  std::vector<int> next_out(n, 0), blocked;
   int first = 0, outs_done = 0;
   gempic_status result = GEMPIC_OK;
   auto last_move = std::chrono::steady_clock::now();
@@ -1137,15 +1140,26 @@ gempic_status gempic_step_streamed(gempic_sim* s, int32_t n, void* host, size_t 
         s->io_events.push_back(pd.ev);
       }
     }
-    while (e == cudaSuccess && !inq.empty()) {
-      const cudaError_t qe = cudaEventQuery(inq.front().ev);
-      if (qe == cudaErrorNotReady) break;
+    // an s-step's groups are released in order (one word per s-step); the first s-step's
+    // copies run on their own stream, so the next s-step's may finish before them
+    blocked.clear();
+    for (size_t qi = 0; e == cudaSuccess && qi < inq.size();) {
+      const IoPending pd = inq[qi];
+      if (std::find(blocked.begin(), blocked.end(), pd.step) != blocked.end()) {
+        ++qi;
+        continue;
+      }
+      const cudaError_t qe = cudaEventQuery(pd.ev);
+      if (qe == cudaErrorNotReady) {
+        blocked.push_back(pd.step);
+        ++qi;
+        continue;
+      }
       if (qe != cudaSuccess) {
         e = qe;
         break;
       }
-      const IoPending pd = inq.front();
-      inq.pop_front();
+      inq.erase(inq.begin() + (std::ptrdiff_t)qi);
       __atomic_store_n(ready + (k0 + pd.step) % q.io_ring,
                        gempic::io_value(k0 + pd.step, nch, pd.group), __ATOMIC_RELEASE);
       s->io_events.push_back(pd.ev);
@@ -1173,6 +1187,7 @@ gempic_status gempic_step_streamed(gempic_sim* s, int32_t n, void* host, size_t 
   cudaError_t e2 = cudaStreamSynchronize(s->stream);
   cudaError_t e3 = cudaStreamSynchronize(s->io_out);
   cudaError_t e4 = cudaStreamSynchronize(s->io_in);
+  if (e4 == cudaSuccess) e4 = cudaStreamSynchronize(s->io_fill);
   for (const IoPending& pd : outq) s->io_events.push_back(pd.ev);
   for (const IoPending& pd : inq) s->io_events.push_back(pd.ev);
   if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3 != cudaSuccess ? e3 : e4;
@@ -1378,9 +1393,11 @@ void gempic_destroy(gempic_sim* s) {
   cudaStreamSynchronize(s->stream);
   if (s->io_out) cudaStreamSynchronize(s->io_out);
   if (s->io_in) cudaStreamSynchronize(s->io_in);
+  if (s->io_fill) cudaStreamSynchronize(s->io_fill);
   for (cudaEvent_t ev : s->io_events) cudaEventDestroy(ev);
   if (s->io_out) cudaStreamDestroy(s->io_out);
   if (s->io_in) cudaStreamDestroy(s->io_in);
+  if (s->io_fill) cudaStreamDestroy(s->io_fill);
   if (s->io_host) cudaFreeHost(s->io_host);
   if (s->dn_stream) {
     cudaStreamSynchronize(s->dn_stream);

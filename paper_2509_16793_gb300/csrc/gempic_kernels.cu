@@ -2172,10 +2172,14 @@ __device__ void march(const Params& p, const Sm<T>& s, const cg::cluster_group& 
     for (int i = tid; i < 3 * jplane; i += NT) s.Jint[i] = 0;
 
   // per-mode carried state (one mode per thread): thread m owns column position q of kx
-  // column kxl, i.e. the mode (kxl, ky_of_pos(q))
+  // column kxl, i.e. the mode (kxl, ky_of_pos(q)).  Block layout: q fastest (a warp's state
+  // accesses are 32 consecutive words).  Public layout (kx innermost): kxl fastest, so that a
+  // warp reads and writes whole 32-byte runs of its CTA's KB columns in 32 / KB rows, not 32
+  // rows one word each
   const int m = tid;
   const bool has_mode = m < p.M;
-  const int kxl = has_mode ? m >> p.logny : 0, q = has_mode ? m & (p.ny - 1) : 0;
+  const int kxl = !has_mode ? 0 : CANON ? m & (p.KB - 1) : m >> p.logny;
+  const int q = !has_mode ? 0 : CANON ? m >> p.logKB : m & (p.ny - 1);
   const int kyi = ky_of_pos(p.logny, q);
   const T kx = has_mode ? s.kx[(me << p.logKB) + kxl] : T(0);
   const T ky = has_mode ? s.ky[kyi] : T(0);

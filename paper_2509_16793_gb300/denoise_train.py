@@ -1,9 +1,9 @@
-"""Training and judging the learned current denoiser on pairs of runs of this method.
+"""Training and evaluating the learned current denoiser on pairs of runs of this method.
 
 Pairs: the same workload at few (1) and many (16) particles per cell, each s-step's plain
 current kept on the device (GEMPIC_FLAG_CURRENT); the sparse run's current is the input and
 the dense run's the target.  Training: Adam on slabs of consecutive half-slices (full
-transverse planes) drawn at random from the pairs.  Judging: fresh runs, the sparse one with
+transverse planes) drawn at random from the pairs.  Evaluation: fresh runs, the sparse one with
 denoised s-steps, against the dense plain run (on-axis E_z, field energy), the plain deposit
 of the sparse run beside it.  Everything runs in the library's kernels; this module only
 drives them (argument marshalling, choice of slabs, timing with CUDA events).
@@ -83,7 +83,7 @@ def _timed_steps(sim, n: int) -> float:
     return e0.elapsed_time(e1) / n
 
 
-def judge(w_sparse, w_dense, den: "gempic.Denoiser", steps: int, stream=None,
+def evaluate(w_sparse, w_dense, den: "gempic.Denoiser", steps: int, stream=None,
           chain_depths=(2, 3, 4, 5, 6, 7)) -> Dict:
     """Fresh runs of `steps` s-steps: dense plain, sparse plain, sparse denoised.  On-axis E_z
     and field energy of the sparse runs against the dense run after the last s-step, over the
@@ -157,9 +157,9 @@ def time_apply(den: "gempic.Denoiser", w, stream=None, reps: int = 5) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def experiment(pairs: int = 64, iters: int = 6000, judge_steps: int = 8, stream=None) -> Dict:
+def experiment(pairs: int = 96, iters: int = 10000, eval_steps: int = 8, stream=None) -> Dict:
     """The whole experiment on the 128 x 128 x 512 LWFA: pairs of 1- and 16-ppc runs, training,
-    judging.  Returns a summary dict."""
+    evaluation.  Returns a summary dict."""
     from . import workloads as W
     ws, wd = W.lwfa_3d_128x128x512(ppc=1), W.lwfa_3d_128x128x512(ppc=16)
     scale = abs(ws.species[0].charge * ws.species[0].density)
@@ -179,7 +179,7 @@ def experiment(pairs: int = 64, iters: int = 6000, judge_steps: int = 8, stream=
         losses = train(den, xs, ts, iters)
         t2 = time.perf_counter()
         del xs, ts
-        res = judge(ws, wd, den, judge_steps, stream)
+        res = evaluate(ws, wd, den, eval_steps, stream)
         res["apply_ms"] = time_apply(den, ws, stream)
     res["training"] = {"pairs": pairs, "iters": iters, "loss_first": float(np.mean(losses[:20])),
                        "loss_last": float(np.mean(losses[-20:])), "generate_s": t1 - t0,
@@ -197,8 +197,8 @@ if __name__ == "__main__":
     from . import build, workloads as W
     ap = argparse.ArgumentParser()
     ap.add_argument("--apply", type=int, default=0)
-    ap.add_argument("--pairs", type=int, default=64)
-    ap.add_argument("--iters", type=int, default=6000)
+    ap.add_argument("--pairs", type=int, default=96)
+    ap.add_argument("--iters", type=int, default=10000)
     a = ap.parse_args()
     build.build()
     if a.apply:

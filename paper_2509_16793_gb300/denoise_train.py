@@ -38,11 +38,17 @@ def generate_pairs(w_sparse, w_dense, steps: int, stream=None) -> Tuple[list, li
 
 
 def train(den: "gempic.Denoiser", xs: list, ts: list, iters: int, slab: int = 32,
-          lr: float = 1e-3, seed: int = 0, z_margin: int = 3) -> List[float]:
-    """Adam steps on random slabs of `slab` consecutive half-slices of random pairs."""
+          lr: float = 1e-3, seed: int = 0, z_margin: int = 3, average_tail: float = 0.2,
+          average_every: int = 10) -> List[float]:
+    """Adam steps on random slabs of `slab` consecutive half-slices of random pairs; the rate
+    drops tenfold for the last fifth.  average_tail > 0: the parameters are averaged over that
+    last fraction of the steps (every `average_every` steps; stochastic weight averaging) and
+    the average is what the denoiser keeps."""
     rng = np.random.default_rng(seed)
     nz = xs[0].shape[0]
     losses = []
+    first_avg = int(iters * (1.0 - average_tail)) if average_tail > 0 else iters
+    acc, nacc = None, 0
     for it in range(iters):
         k = int(rng.integers(len(xs)))
         z0 = int(rng.integers(0, nz - slab + 1))
@@ -50,6 +56,12 @@ def train(den: "gempic.Denoiser", xs: list, ts: list, iters: int, slab: int = 32
         t = ts[k][z0:z0 + slab].contiguous()
         rate = lr * (0.1 if it > 0.8 * iters else 1.0)
         losses.append(den.train_step(x, t, rate, z_margin=z_margin))
+        if it >= first_avg and (iters - 1 - it) % average_every == 0:
+            p = den.params().astype(np.float64)
+            acc = p if acc is None else acc + p
+            nacc += 1
+    if nacc:
+        den.set_params((acc / nacc).astype(np.float32))
     return losses
 
 
@@ -157,7 +169,8 @@ def time_apply(den: "gempic.Denoiser", w, stream=None, reps: int = 5) -> float:
     return e0.elapsed_time(e1) / reps
 
 
-def experiment(pairs: int = 96, iters: int = 10000, eval_steps: int = 8, stream=None) -> Dict:
+def experiment(pairs: int = 96, iters: int = 10000, eval_steps: int = 8, stream=None,
+               average_tail: float = 0.2) -> Dict:
     """The whole experiment on the 128 x 128 x 512 LWFA: pairs of 1- and 16-ppc runs, training,
     evaluation.  Returns a summary dict."""
     from . import workloads as W
@@ -176,12 +189,13 @@ def experiment(pairs: int = 96, iters: int = 10000, eval_steps: int = 8, stream=
         n2 = 27 * 16 * 16
         p[o2:o2 + n2] = rng.standard_normal(n2) * np.sqrt(2.0 / 432)
         den.set_params(p)
-        losses = train(den, xs, ts, iters)
+        losses = train(den, xs, ts, iters, average_tail=average_tail)
         t2 = time.perf_counter()
         del xs, ts
         res = evaluate(ws, wd, den, eval_steps, stream)
         res["apply_ms"] = time_apply(den, ws, stream)
-    res["training"] = {"pairs": pairs, "iters": iters, "loss_first": float(np.mean(losses[:20])),
+    res["training"] = {"pairs": pairs, "iters": iters, "average_tail": average_tail,
+                       "loss_first": float(np.mean(losses[:20])),
                        "loss_last": float(np.mean(losses[-20:])), "generate_s": t1 - t0,
                        "train_s": t2 - t1, "s_per_step_generate": gen}
     res["workload"] = {"sparse": ws.name, "dense": wd.name}
@@ -199,6 +213,8 @@ if __name__ == "__main__":
     ap.add_argument("--apply", type=int, default=0)
     ap.add_argument("--pairs", type=int, default=96)
     ap.add_argument("--iters", type=int, default=10000)
+    ap.add_argument("--average-tail", type=float, default=0.2,
+                    help="fraction of the last steps whose parameters are averaged (0: none)")
     a = ap.parse_args()
     build.build()
     if a.apply:
@@ -208,4 +224,4 @@ if __name__ == "__main__":
             den.set_params(rng.standard_normal(den.n).astype(np.float32) * 0.05)
             print(json.dumps({"apply_ms": time_apply(den, w, reps=3), "nzeta": a.apply}))
     else:
-        print(json.dumps(experiment(a.pairs, a.iters), indent=1))
+        print(json.dumps(experiment(a.pairs, a.iters, average_tail=a.average_tail), indent=1))

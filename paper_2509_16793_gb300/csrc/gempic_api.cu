@@ -1088,6 +1088,7 @@ gempic_status gempic_step_streamed(gempic_sim* s, int32_t n, void* host, size_t 
   s->launches++;
   if (e != cudaSuccess) {
     cudaStreamSynchronize(s->io_fill);
+    for (const IoPending& pd : inq) s->io_events.push_back(pd.ev);
     return cuda_fail(s, e);
   }
   // Drive the copies: a group of s-step i's result goes out once its march has written it,

@@ -879,7 +879,8 @@ def test_beyond_the_largest_sizes_is_rejected():
     from paper_2509_16793_gb300 import gempic
     for w in (W.small_3d(nx=256, ny=256, nzeta=16, ppc=1, precision=32),   # 2048 modes per CTA
               W.small_2d(nx=2048, nzeta=16, ppc=1, precision=32),         # nx above 1024
-              W.small_2d(nx=1024, nzeta=16, ppc=1, precision=64)):        # FP64 planes too big
+              W.small_2d(nx=1024, nzeta=16, ppc=1, precision=64),         # FP64 planes too big
+              W.small_3d(nx=192, ny=192, nzeta=16, ppc=1, precision=32)):  # not a power of two
         with pytest.raises(gempic.GempicError) as e:
             gempic.Sim(w)
         assert e.value.status == -1
